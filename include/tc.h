@@ -1,0 +1,171 @@
+/*
+ * tc.h -- exact directed-graph triad census on one NVIDIA B300 (sm_103a).
+ *
+ * The library implements the subquadratic triad census of the thesis
+ * "Study and evaluation of an Irregular Graph Algorithm on Multicore and GPU
+ * Processor Architectures" (arXiv 1603.02655): for every unordered vertex
+ * triple of a strict digraph, count which of the 16 MAN isomorphism classes
+ * its induced sub-digraph belongs to (Sec. 2.2).  The problem statement of
+ * Sec. 2.2 fixes the interface: input a digraph G=[V,E] with an explicit
+ * order n, output the Census array of 16 frequencies.
+ *
+ * Conventions for every call
+ *   - Vertex ids are 0-based int32 in [0, n).  (The thesis reads 0- or
+ *     1-based files, Sec. 5.1.1; a caller with 1-based ids subtracts 1.)
+ *   - Self-loops are dropped and duplicate arcs collapse: the census is of
+ *     the strict digraph the arcs describe.  Isolated vertices count in C(n,3).
+ *   - n must be < 2^30 (ids are packed as id<<2 | 2-bit tag in 32 bits).
+ *   - Every call returns a tc_status and never aborts the process; no C++
+ *     exception crosses this boundary.  On failure, tc_last_error() returns a
+ *     thread-local description of the most recent error.
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream).  The
+ *     caller owns every input and output buffer; the library copies inputs
+ *     it keeps and never frees caller memory.
+ *   - A tc_graph is owned by the library until tc_graph_free.  Calls on the
+ *     same graph must not run concurrently (they share its work space).
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_graph_s* tc_graph;
+
+typedef enum {
+    TC_OK = 0,
+    TC_ERR_ARG = 1,         /* null pointer, negative size, unknown flag */
+    TC_ERR_ID_RANGE = 2,    /* an arc endpoint outside [0, n) */
+    TC_ERR_OOM = 3,         /* a device allocation failed; nothing is leaked */
+    TC_ERR_CUDA = 4,        /* a CUDA runtime call failed (see tc_last_error) */
+    TC_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+    TC_ERR_UNSUPPORTED = 6  /* n >= 2^30, sizes beyond a stated limit, no device */
+} tc_status;
+
+/* Census in MAN order: count[t] for t = 0..15 is the thesis's type t+1,
+ * 003 012 102 021D 021U 021C 111D 111U 030T 030C 201 120D 120U 120C 210 300
+ * (Sec. 2.2).  The 003 count is C(n,3) minus all others (Sec. 2.2, the
+ * null-triad step) and is returned as a 128-bit value: count[0] holds its
+ * low 64 bits and count003_hi its high 64 bits, so it stays exact for every
+ * n < 2^30.  The other fifteen counts are exact as long as they are below
+ * 2^64 (true whenever |dyads| * n < 2^64). */
+typedef struct {
+    uint64_t count[16];
+    uint64_t count003_hi;
+} tc_census_t;
+
+/* Statistics of a built graph (per graph of a batched build). */
+typedef struct {
+    int64_t n;              /* vertices */
+    int64_t arcs;           /* distinct arcs after dropping loops/duplicates */
+    int64_t dyads;          /* connected (canonical) dyads |U| */
+    int64_t mutual;         /* mutual dyads */
+    int64_t asym;           /* asymmetric dyads */
+    int64_t merged_entries; /* sum over canonical dyads of |N(u)|+|N(v)| = sum_v d_v^2 */
+    int64_t max_degree;     /* largest undirected degree */
+} tc_graph_stats_t;
+
+/* Task binning (Sec. 4.3.1: canonical-dyad tasks, cost |N(u)|+|N(v)|-2). */
+enum { TC_BIN_HEURISTIC = 0, TC_BIN_MLP = 1 };
+
+typedef struct {
+    int32_t bin_mode;     /* TC_BIN_HEURISTIC (degree sum) or TC_BIN_MLP */
+    int32_t thr_thread;   /* tasks with |N(u)|+|N(v)| <= thr_thread: one thread each */
+    int32_t thr_warp;     /* <= thr_warp: one warp each; larger: CTA chunks */
+    int32_t chunk;        /* merge length of one CTA chunk (splits hub tasks) */
+    int32_t reserved[4];  /* must be zero */
+} tc_opts;
+
+/* tc_graph_build flags */
+#define TC_DEVICE_PTRS 1u   /* src/dst (and arc offsets) are device pointers */
+/* tc_census / tc_census_batched flags */
+#define TC_OUT_DEVICE 2u    /* out is device memory: the call only enqueues work
+                               on `stream` and returns without synchronising */
+
+/* Fill *o with the defaults (degree-sum binning, tuned thresholds). */
+tc_status tc_opts_default(tc_opts* o);
+
+/*
+ * tc_graph_build -- turn an arc list into the device adjacency the census reads
+ * (the CRS "adjacency array" of Sec. 2.5.1 / 5.1.1, with the thesis's separate
+ * edge and neighbour arrays folded into one list).
+ *   n          vertex count, 0 <= n < 2^30.
+ *   src, dst   m arc endpoints (arc src[i] -> dst[i]), int32, host memory or,
+ *              with TC_DEVICE_PTRS, device memory.  Not retained.
+ *   m          number of arcs, >= 0.
+ *   stream     stream the build runs on; the call synchronises it before
+ *              returning (it reads back the graph statistics).
+ *   out        receives the new graph handle.
+ * Layout built on the device: row_ptr int64[n+1]; adj uint32[2|U|] where the
+ * entry for neighbour y of row x is (y << 2) | tag, tag bit0 = arc x->y,
+ * bit1 = arc y->x (3 = mutual dyad); each row sorted by neighbour id.
+ * Errors: TC_ERR_ARG (null pointers with m > 0, n < 0, m < 0),
+ * TC_ERR_UNSUPPORTED (n >= 2^30), TC_ERR_ID_RANGE, TC_ERR_OOM, TC_ERR_CUDA.
+ */
+tc_status tc_graph_build(int32_t n, const int32_t* src, const int32_t* dst, int64_t m,
+                         uint32_t flags, void* stream, tc_graph* out);
+
+/*
+ * tc_graph_build_batched -- build G independent graphs in one pass.
+ *   ns        host int32[G]: vertex count of each graph.
+ *   arc_off   host int64[G+1]: graph g owns arcs arc_off[g] .. arc_off[g+1]-1
+ *             of src/dst; arc_off[0] == 0.
+ *   src, dst  concatenated arcs with ids LOCAL to their graph ([0, ns[g])).
+ *   outs      receives G handles; they share one device allocation, which is
+ *             released when the last of them is freed.
+ * Errors as tc_graph_build; additionally sum(ns) must be < 2^31.
+ */
+tc_status tc_graph_build_batched(int32_t G, const int32_t* ns, const int64_t* arc_off,
+                                 const int32_t* src, const int32_t* dst, uint32_t flags,
+                                 void* stream, tc_graph* outs);
+
+/* Statistics of one graph (host copy made at build time; no device work). */
+tc_status tc_graph_stats(tc_graph g, tc_graph_stats_t* out);
+
+/* Copy a graph's adjacency to host memory: row_ptr int64[n+1] (offsets
+ * relative to the graph's first entry) and adj uint32[2*dyads] in the layout
+ * described at tc_graph_build.  Synchronises the device. */
+tc_status tc_graph_export(tc_graph g, int64_t* row_ptr, uint32_t* adj);
+
+/*
+ * tc_census -- the census of one graph (Sec. 2.2, Fig. "Subquadratic Triad
+ * Census Algorithm"; task queues of Sec. 4.3.1 / 5.1.1).
+ *   opts    NULL for the defaults.
+ *   out     one tc_census_t, host memory (the call synchronises `stream`) or,
+ *           with TC_OUT_DEVICE, device memory (asynchronous).
+ * Errors: TC_ERR_ARG, TC_ERR_OOM (work space), TC_ERR_CUDA.
+ */
+tc_status tc_census(tc_graph g, const tc_opts* opts, tc_census_t* out, uint32_t flags,
+                    void* stream);
+
+/*
+ * tc_census_batched -- censuses of G graphs in one pass over their combined
+ * task set; out[i] is the census of gs[i].  All handles must come from ONE
+ * tc_graph_build_batched (or be the same single graph); any subset and order
+ * is allowed.  Errors as tc_census, plus TC_ERR_UNSUPPORTED for handles from
+ * different builds.
+ */
+tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts,
+                            tc_census_t* out, uint32_t flags, void* stream);
+
+/* MAN type index (0..15, order of tc_census_t) of the labelled triad with the
+ * given 6-bit code, bit order of Sec. 2.2 Fig. "Triad Code Algorithm":
+ * e(u,v)=1, e(v,u)=2, e(u,w)=4, e(w,u)=8, e(v,w)=16, e(w,v)=32 (the thesis's
+ * TriadTable, whose printed form is lost).  Returns -1 for codes outside
+ * [0, 64). */
+int tc_triad_type(int code);
+
+/* Release a graph handle (synchronises the device first). NULL is a no-op. */
+void tc_graph_free(tc_graph g);
+
+const char* tc_status_str(tc_status s);
+const char* tc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,275 @@
+"""Python binding for libtc, the exact triad-census library for one B300.
+
+This module only marshals arguments for the C-ABI in ``include/tc.h``; every
+step of the census runs in the library's CUDA kernels.  Entry points keep the
+C names:
+
+    tc_graph_build, tc_graph_build_batched, tc_graph_stats, tc_graph_export,
+    tc_census, tc_census_batched, tc_graph_free, tc_opts_default,
+    tc_triad_type, tc_status_str, tc_last_error
+
+Host inputs are numpy arrays (or anything ``np.asarray`` accepts); device
+inputs are CUDA torch tensors (their ``data_ptr`` is passed with the
+TC_DEVICE_PTRS flag).  Census results come back as lists of 16 Python ints in
+MAN order (003 012 102 021D 021U 021C 111D 111U 030T 030C 201 120D 120U 120C
+210 300), the 003 count rebuilt from its two 64-bit halves.
+
+There is no CPU fallback: if ``libtc.so`` is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+TYPE_NAMES = ("003", "012", "102", "021D", "021U", "021C", "111D", "111U",
+              "030T", "030C", "201", "120D", "120U", "120C", "210", "300")
+
+TC_OK, TC_ERR_ARG, TC_ERR_ID_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED = range(7)
+TC_BIN_HEURISTIC, TC_BIN_MLP = 0, 1
+TC_DEVICE_PTRS = 1
+TC_OUT_DEVICE = 2
+
+EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
+           "tc_graph_export", "tc_census", "tc_census_batched", "tc_triad_type",
+           "tc_graph_free", "tc_status_str", "tc_last_error")
+
+
+class TcCensus(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64 * 16), ("count003_hi", ctypes.c_uint64)]
+
+    def to_list(self) -> list[int]:
+        c = [int(x) for x in self.count]
+        c[0] |= int(self.count003_hi) << 64
+        return c
+
+
+class TcStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in
+                ("n", "arcs", "dyads", "mutual", "asym", "merged_entries", "max_degree")]
+
+    def to_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class TcOpts(ctypes.Structure):
+    _fields_ = [("bin_mode", ctypes.c_int32), ("thr_thread", ctypes.c_int32),
+                ("thr_warp", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} [status {status}]")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libtc.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libtc.so is missing ({LIB_PATH}); build it with "
+                           "`python -m paper_1603_02655_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    lib.tc_opts_default.argtypes = [P]
+    lib.tc_graph_build.argtypes = [i32, P, P, i64, u32, P, P]
+    lib.tc_graph_build_batched.argtypes = [i32, P, P, P, P, u32, P, P]
+    lib.tc_graph_stats.argtypes = [P, P]
+    lib.tc_graph_export.argtypes = [P, P, P]
+    lib.tc_census.argtypes = [P, P, P, u32, P]
+    lib.tc_census_batched.argtypes = [i32, P, P, P, u32, P]
+    lib.tc_triad_type.argtypes = [ctypes.c_int]
+    lib.tc_triad_type.restype = ctypes.c_int
+    lib.tc_graph_free.argtypes = [P]
+    lib.tc_graph_free.restype = None
+    lib.tc_status_str.argtypes = [ctypes.c_int]
+    lib.tc_status_str.restype = ctypes.c_char_p
+    lib.tc_last_error.argtypes = []
+    lib.tc_last_error.restype = ctypes.c_char_p
+    for name in ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
+                 "tc_graph_export", "tc_census", "tc_census_batched"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != TC_OK:
+        lib = load()
+        raise TcError(status, f"{what}: {lib.tc_status_str(status).decode()}: "
+                              f"{lib.tc_last_error().decode()}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _arr(x, dtype):
+    """(pointer, keepalive, is_device) for a host array or a CUDA torch tensor."""
+    if hasattr(x, "is_cuda") and x.is_cuda:
+        import torch
+        want = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"device array must be a contiguous {want} tensor")
+        return x.data_ptr(), x, True
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype).reshape(-1))
+    return a.ctypes.data, a, False
+
+
+# ------------------------------------------------------------------ calls
+
+def tc_status_str(status: int) -> str:
+    return load().tc_status_str(int(status)).decode()
+
+
+def tc_last_error() -> str:
+    return load().tc_last_error().decode()
+
+
+def tc_triad_type(code: int) -> int:
+    return int(load().tc_triad_type(int(code)))
+
+
+def tc_opts_default(**over) -> TcOpts:
+    o = TcOpts()
+    _check(load().tc_opts_default(ctypes.byref(o)), "tc_opts_default")
+    for k, v in over.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def tc_graph_build(n: int, src, dst, stream=None) -> int:
+    """Build one graph; returns the opaque handle (an int)."""
+    ps, ks, ds = _arr(src, np.int32)
+    pd, kd, dd = _arr(dst, np.int32)
+    if ds != dd:
+        raise TypeError("src and dst must both be host or both be device arrays")
+    m = int(ks.numel() if ds else ks.size)
+    if m != int(kd.numel() if dd else kd.size):
+        raise ValueError("src and dst differ in length")
+    h = ctypes.c_void_p()
+    st = load().tc_graph_build(int(n), ps if m else None, pd if m else None, m,
+                               TC_DEVICE_PTRS if ds else 0, _stream(stream), ctypes.byref(h))
+    _check(st, "tc_graph_build")
+    return h.value
+
+
+def tc_graph_build_batched(ns, arc_off, src, dst, stream=None) -> list[int]:
+    """Build G graphs (ids local to each graph); returns G handles."""
+    ns = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
+    off = np.ascontiguousarray(np.asarray(arc_off, dtype=np.int64))
+    G = int(ns.size)
+    if off.size != G + 1:
+        raise ValueError("arc_off must have G+1 entries")
+    ps, ks, ds = _arr(src, np.int32)
+    pd, kd, dd = _arr(dst, np.int32)
+    if ds != dd:
+        raise TypeError("src and dst must both be host or both be device arrays")
+    out = (ctypes.c_void_p * G)()
+    st = load().tc_graph_build_batched(G, ns.ctypes.data, off.ctypes.data, ps, pd,
+                                       TC_DEVICE_PTRS if ds else 0, _stream(stream), out)
+    _check(st, "tc_graph_build_batched")
+    return [out[i] for i in range(G)]
+
+
+def tc_graph_stats(g: int) -> dict:
+    s = TcStats()
+    _check(load().tc_graph_stats(g, ctypes.byref(s)), "tc_graph_stats")
+    return s.to_dict()
+
+
+def tc_graph_export(g: int):
+    """(row_ptr int64[n+1], adj uint32[2*dyads]) copied to host."""
+    st = tc_graph_stats(g)
+    rp = np.zeros(st["n"] + 1, dtype=np.int64)
+    adj = np.zeros(max(1, 2 * st["dyads"]), dtype=np.uint32)
+    _check(load().tc_graph_export(g, rp.ctypes.data, adj.ctypes.data), "tc_graph_export")
+    return rp, adj[: 2 * st["dyads"]]
+
+
+def tc_census(g: int, opts: TcOpts | None = None, out=None, stream=None):
+    """Census of one graph.  Without `out`: host result, a list of 16 ints.
+    With `out` (a CUDA tensor of >= 17 int64): asynchronous device result."""
+    lib = load()
+    po = ctypes.byref(opts) if opts is not None else None
+    if out is None:
+        c = TcCensus()
+        _check(lib.tc_census(g, po, ctypes.byref(c), 0, _stream(stream)), "tc_census")
+        return c.to_list()
+    _check(lib.tc_census(g, po, out.data_ptr(), TC_OUT_DEVICE, _stream(stream)), "tc_census")
+    return out
+
+
+def tc_census_batched(gs, opts: TcOpts | None = None, out=None, stream=None):
+    """Censuses of graphs `gs` (handles of one batched build).  Without `out`:
+    list of per-graph lists; with `out` (CUDA tensor of >= 17*G int64):
+    asynchronous device result."""
+    lib = load()
+    G = len(gs)
+    arr = (ctypes.c_void_p * max(G, 1))(*gs)
+    po = ctypes.byref(opts) if opts is not None else None
+    if out is None:
+        res = (TcCensus * max(G, 1))()
+        _check(lib.tc_census_batched(G, arr, po, res, 0, _stream(stream)), "tc_census_batched")
+        return [res[i].to_list() for i in range(G)]
+    _check(lib.tc_census_batched(G, arr, po, out.data_ptr(), TC_OUT_DEVICE, _stream(stream)),
+           "tc_census_batched")
+    return out
+
+
+def tc_graph_free(g: int) -> None:
+    if g:
+        load().tc_graph_free(g)
+
+
+def census_from_device_words(words) -> list[int]:
+    """Decode one 17-word device census (int64 tensor/array) into 16 ints."""
+    w = [int(x) & ((1 << 64) - 1) for x in words[:17]]
+    c = w[:16]
+    c[0] |= w[16] << 64
+    return c
+
+
+class Graph:
+    """Owning wrapper around a tc_graph handle."""
+
+    def __init__(self, n: int, src, dst, stream=None):
+        self.n = int(n)
+        self.h = tc_graph_build(n, src, dst, stream)
+
+    def stats(self) -> dict:
+        return tc_graph_stats(self.h)
+
+    def census(self, opts=None, out=None, stream=None):
+        return tc_census(self.h, opts, out, stream)
+
+    def close(self):
+        if self.h:
+            tc_graph_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

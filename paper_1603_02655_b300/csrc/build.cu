@@ -1,0 +1,356 @@
+// tc_graph_build / tc_graph_build_batched: arc lists -> tagged combined CRS.
+//
+// The thesis builds, on the host, one CRS for out-arcs E(u) and one for the
+// undirected neighbourhoods N(u) (Sec. 5.1.1).  Here both are one device
+// array: row x holds every neighbour y of x once, as (y << 2) | tag with tag
+// bit0 = arc x->y and bit1 = arc y->x, sorted by y.  The census then reads
+// IsEdge and IsNeighbour from the tags of the merge instead of searching.
+//
+// Steps (all on the device, on the caller's stream):
+//   1 keys: each arc x->y emits (row x, nbr y, bit0) and (row y, nbr x, bit1);
+//     self-loops emit a sentinel key that sorts last; ids are range-checked.
+//   2 one radix sort of the 64-bit keys (library primitive: CUB).
+//   3 run heads over (row, nbr); exclusive scan gives each run its slot.
+//   4 each run writes one entry with the OR of its tags and counts its row.
+//   5 scan of the row counts -> row_ptr; per-row tag counts and per-graph
+//     statistics (arcs, dyads, mutual, merged entries = sum d^2, max degree).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+#include <cstring>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+namespace {
+
+constexpr uint64_t KEY_SENT = ~0ull;
+
+__device__ __forceinline__ int find_graph(const int64_t* off, int G, int64_t i) {
+    // largest g with off[g] <= i
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                       const int64_t* __restrict__ arc_off, const int64_t* __restrict__ voff,
+                       int G, int sh, uint64_t* __restrict__ keys, int* __restrict__ err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = G == 1 ? 0 : find_graph(arc_off, G, i);
+        const int64_t base = voff[g], n = voff[g + 1] - base;
+        const int32_t s = src[i], d = dst[i];
+        uint64_t k1 = KEY_SENT, k2 = KEY_SENT;
+        if (s < 0 || s >= n || d < 0 || d >= n) {
+            atomicOr(err, 1);
+        } else if (s != d) {
+            k1 = ((uint64_t)(base + s) << sh) | ((uint64_t)d << 2) | 1u;  // row s: arc s->d
+            k2 = ((uint64_t)(base + d) << sh) | ((uint64_t)s << 2) | 2u;  // row d: arc s->d seen from d
+        }
+        keys[2 * i] = k1;
+        keys[2 * i + 1] = k2;
+    }
+}
+
+__global__ void k_heads(const uint64_t* __restrict__ k, int64_t N, int32_t* __restrict__ head) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = k[i];
+        head[i] = (a != KEY_SENT) && (i == 0 || (k[i - 1] >> 2) != (a >> 2));
+    }
+}
+
+__global__ void k_write(const uint64_t* __restrict__ k, int64_t N, const int32_t* __restrict__ head,
+                        const int32_t* __restrict__ pos, int sh, uint32_t nbr_mask,
+                        uint32_t* __restrict__ adj, unsigned long long* __restrict__ cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!head[i]) continue;
+        const uint64_t key = k[i] >> 2;
+        uint32_t tag = 0;
+        for (int64_t j = i; j < N && (k[j] >> 2) == key; ++j) tag |= (uint32_t)(k[j] & 3u);
+        const uint32_t nbr = (uint32_t)(key & nbr_mask);
+        adj[pos[i]] = (nbr << 2) | tag;
+        atomicAdd(&cnt[k[i] >> sh], 1ull);
+    }
+}
+
+__global__ void k_fill_sent(uint32_t* __restrict__ p, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = SENT;
+}
+
+// Warp per row: degree, per-row tag counts, and per-graph statistics
+// (accumulated per warp while its rows stay in one graph).
+__global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+                           const int64_t* __restrict__ voff, int G, int64_t total_n,
+                           int32_t* __restrict__ deg, int32_t* __restrict__ vtag,
+                           unsigned long long* __restrict__ gstat /* [G][6] */,
+                           unsigned long long* __restrict__ cursor) {
+    const int lane = threadIdx.x & 31;
+    constexpr int ROWS = 64;
+    int g = -1;
+    unsigned long long a_arcs = 0, a_deg = 0, a_mut = 0, a_sq = 0, a_max = 0;
+    auto flush = [&]() {
+        if (g >= 0 && lane == 0) {
+            unsigned long long* s = gstat + 6 * (size_t)g;
+            if (a_arcs) atomicAdd(s + 0, a_arcs);
+            if (a_deg) atomicAdd(s + 1, a_deg);
+            if (a_mut) atomicAdd(s + 2, a_mut);
+            if (a_sq) atomicAdd(s + 3, a_sq);
+            if (a_max) atomicMax(s + 4, a_max);
+        }
+        a_arcs = a_deg = a_mut = a_sq = a_max = 0;
+    };
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)ROWS);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((int64_t)base >= total_n) break;
+        const int64_t rend = min((int64_t)base + ROWS, total_n);
+        for (int64_t x = (int64_t)base; x < rend; ++x) {
+            const int gx = G == 1 ? 0 : find_graph(voff, G, x);
+            if (gx != g) { flush(); g = gx; }
+            const int64_t b = row_ptr[x], e = row_ptr[x + 1];
+            int c1 = 0, c2 = 0, c3 = 0;
+            for (int64_t k = b + lane; k < e + ((32 - ((e - b) & 31)) & 31); k += 32) {
+                const bool v = k < e;
+                const uint32_t t = v ? (adj[k] & 3u) : 0u;
+                c1 += __popc(__ballot_sync(0xffffffffu, t == 1));
+                c2 += __popc(__ballot_sync(0xffffffffu, t == 2));
+                c3 += __popc(__ballot_sync(0xffffffffu, t == 3));
+            }
+            const unsigned long long d = (unsigned long long)(e - b);
+            if (lane == 0) {
+                deg[x] = (int32_t)d;
+                vtag[3 * x + 0] = c1;
+                vtag[3 * x + 1] = c2;
+                vtag[3 * x + 2] = c3;
+            }
+            a_arcs += (unsigned long long)(c1 + c3);
+            a_deg += d;
+            a_mut += (unsigned long long)c3;
+            a_sq += d * d;
+            a_max = a_max > d ? a_max : d;
+        }
+    }
+    flush();
+}
+
+int bits_for(uint64_t x) {  // smallest b with x < 2^b
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <class T>
+    cudaError_t get(T** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = dev_alloc(&q, count * sizeof(T), s);
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = (T*)q;
+        return e;
+    }
+    ~Scratch() {
+        for (void* p : ptrs) dev_free(p, s);
+    }
+};
+
+int grid_for(int64_t work, int threads) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t g = (work + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
+}
+
+tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const int32_t* src,
+                     const int32_t* dst, uint32_t flags, cudaStream_t st, tc_graph* outs) {
+    if (G < 1 || !ns || !arc_off || !outs) return fail(TC_ERR_ARG, "graph build: null argument or G < 1");
+    if (flags & ~TC_DEVICE_PTRS) return fail(TC_ERR_ARG, "graph build: unknown flag");
+    std::vector<int64_t> voff((size_t)G + 1, 0), aoff((size_t)G + 1, 0);
+    int64_t max_n = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        if (ns[g] < 0) return fail(TC_ERR_ARG, "graph build: n < 0");
+        if (ns[g] >= (1 << 30)) return fail(TC_ERR_UNSUPPORTED, "graph build: n must be < 2^30");
+        voff[g + 1] = voff[g] + ns[g];
+        max_n = std::max<int64_t>(max_n, ns[g]);
+    }
+    std::memcpy(aoff.data(), arc_off, sizeof(int64_t) * ((size_t)G + 1));
+    if (aoff[0] != 0) return fail(TC_ERR_ARG, "graph build: arc_off[0] must be 0");
+    for (int32_t g = 0; g < G; ++g)
+        if (aoff[g + 1] < aoff[g]) return fail(TC_ERR_ARG, "graph build: arc offsets decrease");
+    const int64_t m = aoff[G];
+    const int64_t total_n = voff[G];
+    if (total_n >= ((int64_t)1 << 31)) return fail(TC_ERR_UNSUPPORTED, "graph build: total vertices must be < 2^31");
+    if (m > 0 && (!src || !dst)) return fail(TC_ERR_ARG, "graph build: null arc arrays");
+    if (2 * m >= ((int64_t)1 << 31) - 1) return fail(TC_ERR_UNSUPPORTED, "graph build: m must be < 2^30");
+    const int nb = std::max(1, bits_for((uint64_t)std::max<int64_t>(max_n - 1, 0)));
+    const int rb = std::max(1, bits_for((uint64_t)total_n));  // total_n itself < 2^rb: no real key is all ones
+    const int sh = nb + 2;
+    if (sh + rb > 64) return fail(TC_ERR_UNSUPPORTED, "graph build: key does not fit 64 bits");
+
+    auto set = std::make_shared<GraphSet>();
+    set->G = G;
+    set->total_n = total_n;
+    set->voff = voff;
+    set->max_n = max_n;
+    set->stats.assign((size_t)G, tc_graph_stats_t{});
+    const int64_t N = 2 * m;
+    set->adj_cap = N;
+    TC_CUDA(dev_alloc((void**)&set->row_ptr, sizeof(int64_t) * (size_t)(total_n + 1), st));
+    TC_CUDA(dev_alloc((void**)&set->adj, sizeof(uint32_t) * (size_t)(N + ADJ_PAD), st));
+    TC_CUDA(dev_alloc((void**)&set->deg, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
+    TC_CUDA(dev_alloc((void**)&set->vtag, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
+
+    Scratch S(st);
+    int32_t *d_src = nullptr, *d_dst = nullptr;
+    if (m > 0) {
+        if (flags & TC_DEVICE_PTRS) {
+            d_src = const_cast<int32_t*>(src);
+            d_dst = const_cast<int32_t*>(dst);
+        } else {
+            TC_CUDA(S.get(&d_src, (size_t)m));
+            TC_CUDA(S.get(&d_dst, (size_t)m));
+            TC_CUDA(cudaMemcpyAsync(d_src, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st));
+            TC_CUDA(cudaMemcpyAsync(d_dst, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st));
+        }
+    }
+    int64_t *d_aoff = nullptr, *d_voff = nullptr;
+    int* d_err = nullptr;
+    unsigned long long *d_cnt = nullptr, *d_gstat = nullptr, *d_cursor = nullptr;
+    TC_CUDA(S.get(&d_aoff, (size_t)G + 1));
+    TC_CUDA(S.get(&d_voff, (size_t)G + 1));
+    TC_CUDA(S.get(&d_err, 1));
+    TC_CUDA(S.get(&d_cnt, (size_t)total_n + 1));
+    TC_CUDA(S.get(&d_gstat, 6 * (size_t)G + 8));
+    TC_CUDA(S.get(&d_cursor, 1));
+    TC_CUDA(cudaMemcpyAsync(d_aoff, aoff.data(), sizeof(int64_t) * ((size_t)G + 1), cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaMemcpyAsync(d_voff, voff.data(), sizeof(int64_t) * ((size_t)G + 1), cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    TC_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * ((size_t)total_n + 1), st));
+    TC_CUDA(cudaMemsetAsync(d_gstat, 0, sizeof(unsigned long long) * (6 * (size_t)G + 8), st));
+    TC_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(unsigned long long), st));
+
+    int32_t* d_pos = nullptr;
+    int32_t nnz_host = 0;
+    if (N > 0) {
+        uint64_t *k0 = nullptr, *k1 = nullptr;
+        int32_t* head = nullptr;
+        TC_CUDA(S.get(&k0, (size_t)N));
+        TC_CUDA(S.get(&k1, (size_t)N));
+        TC_CUDA(S.get(&head, (size_t)N));
+        TC_CUDA(S.get(&d_pos, (size_t)N));
+        k_keys<<<grid_for(m, 256), 256, 0, st>>>(d_src, d_dst, m, d_aoff, d_voff, G, sh, k0, d_err);
+        TC_CUDA(cudaGetLastError());
+        cub::DoubleBuffer<uint64_t> db(k0, k1);
+        size_t tmp_bytes = 0;
+        TC_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, db, (int)N, 2, sh + rb, st));
+        void* tmp = nullptr;
+        TC_CUDA(S.get((char**)&tmp, tmp_bytes));
+        TC_CUDA(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, db, (int)N, 2, sh + rb, st));
+        const uint64_t* ks = db.Current();
+        k_heads<<<grid_for(N, 256), 256, 0, st>>>(ks, N, head);
+        TC_CUDA(cudaGetLastError());
+        size_t scan_bytes = 0;
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, head, d_pos, (int)N, st));
+        void* tmp2 = nullptr;
+        TC_CUDA(S.get((char**)&tmp2, scan_bytes));
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp2, scan_bytes, head, d_pos, (int)N, st));
+        k_write<<<grid_for(N, 256), 256, 0, st>>>(ks, N, head, d_pos, sh, (uint32_t)((1ull << nb) - 1),
+                                                  set->adj, d_cnt);
+        TC_CUDA(cudaGetLastError());
+        int32_t last_pos = 0, last_head = 0;
+        TC_CUDA(cudaMemcpyAsync(&last_pos, d_pos + N - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaMemcpyAsync(&last_head, head + N - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        nnz_host = last_pos + last_head;
+    }
+    set->nnz = nnz_host;
+    // row_ptr = exclusive scan of the row counts (total_n + 1 items, last count 0)
+    {
+        size_t scan_bytes = 0;
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, d_cnt,
+                                              (unsigned long long*)set->row_ptr, (int)(total_n + 1), st));
+        void* tmp = nullptr;
+        TC_CUDA(S.get((char**)&tmp, scan_bytes));
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, scan_bytes, d_cnt,
+                                              (unsigned long long*)set->row_ptr, (int)(total_n + 1), st));
+    }
+    k_fill_sent<<<grid_for(ADJ_PAD + (N - nnz_host), 256), 256, 0, st>>>(set->adj + nnz_host,
+                                                                        ADJ_PAD + (N - nnz_host));
+    TC_CUDA(cudaGetLastError());
+    if (total_n > 0) {
+        k_rowstats<<<grid_for(total_n * 32, 256), 256, 0, st>>>(set->row_ptr, set->adj, d_voff, G, total_n,
+                                                               set->deg, set->vtag, d_gstat, d_cursor);
+        TC_CUDA(cudaGetLastError());
+    }
+    std::vector<unsigned long long> gstat(6 * (size_t)G);
+    int err = 0;
+    TC_CUDA(cudaMemcpyAsync(gstat.data(), d_gstat, sizeof(unsigned long long) * 6 * (size_t)G,
+                            cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (err) return fail(TC_ERR_ID_RANGE, "graph build: an arc endpoint lies outside [0, n)");
+    for (int32_t g = 0; g < G; ++g) {
+        tc_graph_stats_t& s = set->stats[(size_t)g];
+        const unsigned long long* x = gstat.data() + 6 * (size_t)g;
+        s.n = ns[g];
+        s.arcs = (int64_t)x[0];
+        s.dyads = (int64_t)(x[1] / 2);
+        s.mutual = (int64_t)(x[2] / 2);
+        s.asym = s.dyads - s.mutual;
+        s.merged_entries = (int64_t)x[3];
+        s.max_degree = (int64_t)x[4];
+    }
+    for (int32_t g = 0; g < G; ++g) {
+        outs[g] = new tc_graph_s;
+        outs[g]->set = set;
+        outs[g]->index = g;
+    }
+    return TC_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" {
+
+tc_status tc_graph_build(int32_t n, const int32_t* src, const int32_t* dst, int64_t m, uint32_t flags,
+                         void* stream, tc_graph* out) {
+    if (!out) return tc::fail(TC_ERR_ARG, "tc_graph_build: out is null");
+    *out = nullptr;
+    if (n < 0 || m < 0) return tc::fail(TC_ERR_ARG, "tc_graph_build: negative size");
+    int64_t off[2] = {0, m};
+    try {
+        return tc::build_impl(1, &n, off, src, dst, flags, (cudaStream_t)stream, out);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_graph_build: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_graph_build: unexpected exception");
+    }
+}
+
+tc_status tc_graph_build_batched(int32_t G, const int32_t* ns, const int64_t* arc_off, const int32_t* src,
+                                 const int32_t* dst, uint32_t flags, void* stream, tc_graph* outs) {
+    if (!outs) return tc::fail(TC_ERR_ARG, "tc_graph_build_batched: outs is null");
+    try {
+        return tc::build_impl(G, ns, arc_off, src, dst, flags, (cudaStream_t)stream, outs);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_graph_build_batched: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_graph_build_batched: unexpected exception");
+    }
+}
+
+}  // extern "C"

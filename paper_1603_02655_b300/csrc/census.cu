@@ -1,0 +1,745 @@
+// tc_census / tc_census_batched: the per-canonical-dyad merge/classify pass.
+//
+// Method (Sec. 2.2, Fig. "Subquadratic Triad Census Algorithm", with the v0.4
+// pre-computed dyad code of Sec. 4.2.4 and the canonical-dyad task queues of
+// Sec. 4.3.1 / 5.1.1).  For every canonical dyad <u,v>, u < v adjacent, with
+// pre = e(u,v) + 2e(v,u), A = N(u), B = N(v) (tagged, sorted):
+//   dyadic term   Census[pre==3 ? 102 : 012] += n - |S| - 2,
+//                 S = A u B \ {u,v},  |S| = |A| + |B| - 2 - |A n B|;
+//   connected     every w in S with  v < w  or  (u < w < v and w not in N(u))
+//                 adds 1 to code pre + 4*tag_u(w) + 16*tag_v(w)
+//                 (tag_x(w) = e(x,w) + 2e(w,x), 0 when w is not a neighbour).
+// 003 = C(n,3) - sum of the other fifteen (128-bit).
+//
+// How the work is split across kernels (the result is the same integer sum,
+// regrouped; every per-dyad contribution is counted exactly once):
+//  * w only in A (tag_v = 0) is counted iff w > v, i.e. it is one of the
+//    entries of row u after v; w only in B (tag_u = 0) is counted iff w > u,
+//    i.e. one of the entries of row v after u.  k_tasks walks each row once,
+//    keeps suffix counts of the three tag values, and adds, per dyad, the
+//    counts of A after v into codes pre+4t and the counts of B after u into
+//    codes pre+16t, as if no element were shared, plus n - |A| - |B| into the
+//    dyadic slot.  It also emits the dyad as a task, binned by |A|+|B|.
+//  * The merge kernels stream A and B (the full lists: the union merge of the
+//    method) and find the shared elements w.  Each adds 1 to the dyadic slot
+//    (|S| shrinks by one) and corrects the classification: if w > v it was
+//    counted as pre+4tu and pre+16tv and is moved to pre+4tu+16tv; if
+//    u < w < v it was counted as pre+16tv and must not count at all.
+//  * k_fold maps the 64 codes onto the 16 MAN types and closes 003.
+#include <algorithm>
+#include <cstring>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+namespace {
+
+constexpr int WARPS = 8;  // warps per 256-thread block
+
+// ------------------------------------------------------------ type table --
+// MAN type of the labelled triad with 6-bit code (bit order of Fig. "Triad
+// Code Algorithm": e(u,v)=1, e(v,u)=2, e(u,w)=4, e(w,u)=8, e(v,w)=16,
+// e(w,v)=32), decided from the mutual/asymmetric dyad counts and the vertex
+// degree signatures of the triad.
+__host__ __device__ __forceinline__ int triad_type(int code) {
+    const int e01 = code & 1, e10 = (code >> 1) & 1, e02 = (code >> 2) & 1;
+    const int e20 = (code >> 3) & 1, e12 = (code >> 4) & 1, e21 = (code >> 5) & 1;
+    const int od[3] = {e01 + e02, e10 + e12, e20 + e21};
+    const int id[3] = {e10 + e20, e01 + e21, e02 + e12};
+    const int M = (e01 & e10) + (e02 & e20) + (e12 & e21);
+    const int A = (e01 ^ e10) + (e02 ^ e20) + (e12 ^ e21);
+    bool out2 = false, in2 = false, src2 = false, snk2 = false;
+    for (int x = 0; x < 3; ++x) {
+        out2 |= od[x] == 2;
+        in2 |= id[x] == 2;
+        src2 |= od[x] == 2 && id[x] == 0;  // sends two arcs, receives none
+        snk2 |= id[x] == 2 && od[x] == 0;  // receives two arcs, sends none
+    }
+    if (M == 0 && A == 0) return 0;                 // 003
+    if (M == 0 && A == 1) return 1;                 // 012
+    if (M == 1 && A == 0) return 2;                 // 102
+    if (M == 0 && A == 2) return out2 ? 3 : (in2 ? 4 : 5);  // 021D 021U 021C
+    if (M == 1 && A == 1) return in2 ? 6 : 7;       // 111D (arc into the pair) 111U
+    if (M == 0 && A == 3) return out2 ? 8 : 9;      // 030T 030C
+    if (M == 2 && A == 0) return 10;                // 201
+    if (M == 1 && A == 2) return src2 ? 11 : (snk2 ? 12 : 13);  // 120D 120U 120C
+    if (M == 2 && A == 1) return 14;                // 210
+    return 15;                                      // 300
+}
+
+// ---------------------------------------------------------- device types --
+struct SegDev {
+    int64_t rb;    // first global row of the graph (local id = global - rb)
+    int64_t n;     // vertices
+    int32_t slot;  // output index
+    int32_t pad;
+};
+
+struct Bins {
+    uint4* rec[3];        // {u global, v global, seg<<2 | pre, d_begin}
+    uint32_t cap[3];
+    unsigned int* cnt;    // [3] records appended per bin
+    int* overflow;
+};
+
+struct BinParams {
+    int thr_thread, thr_warp, chunk;
+};
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int seg_of(const int64_t* pfx, int nseg, int64_t r) {
+    int lo = 0, hi = nseg - 1;  // largest s with pfx[s] <= r
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pfx[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// --------------------------------------------------------------- k_tasks --
+// One warp per row x (rows pulled in blocks from a global cursor).  For each
+// entry (y, t) of row x at position k: suffix counts S1..S3 of the tags of
+// entries after k.  y > x: canonical dyad <x,y> (pre = t): add S into codes
+// pre+4t', n-|A|-|B| into the dyadic slot, emit the task.  y < x: row x is
+// B of dyad <y,x> (pre = swapped t): add S into codes pre+16t'.
+__global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_ptr,
+                                               const uint32_t* __restrict__ adj,
+                                               const int32_t* __restrict__ deg,
+                                               const SegDev* __restrict__ seg,
+                                               const int64_t* __restrict__ pfx, int nseg,
+                                               int64_t total_rows, BinParams bp, Bins bins,
+                                               unsigned long long* __restrict__ acc,
+                                               unsigned long long* __restrict__ cursor) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const unsigned above = lane == 31 ? 0u : (full << (lane + 1));
+    const unsigned below = (1u << lane) - 1u;
+    constexpr int ROWS = 32;
+    int s = -1;
+    int64_t rb = 0, n = 0, sp = 0;
+    unsigned long long Aa[3][3], Bb[3][3], Dd[2];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Aa[p][q] = Bb[p][q] = 0;
+    Dd[0] = Dd[1] = 0;
+
+    auto flush = [&]() {
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                unsigned long long a = warp_sum64(Aa[p][q]), b = warp_sum64(Bb[p][q]);
+                if (lane == 0 && s >= 0) {
+                    if (a) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 4 * (q + 1), a);
+                    if (b) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 16 * (q + 1), b);
+                }
+                Aa[p][q] = Bb[p][q] = 0;
+            }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            unsigned long long d = warp_sum64(Dd[q]);
+            if (lane == 0 && s >= 0 && d) atomicAdd(acc + (size_t)s * ACC + 64 + q, d);
+            Dd[q] = 0;
+        }
+    };
+
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)ROWS);
+        base = __shfl_sync(full, base, 0);
+        if ((int64_t)base >= total_rows) break;
+        const int64_t rend = min((int64_t)base + ROWS, total_rows);
+        for (int64_t r = (int64_t)base; r < rend; ++r) {
+            const int sr = nseg == 1 ? 0 : seg_of(pfx, nseg, r);
+            if (sr != s) {
+                flush();
+                s = sr;
+                rb = seg[s].rb;
+                n = seg[s].n;
+                sp = pfx[s];
+            }
+            const int64_t xl = r - sp;
+            const int64_t x = rb + xl;
+            const int64_t beg = row_ptr[x];
+            const int d = deg[x];
+            int c1 = 0, c2 = 0, c3 = 0;
+            for (int cb = ((d - 1) >> 5) << 5; cb >= 0; cb -= 32) {
+                const int k = cb + lane;
+                const bool valid = k < d;
+                const uint32_t e = valid ? __ldg(adj + beg + k) : 0u;
+                const uint32_t y = e >> 2;
+                const int t = (int)(e & 3u);
+                const unsigned m1 = __ballot_sync(full, valid && t == 1);
+                const unsigned m2 = __ballot_sync(full, valid && t == 2);
+                const unsigned m3 = __ballot_sync(full, valid && t == 3);
+                const unsigned long long S1 = (unsigned)(c1 + __popc(m1 & above));
+                const unsigned long long S2 = (unsigned)(c2 + __popc(m2 & above));
+                const unsigned long long S3 = (unsigned)(c3 + __popc(m3 & above));
+                c1 += __popc(m1);
+                c2 += __popc(m2);
+                c3 += __popc(m3);
+                const bool is_task = valid && (int64_t)y > xl;
+                const bool is_twin = valid && (int64_t)y < xl;
+                const int pre_task = t;
+                const int pre_twin = ((t & 1) << 1) | (t >> 1);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    const bool ta = is_task && pre_task == p + 1;
+                    const bool tb = is_twin && pre_twin == p + 1;
+                    Aa[p][0] += ta ? S1 : 0ull;
+                    Aa[p][1] += ta ? S2 : 0ull;
+                    Aa[p][2] += ta ? S3 : 0ull;
+                    Bb[p][0] += tb ? S1 : 0ull;
+                    Bb[p][1] += tb ? S2 : 0ull;
+                    Bb[p][2] += tb ? S3 : 0ull;
+                }
+                int L = 0;
+                int bin = -1;
+                if (is_task) {
+                    const int dv = deg[rb + y];
+                    L = d + dv;
+                    const unsigned long long dy = (unsigned long long)(n - (int64_t)d - (int64_t)dv);
+                    Dd[0] += pre_task == 3 ? 0ull : dy;
+                    Dd[1] += pre_task == 3 ? dy : 0ull;
+                    bin = L <= bp.thr_thread ? 0 : (L <= bp.thr_warp ? 1 : 2);
+                }
+                const uint4 rec = make_uint4((uint32_t)x, (uint32_t)(rb + y),
+                                             ((uint32_t)s << 2) | (uint32_t)pre_task, 0u);
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const bool mine = bin == b;
+                    const unsigned mask = __ballot_sync(full, mine);
+                    if (mask) {
+                        const int leader = __ffs(mask) - 1;
+                        unsigned int at = 0;
+                        if (lane == leader) at = atomicAdd(bins.cnt + b, (unsigned)__popc(mask));
+                        at = __shfl_sync(full, at, leader);
+                        if (mine) {
+                            const unsigned idx = at + __popc(mask & below);
+                            if (idx < bins.cap[b]) bins.rec[b][idx] = rec;
+                            else atomicOr(bins.overflow, 1);
+                        }
+                    }
+                }
+                // CTA chunks: ceil(L / chunk) records per task
+                {
+                    const unsigned nch = bin == 2 ? (unsigned)((L + bp.chunk - 1) / bp.chunk) : 0u;
+                    unsigned incl = nch;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned v = __shfl_up_sync(full, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const unsigned total = __shfl_sync(full, incl, 31);
+                    if (total) {
+                        unsigned int at = 0;
+                        if (lane == 0) at = atomicAdd(bins.cnt + 2, total);
+                        at = __shfl_sync(full, at, 0);
+                        const unsigned first = at + incl - nch;
+                        for (unsigned c = 0; c < nch; ++c) {
+                            uint4 rc = rec;
+                            rc.w = c * (unsigned)bp.chunk;
+                            if (first + c < bins.cap[2]) bins.rec[2][first + c] = rc;
+                            else atomicOr(bins.overflow, 1);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    flush();
+}
+
+// --------------------------------------------------------------- k_split --
+// Start of each CTA chunk on its dyad's merge path: the number of A entries
+// among the first d_begin outputs (ties taken from A first).
+__global__ void k_split(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+                        const uint4* __restrict__ rec, const unsigned int* __restrict__ cnt,
+                        uint32_t cap, int32_t* __restrict__ ia_out) {
+    const unsigned n2 = min(*cnt, cap);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+        const uint4 r = rec[i];
+        const int64_t d = r.w;
+        int64_t lo = 0;
+        if (d > 0) {
+            const int64_t ab = row_ptr[r.x], a = row_ptr[r.x + 1] - ab;
+            const int64_t bb = row_ptr[r.y], b = row_ptr[r.y + 1] - bb;
+            lo = max((int64_t)0, d - b);
+            int64_t hi = min(d, a);
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((__ldg(adj + ab + mid) | 3u) <= (__ldg(adj + bb + d - 1 - mid) | 3u)) lo = mid + 1;
+                else hi = mid;
+            }
+        }
+        ia_out[i] = (int32_t)lo;
+    }
+}
+
+// ----------------------------------------------------- shared-element fix --
+// w is in both N(u) and N(v) (tags tu, tv).  Move its contribution from the
+// single-list codes to the joint code (w > v), or drop it (u < w < v).
+__device__ __forceinline__ void on_shared(unsigned long long* h, uint32_t w, uint32_t ul, uint32_t vl,
+                                          uint32_t pre, uint32_t tu, uint32_t tv) {
+    if (w > vl) {
+        atomicAdd(h + pre + 4 * tu, ~0ull);
+        atomicAdd(h + pre + 16 * tv, ~0ull);
+        atomicAdd(h + pre + 4 * tu + 16 * tv, 1ull);
+    } else if (w > ul) {
+        atomicAdd(h + pre + 16 * tv, ~0ull);
+    }
+}
+
+template <int WPB>
+__device__ __forceinline__ void flush_hist(unsigned long long* hs, unsigned long long* acc, int tag, int lane) {
+    if (tag >= 0)
+        for (int j = lane; j < ACC; j += 32) {
+            const unsigned long long v = hs[j];
+            if (v) atomicAdd(acc + (size_t)tag * ACC + j, v);
+            hs[j] = 0;
+        }
+    else
+        for (int j = lane; j < ACC; j += 32) hs[j] = 0;
+}
+
+// ------------------------------------------------------------- k_thread --
+// One thread per small task: a plain two-pointer merge from global memory.
+__global__ void __launch_bounds__(256) k_thread(const int64_t* __restrict__ row_ptr,
+                                                const uint32_t* __restrict__ adj,
+                                                const SegDev* __restrict__ seg,
+                                                const uint4* __restrict__ rec,
+                                                const unsigned int* __restrict__ cnt, uint32_t cap,
+                                                unsigned long long* __restrict__ acc) {
+    __shared__ unsigned long long hs_all[WARPS][ACC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long* hs = hs_all[warp];
+    for (int j = lane; j < ACC; j += 32) hs[j] = 0;
+    __syncwarp();
+    int tag = -1;
+    const unsigned ntask = min(*cnt, cap);
+    for (unsigned base = blockIdx.x * blockDim.x; base < ntask; base += gridDim.x * blockDim.x) {
+        const unsigned ti = base + threadIdx.x;
+        const bool has = ti < ntask;
+        uint4 r = has ? rec[ti] : make_uint4(0, 0, 0, 0);
+        const int s = (int)(r.z >> 2);
+        const int s0 = __shfl_sync(0xffffffffu, s, 0);
+        if (s0 != tag) {
+            flush_hist<WARPS>(hs, acc, tag, lane);
+            __syncwarp();
+            tag = s0;
+        }
+        unsigned long long* h = (s == tag) ? hs : acc + (size_t)s * ACC;
+        uint32_t c = 0;
+        uint32_t pre = r.z & 3u;
+        if (has) {
+            const int64_t rb = seg[s].rb;
+            const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
+            int64_t ia = row_ptr[r.x], ib = row_ptr[r.y];
+            const int64_t ae = row_ptr[r.x + 1], be = row_ptr[r.y + 1];
+            uint32_t eA = ia < ae ? __ldg(adj + ia) : SENT;
+            uint32_t eB = ib < be ? __ldg(adj + ib) : SENT;
+            for (;;) {
+                const uint32_t kA = eA | 3u, kB = eB | 3u;
+                if (kA == SENT && kB == SENT) break;
+                if (kA == kB) {
+                    ++c;
+                    on_shared(h, kA >> 2, ul, vl, pre, eA & 3u, eB & 3u);
+                    ++ia; ++ib;
+                    eA = ia < ae ? __ldg(adj + ia) : SENT;
+                    eB = ib < be ? __ldg(adj + ib) : SENT;
+                } else if (kA < kB) {
+                    ++ia;
+                    eA = ia < ae ? __ldg(adj + ia) : SENT;
+                } else {
+                    ++ib;
+                    eB = ib < be ? __ldg(adj + ib) : SENT;
+                }
+            }
+            if (c) atomicAdd(h + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    flush_hist<WARPS>(hs, acc, tag, lane);
+}
+
+// ------------------------------------------------------- tile merge (a3) --
+// NT cooperating threads stream the merge path of A and B in tiles of
+// T = NT*K outputs.  Each tile copies windows A[i0 .. i0+T] and B[j0 .. j0+T]
+// into shared memory with 16-byte loads (entries past a list's end read as
+// the sentinel), each thread finds its start on the merge path by binary
+// search at diagonal tid*K, then takes K steps of the two-pointer merge,
+// reporting every shared element to on_shared.
+template <int NT, int W>
+__device__ __forceinline__ int load_window(uint32_t* __restrict__ s_raw, const uint32_t* __restrict__ adj,
+                                           int64_t p, int64_t end, int tid) {
+    const int64_t q = p & ~(int64_t)3;
+    const uint4* src = reinterpret_cast<const uint4*>(adj + q);
+    uint4* dst = reinterpret_cast<uint4*>(s_raw);
+    constexpr int NQ = W / 4;
+    if (q + W <= end) {
+        for (int m = tid; m < NQ; m += NT) dst[m] = __ldg(src + m);
+    } else {
+        for (int m = tid; m < NQ; m += NT) {
+            uint4 x = __ldg(src + m);
+            const int64_t a = q + 4 * (int64_t)m;
+            x.x = a < end ? x.x : SENT;
+            x.y = a + 1 < end ? x.y : SENT;
+            x.z = a + 2 < end ? x.z : SENT;
+            x.w = a + 3 < end ? x.w : SENT;
+            dst[m] = x;
+        }
+    }
+    return (int)(p - q);
+}
+
+__device__ __forceinline__ int mp_search(const uint32_t* sA, const uint32_t* sB, int d) {
+    int lo = 0, hi = d;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((sA[mid] | 3u) <= (sB[d - 1 - mid] | 3u)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int NT, int K, bool CTA>
+__device__ __forceinline__ uint32_t merge_range(const uint32_t* __restrict__ adj, int64_t a_beg, int64_t a_end,
+                                                int64_t b_beg, int64_t b_end, int64_t i0, int64_t j0,
+                                                int64_t count, uint32_t ul, uint32_t vl, uint32_t pre,
+                                                uint32_t* sA_raw, uint32_t* sB_raw, int* bc,
+                                                unsigned long long* h, int tid) {
+    constexpr int T = NT * K;
+    constexpr int W = T + 4;
+    uint32_t c = 0;
+    for (int64_t d0 = 0; d0 < count; d0 += T) {
+        const int rem = (int)min((int64_t)T, count - d0);
+        const int oA = load_window<NT, W>(sA_raw, adj, a_beg + i0, a_end, tid);
+        const int oB = load_window<NT, W>(sB_raw, adj, b_beg + j0, b_end, tid);
+        if (CTA) __syncthreads(); else __syncwarp();
+        const uint32_t* sA = sA_raw + oA;
+        const uint32_t* sB = sB_raw + oB;
+        const int dl = min(tid * K, rem);
+        int ia = mp_search(sA, sB, dl);
+        int ib = dl - ia;
+        const int steps = min(K, rem - dl);
+        uint32_t eA = sA[ia], eB = sB[ib];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s < steps) {
+                const uint32_t kA = eA | 3u, kB = eB | 3u;
+                const bool takeA = kA <= kB;
+                if (kA == kB) {
+                    ++c;
+                    on_shared(h, kA >> 2, ul, vl, pre, eA & 3u, eB & 3u);
+                }
+                ia += takeA;
+                ib += !takeA;
+                const uint32_t nx = takeA ? sA[ia] : sB[ib];
+                eA = takeA ? nx : eA;
+                eB = takeA ? eB : nx;
+            }
+        }
+        if (CTA) {
+            __syncthreads();
+            if (tid == NT - 1) { bc[0] = ia; bc[1] = ib; }
+            __syncthreads();
+            i0 += bc[0];
+            j0 += bc[1];
+        } else {
+            i0 += __shfl_sync(0xffffffffu, ia, 31);
+            j0 += __shfl_sync(0xffffffffu, ib, 31);
+            __syncwarp();
+        }
+    }
+    return c;
+}
+
+// --------------------------------------------------------------- k_warp --
+template <int K>
+__global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_ptr,
+                                              const uint32_t* __restrict__ adj,
+                                              const SegDev* __restrict__ seg,
+                                              const uint4* __restrict__ rec,
+                                              const unsigned int* __restrict__ cnt, uint32_t cap,
+                                              unsigned long long* __restrict__ acc) {
+    constexpr int W = 32 * K + 4;
+    __shared__ __align__(16) uint32_t sbuf[WARPS][2][W];
+    __shared__ unsigned long long hs_all[WARPS][ACC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long* hs = hs_all[warp];
+    for (int j = lane; j < ACC; j += 32) hs[j] = 0;
+    __syncwarp();
+    int tag = -1;
+    const unsigned ntask = min(*cnt, cap);
+    for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS) {
+        const uint4 r = rec[i];
+        const int s = (int)(r.z >> 2);
+        const uint32_t pre = r.z & 3u;
+        if (s != tag) {
+            flush_hist<WARPS>(hs, acc, tag, lane);
+            __syncwarp();
+            tag = s;
+        }
+        const int64_t rb = seg[s].rb;
+        const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
+        const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+        uint32_t c = merge_range<32, K, false>(adj, ab, ae, bb, be, 0, 0, (ae - ab) + (be - bb),
+                                               (uint32_t)(r.x - rb), (uint32_t)(r.y - rb), pre,
+                                               sbuf[warp][0], sbuf[warp][1], nullptr, hs, lane);
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    }
+    __syncwarp();
+    flush_hist<WARPS>(hs, acc, tag, lane);
+}
+
+// ---------------------------------------------------------------- k_cta --
+template <int NT, int K>
+__global__ void __launch_bounds__(NT) k_cta(const int64_t* __restrict__ row_ptr,
+                                            const uint32_t* __restrict__ adj,
+                                            const SegDev* __restrict__ seg,
+                                            const uint4* __restrict__ rec,
+                                            const int32_t* __restrict__ ia_start,
+                                            const unsigned int* __restrict__ cnt, uint32_t cap,
+                                            int chunk, unsigned long long* __restrict__ acc) {
+    constexpr int W = NT * K + 4;
+    __shared__ __align__(16) uint32_t sbuf[2][W];
+    __shared__ unsigned long long hs[ACC];
+    __shared__ int bc[2];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int j = tid; j < ACC; j += NT) hs[j] = 0;
+    __syncthreads();
+    int tag = -1;
+    const unsigned n2 = min(*cnt, cap);
+    for (unsigned i = blockIdx.x; i < n2; i += gridDim.x) {
+        const uint4 r = rec[i];
+        const int s = (int)(r.z >> 2);
+        const uint32_t pre = r.z & 3u;
+        if (s != tag) {
+            __syncthreads();
+            if (tid < 32) flush_hist<1>(hs, acc, tag, lane);
+            __syncthreads();
+            tag = s;
+        }
+        const int64_t rb = seg[s].rb;
+        const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
+        const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+        const int64_t L = (ae - ab) + (be - bb);
+        const int64_t d0 = r.w;
+        const int64_t ia = ia_start[i];
+        const int64_t count = min((int64_t)chunk, L - d0);
+        uint32_t c = merge_range<NT, K, true>(adj, ab, ae, bb, be, ia, d0 - ia, count,
+                                              (uint32_t)(r.x - rb), (uint32_t)(r.y - rb), pre,
+                                              sbuf[0], sbuf[1], bc, hs, tid);
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    }
+    __syncthreads();
+    if (tid < 32) flush_hist<1>(hs, acc, tag, lane);
+}
+
+// ---------------------------------------------------------------- k_fold --
+// 64 codes -> 16 MAN types; 003 = C(n,3) - the rest, in 128-bit (Sec. 2.2).
+__global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev* __restrict__ seg, int nseg,
+                       tc_census_t* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const unsigned long long* h = acc + (size_t)s * ACC;
+    unsigned long long cnt[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) cnt[t] = 0;
+    for (int code = 0; code < 64; ++code) cnt[triad_type(code)] += h[code];
+    cnt[1] += h[64];
+    cnt[2] += h[65];
+    const unsigned __int128 n = (unsigned __int128)(unsigned long long)seg[s].n;
+    unsigned __int128 all = n >= 3 ? n * (n - 1) * (n - 2) / 6 : 0;
+    for (int t = 1; t < 16; ++t) all -= cnt[t];
+    tc_census_t o;
+    o.count[0] = (uint64_t)all;
+    o.count003_hi = (uint64_t)(all >> 64);
+    for (int t = 1; t < 16; ++t) o.count[t] = cnt[t];
+    out[seg[s].slot] = o;
+}
+
+// ------------------------------------------------------------- host side --
+constexpr int K_WARP = 7;
+constexpr int CTA_NT = 256;
+constexpr int K_CTA = 15;
+
+struct Launch {
+    int sms = 148;
+    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1;
+    bool ready = false;
+};
+
+tc_status launch_info(Launch& L) {
+    static Launch cache[64];
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    Launch& c = cache[dev & 63];
+    if (!c.ready) {
+        TC_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks, k_tasks, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_thread, k_thread, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_warp, k_warp<K_WARP>, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_cta, k_cta<CTA_NT, K_CTA>, CTA_NT, 0));
+        c.occ_tasks = std::max(1, c.occ_tasks);
+        c.occ_thread = std::max(1, c.occ_thread);
+        c.occ_warp = std::max(1, c.occ_warp);
+        c.occ_cta = std::max(1, c.occ_cta);
+        c.ready = true;
+    }
+    L = c;
+    return TC_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
+                      tc_census_t* out, uint32_t flags, cudaStream_t st) {
+    if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
+    tc_opts o;
+    tc_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (o.bin_mode != TC_BIN_HEURISTIC && o.bin_mode != TC_BIN_MLP)
+        return fail(TC_ERR_ARG, "census: unknown bin_mode");
+    if (o.thr_thread < 0 || o.thr_warp < o.thr_thread || o.chunk < 256)
+        return fail(TC_ERR_ARG, "census: need 0 <= thr_thread <= thr_warp and chunk >= 256");
+    const int nseg = (int)gidx.size();
+    std::vector<SegDev> segs((size_t)nseg);
+    std::vector<int64_t> pfx((size_t)nseg + 1, 0);
+    int64_t dyads = 0, merged = 0;
+    for (int i = 0; i < nseg; ++i) {
+        const int g = gidx[(size_t)i];
+        segs[(size_t)i].rb = set.voff[(size_t)g];
+        segs[(size_t)i].n = set.voff[(size_t)g + 1] - set.voff[(size_t)g];
+        segs[(size_t)i].slot = i;
+        segs[(size_t)i].pad = 0;
+        pfx[(size_t)i + 1] = pfx[(size_t)i] + segs[(size_t)i].n;
+        dyads += set.stats[(size_t)g].dyads;
+        merged += set.stats[(size_t)g].merged_entries;
+    }
+    const int64_t rows = pfx[(size_t)nseg];
+    const uint64_t cap01 = (uint64_t)dyads + 1;
+    const uint64_t cap2 = (uint64_t)(merged / o.chunk) + (uint64_t)dyads + 1;
+    if (cap01 >= 0xffffffffull || cap2 >= 0xffffffffull)
+        return fail(TC_ERR_UNSUPPORTED, "census: more than 2^32 tasks");
+    // work space layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
+    const size_t o_acc = take(sizeof(unsigned long long) * ACC * (size_t)nseg);
+    const size_t o_ctr = take(64);
+    const size_t o_seg = take(sizeof(SegDev) * (size_t)nseg);
+    const size_t o_pfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
+    const size_t o_out = take(sizeof(tc_census_t) * (size_t)nseg);
+    const size_t o_r0 = take(sizeof(uint4) * cap01);
+    const size_t o_r1 = take(sizeof(uint4) * cap01);
+    const size_t o_r2 = take(sizeof(uint4) * cap2);
+    const size_t o_ia = take(sizeof(int32_t) * cap2);
+    const size_t need = off;
+    if (set.ws_bytes < need) {
+        dev_free(set.ws, st);
+        set.ws = nullptr;
+        set.ws_bytes = 0;
+        TC_CUDA(dev_alloc(&set.ws, need, st));
+        set.ws_bytes = need;
+    }
+    char* ws = (char*)set.ws;
+    unsigned long long* acc = (unsigned long long*)(ws + o_acc);
+    unsigned int* ctr = (unsigned int*)(ws + o_ctr);  // [0..2] bin counts, [4] overflow, [8..9] cursor (u64)
+    SegDev* d_seg = (SegDev*)(ws + o_seg);
+    int64_t* d_pfx = (int64_t*)(ws + o_pfx);
+    tc_census_t* d_out = (flags & TC_OUT_DEVICE) ? out : (tc_census_t*)(ws + o_out);
+    Bins bins;
+    bins.rec[0] = (uint4*)(ws + o_r0);
+    bins.rec[1] = (uint4*)(ws + o_r1);
+    bins.rec[2] = (uint4*)(ws + o_r2);
+    bins.cap[0] = bins.cap[1] = (uint32_t)cap01;
+    bins.cap[2] = (uint32_t)cap2;
+    bins.cnt = ctr;
+    bins.overflow = (int*)(ctr + 4);
+    unsigned long long* cursor = (unsigned long long*)(ctr + 8);
+    int32_t* d_ia = (int32_t*)(ws + o_ia);
+
+    TC_CUDA(cudaMemcpyAsync(d_seg, segs.data(), sizeof(SegDev) * (size_t)nseg, cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaMemcpyAsync(d_pfx, pfx.data(), sizeof(int64_t) * ((size_t)nseg + 1), cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaMemsetAsync(ws, 0, o_seg, st));  // accumulators + counters
+
+    Launch L;
+    if (tc_status s = launch_info(L); s != TC_OK) return s;
+    BinParams bp{o.thr_thread, o.thr_warp, o.chunk};
+    if (rows > 0) {
+        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, nseg, rows, bp,
+                                                     bins, acc, cursor);
+        TC_CUDA(cudaGetLastError());
+        k_split<<<L.sms * 4, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], d_ia);
+        TC_CUDA(cudaGetLastError());
+        k_cta<CTA_NT, K_CTA><<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[2], d_ia,
+                                                                   ctr + 2, bins.cap[2], o.chunk, acc);
+        TC_CUDA(cudaGetLastError());
+        k_warp<K_WARP><<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], ctr + 1,
+                                                            bins.cap[1], acc);
+        TC_CUDA(cudaGetLastError());
+        k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
+                                                        bins.cap[0], acc);
+        TC_CUDA(cudaGetLastError());
+    }
+    k_fold<<<(nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, nseg, d_out);
+    TC_CUDA(cudaGetLastError());
+    if (!(flags & TC_OUT_DEVICE)) {
+        int ovf = 0;
+        TC_CUDA(cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * (size_t)nseg, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaMemcpyAsync(&ovf, bins.overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        if (ovf) return fail(TC_ERR_CUDA, "census: task bin overflow (internal error)");
+    }
+    return TC_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" {
+
+int tc_triad_type(int code) { return (code < 0 || code > 63) ? -1 : tc::triad_type(code); }
+
+tc_status tc_census(tc_graph g, const tc_opts* opts, tc_census_t* out, uint32_t flags, void* stream) {
+    if (!g || !out) return tc::fail(TC_ERR_ARG, "tc_census: null argument");
+    try {
+        std::vector<int32_t> idx{g->index};
+        return tc::census_impl(*g->set, idx, opts, out, flags, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_census: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_census: unexpected exception");
+    }
+}
+
+tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_census_t* out,
+                            uint32_t flags, void* stream) {
+    if (G < 0 || (G > 0 && (!gs || !out))) return tc::fail(TC_ERR_ARG, "tc_census_batched: bad arguments");
+    if (G == 0) return TC_OK;
+    try {
+        std::vector<int32_t> idx((size_t)G);
+        for (int32_t i = 0; i < G; ++i) {
+            if (!gs[i]) return tc::fail(TC_ERR_ARG, "tc_census_batched: null handle");
+            if (gs[i]->set != gs[0]->set)
+                return tc::fail(TC_ERR_UNSUPPORTED, "tc_census_batched: handles come from different builds");
+            idx[(size_t)i] = gs[i]->index;
+        }
+        return tc::census_impl(*gs[0]->set, idx, opts, out, flags, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_census_batched: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_census_batched: unexpected exception");
+    }
+}
+
+}  // extern "C"

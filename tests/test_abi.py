@@ -1,0 +1,70 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/tc.h declares, and its host-only calls behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_1603_02655_b300 as tc
+from paper_1603_02655_b300 import build as tcbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "tc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tc_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    tcbuild.build()
+    return tc.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(lib, name), name
+    # the Python binding wraps exactly the declared entry points
+    assert set(names) == set(tc.EXPORTS)
+
+
+def test_library_table_matches_oracle_table(lib):
+    assert [tc.tc_triad_type(c) for c in range(64)] == oracle.triad_table()
+    assert tc.tc_triad_type(-1) == -1 and tc.tc_triad_type(64) == -1
+
+
+def test_status_strings_and_defaults(lib):
+    for s in range(7):
+        assert tc.tc_status_str(s).startswith("TC_")
+    o = tc.tc_opts_default()
+    assert o.bin_mode == tc.TC_BIN_HEURISTIC
+    assert 0 <= o.thr_thread <= o.thr_warp and o.chunk >= 256
+
+
+def test_argument_errors_need_no_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.tc_graph_build(-1, None, None, 0, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG
+    assert lib.tc_graph_build(5, None, None, -3, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG
+    assert lib.tc_graph_build(5, None, None, 4, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG
+    assert lib.tc_graph_build(1 << 30, None, None, 0, 0, None, ctypes.byref(h)) == tc.TC_ERR_UNSUPPORTED
+    assert lib.tc_graph_build(5, None, None, 0, 0x80, None, ctypes.byref(h)) == tc.TC_ERR_ARG
+    assert lib.tc_census(None, None, None, 0, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_batched(-1, None, None, None, 0, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_batched(0, None, None, None, 0, None) == tc.TC_OK
+    assert lib.tc_graph_stats(None, None) == tc.TC_ERR_ARG
+    assert lib.tc_opts_default(None) == tc.TC_ERR_ARG
+    assert "null" in tc.tc_last_error() or tc.tc_last_error()
+    lib.tc_graph_free(None)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(tc, "_lib", None)
+    monkeypatch.setattr(tc, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError):
+        tc.load()

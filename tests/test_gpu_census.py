@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA census against the CPU oracle, element by element
+(all 16 counts, exact integers), through the C-ABI."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1603_02655_b300 as tc
+from paper_1603_02655_b300 import build as tcbuild
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+THREADS = min(os.cpu_count() or 1, 32)
+BIG = 1 << 30
+
+# binning configurations: default, everything per thread, per warp, per CTA
+# chunk (tiny chunks: every task split), and small mixed thresholds
+BINS = {
+    "default": {},
+    "thread": dict(thr_thread=BIG, thr_warp=BIG),
+    "warp": dict(thr_thread=0, thr_warp=BIG),
+    "cta": dict(thr_thread=0, thr_warp=0, chunk=256),
+    "mixed": dict(thr_thread=8, thr_warp=40, chunk=512),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib(cuda_ok):
+    tcbuild.build()
+    return tc.load()
+
+
+def opts(name):
+    return tc.tc_opts_default(**BINS[name])
+
+
+def gpu_census(n, src, dst, o=None):
+    g = tc.tc_graph_build(n, src, dst)
+    try:
+        return tc.tc_census(g, o)
+    finally:
+        tc.tc_graph_free(g)
+
+
+def rand_graph(rng, n, p, r):
+    s, d = np.nonzero(rng.random((n, n)) < p)
+    keep = s != d
+    s, d = s[keep], d[keep]
+    rec = rng.random(s.size) < r
+    return (np.concatenate([s, d[rec]]).astype(np.int32),
+            np.concatenate([d, s[rec]]).astype(np.int32))
+
+
+def hub_graph(rng, n, hubs, hub_deg, extra, recip):
+    """A few hubs joined to many vertices plus random arcs: tasks of every bin."""
+    src, dst = [], []
+    for h in range(hubs):
+        nb = rng.choice(n, size=hub_deg, replace=False)
+        out = rng.random(hub_deg) < 0.5
+        src.append(np.where(out, h, nb))
+        dst.append(np.where(out, nb, h))
+    src.append(rng.integers(0, n, extra))
+    dst.append(rng.integers(0, n, extra))
+    s = np.concatenate(src).astype(np.int32)
+    d = np.concatenate(dst).astype(np.int32)
+    rec = rng.random(s.size) < recip
+    return np.concatenate([s, d[rec]]), np.concatenate([d, s[rec]])
+
+
+# ------------------------------------------------------------ tiny graphs
+
+def test_all_64_triads_batched():
+    T = oracle.triad_table()
+    bits = {(0, 1): 1, (1, 0): 2, (0, 2): 4, (2, 0): 8, (1, 2): 16, (2, 1): 32}
+    src, dst, off = [], [], [0]
+    for c in range(64):
+        arcs = [ab for ab, b in bits.items() if c & b]
+        src += [a for a, _ in arcs]
+        dst += [b for _, b in arcs]
+        off.append(len(src))
+    gs = tc.tc_graph_build_batched([3] * 64, off, src, dst)
+    try:
+        for name in BINS:
+            res = tc.tc_census_batched(gs, opts(name))
+            for c in range(64):
+                want = [0] * 16
+                want[T[c]] = 1
+                assert res[c] == want, (name, c)
+    finally:
+        for g in gs:
+            tc.tc_graph_free(g)
+
+
+def test_all_4096_four_vertex_digraphs_batched():
+    pairs = [(a, b) for a in range(4) for b in range(4) if a != b]
+    src, dst, off, want = [], [], [0], []
+    for mask in range(1 << 12):
+        arcs = [pairs[k] for k in range(12) if mask >> k & 1]
+        s = [a for a, _ in arcs]
+        d = [b for _, b in arcs]
+        src += s
+        dst += d
+        off.append(len(src))
+        want.append(oracle.brute_census(4, s, d))
+    gs = tc.tc_graph_build_batched([4] * 4096, off, src, dst)
+    try:
+        for name in ("default", "cta", "mixed"):
+            assert tc.tc_census_batched(gs, opts(name)) == want, name
+        # a shuffled subset keeps each result with its own graph
+        rng = np.random.default_rng(3)
+        pick = rng.permutation(4096)[:1000]
+        sub = tc.tc_census_batched([gs[i] for i in pick])
+        assert sub == [want[i] for i in pick]
+    finally:
+        for g in gs:
+            tc.tc_graph_free(g)
+
+
+# ------------------------------------------------------------ random graphs
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_graphs_all_bins(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 400))
+    p = float(rng.choice([0.005, 0.03, 0.1, 0.4]))
+    r = float(rng.choice([0.0, 0.3, 1.0]))
+    src, dst = rand_graph(rng, n, p, r)
+    want = oracle.census(n, src, dst, threads=THREADS)
+    for name in BINS:
+        assert gpu_census(n, src, dst, opts(name)) == want, name
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_hub_graphs_span_tiles_and_chunks(seed):
+    # hub tasks of |N(u)|+|N(v)| ~ 4000-9000: several 3840-entry CTA tiles,
+    # split into chunks, with ragged tails
+    rng = np.random.default_rng(50 + seed)
+    n = 9000
+    src, dst = hub_graph(rng, n, hubs=3, hub_deg=int(rng.integers(2500, 4500)), extra=30000,
+                         recip=0.2)
+    want = oracle.census(n, src, dst, threads=THREADS)
+    for name in BINS:
+        assert gpu_census(n, src, dst, opts(name)) == want, name
+
+
+def test_c1_matches_golden_and_brute():
+    a = synth.c1()
+    gold = json.load(open(os.path.join(GOLDEN, "census_c1.json")))["census"]
+    assert oracle.brute_census(a.n, a.src, a.dst) == gold
+    for name in BINS:
+        assert gpu_census(a.n, a.src, a.dst, opts(name)) == gold, name
+
+
+# ------------------------------------------------------------ closed forms
+
+def C3(n):
+    return n * (n - 1) * (n - 2) // 6
+
+
+def idx(name):
+    return tc.TYPE_NAMES.index(name)
+
+
+def test_closed_forms():
+    n = 1000
+    c = gpu_census(n, [], [])
+    assert c[0] == C3(n) and sum(c[1:]) == 0
+    m = 120
+    s, d = map(list, zip(*[(a, b) for a in range(m) for b in range(m) if a != b]))
+    assert gpu_census(m, s, d)[idx("300")] == C3(m)
+    s, d = map(list, zip(*[(a, b) for a in range(m) for b in range(m) if a < b]))
+    assert gpu_census(m, s, d)[idx("030T")] == C3(m)
+    c = gpu_census(n, [0, 1, 2], [1, 2, 0])
+    want = [0] * 16
+    want[idx("030C")] = 1
+    want[idx("012")] = 3 * (n - 3)
+    want[0] = C3(n) - 1 - 3 * (n - 3)
+    assert c == want
+
+
+@pytest.mark.parametrize("n", [3, 100, 50_000])
+def test_stars(n):
+    # the hub task has |N(u)|+|N(v)| = n: at 50k it is split over CTA chunks
+    leaves = np.arange(1, n, dtype=np.int32)
+    hub = np.zeros(n - 1, dtype=np.int32)
+    for name in ("default", "cta"):
+        c = gpu_census(n, hub, leaves, opts(name))
+        assert c[idx("021D")] == (n - 1) * (n - 2) // 2 and c[0] == C3(n - 1) and sum(c) == C3(n)
+        c = gpu_census(n, leaves, hub, opts(name))
+        assert c[idx("021U")] == (n - 1) * (n - 2) // 2 and c[0] == C3(n - 1)
+
+
+def test_large_n_needs_128_bit_null_count():
+    n = 5_000_000  # C(n,3) > 2^64
+    c = gpu_census(n, [0, 1], [1, 2])
+    assert c[0] == C3(n) - c[idx("021C")] - c[idx("012")]
+    assert c[0] >= 1 << 64
+    assert sum(c) == C3(n)
+
+
+def test_input_policy():
+    base = gpu_census(6, [0, 1, 2], [1, 2, 3])
+    assert gpu_census(6, [0, 1, 2, 0, 0, 4], [1, 2, 3, 1, 0, 4]) == base
+    assert gpu_census(2, [0], [1]) == [0] * 16
+    assert gpu_census(0, [], []) == [0] * 16
+    with pytest.raises(tc.TcError) as e:
+        gpu_census(3, [0, 1], [1, 3])
+    assert e.value.status == tc.TC_ERR_ID_RANGE
+    with pytest.raises(tc.TcError) as e:
+        gpu_census(3, [0, -1], [1, 2])
+    assert e.value.status == tc.TC_ERR_ID_RANGE
+
+
+def test_build_layout_matches_definition():
+    rng = np.random.default_rng(9)
+    n = 500
+    src, dst = rand_graph(rng, n, 0.02, 0.3)
+    src = np.concatenate([src, src[:50], np.arange(10, dtype=np.int32)])  # dups + loops
+    dst = np.concatenate([dst, dst[:50], np.arange(10, dtype=np.int32)])
+    g = tc.tc_graph_build(n, src, dst)
+    try:
+        rp, adj = tc.tc_graph_export(g)
+        st = tc.tc_graph_stats(g)
+    finally:
+        tc.tc_graph_free(g)
+    arcs = {(int(a), int(b)) for a, b in zip(src, dst) if a != b}
+    rows = {x: {} for x in range(n)}
+    for a, b in arcs:
+        rows[a][b] = rows[a].get(b, 0) | 1
+        rows[b][a] = rows[b].get(a, 0) | 2
+    for x in range(n):
+        got = [(int(e) >> 2, int(e) & 3) for e in adj[rp[x]:rp[x + 1]]]
+        assert got == sorted(rows[x].items()), x
+    og = oracle.Graph(n, src, dst).stats()
+    for k in ("arcs", "dyads", "mutual", "asym", "merged_entries", "max_degree"):
+        assert st[k] == og[k], k
+
+
+def test_device_inputs_and_device_output_on_a_stream():
+    import torch
+    a = synth.c1()
+    gold = json.load(open(os.path.join(GOLDEN, "census_c1.json")))["census"]
+    s = torch.cuda.Stream()
+    src = torch.from_numpy(a.src).cuda()
+    dst = torch.from_numpy(a.dst).cuda()
+    torch.cuda.synchronize()
+    g = tc.tc_graph_build(a.n, src, dst, stream=s)
+    try:
+        out = torch.zeros(17, dtype=torch.int64, device="cuda")
+        tc.tc_census(g, None, out=out, stream=s)
+        s.synchronize()
+        assert tc.census_from_device_words(out.cpu().tolist()) == gold
+    finally:
+        tc.tc_graph_free(g)
+
+
+def test_repeated_calls_are_identical():
+    rng = np.random.default_rng(77)
+    src, dst = hub_graph(rng, 5000, 2, 3000, 20000, 0.3)
+    g = tc.tc_graph_build(5000, src, dst)
+    try:
+        first = tc.tc_census(g)
+        for _ in range(5):
+            assert tc.tc_census(g) == first
+    finally:
+        tc.tc_graph_free(g)
