@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the triad-census hot path on B300 (one JSON line on stdout).
+
+A step is one pass of the whole hot path over the workload's arc list, which
+is already resident in HBM: device graph build (dedup, tagged adjacency) and
+the census (task build + binning, union merges, classification, fold and
+003 closure).  `value` is merged adjacency entries per second of step time
+(entries = sum over canonical dyads of |N(u)|+|N(v)|, the data the merges must
+read); `census_ms` in the breakdown is the census alone.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3]
+    python bench.py --impl reference ...   # the CPU oracle on host cores
+
+With N > 1 (torchrun) every rank censuses its own replica of the workload
+(weak scaling, no collective on the data path); only the timing uses a
+barrier and a max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "census time; merged adjacency entries/s vs HBM roofline; graphs/s batched"
+UNIT = "merged adjacency entries/s"
+WORKLOAD_DESC = {
+    "c1": "G(n,p) n=1024 p=8/1023 reciprocity 0.25 seed 1",
+    "c2": "R-MAT scale 20 edge factor 8 (.57,.19,.19,.05) 10% reciprocated, ids permuted, seed 2",
+    "c3": "R-MAT scale 22 edge factor 4 (.57,.19,.19,.05), arcs oriented high->low id, ids permuted, seed 3",
+    "c3s": "R-MAT scale 21 edge factor 4, arcs oriented high->low id, ids permuted, seed 3 (profiling case)",
+    "c5": "Chung-Lu n=2^22 gamma 2.1 mean total degree 16 max 1e5 reciprocity 0.15, seed 5",
+}
+OWN_BUILD_KERNELS = 5   # k_keys k_heads k_write k_fill_sent k_rowstats (plus CUB sort/scan)
+FLUSH_BYTES = 512 << 20  # > 126 MB L2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1603_02655_b300", "csrc", "census.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[2] == sha:
+                return int(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(x, pg):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    if pg.get_backend() == "nccl":
+        t = t.cuda()
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+def oracle_sample_rate(arcs, seconds, threads=None):
+    """Run the oracle census on disjoint vertex ranges (ids are a random
+    permutation, so a range of low endpoints is a random sample of dyads) for
+    about `seconds` of wall time on `threads` host threads."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    og = oracle.Graph(arcs.n, arcs.src, arcs.dst)
+    n = arcs.n
+    # calibrate on one small range
+    r0 = max(1, n // 20000)
+    t = time.perf_counter()
+    _, e0 = og.census_range(0, r0)
+    dt = max(time.perf_counter() - t, 1e-4)
+    per_vertex = dt / r0
+    total_vertices = int(min(n, max(threads, seconds * threads / per_vertex)))
+    step = max(1, total_vertices // (threads * 8))
+    ranges = [(a, min(a + step, total_vertices)) for a in range(r0, total_vertices, step)]
+    lock = threading.Lock()
+    done = {"entries": e0, "vertices": r0}
+
+    def work():
+        while True:
+            with lock:
+                if not ranges:
+                    return
+                a, b = ranges.pop()
+            _, e = og.census_range(a, b)
+            with lock:
+                done["entries"] += e
+                done["vertices"] += b - a
+
+    t = time.perf_counter()
+    pool = [threading.Thread(target=work) for _ in range(threads)]
+    for th in pool:
+        th.start()
+    for th in pool:
+        th.join()
+    wall = time.perf_counter() - t + dt
+    og.close()
+    return done["entries"] / wall, threads, done["vertices"], done["entries"], wall
+
+
+def run_reference(args, world, rank, pg):
+    import synth
+    if rank != 0:
+        return
+    arcs = synth.WORKLOADS[args.workload]()
+    import oracle
+    og = oracle.Graph(arcs.n, arcs.src, arcs.dst)
+    stats = og.stats()
+    threads = os.cpu_count() or 1
+    per_step_s = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates, walls = [], []
+    for i in range(args.warmup + args.steps):
+        rate, thr, verts, ents, wall = oracle_sample_rate(arcs, per_step_s, threads)
+        if i >= args.warmup:
+            rates.append(rate)
+            walls.append(wall)
+    value = float(np.mean(rates))
+    sample = (f"oracle census of the canonical dyads whose lower endpoint lies in disjoint vertex "
+              f"ranges (~{per_step_s:.0f} s per step on {threads} host threads) of workload "
+              f"{args.workload}; rate = merged entries processed / wall time")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOAD_DESC.get(args.workload, '')}",
+                   "n": arcs.n, "arcs": stats["arcs"], "merged_entries": stats["merged_entries"],
+                   "parallelism": f"host threads x{threads}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ native arm
+
+def run_native(args, world, rank, local, pg):
+    import torch
+    import synth
+    import paper_1603_02655_b300 as tc
+    from paper_1603_02655_b300 import build as tcbuild
+
+    torch.cuda.set_device(local)
+    tcbuild.build()
+    tc.load()
+    arcs = synth.WORKLOADS[args.workload]()
+    src_d = torch.from_numpy(arcs.src).cuda()
+    dst_d = torch.from_numpy(arcs.dst).cuda()
+    src_h = torch.from_numpy(arcs.src).pin_memory()
+    dst_h = torch.from_numpy(arcs.dst).pin_memory()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    out = torch.zeros(17, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    prof_opts = tc.tc_opts_default(profile=1)
+
+    def step_device():
+        g = tc.tc_graph_build(arcs.n, src_d, dst_d, stream=stream)
+        tc.tc_census(g, prof_opts, out=out, stream=stream)
+        return g
+
+    # warm-up
+    for _ in range(args.warmup):
+        g = step_device()
+        tc.tc_graph_free(g)
+    torch.cuda.synchronize()
+    g = tc.tc_graph_build(arcs.n, src_d, dst_d)
+    stats = tc.tc_graph_stats(g)
+    tc.tc_census(g, prof_opts, out=out)
+    torch.cuda.synchronize()
+    census = tc.census_from_device_words(out.cpu().tolist())
+    tc.tc_graph_free(g)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    profs = []
+    barrier(pg)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k)   # L2 flush between steps (outside the step's events)
+            a, b, c = ev[k]
+            a.record(stream)
+            g = tc.tc_graph_build(arcs.n, src_d, dst_d, stream=stream)
+            b.record(stream)
+            tc.tc_census(g, prof_opts, out=out, stream=stream)
+            c.record(stream)
+            profs.append(tc.tc_census_profile())
+            tc.tc_graph_free(g)
+        torch.cuda.synchronize()
+    barrier(pg)
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    build_ms = [a.elapsed_time(b) for a, b, c in ev]
+    census_ms = [b.elapsed_time(c) for a, b, c in ev]
+    total_ms = max_over_ranks(sum(step_ms), pg)
+    ms_per_step = total_ms / args.steps
+    value = world * stats["merged_entries"] * args.steps / (total_ms / 1e3)
+
+    # dominant kernel and its roofline (algorithmic bytes = 4 B per merged entry)
+    kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_cta": "ms_cta", "k_warp": "ms_warp",
+            "k_thread": "ms_thread", "k_fold": "ms_fold"}
+    avg = {k: float(np.mean([p[f] for p in profs])) for k, f in kern.items()}
+    merge_bin = {"k_cta": 2, "k_warp": 1, "k_thread": 0}
+    top = max(merge_bin, key=lambda k: avg[k])
+    entries_top = profs[-1]["bin_entries"][merge_bin[top]]
+    peak, peak_kind = peaks()
+    achieved = 4.0 * entries_top / (avg[top] / 1e3) / 1e9
+    traffic = recorded_traffic(top)
+    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": 4 * entries_top,
+                "ms_per_launch": avg[top]}
+    merge_ms = avg["k_cta"] + avg["k_warp"] + avg["k_thread"]
+
+    # end to end through the public API from pinned host memory
+    e2e_steps = max(3, min(args.steps, 5))
+    host_out = None
+    e2e_ms = []
+    for k in range(e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = tc.tc_graph_build(arcs.n, src_h.numpy(), dst_h.numpy())
+        host_out = tc.tc_census(g)
+        t1 = time.perf_counter()
+        tc.tc_graph_free(g)
+        if k > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    assert host_out == census, "end-to-end census differs from the device-resident run"
+    e2e_total = max_over_ranks(sum(e2e_ms), pg)
+    e2e = {"value": world * stats["merged_entries"] * e2e_steps / (e2e_total / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(arcs.src.nbytes + arcs.dst.nbytes),
+           "d2h_bytes_per_step": 17 * 8, "ms_per_step": e2e_total / e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, thr, verts, ents, wall = oracle_sample_rate(arcs, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"oracle census of the canonical dyads with lower endpoint in {verts} of "
+                         f"{arcs.n} vertices ({ents:.3e} merged entries, {wall:.1f} s on {thr} "
+                         f"host threads)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_DESC.get(args.workload, '')}",
+                       "n": arcs.n, "arcs": stats["arcs"], "dyads": stats["dyads"],
+                       "merged_entries": stats["merged_entries"],
+                       "max_degree": stats["max_degree"],
+                       "step": "graph build + census, arc list resident in HBM",
+                       "l2": "512 MB buffer written between timed steps (L2 flush)",
+                       "parallelism": "single GPU" if world == 1 else f"replicas x{world}"},
+            "breakdown": {"census_ms": float(np.mean(census_ms)), "build_ms": float(np.mean(build_ms)),
+                          "merge_ms": merge_ms, "kernel_ms": avg,
+                          "bin_tasks": profs[-1]["bin_tasks"], "bin_entries": profs[-1]["bin_entries"],
+                          "chunks": profs[-1]["chunks"],
+                          "census_entries_per_s": stats["merged_entries"] / (np.mean(census_ms) / 1e3)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * (OWN_BUILD_KERNELS + profs[-1]["launches"]),
+            "census": [str(x) for x in census],
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank, pg)
+        else:
+            run_native(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

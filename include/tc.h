@@ -76,8 +76,29 @@ typedef struct {
     int32_t thr_thread;   /* tasks with |N(u)|+|N(v)| <= thr_thread: one thread each */
     int32_t thr_warp;     /* <= thr_warp: one warp each; larger: CTA chunks */
     int32_t chunk;        /* merge length of one CTA chunk (splits hub tasks) */
-    int32_t reserved[4];  /* must be zero */
+    int32_t profile;      /* 1: time each kernel with CUDA events and keep the
+                             task/bin counts (read with tc_census_profile);
+                             the call then synchronises `stream` */
+    int32_t reserved[3];  /* must be zero */
 } tc_opts;
+
+/* Per-kernel timing and binning of the calling thread's most recent
+ * tc_census / tc_census_batched call made with opts.profile = 1. */
+typedef struct {
+    float ms_tasks;          /* task build + suffix-count terms (k_tasks) */
+    float ms_split;          /* chunk start partitions (k_split) */
+    float ms_cta;            /* CTA-chunk merges (k_cta) */
+    float ms_warp;           /* warp-per-task merges (k_warp) */
+    float ms_thread;         /* thread-per-task merges (k_thread) */
+    float ms_fold;           /* 64->16 fold and 003 closure (k_fold) */
+    float ms_total;          /* first to last kernel */
+    int32_t launches;        /* kernels launched by the call */
+    int64_t bin_tasks[3];    /* dyads per bin: thread, warp, CTA */
+    int64_t bin_entries[3];  /* merged entries |N(u)|+|N(v)| per bin */
+    int64_t chunks;          /* CTA chunk records */
+} tc_profile_t;
+
+tc_status tc_census_profile(tc_profile_t* out);
 
 /* tc_graph_build flags */
 #define TC_DEVICE_PTRS 1u   /* src/dst (and arc offsets) are device pointers */

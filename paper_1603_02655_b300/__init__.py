@@ -36,7 +36,7 @@ TC_OUT_DEVICE = 2
 
 EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
            "tc_graph_export", "tc_census", "tc_census_batched", "tc_triad_type",
-           "tc_graph_free", "tc_status_str", "tc_last_error")
+           "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile")
 
 
 class TcCensus(ctypes.Structure):
@@ -59,7 +59,22 @@ class TcStats(ctypes.Structure):
 class TcOpts(ctypes.Structure):
     _fields_ = [("bin_mode", ctypes.c_int32), ("thr_thread", ctypes.c_int32),
                 ("thr_warp", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class TcProfile(ctypes.Structure):
+    _fields_ = [("ms_tasks", ctypes.c_float), ("ms_split", ctypes.c_float),
+                ("ms_cta", ctypes.c_float), ("ms_warp", ctypes.c_float),
+                ("ms_thread", ctypes.c_float), ("ms_fold", ctypes.c_float),
+                ("ms_total", ctypes.c_float), ("launches", ctypes.c_int32),
+                ("bin_tasks", ctypes.c_int64 * 3), ("bin_entries", ctypes.c_int64 * 3),
+                ("chunks", ctypes.c_int64)]
+
+    def to_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        for k in ("bin_tasks", "bin_entries"):
+            d[k] = [int(x) for x in d[k]]
+        return d
 
 
 class TcError(RuntimeError):
@@ -90,6 +105,8 @@ def load():
     lib.tc_census_batched.argtypes = [i32, P, P, P, u32, P]
     lib.tc_triad_type.argtypes = [ctypes.c_int]
     lib.tc_triad_type.restype = ctypes.c_int
+    lib.tc_census_profile.argtypes = [P]
+    lib.tc_census_profile.restype = ctypes.c_int
     lib.tc_graph_free.argtypes = [P]
     lib.tc_graph_free.restype = None
     lib.tc_status_str.argtypes = [ctypes.c_int]
@@ -229,6 +246,13 @@ def tc_census_batched(gs, opts: TcOpts | None = None, out=None, stream=None):
     _check(lib.tc_census_batched(G, arr, po, out.data_ptr(), TC_OUT_DEVICE, _stream(stream)),
            "tc_census_batched")
     return out
+
+
+def tc_census_profile() -> dict:
+    """Kernel times and bin counts of this thread's last profiled census."""
+    p = TcProfile()
+    _check(load().tc_census_profile(ctypes.byref(p)), "tc_census_profile")
+    return p.to_dict()
 
 
 def tc_graph_free(g: int) -> None:

@@ -36,6 +36,27 @@ namespace {
 
 constexpr int WARPS = 8;  // warps per 256-thread block
 
+thread_local tc_profile_t g_profile;
+thread_local bool g_profile_valid = false;
+
+struct ProfileEvents {
+    cudaEvent_t ev[7];
+};
+
+tc_status profile_events(ProfileEvents** out) {
+    static thread_local ProfileEvents pe[64];
+    static thread_local bool made[64];
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    dev &= 63;
+    if (!made[dev]) {
+        for (int k = 0; k < 7; ++k) TC_CUDA(cudaEventCreate(&pe[dev].ev[k]));
+        made[dev] = true;
+    }
+    *out = &pe[dev];
+    return TC_OK;
+}
+
 // ------------------------------------------------------------ type table --
 // MAN type of the labelled triad with 6-bit code (bit order of Fig. "Triad
 // Code Algorithm": e(u,v)=1, e(v,u)=2, e(u,w)=4, e(w,u)=8, e(v,w)=16,
@@ -80,6 +101,8 @@ struct Bins {
     uint32_t cap[3];
     unsigned int* cnt;    // [3] records appended per bin
     int* overflow;
+    unsigned long long* entries;  // [3] merged entries per bin
+    unsigned long long* tasks2;   // dyads routed to CTA chunks
 };
 
 struct BinParams {
@@ -122,12 +145,14 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
     constexpr int ROWS = 32;
     int s = -1;
     int64_t rb = 0, n = 0, sp = 0;
-    unsigned long long Aa[3][3], Bb[3][3], Dd[2];
+    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[3];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int q = 0; q < 3; ++q) Aa[p][q] = Bb[p][q] = 0;
     Dd[0] = Dd[1] = 0;
+    Ee[0] = Ee[1] = Ee[2] = 0;
+    unsigned long long T2 = 0;
 
     auto flush = [&]() {
 #pragma unroll
@@ -209,6 +234,9 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                     Dd[1] += pre_task == 3 ? dy : 0ull;
                     bin = L <= bp.thr_thread ? 0 : (L <= bp.thr_warp ? 1 : 2);
                 }
+#pragma unroll
+                for (int b = 0; b < 3; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
+                T2 += bin == 2 ? 1ull : 0ull;
                 const uint4 rec = make_uint4((uint32_t)x, (uint32_t)(rb + y),
                                              ((uint32_t)s << 2) | (uint32_t)pre_task, 0u);
 #pragma unroll
@@ -254,6 +282,13 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
         }
     }
     flush();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const unsigned long long e = warp_sum64(Ee[b]);
+        if (lane == 0 && e) atomicAdd(bins.entries + b, e);
+    }
+    T2 = warp_sum64(T2);
+    if (lane == 0 && T2) atomicAdd(bins.tasks2, T2);
 }
 
 // --------------------------------------------------------------- k_split --
@@ -635,7 +670,7 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
     const size_t o_acc = take(sizeof(unsigned long long) * ACC * (size_t)nseg);
-    const size_t o_ctr = take(64);
+    const size_t o_ctr = take(128);
     const size_t o_seg = take(sizeof(SegDev) * (size_t)nseg);
     const size_t o_pfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
     const size_t o_out = take(sizeof(tc_census_t) * (size_t)nseg);
@@ -666,6 +701,8 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
     bins.cnt = ctr;
     bins.overflow = (int*)(ctr + 4);
     unsigned long long* cursor = (unsigned long long*)(ctr + 8);
+    bins.entries = (unsigned long long*)(ctr + 10);
+    bins.tasks2 = (unsigned long long*)(ctr + 16);
     int32_t* d_ia = (int32_t*)(ws + o_ia);
 
     TC_CUDA(cudaMemcpyAsync(d_seg, segs.data(), sizeof(SegDev) * (size_t)nseg, cudaMemcpyHostToDevice, st));
@@ -675,24 +712,62 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
     Launch L;
     if (tc_status s = launch_info(L); s != TC_OK) return s;
     BinParams bp{o.thr_thread, o.thr_warp, o.chunk};
+    ProfileEvents* pe = nullptr;
+    if (o.profile) {
+        if (tc_status s = profile_events(&pe); s != TC_OK) return s;
+    }
+    auto mark = [&](int k) {
+        if (pe) cudaEventRecord(pe->ev[k], st);
+    };
+    mark(0);
     if (rows > 0) {
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, nseg, rows, bp,
                                                      bins, acc, cursor);
         TC_CUDA(cudaGetLastError());
+        mark(1);
         k_split<<<L.sms * 4, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], d_ia);
         TC_CUDA(cudaGetLastError());
+        mark(2);
         k_cta<CTA_NT, K_CTA><<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[2], d_ia,
                                                                    ctr + 2, bins.cap[2], o.chunk, acc);
         TC_CUDA(cudaGetLastError());
+        mark(3);
         k_warp<K_WARP><<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], ctr + 1,
                                                             bins.cap[1], acc);
         TC_CUDA(cudaGetLastError());
+        mark(4);
         k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
                                                         bins.cap[0], acc);
         TC_CUDA(cudaGetLastError());
     }
+    mark(5);
     k_fold<<<(nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, nseg, d_out);
     TC_CUDA(cudaGetLastError());
+    mark(6);
+    if (pe) {
+        unsigned int c[18];
+        TC_CUDA(cudaMemcpyAsync(c, ctr, sizeof c, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        tc_profile_t& P = g_profile;
+        P = tc_profile_t{};
+        float ms[7] = {0};
+        for (int k = 0; k < 6; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
+        TC_CUDA(cudaEventElapsedTime(&ms[6], pe->ev[0], pe->ev[6]));
+        if (rows > 0) {
+            P.ms_tasks = ms[0]; P.ms_split = ms[1]; P.ms_cta = ms[2]; P.ms_warp = ms[3]; P.ms_thread = ms[4];
+        }
+        P.ms_fold = ms[5];
+        P.ms_total = ms[6];
+        P.launches = rows > 0 ? 6 : 1;
+        for (int b = 0; b < 3; ++b) {
+            P.bin_entries[b] = (int64_t)(((unsigned long long)c[10 + 2 * b + 1] << 32) | c[10 + 2 * b]);
+        }
+        P.chunks = c[2];
+        P.bin_tasks[0] = c[0];
+        P.bin_tasks[1] = c[1];
+        P.bin_tasks[2] = (int64_t)(((unsigned long long)c[17] << 32) | c[16]);
+        g_profile_valid = true;
+    }
     if (!(flags & TC_OUT_DEVICE)) {
         int ovf = 0;
         TC_CUDA(cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * (size_t)nseg, cudaMemcpyDeviceToHost, st));
@@ -707,6 +782,13 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
 }  // namespace tc
 
 extern "C" {
+
+tc_status tc_census_profile(tc_profile_t* out) {
+    if (!out) return tc::fail(TC_ERR_ARG, "tc_census_profile: null");
+    if (!tc::g_profile_valid) return tc::fail(TC_ERR_ARG, "tc_census_profile: no profiled census on this thread");
+    *out = tc::g_profile;
+    return TC_OK;
+}
 
 int tc_triad_type(int code) { return (code < 0 || code > 63) ? -1 : tc::triad_type(code); }
 

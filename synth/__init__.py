@@ -158,4 +158,10 @@ def c5() -> Arcs:
     return chung_lu(1 << 22, 2.1, 16.0, 1e5, 0.15, seed=5)
 
 
-WORKLOADS = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "c5": c5}
+def c3s() -> Arcs:
+    """Half-size c3 (R-MAT scale 21): a profiling case whose adjacency and
+    task arrays still exceed the 126 MB L2."""
+    return rmat(21, 4, recip=0.0, orient_down=True, permute=True, seed=3)
+
+
+WORKLOADS = {"c1": c1, "c2": c2, "c3": c3, "c3s": c3s, "c4": c4, "c5": c5}
