@@ -172,6 +172,41 @@ tc_status tc_census(tc_graph g, const tc_opts* opts, tc_census_t* out, uint32_t 
 tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts,
                             tc_census_t* out, uint32_t flags, void* stream);
 
+/*
+ * tc_census_csr_noalloc -- the census of a graph the caller already holds in
+ * device memory, computed WITHOUT ALLOCATING any device memory.  (The thesis
+ * has no counterpart: this entry point exists for callers of this library.)
+ *
+ * Who needs it: callers that may not call cudaMalloc or any allocating
+ * routine -- e.g. a host application whose memory manager owns the whole GPU
+ * (a framework's caching allocator reserved it), a plugin that may only use
+ * buffers handed to it, or a real-time service that forbids allocation after
+ * start-up because an allocation can block and synchronise the device.
+ *
+ *   n        vertices, 0 <= n <= TC_NOALLOC_MAX_N.
+ *   row_ptr  device int64[n+1], adj device uint32[nnz]: the tagged adjacency
+ *            in exactly the layout tc_graph_build produces (see there; it can
+ *            be copied out with tc_graph_export).  No padding is required.
+ *   nnz      row_ptr[n] (= 2 * dyads), with nnz/2 <= TC_NOALLOC_MAX_DYADS.
+ *   out      device tc_census_t, written by the call.
+ *   stream   the work runs on it; the call synchronises it before returning
+ *            (it reads back a capacity check).
+ * Scratch: a fixed area of about 5 MB compiled into the library as a static
+ * device array; every GPU that loads the library holds it until the process
+ * exits.  The first call on a device looks up its device address (set-up);
+ * make that first call before any stream capture.  All calls share the one
+ * area and it keeps the previous call's contents (the call clears what must
+ * start at zero), so calls that overlap on the GPU -- from two streams or two
+ * host threads -- race: serialise them.
+ * Errors: TC_ERR_ARG (null pointers, negative or odd nnz), TC_ERR_UNSUPPORTED
+ * (n or nnz/2 beyond the maxima, or the CSR holds more dyads than nnz/2),
+ * TC_ERR_CUDA.
+ */
+#define TC_NOALLOC_MAX_N 262144
+#define TC_NOALLOC_MAX_DYADS 262144
+tc_status tc_census_csr_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj, int64_t nnz,
+                                tc_census_t* out, void* stream);
+
 /* MAN type index (0..15, order of tc_census_t) of the labelled triad with the
  * given 6-bit code, bit order of Sec. 2.2 Fig. "Triad Code Algorithm":
  * e(u,v)=1, e(v,u)=2, e(u,w)=4, e(w,u)=8, e(v,w)=16, e(w,v)=32 (the thesis's

@@ -36,7 +36,10 @@ TC_OUT_DEVICE = 2
 
 EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
            "tc_graph_export", "tc_census", "tc_census_batched", "tc_triad_type",
-           "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile")
+           "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile",
+           "tc_census_csr_noalloc")
+TC_NOALLOC_MAX_N = 262144
+TC_NOALLOC_MAX_DYADS = 262144
 
 
 class TcCensus(ctypes.Structure):
@@ -107,6 +110,8 @@ def load():
     lib.tc_triad_type.restype = ctypes.c_int
     lib.tc_census_profile.argtypes = [P]
     lib.tc_census_profile.restype = ctypes.c_int
+    lib.tc_census_csr_noalloc.argtypes = [i32, P, P, i64, P, P]
+    lib.tc_census_csr_noalloc.restype = ctypes.c_int
     lib.tc_graph_free.argtypes = [P]
     lib.tc_graph_free.restype = None
     lib.tc_status_str.argtypes = [ctypes.c_int]
@@ -253,6 +258,17 @@ def tc_census_profile() -> dict:
     p = TcProfile()
     _check(load().tc_census_profile(ctypes.byref(p)), "tc_census_profile")
     return p.to_dict()
+
+
+def tc_census_csr_noalloc(n: int, row_ptr, adj, nnz: int, out, stream=None):
+    """Census of a caller-held device CSR (row_ptr int64[n+1], adj 32-bit
+    [nnz] CUDA tensors) into `out` (CUDA int64 tensor of >= 17 words), using
+    only the library's fixed scratch area: no device allocation."""
+    p_adj = adj.data_ptr() if nnz else None
+    st = load().tc_census_csr_noalloc(int(n), row_ptr.data_ptr(), p_adj, int(nnz), out.data_ptr(),
+                                      _stream(stream))
+    _check(st, "tc_census_csr_noalloc")
+    return out
 
 
 def tc_graph_free(g: int) -> None:

@@ -28,6 +28,7 @@
 //  * k_fold maps the 64 codes onto the 16 MAN types and closes 003.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "tc_internal.cuh"
 
@@ -825,3 +826,123 @@ tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free census --
+// tc_census_csr_noalloc: the census of a caller-held device CSR using only a
+// fixed scratch area compiled into the library (see tc.h for who needs it).
+// It runs the same task-build, per-thread merge and fold kernels as
+// tc_census, with every dyad routed to the thread-per-task merge, which reads
+// no word past the end of a neighbour list, so the caller's adjacency needs
+// no padding.
+namespace tc {
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = TC_NOALLOC_MAX_N;
+constexpr int64_t NOALLOC_MAX_DYADS = TC_NOALLOC_MAX_DYADS;
+
+struct NoallocLayout {
+    unsigned long long acc[ACC];  // per-code accumulators + dyadic slots
+    unsigned int ctr[32];         // bin counters, capacity flag, row cursor, bin sums
+    SegDev seg;                   // the single graph
+    int64_t pfx[2];
+    int32_t deg[NOALLOC_MAX_N];
+    uint4 rec[NOALLOC_MAX_DYADS];
+};
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// device object: kernels receive the address looked up below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocLayout)];
+
+std::mutex g_noalloc_mu;
+NoallocLayout* g_noalloc_ptr[64];
+
+// Set-up, once per device with that device current: the device address of
+// the scratch.
+tc_status noalloc_scratch(NoallocLayout** out) {
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: device index >= 64");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
+        g_noalloc_ptr[dev] = (NoallocLayout*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return TC_OK;
+}
+
+// Clears the accumulators and counters left by the previous call and fills
+// the graph descriptor and the degree array.
+__global__ void k_noalloc_init(NoallocLayout* s, const int64_t* __restrict__ row_ptr, int32_t n) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid < ACC) s->acc[tid] = 0;
+    if (tid < 32) s->ctr[tid] = 0;
+    if (tid == 0) {
+        s->seg.rb = 0;
+        s->seg.n = n;
+        s->seg.slot = 0;
+        s->seg.pad = 0;
+        s->pfx[0] = 0;
+        s->pfx[1] = n;
+    }
+    for (int64_t x = tid; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        s->deg[x] = (int32_t)(row_ptr[x + 1] - row_ptr[x]);
+}
+
+tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj, int64_t nnz,
+                         tc_census_t* out, cudaStream_t st) {
+    if (n < 0 || nnz < 0 || (nnz & 1)) return fail(TC_ERR_ARG, "tc_census_csr_noalloc: negative or odd size");
+    if (!row_ptr || !out || (nnz > 0 && !adj)) return fail(TC_ERR_ARG, "tc_census_csr_noalloc: null pointer");
+    if (n > NOALLOC_MAX_N)
+        return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: n exceeds TC_NOALLOC_MAX_N (262144)");
+    if (nnz / 2 > NOALLOC_MAX_DYADS)
+        return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: nnz/2 exceeds TC_NOALLOC_MAX_DYADS (262144)");
+    NoallocLayout* s = nullptr;
+    if (tc_status r = noalloc_scratch(&s); r != TC_OK) return r;
+    Launch L;
+    if (tc_status r = launch_info(L); r != TC_OK) return r;
+    k_noalloc_init<<<std::max(1, (int)std::min<int64_t>((n + 255) / 256, (int64_t)L.sms * 8)), 256, 0, st>>>(
+        s, row_ptr, n);
+    TC_CUDA(cudaGetLastError());
+    Bins bins;
+    bins.rec[0] = bins.rec[1] = bins.rec[2] = s->rec;
+    bins.cap[0] = (uint32_t)NOALLOC_MAX_DYADS;
+    bins.cap[1] = bins.cap[2] = 0;
+    bins.cnt = s->ctr;
+    bins.overflow = (int*)(s->ctr + 4);
+    bins.entries = (unsigned long long*)(s->ctr + 10);
+    bins.tasks2 = (unsigned long long*)(s->ctr + 16);
+    unsigned long long* cursor = (unsigned long long*)(s->ctr + 8);
+    const BinParams bp{0x7fffffff, 0x7fffffff, 0x40000000};
+    if (n > 0) {
+        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
+                                                     s->acc, cursor);
+        TC_CUDA(cudaGetLastError());
+        k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(row_ptr, adj, &s->seg, s->rec, s->ctr + 0,
+                                                        bins.cap[0], s->acc);
+        TC_CUDA(cudaGetLastError());
+    }
+    k_fold<<<1, 128, 0, st>>>(s->acc, &s->seg, 1, out);
+    TC_CUDA(cudaGetLastError());
+    int ovf = 0;
+    TC_CUDA(cudaMemcpyAsync(&ovf, s->ctr + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (ovf)
+        return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: the CSR holds more dyads than nnz/2 says "
+                                        "(scratch capacity exceeded; result invalid)");
+    return TC_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" tc_status tc_census_csr_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj, int64_t nnz,
+                                           tc_census_t* out, void* stream) {
+    try {
+        return tc::census_noalloc(n, row_ptr, adj, nnz, out, (cudaStream_t)stream);
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_census_csr_noalloc: unexpected exception");
+    }
+}
