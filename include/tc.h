@@ -74,12 +74,16 @@ enum { TC_BIN_HEURISTIC = 0, TC_BIN_MLP = 1 };
 typedef struct {
     int32_t bin_mode;     /* TC_BIN_HEURISTIC (degree sum) or TC_BIN_MLP */
     int32_t thr_thread;   /* tasks with |N(u)|+|N(v)| <= thr_thread: one thread each */
-    int32_t thr_warp;     /* <= thr_warp: one warp each; larger: CTA chunks */
-    int32_t chunk;        /* merge length of one CTA chunk (splits hub tasks) */
+    int32_t thr_warp;     /* <= thr_warp (capped at 1024): one warp each;
+                             larger tasks are split into tiles */
+    int32_t chunk;        /* merge outputs per tile of a split task: 256..1024
+                             for warp tiles, 256..3840 for CTA tiles */
     int32_t profile;      /* 1: time each kernel with CUDA events and keep the
                              task/bin counts (read with tc_census_profile);
                              the call then synchronises `stream` */
-    int32_t reserved[3];  /* must be zero */
+    int32_t split_cta;    /* 0: tiles of split tasks run one per warp;
+                             1: one per 256-thread CTA */
+    int32_t reserved[2];  /* must be zero */
 } tc_opts;
 
 /* Per-kernel timing and binning of the calling thread's most recent
@@ -87,15 +91,15 @@ typedef struct {
 typedef struct {
     float ms_tasks;          /* task build + suffix-count terms (k_tasks) */
     float ms_split;          /* chunk start partitions (k_split) */
-    float ms_cta;            /* CTA-chunk merges (k_cta) */
-    float ms_warp;           /* warp-per-task merges (k_warp) */
+    float ms_tiles;          /* tiles of split tasks (k_warp or k_cta) */
+    float ms_warp;           /* whole tasks, one warp each (k_warp) */
     float ms_thread;         /* thread-per-task merges (k_thread) */
     float ms_fold;           /* 64->16 fold and 003 closure (k_fold) */
     float ms_total;          /* first to last kernel */
     int32_t launches;        /* kernels launched by the call */
-    int64_t bin_tasks[3];    /* dyads per bin: thread, warp, CTA */
+    int64_t bin_tasks[3];    /* dyads per bin: thread, warp, split into tiles */
     int64_t bin_entries[3];  /* merged entries |N(u)|+|N(v)| per bin */
-    int64_t chunks;          /* CTA chunk records */
+    int64_t chunks;          /* tile records of split tasks */
 } tc_profile_t;
 
 tc_status tc_census_profile(tc_profile_t* out);

@@ -62,12 +62,13 @@ class TcStats(ctypes.Structure):
 class TcOpts(ctypes.Structure):
     _fields_ = [("bin_mode", ctypes.c_int32), ("thr_thread", ctypes.c_int32),
                 ("thr_warp", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("profile", ctypes.c_int32), ("split_cta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class TcProfile(ctypes.Structure):
     _fields_ = [("ms_tasks", ctypes.c_float), ("ms_split", ctypes.c_float),
-                ("ms_cta", ctypes.c_float), ("ms_warp", ctypes.c_float),
+                ("ms_tiles", ctypes.c_float), ("ms_warp", ctypes.c_float),
                 ("ms_thread", ctypes.c_float), ("ms_fold", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int32),
                 ("bin_tasks", ctypes.c_int64 * 3), ("bin_entries", ctypes.c_int64 * 3),

@@ -95,8 +95,8 @@ tc_status tc_opts_default(tc_opts* o) {
     *o = tc_opts{};
     o->bin_mode = TC_BIN_HEURISTIC;
     o->thr_thread = 48;
-    o->thr_warp = 4096;
-    o->chunk = 7680;
+    o->thr_warp = 1024;
+    o->chunk = 1024;
     return TC_OK;
 }
 

@@ -405,108 +405,133 @@ __global__ void __launch_bounds__(256) k_thread(const int64_t* __restrict__ row_
     flush_hist<WARPS>(hs, acc, tag, lane);
 }
 
-// ------------------------------------------------------- tile merge (a3) --
-// NT cooperating threads stream the merge path of A and B in tiles of
-// T = NT*K outputs.  Each tile copies windows A[i0 .. i0+T] and B[j0 .. j0+T]
-// into shared memory with 16-byte loads (entries past a list's end read as
-// the sentinel), each thread finds its start on the merge path by binary
-// search at diagonal tid*K, then takes K steps of the two-pointer merge,
-// reporting every shared element to on_shared.
-template <int NT, int W>
-__device__ __forceinline__ int load_window(uint32_t* __restrict__ s_raw, const uint32_t* __restrict__ adj,
-                                           int64_t p, int64_t end, int tid) {
+// ------------------------------------------------------- merge spans (a3) --
+// A span of a neighbour list is copied to shared memory with 16-byte loads
+// from the 16-byte boundary at or below its start; the returned offset is
+// where the span begins in `raw`.  Words at absolute positions >= lim are
+// stored as the sentinel.  `count` words after the start are guaranteed.
+template <int NT>
+__device__ __forceinline__ int load_span(uint32_t* __restrict__ raw, const uint32_t* __restrict__ adj,
+                                         int64_t p, int count, int64_t lim, int tid) {
     const int64_t q = p & ~(int64_t)3;
+    const int o = (int)(p - q);
+    const int nq = (o + count + 3) >> 2;
     const uint4* src = reinterpret_cast<const uint4*>(adj + q);
-    uint4* dst = reinterpret_cast<uint4*>(s_raw);
-    constexpr int NQ = W / 4;
-    if (q + W <= end) {
-        for (int m = tid; m < NQ; m += NT) dst[m] = __ldg(src + m);
-    } else {
-        for (int m = tid; m < NQ; m += NT) {
-            uint4 x = __ldg(src + m);
-            const int64_t a = q + 4 * (int64_t)m;
-            x.x = a < end ? x.x : SENT;
-            x.y = a + 1 < end ? x.y : SENT;
-            x.z = a + 2 < end ? x.z : SENT;
-            x.w = a + 3 < end ? x.w : SENT;
-            dst[m] = x;
+    uint4* dst = reinterpret_cast<uint4*>(raw);
+    for (int m = tid; m < nq; m += NT) {
+        uint4 x = __ldg(src + m);
+        const int64_t a = q + 4 * (int64_t)m;
+        if (a + 3 >= lim) {
+            x.x = a < lim ? x.x : SENT;
+            x.y = a + 1 < lim ? x.y : SENT;
+            x.z = a + 2 < lim ? x.z : SENT;
+            x.w = a + 3 < lim ? x.w : SENT;
         }
+        dst[m] = x;
     }
-    return (int)(p - q);
+    return o;
 }
 
-__device__ __forceinline__ int mp_search(const uint32_t* sA, const uint32_t* sB, int d) {
-    int lo = 0, hi = d;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((sA[mid] | 3u) <= (sB[d - 1 - mid] | 3u)) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
+__device__ __forceinline__ int ceil_log2(int x) {  // smallest k with 2^k >= x (x >= 1)
+    return 32 - __clz(max(x, 1) - 1);
 }
 
-template <int NT, int K, bool CTA>
-__device__ __forceinline__ uint32_t merge_range(const uint32_t* __restrict__ adj, int64_t a_beg, int64_t a_end,
-                                                int64_t b_beg, int64_t b_end, int64_t i0, int64_t j0,
-                                                int64_t count, uint32_t ul, uint32_t vl, uint32_t pre,
-                                                uint32_t* sA_raw, uint32_t* sB_raw, int* bc,
-                                                unsigned long long* h, int tid) {
-    constexpr int T = NT * K;
-    constexpr int W = T + 4;
+// Shared elements of A[0..na) and B[0..nb) (sorted spans in shared memory),
+// found by one of two exact strategies over the same data:
+//  * search: every element of the shorter span is located in the longer one
+//    by binary search (cheap when one span is much shorter: hub vs leaf);
+//  * merge: the merge path of the two spans is cut at equal diagonals, one
+//    cut per thread (binary search), and each thread takes its steps of the
+//    two-pointer merge; an element of A taken while the equal element of B
+//    is at the B head is a shared element (ties are taken from A first).
+// A[na] must be the sentinel and B[nb] must be the element that follows the
+// span in B (or the sentinel): the merge then also reports the pair
+// (A[na-1], B[nb]) -- an element shared across the span boundary -- and the
+// search strategy checks that pair explicitly when `boundary` is set.
+template <int NT>
+__device__ __forceinline__ uint32_t shared_elements(const uint32_t* sA, int na, const uint32_t* sB, int nb,
+                                                    bool boundary, uint32_t ul, uint32_t vl, uint32_t pre,
+                                                    unsigned long long* h, int tid) {
     uint32_t c = 0;
-    for (int64_t d0 = 0; d0 < count; d0 += T) {
-        const int rem = (int)min((int64_t)T, count - d0);
-        const int oA = load_window<NT, W>(sA_raw, adj, a_beg + i0, a_end, tid);
-        const int oB = load_window<NT, W>(sB_raw, adj, b_beg + j0, b_end, tid);
-        if (CTA) __syncthreads(); else __syncwarp();
-        const uint32_t* sA = sA_raw + oA;
-        const uint32_t* sB = sB_raw + oB;
-        const int dl = min(tid * K, rem);
-        int ia = mp_search(sA, sB, dl);
-        int ib = dl - ia;
-        const int steps = min(K, rem - dl);
-        uint32_t eA = sA[ia], eB = sB[ib];
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            if (s < steps) {
-                const uint32_t kA = eA | 3u, kB = eB | 3u;
-                const bool takeA = kA <= kB;
-                if (kA == kB) {
+    const int tot = na + nb;
+    const int ns = min(na, nb), nl = max(na, nb);
+    if (ns == 0 && !boundary) return 0;
+    if ((int64_t)ns * (ceil_log2(nl + 1) + 1) <= (int64_t)tot + (tot >> 1)) {
+        const bool small_is_A = na <= nb;
+        const uint32_t* sm = small_is_A ? sA : sB;
+        const uint32_t* lg = small_is_A ? sB : sA;
+        for (int k = tid; k < ns; k += NT) {
+            const uint32_t x = sm[k];
+            const uint32_t key = x | 3u;
+            int lo = 0, hi = nl;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((lg[mid] | 3u) < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < nl) {
+                const uint32_t y = lg[lo];
+                if ((y | 3u) == key) {
                     ++c;
-                    on_shared(h, kA >> 2, ul, vl, pre, eA & 3u, eB & 3u);
+                    on_shared(h, key >> 2, ul, vl, pre, small_is_A ? (x & 3u) : (y & 3u),
+                              small_is_A ? (y & 3u) : (x & 3u));
                 }
-                ia += takeA;
-                ib += !takeA;
-                const uint32_t nx = takeA ? sA[ia] : sB[ib];
-                eA = takeA ? nx : eA;
-                eB = takeA ? eB : nx;
             }
         }
-        if (CTA) {
-            __syncthreads();
-            if (tid == NT - 1) { bc[0] = ia; bc[1] = ib; }
-            __syncthreads();
-            i0 += bc[0];
-            j0 += bc[1];
-        } else {
-            i0 += __shfl_sync(0xffffffffu, ia, 31);
-            j0 += __shfl_sync(0xffffffffu, ib, 31);
-            __syncwarp();
+        if (boundary && tid == 0 && na > 0) {
+            const uint32_t x = sA[na - 1], y = sB[nb];
+            if ((x | 3u) == (y | 3u)) {
+                ++c;
+                on_shared(h, x >> 2, ul, vl, pre, x & 3u, y & 3u);
+            }
+        }
+    } else {
+        const int K = (tot + NT - 1) / NT;
+        const int dl = min(tid * K, tot);
+        const int steps = min(K, tot - dl);
+        int lo = max(0, dl - nb), hi = min(dl, na);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((sA[mid] | 3u) <= (sB[dl - 1 - mid] | 3u)) lo = mid + 1;
+            else hi = mid;
+        }
+        int ia = lo, ib = dl - lo;
+        uint32_t eA = sA[ia], eB = sB[ib];
+        for (int s = 0; s < steps; ++s) {
+            const uint32_t kA = eA | 3u, kB = eB | 3u;
+            const bool takeA = kA <= kB;
+            if (kA == kB) {
+                ++c;
+                on_shared(h, kA >> 2, ul, vl, pre, eA & 3u, eB & 3u);
+            }
+            ia += takeA;
+            ib += !takeA;
+            const uint32_t nx = takeA ? sA[ia] : sB[ib];
+            eA = takeA ? nx : eA;
+            eB = takeA ? eB : nx;
         }
     }
     return c;
 }
 
 // --------------------------------------------------------------- k_warp --
-template <int K>
+// One warp per record.  Without ia_start a record is a whole task with
+// |A|+|B| <= WARP_LMAX: both lists, each followed by a sentinel, are copied
+// into the warp's shared memory.  With ia_start a record is one tile of at
+// most `tile` merge outputs of a larger task: it starts where k_split put it
+// on the merge path and ends where the task's next tile starts (or at the end
+// of both lists), so exactly the spans A[is..ie) and B[js..je) are loaded,
+// plus B[je] for the pair that straddles the tile boundary.
+constexpr int WARP_LMAX = 1024;
+
 __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_ptr,
                                               const uint32_t* __restrict__ adj,
                                               const SegDev* __restrict__ seg,
                                               const uint4* __restrict__ rec,
+                                              const int32_t* __restrict__ ia_start,
                                               const unsigned int* __restrict__ cnt, uint32_t cap,
-                                              unsigned long long* __restrict__ acc) {
-    constexpr int W = 32 * K + 4;
-    __shared__ __align__(16) uint32_t sbuf[WARPS][2][W];
+                                              int tile, unsigned long long* __restrict__ acc) {
+    __shared__ __align__(16) uint32_t sbuf[WARPS][WARP_LMAX + 16];
     __shared__ unsigned long long hs_all[WARPS][ACC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* hs = hs_all[warp];
@@ -526,31 +551,50 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
         const int64_t rb = seg[s].rb;
         const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
         const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
-        uint32_t c = merge_range<32, K, false>(adj, ab, ae, bb, be, 0, 0, (ae - ab) + (be - bb),
-                                               (uint32_t)(r.x - rb), (uint32_t)(r.y - rb), pre,
-                                               sbuf[warp][0], sbuf[warp][1], nullptr, hs, lane);
+        int64_t is = 0, ie = ae - ab, js = 0, je = be - bb;
+        if (ia_start) {
+            const int64_t L = ie + je, d0 = r.w, d1 = min(d0 + (int64_t)tile, L);
+            is = ia_start[i];
+            ie = d1 == L ? ie : (int64_t)ia_start[min(i + 1, ntask - 1)];
+            js = d0 - is;
+            je = d1 - ie;
+        }
+        const int na = (int)(ie - is), nb = (int)(je - js);
+        uint32_t* raw = sbuf[warp];
+        const int oA = load_span<32>(raw, adj, ab + is, na + 1, ab + ie, lane);
+        uint32_t* rawB = raw + ((oA + na + 1 + 3) & ~3);
+        const int oB = load_span<32>(rawB, adj, bb + js, nb + 1, min(bb + je + 1, be), lane);
+        __syncwarp();
+        uint32_t c = shared_elements<32>(raw + oA, na, rawB + oB, nb, ia_start != nullptr,
+                                         (uint32_t)(r.x - rb), (uint32_t)(r.y - rb), pre, hs, lane);
         c = __reduce_add_sync(0xffffffffu, c);
         if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+        __syncwarp();
     }
     __syncwarp();
     flush_hist<WARPS>(hs, acc, tag, lane);
 }
 
 // ---------------------------------------------------------------- k_cta --
-template <int NT, int K>
-__global__ void __launch_bounds__(NT) k_cta(const int64_t* __restrict__ row_ptr,
-                                            const uint32_t* __restrict__ adj,
-                                            const SegDev* __restrict__ seg,
-                                            const uint4* __restrict__ rec,
-                                            const int32_t* __restrict__ ia_start,
-                                            const unsigned int* __restrict__ cnt, uint32_t cap,
-                                            int chunk, unsigned long long* __restrict__ acc) {
-    constexpr int W = NT * K + 4;
-    __shared__ __align__(16) uint32_t sbuf[2][W];
+// One CTA per tile of at most TILE merge outputs of a large task.  The tile
+// starts where k_split put it on the merge path and ends where the task's
+// next tile starts (or at the end of both lists), so exactly the tile's spans
+// A[is..ie) and B[js..je) are loaded, plus B[je] for the boundary pair.
+constexpr int CTA_NT = 256;
+constexpr int TILE = 3840;
+
+__global__ void __launch_bounds__(CTA_NT) k_cta(const int64_t* __restrict__ row_ptr,
+                                                const uint32_t* __restrict__ adj,
+                                                const SegDev* __restrict__ seg,
+                                                const uint4* __restrict__ rec,
+                                                const int32_t* __restrict__ ia_start,
+                                                const unsigned int* __restrict__ cnt, uint32_t cap,
+                                                int tile, unsigned long long* __restrict__ acc) {
+    __shared__ __align__(16) uint32_t rawA[TILE + 8];
+    __shared__ __align__(16) uint32_t rawB[TILE + 8];
     __shared__ unsigned long long hs[ACC];
-    __shared__ int bc[2];
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int j = tid; j < ACC; j += NT) hs[j] = 0;
+    for (int j = tid; j < ACC; j += CTA_NT) hs[j] = 0;
     __syncthreads();
     int tag = -1;
     const unsigned n2 = min(*cnt, cap);
@@ -558,8 +602,8 @@ __global__ void __launch_bounds__(NT) k_cta(const int64_t* __restrict__ row_ptr,
         const uint4 r = rec[i];
         const int s = (int)(r.z >> 2);
         const uint32_t pre = r.z & 3u;
+        __syncthreads();  // the previous tile's shared-memory reads are done
         if (s != tag) {
-            __syncthreads();
             if (tid < 32) flush_hist<1>(hs, acc, tag, lane);
             __syncthreads();
             tag = s;
@@ -567,13 +611,17 @@ __global__ void __launch_bounds__(NT) k_cta(const int64_t* __restrict__ row_ptr,
         const int64_t rb = seg[s].rb;
         const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
         const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
-        const int64_t L = (ae - ab) + (be - bb);
-        const int64_t d0 = r.w;
-        const int64_t ia = ia_start[i];
-        const int64_t count = min((int64_t)chunk, L - d0);
-        uint32_t c = merge_range<NT, K, true>(adj, ab, ae, bb, be, ia, d0 - ia, count,
-                                              (uint32_t)(r.x - rb), (uint32_t)(r.y - rb), pre,
-                                              sbuf[0], sbuf[1], bc, hs, tid);
+        const int64_t a = ae - ab, L = a + (be - bb);
+        const int64_t d0 = r.w, d1 = min(d0 + (int64_t)tile, L);
+        const int64_t is = ia_start[i];
+        const int64_t ie = d1 == L ? a : (int64_t)ia_start[min(i + 1, n2 - 1)];
+        const int64_t js = d0 - is, je = d1 - ie;
+        const int na = (int)(ie - is), nb = (int)(je - js);
+        const int oA = load_span<CTA_NT>(rawA, adj, ab + is, na + 1, ab + ie, tid);
+        const int oB = load_span<CTA_NT>(rawB, adj, bb + js, nb + 1, min(bb + je + 1, be), tid);
+        __syncthreads();
+        uint32_t c = shared_elements<CTA_NT>(rawA + oA, na, rawB + oB, nb, true, (uint32_t)(r.x - rb),
+                                             (uint32_t)(r.y - rb), pre, hs, tid);
         c = __reduce_add_sync(0xffffffffu, c);
         if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
     }
@@ -605,9 +653,6 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 }
 
 // ------------------------------------------------------------- host side --
-constexpr int K_WARP = 7;
-constexpr int CTA_NT = 256;
-constexpr int K_CTA = 15;
 
 struct Launch {
     int sms = 148;
@@ -624,8 +669,8 @@ tc_status launch_info(Launch& L) {
         TC_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks, k_tasks, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_thread, k_thread, 256, 0));
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_warp, k_warp<K_WARP>, 256, 0));
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_cta, k_cta<CTA_NT, K_CTA>, CTA_NT, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_warp, k_warp, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_cta, k_cta, CTA_NT, 0));
         c.occ_tasks = std::max(1, c.occ_tasks);
         c.occ_thread = std::max(1, c.occ_thread);
         c.occ_warp = std::max(1, c.occ_warp);
@@ -646,8 +691,12 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
     if (opts_in) o = *opts_in;
     if (o.bin_mode != TC_BIN_HEURISTIC && o.bin_mode != TC_BIN_MLP)
         return fail(TC_ERR_ARG, "census: unknown bin_mode");
-    if (o.thr_thread < 0 || o.thr_warp < o.thr_thread || o.chunk < 256)
-        return fail(TC_ERR_ARG, "census: need 0 <= thr_thread <= thr_warp and chunk >= 256");
+    if (o.thr_thread < 0 || o.thr_warp < o.thr_thread || o.chunk < 256 ||
+        o.chunk > (o.split_cta ? TILE : WARP_LMAX))
+        return fail(TC_ERR_ARG, "census: need 0 <= thr_thread <= thr_warp and 256 <= chunk <= "
+                                "1024 (warp tiles) or 3840 (split_cta = 1)");
+    // a warp holds both lists in shared memory: larger tasks go to CTA tiles
+    o.thr_warp = std::min(o.thr_warp, WARP_LMAX);
     const int nseg = (int)gidx.size();
     std::vector<SegDev> segs((size_t)nseg);
     std::vector<int64_t> pfx((size_t)nseg + 1, 0);
@@ -729,12 +778,16 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         k_split<<<L.sms * 4, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], d_ia);
         TC_CUDA(cudaGetLastError());
         mark(2);
-        k_cta<CTA_NT, K_CTA><<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[2], d_ia,
-                                                                   ctr + 2, bins.cap[2], o.chunk, acc);
+        if (o.split_cta)
+            k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[2], d_ia, ctr + 2,
+                                                        bins.cap[2], o.chunk, acc);
+        else
+            k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[2], d_ia, ctr + 2,
+                                                        bins.cap[2], o.chunk, acc);
         TC_CUDA(cudaGetLastError());
         mark(3);
-        k_warp<K_WARP><<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], ctr + 1,
-                                                            bins.cap[1], acc);
+        k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], nullptr, ctr + 1,
+                                                            bins.cap[1], 0, acc);
         TC_CUDA(cudaGetLastError());
         mark(4);
         k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
@@ -755,7 +808,7 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         for (int k = 0; k < 6; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
         TC_CUDA(cudaEventElapsedTime(&ms[6], pe->ev[0], pe->ev[6]));
         if (rows > 0) {
-            P.ms_tasks = ms[0]; P.ms_split = ms[1]; P.ms_cta = ms[2]; P.ms_warp = ms[3]; P.ms_thread = ms[4];
+            P.ms_tasks = ms[0]; P.ms_split = ms[1]; P.ms_tiles = ms[2]; P.ms_warp = ms[3]; P.ms_thread = ms[4];
         }
         P.ms_fold = ms[5];
         P.ms_total = ms[6];

@@ -22,7 +22,9 @@ BINS = {
     "default": {},
     "thread": dict(thr_thread=BIG, thr_warp=BIG),
     "warp": dict(thr_thread=0, thr_warp=BIG),
-    "cta": dict(thr_thread=0, thr_warp=0, chunk=256),
+    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1),
+    "wtile": dict(thr_thread=0, thr_warp=0, chunk=256),
+    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1),
     "mixed": dict(thr_thread=8, thr_warp=40, chunk=512),
 }
 
