@@ -297,9 +297,9 @@ def run_native(args, world, rank, local, pg):
 
     # dominant kernel and its roofline (algorithmic bytes = 4 B per merged entry)
     kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_warp[tiles]": "ms_tiles",
-            "k_warp": "ms_warp", "k_thread": "ms_thread", "k_fold": "ms_fold"}
+            "k_stream": "ms_stream", "k_warp": "ms_warp", "k_thread": "ms_thread", "k_fold": "ms_fold"}
     avg = {k: float(np.mean([p[f] for p in profs])) for k, f in kern.items()}
-    merge_bin = {"k_warp[tiles]": 2, "k_warp": 1, "k_thread": 0}
+    merge_bin = {"k_warp[tiles]": 2, "k_stream": 3, "k_warp": 1, "k_thread": 0}
     top = max(merge_bin, key=lambda k: avg[k])
     entries_top = profs[-1]["bin_entries"][merge_bin[top]]
     peak, peak_kind = peaks()
@@ -309,7 +309,7 @@ def run_native(args, world, rank, local, pg):
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": 4 * entries_top,
                 "ms_per_launch": avg[top]}
-    merge_ms = avg["k_warp[tiles]"] + avg["k_warp"] + avg["k_thread"]
+    merge_ms = sum(avg[k] for k in merge_bin)
 
     # end to end through the public API from pinned host memory
     e2e_steps = max(3, min(args.steps, 5))

@@ -83,7 +83,10 @@ typedef struct {
                              the call then synchronises `stream` */
     int32_t split_cta;    /* 0: tiles of split tasks run one per warp;
                              1: one per 256-thread CTA */
-    int32_t reserved[2];  /* must be zero */
+    int32_t stream_max;   /* tasks above thr_warp whose shorter list has at most
+                             stream_max (capped at 1024) entries are streamed by
+                             one warp; the others are split into tiles */
+    int32_t reserved[1];  /* must be zero */
 } tc_opts;
 
 /* Per-kernel timing and binning of the calling thread's most recent
@@ -92,13 +95,14 @@ typedef struct {
     float ms_tasks;          /* task build + suffix-count terms (k_tasks) */
     float ms_split;          /* chunk start partitions (k_split) */
     float ms_tiles;          /* tiles of split tasks (k_warp or k_cta) */
+    float ms_stream;         /* streamed tasks (k_stream) */
     float ms_warp;           /* whole tasks, one warp each (k_warp) */
     float ms_thread;         /* thread-per-task merges (k_thread) */
     float ms_fold;           /* 64->16 fold and 003 closure (k_fold) */
     float ms_total;          /* first to last kernel */
     int32_t launches;        /* kernels launched by the call */
-    int64_t bin_tasks[3];    /* dyads per bin: thread, warp, split into tiles */
-    int64_t bin_entries[3];  /* merged entries |N(u)|+|N(v)| per bin */
+    int64_t bin_tasks[4];    /* dyads per bin: thread, warp, split into tiles, streamed */
+    int64_t bin_entries[4];  /* merged entries |N(u)|+|N(v)| per bin */
     int64_t chunks;          /* tile records of split tasks */
 } tc_profile_t;
 

@@ -63,15 +63,16 @@ class TcOpts(ctypes.Structure):
     _fields_ = [("bin_mode", ctypes.c_int32), ("thr_thread", ctypes.c_int32),
                 ("thr_warp", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("split_cta", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("stream_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class TcProfile(ctypes.Structure):
     _fields_ = [("ms_tasks", ctypes.c_float), ("ms_split", ctypes.c_float),
-                ("ms_tiles", ctypes.c_float), ("ms_warp", ctypes.c_float),
+                ("ms_tiles", ctypes.c_float), ("ms_stream", ctypes.c_float),
+                ("ms_warp", ctypes.c_float),
                 ("ms_thread", ctypes.c_float), ("ms_fold", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int32),
-                ("bin_tasks", ctypes.c_int64 * 3), ("bin_entries", ctypes.c_int64 * 3),
+                ("bin_tasks", ctypes.c_int64 * 4), ("bin_entries", ctypes.c_int64 * 4),
                 ("chunks", ctypes.c_int64)]
 
     def to_dict(self) -> dict:

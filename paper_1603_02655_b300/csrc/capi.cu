@@ -97,6 +97,7 @@ tc_status tc_opts_default(tc_opts* o) {
     o->thr_thread = 48;
     o->thr_warp = 1024;
     o->chunk = 1024;
+    o->stream_max = 1024;
     return TC_OK;
 }
 

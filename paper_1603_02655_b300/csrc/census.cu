@@ -41,7 +41,7 @@ thread_local tc_profile_t g_profile;
 thread_local bool g_profile_valid = false;
 
 struct ProfileEvents {
-    cudaEvent_t ev[7];
+    cudaEvent_t ev[8];
 };
 
 tc_status profile_events(ProfileEvents** out) {
@@ -51,7 +51,7 @@ tc_status profile_events(ProfileEvents** out) {
     TC_CUDA(cudaGetDevice(&dev));
     dev &= 63;
     if (!made[dev]) {
-        for (int k = 0; k < 7; ++k) TC_CUDA(cudaEventCreate(&pe[dev].ev[k]));
+        for (int k = 0; k < 8; ++k) TC_CUDA(cudaEventCreate(&pe[dev].ev[k]));
         made[dev] = true;
     }
     *out = &pe[dev];
@@ -97,17 +97,20 @@ struct SegDev {
     int32_t pad;
 };
 
+// Task bins: 0 thread per task, 1 warp per task, 2 split into tiles,
+// 3 stream (warp per task, short list staged, long list streamed).
+constexpr int NBIN = 4;
+
 struct Bins {
-    uint4* rec[3];        // {u global, v global, seg<<2 | pre, d_begin}
-    uint32_t cap[3];
-    unsigned int* cnt;    // [3] records appended per bin
+    uint4* rec[NBIN];     // {u global, v global, seg<<2 | pre, 0}
+    uint32_t cap[NBIN];
+    unsigned int* cnt;    // [NBIN] records appended per bin
     int* overflow;
-    unsigned long long* entries;  // [3] merged entries per bin
-    unsigned long long* tasks2;   // dyads routed to CTA chunks
+    unsigned long long* entries;  // [NBIN] merged entries per bin
 };
 
 struct BinParams {
-    int thr_thread, thr_warp, chunk;
+    int thr_thread, thr_warp, stream_max;
 };
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
@@ -146,14 +149,14 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
     constexpr int ROWS = 32;
     int s = -1;
     int64_t rb = 0, n = 0, sp = 0;
-    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[3];
+    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int q = 0; q < 3; ++q) Aa[p][q] = Bb[p][q] = 0;
     Dd[0] = Dd[1] = 0;
-    Ee[0] = Ee[1] = Ee[2] = 0;
-    unsigned long long T2 = 0;
+#pragma unroll
+    for (int b = 0; b < NBIN; ++b) Ee[b] = 0;
 
     auto flush = [&]() {
 #pragma unroll
@@ -233,15 +236,16 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                     const unsigned long long dy = (unsigned long long)(n - (int64_t)d - (int64_t)dv);
                     Dd[0] += pre_task == 3 ? 0ull : dy;
                     Dd[1] += pre_task == 3 ? dy : 0ull;
-                    bin = L <= bp.thr_thread ? 0 : (L <= bp.thr_warp ? 1 : 2);
+                    bin = L <= bp.thr_thread ? 0
+                          : L <= bp.thr_warp ? 1
+                          : min(d, dv) <= bp.stream_max ? 3 : 2;
                 }
 #pragma unroll
-                for (int b = 0; b < 3; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
-                T2 += bin == 2 ? 1ull : 0ull;
+                for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
                 const uint4 rec = make_uint4((uint32_t)x, (uint32_t)(rb + y),
                                              ((uint32_t)s << 2) | (uint32_t)pre_task, 0u);
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
+                for (int b = 0; b < NBIN; ++b) {
                     const bool mine = bin == b;
                     const unsigned mask = __ballot_sync(full, mine);
                     if (mask) {
@@ -256,65 +260,88 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                         }
                     }
                 }
-                // CTA chunks: ceil(L / chunk) records per task
-                {
-                    const unsigned nch = bin == 2 ? (unsigned)((L + bp.chunk - 1) / bp.chunk) : 0u;
-                    unsigned incl = nch;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const unsigned v = __shfl_up_sync(full, incl, o);
-                        if (lane >= o) incl += v;
-                    }
-                    const unsigned total = __shfl_sync(full, incl, 31);
-                    if (total) {
-                        unsigned int at = 0;
-                        if (lane == 0) at = atomicAdd(bins.cnt + 2, total);
-                        at = __shfl_sync(full, at, 0);
-                        const unsigned first = at + incl - nch;
-                        for (unsigned c = 0; c < nch; ++c) {
-                            uint4 rc = rec;
-                            rc.w = c * (unsigned)bp.chunk;
-                            if (first + c < bins.cap[2]) bins.rec[2][first + c] = rc;
-                            else atomicOr(bins.overflow, 1);
-                        }
-                    }
-                }
             }
         }
     }
     flush();
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b < NBIN; ++b) {
         const unsigned long long e = warp_sum64(Ee[b]);
         if (lane == 0 && e) atomicAdd(bins.entries + b, e);
     }
-    T2 = warp_sum64(T2);
-    if (lane == 0 && T2) atomicAdd(bins.tasks2, T2);
 }
 
 // --------------------------------------------------------------- k_split --
-// Start of each CTA chunk on its dyad's merge path: the number of A entries
-// among the first d_begin outputs (ties taken from A first).
-__global__ void k_split(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
-                        const uint4* __restrict__ rec, const unsigned int* __restrict__ cnt,
-                        uint32_t cap, int32_t* __restrict__ ia_out) {
-    const unsigned n2 = min(*cnt, cap);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
-        const uint4 r = rec[i];
-        const int64_t d = r.w;
-        int64_t lo = 0;
-        if (d > 0) {
-            const int64_t ab = row_ptr[r.x], a = row_ptr[r.x + 1] - ab;
-            const int64_t bb = row_ptr[r.y], b = row_ptr[r.y + 1] - bb;
-            lo = max((int64_t)0, d - b);
-            int64_t hi = min(d, a);
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if ((__ldg(adj + ab + mid) | 3u) <= (__ldg(adj + bb + d - 1 - mid) | 3u)) lo = mid + 1;
-                else hi = mid;
+// Tasks of the split bin, 32 per warp: cut each task's merge of A and B into
+// tiles of `tile` outputs, reserve consecutive tile records, and find each
+// tile's start on the merge path -- the number of A entries among the first d
+// outputs, ties taken from A first -- by binary search.  The tiles of the 32
+// tasks are spread over the lanes so that 32 searches are in flight.
+__global__ void __launch_bounds__(256) k_split(const int64_t* __restrict__ row_ptr,
+                                               const uint32_t* __restrict__ adj,
+                                               const uint4* __restrict__ task,
+                                               const unsigned int* __restrict__ ntask_p, uint32_t task_cap,
+                                               int tile, uint4* __restrict__ tiles,
+                                               int32_t* __restrict__ ia_out,
+                                               unsigned int* __restrict__ ntile_p, uint32_t tile_cap,
+                                               int* __restrict__ overflow) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned nt = min(*ntask_p, task_cap);
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned w0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32u; w0 < nt; w0 += warps * 32u) {
+        const unsigned i = w0 + lane;
+        const bool has = i < nt;
+        const uint4 r = has ? task[i] : make_uint4(0, 0, 0, 0);
+        int64_t ab = 0, a = 0, bb = 0, b = 0;
+        if (has) {
+            ab = row_ptr[r.x];
+            a = row_ptr[r.x + 1] - ab;
+            bb = row_ptr[r.y];
+            b = row_ptr[r.y + 1] - bb;
+        }
+        const unsigned ntl = has ? (unsigned)((a + b + tile - 1) / tile) : 0u;
+        unsigned incl = ntl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned total = __shfl_sync(full, incl, 31);
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(ntile_p, total);
+        base = __shfl_sync(full, base, 0);
+        for (unsigned k0 = 0; k0 < total; k0 += 32) {
+            const unsigned k = k0 + lane;
+            // owner lane: the first lane whose inclusive tile count exceeds k
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const unsigned v = __shfl_sync(full, incl, lo + step - 1);
+                if (v <= k) lo += step;
+            }
+            const int own = min(lo, 31);
+            const unsigned first = __shfl_sync(full, incl - ntl, own);
+            const uint32_t ox = __shfl_sync(full, r.x, own), oy = __shfl_sync(full, r.y, own);
+            const uint32_t oz = __shfl_sync(full, r.z, own);
+            const int64_t oab = __shfl_sync(full, ab, own), oa = __shfl_sync(full, a, own);
+            const int64_t obb = __shfl_sync(full, bb, own), ob = __shfl_sync(full, b, own);
+            if (k < total) {
+                const int64_t d = (int64_t)(k - first) * tile;
+                int64_t l2 = max((int64_t)0, d - ob), hi = min(d, oa);
+                while (l2 < hi) {
+                    const int64_t mid = (l2 + hi) >> 1;
+                    if ((__ldg(adj + oab + mid) | 3u) <= (__ldg(adj + obb + d - 1 - mid) | 3u)) l2 = mid + 1;
+                    else hi = mid;
+                }
+                if (base + k < tile_cap) {
+                    tiles[base + k] = make_uint4(ox, oy, oz, (uint32_t)d);
+                    ia_out[base + k] = (int32_t)l2;
+                } else {
+                    atomicOr(overflow, 1);
+                }
             }
         }
-        ia_out[i] = (int32_t)lo;
     }
 }
 
@@ -456,7 +483,11 @@ __device__ __forceinline__ uint32_t shared_elements(const uint32_t* sA, int na, 
     const int tot = na + nb;
     const int ns = min(na, nb), nl = max(na, nb);
     if (ns == 0 && !boundary) return 0;
-    if ((int64_t)ns * (ceil_log2(nl + 1) + 1) <= (int64_t)tot + (tot >> 1)) {
+    // issue-slot estimates of the two strategies (per thread: a search step
+    // ~7 instructions, a merge step ~12)
+    const int search_cost = ((ns + NT - 1) / NT) * (ceil_log2(nl + 1) + 1) * 7;
+    const int merge_cost = ((tot + NT - 1) / NT) * 12 + ceil_log2(tot + 1) * 9;
+    if (search_cost <= merge_cost) {
         const bool small_is_A = na <= nb;
         const uint32_t* sm = small_is_A ? sA : sB;
         const uint32_t* lg = small_is_A ? sB : sA;
@@ -486,7 +517,9 @@ __device__ __forceinline__ uint32_t shared_elements(const uint32_t* sA, int na, 
             }
         }
     } else {
-        const int K = (tot + NT - 1) / NT;
+        // odd step count: balanced lanes start an odd stride apart, spreading
+        // their shared-memory reads over the banks
+        const int K = ((tot + NT - 1) / NT) | 1;
         const int dl = min(tid * K, tot);
         const int steps = min(K, tot - dl);
         int lo = max(0, dl - nb), hi = min(dl, na);
@@ -575,6 +608,110 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
     flush_hist<WARPS>(hs, acc, tag, lane);
 }
 
+// ------------------------------------------------------------- k_stream --
+// One warp per task whose shorter list S has at most STREAM_SMAX entries
+// (the longer list G may be a hub's).  S is copied to shared memory (followed
+// by a sentinel); G is streamed through registers in steps of 256 entries
+// (8 consecutive entries per lane, two 16-byte loads), every entry of G being
+// read once.  At each step the entries of S whose keys do not exceed the
+// step's last key are located: the lane holding a key is the first lane whose
+// last key is not smaller (a 5-step search over the lanes by shuffles), and
+// the lane's 8 entries are compared.  Both lists are sorted, so each entry of
+// S is placed in exactly one step and every shared element is found once.
+constexpr int STREAM_SMAX = 1024;
+
+__global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_ptr,
+                                                const uint32_t* __restrict__ adj,
+                                                const SegDev* __restrict__ seg,
+                                                const uint4* __restrict__ rec,
+                                                const unsigned int* __restrict__ cnt, uint32_t cap,
+                                                unsigned long long* __restrict__ acc) {
+    __shared__ __align__(16) uint32_t sbuf[WARPS][STREAM_SMAX + 8];
+    __shared__ unsigned long long hs_all[WARPS][ACC];
+    const unsigned full = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long* hs = hs_all[warp];
+    for (int j = lane; j < ACC; j += 32) hs[j] = 0;
+    __syncwarp();
+    int tag = -1;
+    const unsigned ntask = min(*cnt, cap);
+    for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS) {
+        const uint4 r = rec[i];
+        const int s = (int)(r.z >> 2);
+        const uint32_t pre = r.z & 3u;
+        if (s != tag) {
+            flush_hist<WARPS>(hs, acc, tag, lane);
+            __syncwarp();
+            tag = s;
+        }
+        const int64_t rb = seg[s].rb;
+        const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
+        const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
+        const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+        const bool s_is_A = (ae - ab) <= (be - bb);
+        const int64_t pS = s_is_A ? ab : bb;
+        const int nS = (int)(s_is_A ? ae - ab : be - bb);
+        const int64_t pG = s_is_A ? bb : ab, gend = s_is_A ? be : ae;
+        const int oS = load_span<32>(sbuf[warp], adj, pS, nS + 1, pS + nS, lane);
+        const uint32_t* sS = sbuf[warp] + oS;
+        __syncwarp();
+        int js = 0;
+        uint32_t c = 0;
+        for (int64_t base = pG & ~(int64_t)3; base < gend; base += 256) {
+            const int64_t e0 = base + 8 * lane;
+            const uint4 lo4 = __ldg(reinterpret_cast<const uint4*>(adj + e0));
+            const uint4 hi4 = __ldg(reinterpret_cast<const uint4*>(adj + e0 + 4));
+            uint32_t v[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+            uint32_t lane_last;
+            if (base < pG || base + 256 > gend) {  // first or last step: mask foreign entries
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int64_t idx = e0 + j;
+                    v[j] = (idx >= pG && idx < gend) ? v[j] : SENT;  // never equal to a real key
+                }
+                lane_last = e0 + 7 < pG ? 0u : (e0 + 7 >= gend ? SENT : (v[7] | 3u));
+            } else {
+                lane_last = v[7] | 3u;
+            }
+            const uint32_t step_last = __shfl_sync(full, lane_last, 31);
+            for (;;) {
+                const int jj = js + lane;
+                const uint32_t t = sS[min(jj, nS)];  // sS[nS] is the sentinel
+                const uint32_t tkey = t | 3u;
+                const bool inr = jj < nS && tkey <= step_last;
+                const unsigned m = __ballot_sync(full, inr);
+                if (m == 0) break;
+                int own = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t x = __shfl_sync(full, lane_last, own + step - 1);
+                    if (x < tkey) own += step;
+                }
+                own = min(own, 31);
+                uint32_t hit = SENT;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t x = __shfl_sync(full, v[j], own);
+                    hit = (x | 3u) == tkey ? x : hit;
+                }
+                if (inr && hit != SENT) {
+                    ++c;
+                    on_shared(hs, tkey >> 2, ul, vl, pre, s_is_A ? (t & 3u) : (hit & 3u),
+                              s_is_A ? (hit & 3u) : (t & 3u));
+                }
+                const int k = __popc(m);
+                js += k;
+                if (k < 32) break;
+            }
+        }
+        c = __reduce_add_sync(full, c);
+        if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+        __syncwarp();
+    }
+    __syncwarp();
+    flush_hist<WARPS>(hs, acc, tag, lane);
+}
+
 // ---------------------------------------------------------------- k_cta --
 // One CTA per tile of at most TILE merge outputs of a large task.  The tile
 // starts where k_split put it on the merge path and ends where the task's
@@ -656,7 +793,7 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 
 struct Launch {
     int sms = 148;
-    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1;
+    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1;
     bool ready = false;
 };
 
@@ -675,6 +812,8 @@ tc_status launch_info(Launch& L) {
         c.occ_thread = std::max(1, c.occ_thread);
         c.occ_warp = std::max(1, c.occ_warp);
         c.occ_cta = std::max(1, c.occ_cta);
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_stream, k_stream, 256, 0));
+        c.occ_stream = std::max(1, c.occ_stream);
         c.ready = true;
     }
     L = c;
@@ -697,6 +836,8 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
                                 "1024 (warp tiles) or 3840 (split_cta = 1)");
     // a warp holds both lists in shared memory: larger tasks go to CTA tiles
     o.thr_warp = std::min(o.thr_warp, WARP_LMAX);
+    if (o.stream_max < 0) return fail(TC_ERR_ARG, "census: stream_max < 0");
+    o.stream_max = std::min(o.stream_max, STREAM_SMAX);
     const int nseg = (int)gidx.size();
     std::vector<SegDev> segs((size_t)nseg);
     std::vector<int64_t> pfx((size_t)nseg + 1, 0);
@@ -726,7 +867,9 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
     const size_t o_out = take(sizeof(tc_census_t) * (size_t)nseg);
     const size_t o_r0 = take(sizeof(uint4) * cap01);
     const size_t o_r1 = take(sizeof(uint4) * cap01);
-    const size_t o_r2 = take(sizeof(uint4) * cap2);
+    const size_t o_r2 = take(sizeof(uint4) * cap01);
+    const size_t o_r3 = take(sizeof(uint4) * cap01);
+    const size_t o_tl = take(sizeof(uint4) * cap2);
     const size_t o_ia = take(sizeof(int32_t) * cap2);
     const size_t need = off;
     if (set.ws_bytes < need) {
@@ -738,7 +881,9 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
     }
     char* ws = (char*)set.ws;
     unsigned long long* acc = (unsigned long long*)(ws + o_acc);
-    unsigned int* ctr = (unsigned int*)(ws + o_ctr);  // [0..2] bin counts, [4] overflow, [8..9] cursor (u64)
+    // counters: [0..3] records per bin, [4] overflow flag, [5] tile records,
+    // [8..9] row cursor (u64), [10..17] merged entries per bin (u64)
+    unsigned int* ctr = (unsigned int*)(ws + o_ctr);
     SegDev* d_seg = (SegDev*)(ws + o_seg);
     int64_t* d_pfx = (int64_t*)(ws + o_pfx);
     tc_census_t* d_out = (flags & TC_OUT_DEVICE) ? out : (tc_census_t*)(ws + o_out);
@@ -746,13 +891,13 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
     bins.rec[0] = (uint4*)(ws + o_r0);
     bins.rec[1] = (uint4*)(ws + o_r1);
     bins.rec[2] = (uint4*)(ws + o_r2);
-    bins.cap[0] = bins.cap[1] = (uint32_t)cap01;
-    bins.cap[2] = (uint32_t)cap2;
+    bins.rec[3] = (uint4*)(ws + o_r3);
+    bins.cap[0] = bins.cap[1] = bins.cap[2] = bins.cap[3] = (uint32_t)cap01;
+    uint4* d_tiles = (uint4*)(ws + o_tl);
     bins.cnt = ctr;
     bins.overflow = (int*)(ctr + 4);
     unsigned long long* cursor = (unsigned long long*)(ctr + 8);
     bins.entries = (unsigned long long*)(ctr + 10);
-    bins.tasks2 = (unsigned long long*)(ctr + 16);
     int32_t* d_ia = (int32_t*)(ws + o_ia);
 
     TC_CUDA(cudaMemcpyAsync(d_seg, segs.data(), sizeof(SegDev) * (size_t)nseg, cudaMemcpyHostToDevice, st));
@@ -761,7 +906,7 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
 
     Launch L;
     if (tc_status s = launch_info(L); s != TC_OK) return s;
-    BinParams bp{o.thr_thread, o.thr_warp, o.chunk};
+    BinParams bp{o.thr_thread, o.thr_warp, o.stream_max};
     ProfileEvents* pe = nullptr;
     if (o.profile) {
         if (tc_status s = profile_events(&pe); s != TC_OK) return s;
@@ -775,51 +920,59 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
                                                      bins, acc, cursor);
         TC_CUDA(cudaGetLastError());
         mark(1);
-        k_split<<<L.sms * 4, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], d_ia);
+        k_split<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], o.chunk,
+                                            d_tiles, d_ia, ctr + 5, (uint32_t)cap2, bins.overflow);
         TC_CUDA(cudaGetLastError());
         mark(2);
         if (o.split_cta)
-            k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[2], d_ia, ctr + 2,
-                                                        bins.cap[2], o.chunk, acc);
+            k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5,
+                                                        (uint32_t)cap2, o.chunk, acc);
         else
-            k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[2], d_ia, ctr + 2,
-                                                        bins.cap[2], o.chunk, acc);
+            k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5,
+                                                        (uint32_t)cap2, o.chunk, acc);
         TC_CUDA(cudaGetLastError());
         mark(3);
+        k_stream<<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[3], ctr + 3,
+                                                        bins.cap[3], acc);
+        TC_CUDA(cudaGetLastError());
+        mark(4);
         k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], nullptr, ctr + 1,
                                                             bins.cap[1], 0, acc);
         TC_CUDA(cudaGetLastError());
-        mark(4);
+        mark(5);
         k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
                                                         bins.cap[0], acc);
         TC_CUDA(cudaGetLastError());
     }
-    mark(5);
+    mark(6);
     k_fold<<<(nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, nseg, d_out);
     TC_CUDA(cudaGetLastError());
-    mark(6);
+    mark(7);
     if (pe) {
         unsigned int c[18];
         TC_CUDA(cudaMemcpyAsync(c, ctr, sizeof c, cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         tc_profile_t& P = g_profile;
         P = tc_profile_t{};
-        float ms[7] = {0};
-        for (int k = 0; k < 6; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
-        TC_CUDA(cudaEventElapsedTime(&ms[6], pe->ev[0], pe->ev[6]));
+        float ms[8] = {0};
+        for (int k = 0; k < 7; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
+        TC_CUDA(cudaEventElapsedTime(&ms[7], pe->ev[0], pe->ev[7]));
         if (rows > 0) {
-            P.ms_tasks = ms[0]; P.ms_split = ms[1]; P.ms_tiles = ms[2]; P.ms_warp = ms[3]; P.ms_thread = ms[4];
+            P.ms_tasks = ms[0];
+            P.ms_split = ms[1];
+            P.ms_tiles = ms[2];
+            P.ms_stream = ms[3];
+            P.ms_warp = ms[4];
+            P.ms_thread = ms[5];
         }
-        P.ms_fold = ms[5];
-        P.ms_total = ms[6];
-        P.launches = rows > 0 ? 6 : 1;
-        for (int b = 0; b < 3; ++b) {
+        P.ms_fold = ms[6];
+        P.ms_total = ms[7];
+        P.launches = rows > 0 ? 7 : 1;
+        for (int b = 0; b < NBIN; ++b) {
+            P.bin_tasks[b] = c[b];
             P.bin_entries[b] = (int64_t)(((unsigned long long)c[10 + 2 * b + 1] << 32) | c[10 + 2 * b]);
         }
-        P.chunks = c[2];
-        P.bin_tasks[0] = c[0];
-        P.bin_tasks[1] = c[1];
-        P.bin_tasks[2] = (int64_t)(((unsigned long long)c[17] << 32) | c[16]);
+        P.chunks = c[5];
         g_profile_valid = true;
     }
     if (!(flags & TC_OUT_DEVICE)) {
@@ -960,15 +1113,14 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
         s, row_ptr, n);
     TC_CUDA(cudaGetLastError());
     Bins bins;
-    bins.rec[0] = bins.rec[1] = bins.rec[2] = s->rec;
+    bins.rec[0] = bins.rec[1] = bins.rec[2] = bins.rec[3] = s->rec;
     bins.cap[0] = (uint32_t)NOALLOC_MAX_DYADS;
-    bins.cap[1] = bins.cap[2] = 0;
+    bins.cap[1] = bins.cap[2] = bins.cap[3] = 0;
     bins.cnt = s->ctr;
     bins.overflow = (int*)(s->ctr + 4);
     bins.entries = (unsigned long long*)(s->ctr + 10);
-    bins.tasks2 = (unsigned long long*)(s->ctr + 16);
     unsigned long long* cursor = (unsigned long long*)(s->ctr + 8);
-    const BinParams bp{0x7fffffff, 0x7fffffff, 0x40000000};
+    const BinParams bp{0x7fffffff, 0x7fffffff, 0};
     if (n > 0) {
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
                                                      s->acc, cursor);

@@ -20,11 +20,13 @@ BIG = 1 << 30
 # chunk (tiny chunks: every task split), and small mixed thresholds
 BINS = {
     "default": {},
+    "nostream": dict(stream_max=0),
+    "stream_all": dict(thr_thread=0, thr_warp=0, stream_max=1024),
     "thread": dict(thr_thread=BIG, thr_warp=BIG),
-    "warp": dict(thr_thread=0, thr_warp=BIG),
-    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1),
-    "wtile": dict(thr_thread=0, thr_warp=0, chunk=256),
-    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1),
+    "warp": dict(thr_thread=0, thr_warp=BIG, stream_max=0),
+    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1, stream_max=0),
+    "wtile": dict(thr_thread=0, thr_warp=0, chunk=256, stream_max=0),
+    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1, stream_max=8),
     "mixed": dict(thr_thread=8, thr_warp=40, chunk=512),
 }
 
