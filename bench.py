@@ -251,7 +251,8 @@ def run_native(args, world, rank, local, pg):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     out = torch.zeros(17, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
-    prof_opts = tc.tc_opts_default(profile=1)
+    over = dict(kv.split("=") for kv in args.opts.split(",") if kv) if args.opts else {}
+    prof_opts = tc.tc_opts_default(profile=1, **{k: int(v) for k, v in over.items()})
 
     def step_device():
         g = tc.tc_graph_build(arcs.n, src_d, dst_d, stream=stream)
@@ -319,7 +320,7 @@ def run_native(args, world, rank, local, pg):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = tc.tc_graph_build(arcs.n, src_h.numpy(), dst_h.numpy())
-        host_out = tc.tc_census(g)
+        host_out = tc.tc_census(g, prof_opts)
         t1 = time.perf_counter()
         tc.tc_graph_free(g)
         if k > 0:
@@ -349,7 +350,10 @@ def run_native(args, world, rank, local, pg):
                        "max_degree": stats["max_degree"],
                        "step": "graph build + census, arc list resident in HBM",
                        "l2": "512 MB buffer written between timed steps (L2 flush)",
-                       "parallelism": "single GPU" if world == 1 else f"replicas x{world}"},
+                       "parallelism": "single GPU" if world == 1 else f"replicas x{world}",
+                       "census_opts": {k: getattr(prof_opts, k) for k in
+                                       ("bin_mode", "thr_thread", "thr_warp", "chunk", "split_cta",
+                                        "stream_max")}},
             "breakdown": {"census_ms": float(np.mean(census_ms)), "build_ms": float(np.mean(build_ms)),
                           "merge_ms": merge_ms, "kernel_ms": avg,
                           "bin_tasks": profs[-1]["bin_tasks"], "bin_entries": profs[-1]["bin_entries"],
@@ -374,6 +378,7 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--opts", default="", help="census options, e.g. thr_warp=512,stream_max=1024")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -611,21 +611,25 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
 // ------------------------------------------------------------- k_stream --
 // One warp per task whose shorter list S has at most STREAM_SMAX entries
 // (the longer list G may be a hub's).  S is copied to shared memory (followed
-// by a sentinel); G is streamed through registers in steps of 256 entries
-// (8 consecutive entries per lane, two 16-byte loads), every entry of G being
+// by a sentinel); G is streamed through registers in steps of 32*EPL entries
+// (EPL consecutive entries per lane, 16-byte loads), every entry of G being
 // read once.  At each step the entries of S whose keys do not exceed the
-// step's last key are located: the lane holding a key is the first lane whose
-// last key is not smaller (a 5-step search over the lanes by shuffles), and
-// the lane's 8 entries are compared.  Both lists are sorted, so each entry of
-// S is placed in exactly one step and every shared element is found once.
+// step's last key are located: with few of them, each is broadcast and every
+// lane compares it with its own entries; otherwise the lane holding a key is
+// the first lane whose last key is not smaller (a 5-step search over the
+// lanes by shuffles).  Both lists are sorted, so each entry of S is placed in
+// exactly one step and every shared element is found once.
 constexpr int STREAM_SMAX = 1024;
 
-__global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_ptr,
-                                                const uint32_t* __restrict__ adj,
-                                                const SegDev* __restrict__ seg,
-                                                const uint4* __restrict__ rec,
-                                                const unsigned int* __restrict__ cnt, uint32_t cap,
-                                                unsigned long long* __restrict__ acc) {
+template <int EPL, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_stream(const int64_t* __restrict__ row_ptr,
+                                                      const uint32_t* __restrict__ adj,
+                                                      const SegDev* __restrict__ seg,
+                                                      const uint4* __restrict__ rec,
+                                                      const unsigned int* __restrict__ cnt, uint32_t cap,
+                                                      unsigned long long* __restrict__ acc) {
+    constexpr int STEP = 32 * EPL;
+    constexpr int NQ = EPL / 4;  // 16-byte loads per lane per step
     __shared__ __align__(16) uint32_t sbuf[WARPS][STREAM_SMAX + 8];
     __shared__ unsigned long long hs_all[WARPS][ACC];
     const unsigned full = 0xffffffffu;
@@ -657,21 +661,27 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
         __syncwarp();
         int js = 0;
         uint32_t c = 0;
-        for (int64_t base = pG & ~(int64_t)3; base < gend; base += 256) {
-            const int64_t e0 = base + 8 * lane;
-            const uint4 lo4 = __ldg(reinterpret_cast<const uint4*>(adj + e0));
-            const uint4 hi4 = __ldg(reinterpret_cast<const uint4*>(adj + e0 + 4));
-            uint32_t v[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
-            uint32_t lane_last;
-            if (base < pG || base + 256 > gend) {  // first or last step: mask foreign entries
+        for (int64_t base = pG & ~(int64_t)3; base < gend; base += STEP) {
+            const int64_t e0 = base + EPL * lane;
+            uint32_t v[EPL];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+            for (int q = 0; q < NQ; ++q) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4*>(adj + e0) + q);
+                v[4 * q] = x.x;
+                v[4 * q + 1] = x.y;
+                v[4 * q + 2] = x.z;
+                v[4 * q + 3] = x.w;
+            }
+            uint32_t lane_last;
+            if (base < pG || base + STEP > gend) {  // first or last step: mask foreign entries
+#pragma unroll
+                for (int j = 0; j < EPL; ++j) {
                     const int64_t idx = e0 + j;
                     v[j] = (idx >= pG && idx < gend) ? v[j] : SENT;  // never equal to a real key
                 }
-                lane_last = e0 + 7 < pG ? 0u : (e0 + 7 >= gend ? SENT : (v[7] | 3u));
+                lane_last = e0 + EPL - 1 < pG ? 0u : (e0 + EPL - 1 >= gend ? SENT : (v[EPL - 1] | 3u));
             } else {
-                lane_last = v[7] | 3u;
+                lane_last = v[EPL - 1] | 3u;
             }
             const uint32_t step_last = __shfl_sync(full, lane_last, 31);
             for (;;) {
@@ -681,6 +691,23 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
                 const bool inr = jj < nS && tkey <= step_last;
                 const unsigned m = __ballot_sync(full, inr);
                 if (m == 0) break;
+                const int k = __popc(m);
+                if (k <= 3) {
+                    for (int q = 0; q < k; ++q) {
+                        const uint32_t tq = __shfl_sync(full, t, q);
+                        const uint32_t qkey = tq | 3u;
+                        uint32_t hit = SENT;
+#pragma unroll
+                        for (int j = 0; j < EPL; ++j) hit = (v[j] | 3u) == qkey ? v[j] : hit;
+                        if (hit != SENT) {
+                            ++c;
+                            on_shared(hs, qkey >> 2, ul, vl, pre, s_is_A ? (tq & 3u) : (hit & 3u),
+                                      s_is_A ? (hit & 3u) : (tq & 3u));
+                        }
+                    }
+                    js += k;
+                    break;  // k < 32: the rest of S lies beyond this step
+                }
                 int own = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {
@@ -690,7 +717,7 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
                 own = min(own, 31);
                 uint32_t hit = SENT;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < EPL; ++j) {
                     const uint32_t x = __shfl_sync(full, v[j], own);
                     hit = (x | 3u) == tkey ? x : hit;
                 }
@@ -699,7 +726,6 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
                     on_shared(hs, tkey >> 2, ul, vl, pre, s_is_A ? (t & 3u) : (hit & 3u),
                               s_is_A ? (hit & 3u) : (t & 3u));
                 }
-                const int k = __popc(m);
                 js += k;
                 if (k < 32) break;
             }
@@ -790,6 +816,13 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 }
 
 // ------------------------------------------------------------- host side --
+#ifndef TC_STREAM_EPL
+#define TC_STREAM_EPL 8
+#endif
+#ifndef TC_STREAM_MINB
+#define TC_STREAM_MINB 1
+#endif
+#define STREAM_KERNEL k_stream<TC_STREAM_EPL, TC_STREAM_MINB>
 
 struct Launch {
     int sms = 148;
@@ -812,7 +845,7 @@ tc_status launch_info(Launch& L) {
         c.occ_thread = std::max(1, c.occ_thread);
         c.occ_warp = std::max(1, c.occ_warp);
         c.occ_cta = std::max(1, c.occ_cta);
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_stream, k_stream, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_stream, STREAM_KERNEL, 256, 0));
         c.occ_stream = std::max(1, c.occ_stream);
         c.ready = true;
     }
@@ -932,7 +965,7 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
                                                         (uint32_t)cap2, o.chunk, acc);
         TC_CUDA(cudaGetLastError());
         mark(3);
-        k_stream<<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[3], ctr + 3,
+        STREAM_KERNEL<<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[3], ctr + 3,
                                                         bins.cap[3], acc);
         TC_CUDA(cudaGetLastError());
         mark(4);
