@@ -297,12 +297,16 @@ def run_native(args, world, rank, local, pg):
     value = world * stats["merged_entries"] * args.steps / (total_ms / 1e3)
 
     # dominant kernel and its roofline (algorithmic bytes = 4 B per merged entry)
-    kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_warp[tiles]": "ms_tiles",
-            "k_stream": "ms_stream", "k_warp": "ms_warp", "k_thread": "ms_thread", "k_fold": "ms_fold"}
+    if prof_opts.persistent:
+        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_merge": "ms_merge", "k_fold": "ms_fold"}
+        merge_bin = {"k_merge": (0, 1, 2, 3)}
+    else:
+        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_warp[tiles]": "ms_tiles",
+                "k_stream": "ms_stream", "k_warp": "ms_warp", "k_thread": "ms_thread", "k_fold": "ms_fold"}
+        merge_bin = {"k_warp[tiles]": (2,), "k_stream": (3,), "k_warp": (1,), "k_thread": (0,)}
     avg = {k: float(np.mean([p[f] for p in profs])) for k, f in kern.items()}
-    merge_bin = {"k_warp[tiles]": 2, "k_stream": 3, "k_warp": 1, "k_thread": 0}
     top = max(merge_bin, key=lambda k: avg[k])
-    entries_top = profs[-1]["bin_entries"][merge_bin[top]]
+    entries_top = sum(profs[-1]["bin_entries"][b] for b in merge_bin[top])
     peak, peak_kind = peaks()
     achieved = 4.0 * entries_top / (avg[top] / 1e3) / 1e9
     traffic = recorded_traffic(top)
@@ -353,7 +357,7 @@ def run_native(args, world, rank, local, pg):
                        "parallelism": "single GPU" if world == 1 else f"replicas x{world}",
                        "census_opts": {k: getattr(prof_opts, k) for k in
                                        ("bin_mode", "thr_thread", "thr_warp", "chunk", "split_cta",
-                                        "stream_max")}},
+                                        "stream_max", "persistent")}},
             "breakdown": {"census_ms": float(np.mean(census_ms)), "build_ms": float(np.mean(build_ms)),
                           "merge_ms": merge_ms, "kernel_ms": avg,
                           "bin_tasks": profs[-1]["bin_tasks"], "bin_entries": profs[-1]["bin_entries"],

@@ -86,7 +86,11 @@ typedef struct {
     int32_t stream_max;   /* tasks above thr_warp whose shorter list has at most
                              stream_max (capped at 1024) entries are streamed by
                              one warp; the others are split into tiles */
-    int32_t reserved[1];  /* must be zero */
+    int32_t persistent;   /* 1: the whole merge phase is one persistent launch
+                             whose warps pull streamed tasks, tiles, warp tasks
+                             and thread tasks from four queues (requires
+                             split_cta = 0) */
+    int32_t reserved[4];  /* must be zero */
 } tc_opts;
 
 /* Per-kernel timing and binning of the calling thread's most recent
@@ -98,6 +102,7 @@ typedef struct {
     float ms_stream;         /* streamed tasks (k_stream) */
     float ms_warp;           /* whole tasks, one warp each (k_warp) */
     float ms_thread;         /* thread-per-task merges (k_thread) */
+    float ms_merge;          /* the whole merge phase (all merge kernels, or k_merge) */
     float ms_fold;           /* 64->16 fold and 003 closure (k_fold) */
     float ms_total;          /* first to last kernel */
     int32_t launches;        /* kernels launched by the call */
@@ -221,6 +226,25 @@ tc_status tc_census_csr_noalloc(int32_t n, const int64_t* row_ptr, const uint32_
  * TriadTable, whose printed form is lost).  Returns -1 for codes outside
  * [0, 64). */
 int tc_triad_type(int code);
+
+/*
+ * Batch plans: the census of a fixed list of graphs recorded once as a CUDA
+ * graph and replayed (the batched mode of the census; one persistent merge
+ * launch when opts->persistent is set).
+ *   tc_plan_create  gs: G >= 1 handles of ONE build (any subset/order);
+ *                   opts: NULL = defaults, profile must be 0;
+ *                   out: device tc_census_t[G], written by every run.
+ *                   The plan owns its work space; creating it synchronises
+ *                   `stream` and records the graph on a private stream.
+ *   tc_plan_run     enqueue one replay on `stream` (asynchronous).
+ *   tc_plan_free    synchronise the device and release the plan.
+ * The graphs must outlive the plan.  Runs of one plan must not overlap.
+ */
+typedef struct tc_plan_s* tc_plan;
+tc_status tc_plan_create(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_census_t* out, void* stream,
+                         tc_plan* plan);
+tc_status tc_plan_run(tc_plan plan, void* stream);
+void tc_plan_free(tc_plan plan);
 
 /* Release a graph handle (synchronises the device first). NULL is a no-op. */
 void tc_graph_free(tc_graph g);

@@ -37,7 +37,7 @@ TC_OUT_DEVICE = 2
 EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
            "tc_graph_export", "tc_census", "tc_census_batched", "tc_triad_type",
            "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile",
-           "tc_census_csr_noalloc")
+           "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free")
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
 
@@ -63,14 +63,16 @@ class TcOpts(ctypes.Structure):
     _fields_ = [("bin_mode", ctypes.c_int32), ("thr_thread", ctypes.c_int32),
                 ("thr_warp", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("split_cta", ctypes.c_int32),
-                ("stream_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("stream_max", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class TcProfile(ctypes.Structure):
     _fields_ = [("ms_tasks", ctypes.c_float), ("ms_split", ctypes.c_float),
                 ("ms_tiles", ctypes.c_float), ("ms_stream", ctypes.c_float),
                 ("ms_warp", ctypes.c_float),
-                ("ms_thread", ctypes.c_float), ("ms_fold", ctypes.c_float),
+                ("ms_thread", ctypes.c_float), ("ms_merge", ctypes.c_float),
+                ("ms_fold", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int32),
                 ("bin_tasks", ctypes.c_int64 * 4), ("bin_entries", ctypes.c_int64 * 4),
                 ("chunks", ctypes.c_int64)]
@@ -114,6 +116,12 @@ def load():
     lib.tc_census_profile.restype = ctypes.c_int
     lib.tc_census_csr_noalloc.argtypes = [i32, P, P, i64, P, P]
     lib.tc_census_csr_noalloc.restype = ctypes.c_int
+    lib.tc_plan_create.argtypes = [i32, P, P, P, P, P]
+    lib.tc_plan_create.restype = ctypes.c_int
+    lib.tc_plan_run.argtypes = [P, P]
+    lib.tc_plan_run.restype = ctypes.c_int
+    lib.tc_plan_free.argtypes = [P]
+    lib.tc_plan_free.restype = None
     lib.tc_graph_free.argtypes = [P]
     lib.tc_graph_free.restype = None
     lib.tc_status_str.argtypes = [ctypes.c_int]
@@ -271,6 +279,27 @@ def tc_census_csr_noalloc(n: int, row_ptr, adj, nnz: int, out, stream=None):
                                       _stream(stream))
     _check(st, "tc_census_csr_noalloc")
     return out
+
+
+def tc_plan_create(gs, out, opts: TcOpts | None = None, stream=None) -> int:
+    """Record the census of graphs `gs` (one batched build) as a CUDA graph
+    writing to `out` (CUDA int64 tensor of >= 17*len(gs) words)."""
+    G = len(gs)
+    arr = (ctypes.c_void_p * max(G, 1))(*gs)
+    h = ctypes.c_void_p()
+    po = ctypes.byref(opts) if opts is not None else None
+    _check(load().tc_plan_create(G, arr, po, out.data_ptr(), _stream(stream), ctypes.byref(h)),
+           "tc_plan_create")
+    return h.value
+
+
+def tc_plan_run(plan: int, stream=None) -> None:
+    _check(load().tc_plan_run(plan, _stream(stream)), "tc_plan_run")
+
+
+def tc_plan_free(plan: int) -> None:
+    if plan:
+        load().tc_plan_free(plan)
 
 
 def tc_graph_free(g: int) -> None:

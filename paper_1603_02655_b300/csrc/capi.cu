@@ -98,6 +98,7 @@ tc_status tc_opts_default(tc_opts* o) {
     o->thr_warp = 1024;
     o->chunk = 1024;
     o->stream_max = 1024;
+    o->persistent = 1;
     return TC_OK;
 }
 

@@ -371,8 +371,69 @@ __device__ __forceinline__ void flush_hist(unsigned long long* hs, unsigned long
         for (int j = lane; j < ACC; j += 32) hs[j] = 0;
 }
 
-// ------------------------------------------------------------- k_thread --
-// One thread per small task: a plain two-pointer merge from global memory.
+// --------------------------------------------------------- per-warp state --
+// Each warp accumulates into its own 66-slot histogram in shared memory,
+// tagged with the graph (segment) it currently counts for; when the graph
+// changes the histogram is flushed into that graph's accumulators.
+struct WarpHist {
+    unsigned long long* hs;
+    unsigned long long* acc;
+    int tag;
+    int lane;
+    __device__ __forceinline__ void retag(int s) {
+        if (s != tag) {
+            flush_hist<WARPS>(hs, acc, tag, lane);
+            __syncwarp();
+            tag = s;
+        }
+    }
+};
+
+// ---------------------------------------------------------- thread items --
+// One thread per small task (32 consecutive tasks per warp item): a plain
+// two-pointer merge from global memory.  A lane whose task belongs to
+// another graph than the warp's histogram adds into global memory directly.
+__device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restrict__ row_ptr,
+                                            const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
+                                            const uint4* __restrict__ rec, unsigned base, unsigned ntask) {
+    const unsigned ti = base + w.lane;
+    const bool has = ti < ntask;
+    const uint4 r = has ? rec[ti] : make_uint4(0, 0, 0, 0);
+    const int s = (int)(r.z >> 2);
+    w.retag(__shfl_sync(0xffffffffu, s, 0));
+    unsigned long long* h = (s == w.tag) ? w.hs : w.acc + (size_t)s * ACC;
+    if (has) {
+        uint32_t c = 0;
+        const uint32_t pre = r.z & 3u;
+        const int64_t rb = seg[s].rb;
+        const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
+        int64_t ia = row_ptr[r.x], ib = row_ptr[r.y];
+        const int64_t ae = row_ptr[r.x + 1], be = row_ptr[r.y + 1];
+        uint32_t eA = ia < ae ? __ldg(adj + ia) : SENT;
+        uint32_t eB = ib < be ? __ldg(adj + ib) : SENT;
+        for (;;) {
+            const uint32_t kA = eA | 3u, kB = eB | 3u;
+            if (kA == SENT && kB == SENT) break;
+            if (kA == kB) {
+                ++c;
+                on_shared(h, kA >> 2, ul, vl, pre, eA & 3u, eB & 3u);
+                ++ia;
+                ++ib;
+                eA = ia < ae ? __ldg(adj + ia) : SENT;
+                eB = ib < be ? __ldg(adj + ib) : SENT;
+            } else if (kA < kB) {
+                ++ia;
+                eA = ia < ae ? __ldg(adj + ia) : SENT;
+            } else {
+                ++ib;
+                eB = ib < be ? __ldg(adj + ib) : SENT;
+            }
+        }
+        if (c) atomicAdd(h + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(256) k_thread(const int64_t* __restrict__ row_ptr,
                                                 const uint32_t* __restrict__ adj,
                                                 const SegDev* __restrict__ seg,
@@ -381,55 +442,14 @@ __global__ void __launch_bounds__(256) k_thread(const int64_t* __restrict__ row_
                                                 unsigned long long* __restrict__ acc) {
     __shared__ unsigned long long hs_all[WARPS][ACC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long* hs = hs_all[warp];
-    for (int j = lane; j < ACC; j += 32) hs[j] = 0;
+    WarpHist w{hs_all[warp], acc, -1, lane};
+    for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
     __syncwarp();
-    int tag = -1;
     const unsigned ntask = min(*cnt, cap);
-    for (unsigned base = blockIdx.x * blockDim.x; base < ntask; base += gridDim.x * blockDim.x) {
-        const unsigned ti = base + threadIdx.x;
-        const bool has = ti < ntask;
-        uint4 r = has ? rec[ti] : make_uint4(0, 0, 0, 0);
-        const int s = (int)(r.z >> 2);
-        const int s0 = __shfl_sync(0xffffffffu, s, 0);
-        if (s0 != tag) {
-            flush_hist<WARPS>(hs, acc, tag, lane);
-            __syncwarp();
-            tag = s0;
-        }
-        unsigned long long* h = (s == tag) ? hs : acc + (size_t)s * ACC;
-        uint32_t c = 0;
-        uint32_t pre = r.z & 3u;
-        if (has) {
-            const int64_t rb = seg[s].rb;
-            const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
-            int64_t ia = row_ptr[r.x], ib = row_ptr[r.y];
-            const int64_t ae = row_ptr[r.x + 1], be = row_ptr[r.y + 1];
-            uint32_t eA = ia < ae ? __ldg(adj + ia) : SENT;
-            uint32_t eB = ib < be ? __ldg(adj + ib) : SENT;
-            for (;;) {
-                const uint32_t kA = eA | 3u, kB = eB | 3u;
-                if (kA == SENT && kB == SENT) break;
-                if (kA == kB) {
-                    ++c;
-                    on_shared(h, kA >> 2, ul, vl, pre, eA & 3u, eB & 3u);
-                    ++ia; ++ib;
-                    eA = ia < ae ? __ldg(adj + ia) : SENT;
-                    eB = ib < be ? __ldg(adj + ib) : SENT;
-                } else if (kA < kB) {
-                    ++ia;
-                    eA = ia < ae ? __ldg(adj + ia) : SENT;
-                } else {
-                    ++ib;
-                    eB = ib < be ? __ldg(adj + ib) : SENT;
-                }
-            }
-            if (c) atomicAdd(h + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
-        }
-        __syncwarp();
-    }
+    for (unsigned base = (blockIdx.x * WARPS + warp) * 32u; base < ntask; base += gridDim.x * WARPS * 32u)
+        thread_item(w, row_ptr, adj, seg, rec, base, ntask);
     __syncwarp();
-    flush_hist<WARPS>(hs, acc, tag, lane);
+    flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
 
 // ------------------------------------------------------- merge spans (a3) --
@@ -547,7 +567,7 @@ __device__ __forceinline__ uint32_t shared_elements(const uint32_t* sA, int na, 
     return c;
 }
 
-// --------------------------------------------------------------- k_warp --
+// ------------------------------------------------------------ warp items --
 // One warp per record.  Without ia_start a record is a whole task with
 // |A|+|B| <= WARP_LMAX: both lists, each followed by a sentinel, are copied
 // into the warp's shared memory.  With ia_start a record is one tile of at
@@ -556,6 +576,39 @@ __device__ __forceinline__ uint32_t shared_elements(const uint32_t* sA, int na, 
 // of both lists), so exactly the spans A[is..ie) and B[js..je) are loaded,
 // plus B[je] for the pair that straddles the tile boundary.
 constexpr int WARP_LMAX = 1024;
+constexpr int WARP_BUF = WARP_LMAX + 16;  // words of shared memory per warp
+
+__device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int64_t* __restrict__ row_ptr,
+                                          const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
+                                          const uint4* __restrict__ rec, const int32_t* __restrict__ ia_start,
+                                          unsigned i, unsigned nrec, int tile) {
+    const int lane = w.lane;
+    const uint4 r = rec[i];
+    const int s = (int)(r.z >> 2);
+    const uint32_t pre = r.z & 3u;
+    w.retag(s);
+    const int64_t rb = seg[s].rb;
+    const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
+    const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+    int64_t is = 0, ie = ae - ab, js = 0, je = be - bb;
+    if (ia_start) {
+        const int64_t L = ie + je, d0 = r.w, d1 = min(d0 + (int64_t)tile, L);
+        is = ia_start[i];
+        ie = d1 == L ? ie : (int64_t)ia_start[min(i + 1, nrec - 1)];
+        js = d0 - is;
+        je = d1 - ie;
+    }
+    const int na = (int)(ie - is), nb = (int)(je - js);
+    const int oA = load_span<32>(raw, adj, ab + is, na + 1, ab + ie, lane);
+    uint32_t* rawB = raw + ((oA + na + 1 + 3) & ~3);
+    const int oB = load_span<32>(rawB, adj, bb + js, nb + 1, min(bb + je + 1, be), lane);
+    __syncwarp();
+    uint32_t c = shared_elements<32>(raw + oA, na, rawB + oB, nb, ia_start != nullptr, (uint32_t)(r.x - rb),
+                                     (uint32_t)(r.y - rb), pre, w.hs, lane);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    __syncwarp();
+}
 
 __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_ptr,
                                               const uint32_t* __restrict__ adj,
@@ -564,51 +617,20 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
                                               const int32_t* __restrict__ ia_start,
                                               const unsigned int* __restrict__ cnt, uint32_t cap,
                                               int tile, unsigned long long* __restrict__ acc) {
-    __shared__ __align__(16) uint32_t sbuf[WARPS][WARP_LMAX + 16];
+    __shared__ __align__(16) uint32_t sbuf[WARPS][WARP_BUF];
     __shared__ unsigned long long hs_all[WARPS][ACC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long* hs = hs_all[warp];
-    for (int j = lane; j < ACC; j += 32) hs[j] = 0;
+    WarpHist w{hs_all[warp], acc, -1, lane};
+    for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
     __syncwarp();
-    int tag = -1;
     const unsigned ntask = min(*cnt, cap);
-    for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS) {
-        const uint4 r = rec[i];
-        const int s = (int)(r.z >> 2);
-        const uint32_t pre = r.z & 3u;
-        if (s != tag) {
-            flush_hist<WARPS>(hs, acc, tag, lane);
-            __syncwarp();
-            tag = s;
-        }
-        const int64_t rb = seg[s].rb;
-        const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
-        const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
-        int64_t is = 0, ie = ae - ab, js = 0, je = be - bb;
-        if (ia_start) {
-            const int64_t L = ie + je, d0 = r.w, d1 = min(d0 + (int64_t)tile, L);
-            is = ia_start[i];
-            ie = d1 == L ? ie : (int64_t)ia_start[min(i + 1, ntask - 1)];
-            js = d0 - is;
-            je = d1 - ie;
-        }
-        const int na = (int)(ie - is), nb = (int)(je - js);
-        uint32_t* raw = sbuf[warp];
-        const int oA = load_span<32>(raw, adj, ab + is, na + 1, ab + ie, lane);
-        uint32_t* rawB = raw + ((oA + na + 1 + 3) & ~3);
-        const int oB = load_span<32>(rawB, adj, bb + js, nb + 1, min(bb + je + 1, be), lane);
-        __syncwarp();
-        uint32_t c = shared_elements<32>(raw + oA, na, rawB + oB, nb, ia_start != nullptr,
-                                         (uint32_t)(r.x - rb), (uint32_t)(r.y - rb), pre, hs, lane);
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
-        __syncwarp();
-    }
+    for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
+        warp_item(w, sbuf[warp], row_ptr, adj, seg, rec, ia_start, i, ntask, tile);
     __syncwarp();
-    flush_hist<WARPS>(hs, acc, tag, lane);
+    flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
 
-// ------------------------------------------------------------- k_stream --
+// ---------------------------------------------------------- stream items --
 // One warp per task whose shorter list S has at most STREAM_SMAX entries
 // (the longer list G may be a hub's).  S is copied to shared memory (followed
 // by a sentinel); G is streamed through registers in steps of 32*EPL entries
@@ -620,122 +642,181 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
 // lanes by shuffles).  Both lists are sorted, so each entry of S is placed in
 // exactly one step and every shared element is found once.
 constexpr int STREAM_SMAX = 1024;
+static_assert(STREAM_SMAX + 8 <= WARP_BUF, "stream buffer fits the warp buffer");
 
-template <int EPL, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_stream(const int64_t* __restrict__ row_ptr,
-                                                      const uint32_t* __restrict__ adj,
-                                                      const SegDev* __restrict__ seg,
-                                                      const uint4* __restrict__ rec,
-                                                      const unsigned int* __restrict__ cnt, uint32_t cap,
-                                                      unsigned long long* __restrict__ acc) {
+template <int EPL>
+__device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const int64_t* __restrict__ row_ptr,
+                                            const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
+                                            const uint4 r) {
     constexpr int STEP = 32 * EPL;
     constexpr int NQ = EPL / 4;  // 16-byte loads per lane per step
-    __shared__ __align__(16) uint32_t sbuf[WARPS][STREAM_SMAX + 8];
+    const unsigned full = 0xffffffffu;
+    const int lane = w.lane;
+    const int s = (int)(r.z >> 2);
+    const uint32_t pre = r.z & 3u;
+    w.retag(s);
+    const int64_t rb = seg[s].rb;
+    const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
+    const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
+    const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+    const bool s_is_A = (ae - ab) <= (be - bb);
+    const int64_t pS = s_is_A ? ab : bb;
+    const int nS = (int)(s_is_A ? ae - ab : be - bb);
+    const int64_t pG = s_is_A ? bb : ab, gend = s_is_A ? be : ae;
+    const int oS = load_span<32>(buf, adj, pS, nS + 1, pS + nS, lane);
+    const uint32_t* sS = buf + oS;
+    __syncwarp();
+    int js = 0;
+    uint32_t c = 0;
+    for (int64_t base = pG & ~(int64_t)3; base < gend; base += STEP) {
+        const int64_t e0 = base + EPL * lane;
+        uint32_t v[EPL];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4*>(adj + e0) + q);
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+        uint32_t lane_last;
+        if (base < pG || base + STEP > gend) {  // first or last step: mask foreign entries
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) {
+                const int64_t idx = e0 + j;
+                v[j] = (idx >= pG && idx < gend) ? v[j] : SENT;  // never equal to a real key
+            }
+            lane_last = e0 + EPL - 1 < pG ? 0u : (e0 + EPL - 1 >= gend ? SENT : (v[EPL - 1] | 3u));
+        } else {
+            lane_last = v[EPL - 1] | 3u;
+        }
+        const uint32_t step_last = __shfl_sync(full, lane_last, 31);
+        for (;;) {
+            const int jj = js + lane;
+            const uint32_t t = sS[min(jj, nS)];  // sS[nS] is the sentinel
+            const uint32_t tkey = t | 3u;
+            const bool inr = jj < nS && tkey <= step_last;
+            const unsigned m = __ballot_sync(full, inr);
+            if (m == 0) break;
+            const int k = __popc(m);
+            if (k <= 3) {
+                for (int q = 0; q < k; ++q) {
+                    const uint32_t tq = __shfl_sync(full, t, q);
+                    const uint32_t qkey = tq | 3u;
+                    uint32_t hit = SENT;
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j) hit = (v[j] | 3u) == qkey ? v[j] : hit;
+                    if (hit != SENT) {
+                        ++c;
+                        on_shared(w.hs, qkey >> 2, ul, vl, pre, s_is_A ? (tq & 3u) : (hit & 3u),
+                                  s_is_A ? (hit & 3u) : (tq & 3u));
+                    }
+                }
+                js += k;
+                break;  // k < 32: the rest of S lies beyond this step
+            }
+            int own = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t x = __shfl_sync(full, lane_last, own + step - 1);
+                if (x < tkey) own += step;
+            }
+            own = min(own, 31);
+            uint32_t hit = SENT;
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) {
+                const uint32_t x = __shfl_sync(full, v[j], own);
+                hit = (x | 3u) == tkey ? x : hit;
+            }
+            if (inr && hit != SENT) {
+                ++c;
+                on_shared(w.hs, tkey >> 2, ul, vl, pre, s_is_A ? (t & 3u) : (hit & 3u),
+                          s_is_A ? (hit & 3u) : (t & 3u));
+            }
+            js += k;
+            if (k < 32) break;
+        }
+    }
+    c = __reduce_add_sync(full, c);
+    if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    __syncwarp();
+}
+
+template <int EPL>
+__global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_ptr,
+                                                const uint32_t* __restrict__ adj,
+                                                const SegDev* __restrict__ seg,
+                                                const uint4* __restrict__ rec,
+                                                const unsigned int* __restrict__ cnt, uint32_t cap,
+                                                unsigned long long* __restrict__ acc) {
+    __shared__ __align__(16) uint32_t sbuf[WARPS][WARP_BUF];
+    __shared__ unsigned long long hs_all[WARPS][ACC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpHist w{hs_all[warp], acc, -1, lane};
+    for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
+    __syncwarp();
+    const unsigned ntask = min(*cnt, cap);
+    for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
+        stream_item<EPL>(w, sbuf[warp], row_ptr, adj, seg, rec[i]);
+    __syncwarp();
+    flush_hist<WARPS>(w.hs, acc, w.tag, lane);
+}
+
+// ---------------------------------------------------------------- k_merge --
+// The whole merge phase in one persistent launch: warps pull work from the
+// four bins in decreasing order of task size (streamed tasks, tiles of split
+// tasks, whole warp tasks, groups of 32 thread tasks), each bin through its
+// own atomic cursor, so no bin waits for another kernel's tail.
+struct MergeQueues {
+    const uint4* rec[NBIN];       // bin records (rec[2] unused: tiles below)
+    const unsigned int* cnt;      // records per bin
+    uint32_t cap[NBIN];
+    const uint4* tiles;           // tile records of split tasks
+    const int32_t* ia;            // their merge-path starts
+    const unsigned int* ntile;
+    uint32_t tile_cap;
+    int tile;
+    unsigned int* cursor;         // [4] per-queue cursors, zeroed before launch
+};
+
+template <int EPL>
+__global__ void __launch_bounds__(256) k_merge(const int64_t* __restrict__ row_ptr,
+                                               const uint32_t* __restrict__ adj,
+                                               const SegDev* __restrict__ seg, MergeQueues q,
+                                               unsigned long long* __restrict__ acc) {
+    __shared__ __align__(16) uint32_t sbuf[WARPS][WARP_BUF];
     __shared__ unsigned long long hs_all[WARPS][ACC];
     const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long* hs = hs_all[warp];
-    for (int j = lane; j < ACC; j += 32) hs[j] = 0;
+    WarpHist w{hs_all[warp], acc, -1, lane};
+    for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
     __syncwarp();
-    int tag = -1;
-    const unsigned ntask = min(*cnt, cap);
-    for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS) {
-        const uint4 r = rec[i];
-        const int s = (int)(r.z >> 2);
-        const uint32_t pre = r.z & 3u;
-        if (s != tag) {
-            flush_hist<WARPS>(hs, acc, tag, lane);
-            __syncwarp();
-            tag = s;
-        }
-        const int64_t rb = seg[s].rb;
-        const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
-        const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
-        const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
-        const bool s_is_A = (ae - ab) <= (be - bb);
-        const int64_t pS = s_is_A ? ab : bb;
-        const int nS = (int)(s_is_A ? ae - ab : be - bb);
-        const int64_t pG = s_is_A ? bb : ab, gend = s_is_A ? be : ae;
-        const int oS = load_span<32>(sbuf[warp], adj, pS, nS + 1, pS + nS, lane);
-        const uint32_t* sS = sbuf[warp] + oS;
-        __syncwarp();
-        int js = 0;
-        uint32_t c = 0;
-        for (int64_t base = pG & ~(int64_t)3; base < gend; base += STEP) {
-            const int64_t e0 = base + EPL * lane;
-            uint32_t v[EPL];
+    const unsigned n3 = min(q.cnt[3], q.cap[3]);
+    const unsigned nt = min(*q.ntile, q.tile_cap);
+    const unsigned n1 = min(q.cnt[1], q.cap[1]);
+    const unsigned n0 = min(q.cnt[0], q.cap[0]);
+    const unsigned n0g = (n0 + 31) / 32;
+    // queue k: items, items taken per cursor step
+    const unsigned items[4] = {n3, nt, n1, n0g};
+    const unsigned grab[4] = {1, 2, 4, 2};
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const uint4 x = __ldg(reinterpret_cast<const uint4*>(adj + e0) + q);
-                v[4 * q] = x.x;
-                v[4 * q + 1] = x.y;
-                v[4 * q + 2] = x.z;
-                v[4 * q + 3] = x.w;
-            }
-            uint32_t lane_last;
-            if (base < pG || base + STEP > gend) {  // first or last step: mask foreign entries
-#pragma unroll
-                for (int j = 0; j < EPL; ++j) {
-                    const int64_t idx = e0 + j;
-                    v[j] = (idx >= pG && idx < gend) ? v[j] : SENT;  // never equal to a real key
-                }
-                lane_last = e0 + EPL - 1 < pG ? 0u : (e0 + EPL - 1 >= gend ? SENT : (v[EPL - 1] | 3u));
-            } else {
-                lane_last = v[EPL - 1] | 3u;
-            }
-            const uint32_t step_last = __shfl_sync(full, lane_last, 31);
-            for (;;) {
-                const int jj = js + lane;
-                const uint32_t t = sS[min(jj, nS)];  // sS[nS] is the sentinel
-                const uint32_t tkey = t | 3u;
-                const bool inr = jj < nS && tkey <= step_last;
-                const unsigned m = __ballot_sync(full, inr);
-                if (m == 0) break;
-                const int k = __popc(m);
-                if (k <= 3) {
-                    for (int q = 0; q < k; ++q) {
-                        const uint32_t tq = __shfl_sync(full, t, q);
-                        const uint32_t qkey = tq | 3u;
-                        uint32_t hit = SENT;
-#pragma unroll
-                        for (int j = 0; j < EPL; ++j) hit = (v[j] | 3u) == qkey ? v[j] : hit;
-                        if (hit != SENT) {
-                            ++c;
-                            on_shared(hs, qkey >> 2, ul, vl, pre, s_is_A ? (tq & 3u) : (hit & 3u),
-                                      s_is_A ? (hit & 3u) : (tq & 3u));
-                        }
-                    }
-                    js += k;
-                    break;  // k < 32: the rest of S lies beyond this step
-                }
-                int own = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const uint32_t x = __shfl_sync(full, lane_last, own + step - 1);
-                    if (x < tkey) own += step;
-                }
-                own = min(own, 31);
-                uint32_t hit = SENT;
-#pragma unroll
-                for (int j = 0; j < EPL; ++j) {
-                    const uint32_t x = __shfl_sync(full, v[j], own);
-                    hit = (x | 3u) == tkey ? x : hit;
-                }
-                if (inr && hit != SENT) {
-                    ++c;
-                    on_shared(hs, tkey >> 2, ul, vl, pre, s_is_A ? (t & 3u) : (hit & 3u),
-                              s_is_A ? (hit & 3u) : (t & 3u));
-                }
-                js += k;
-                if (k < 32) break;
+    for (int k = 0; k < 4; ++k) {
+        for (;;) {
+            unsigned at = 0;
+            if (lane == 0) at = atomicAdd(q.cursor + k, grab[k]);
+            at = __shfl_sync(full, at, 0);
+            if (at >= items[k]) break;
+            const unsigned end = min(at + grab[k], items[k]);
+            for (unsigned i = at; i < end; ++i) {
+                if (k == 0) stream_item<EPL>(w, sbuf[warp], row_ptr, adj, seg, q.rec[3][i]);
+                else if (k == 1) warp_item(w, sbuf[warp], row_ptr, adj, seg, q.tiles, q.ia, i, nt, q.tile);
+                else if (k == 2) warp_item(w, sbuf[warp], row_ptr, adj, seg, q.rec[1], nullptr, i, n1, 0);
+                else thread_item(w, row_ptr, adj, seg, q.rec[0], i * 32u, n0);
             }
         }
-        c = __reduce_add_sync(full, c);
-        if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
-        __syncwarp();
     }
     __syncwarp();
-    flush_hist<WARPS>(hs, acc, tag, lane);
+    flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
 
 // ---------------------------------------------------------------- k_cta --
@@ -816,17 +897,11 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 }
 
 // ------------------------------------------------------------- host side --
-#ifndef TC_STREAM_EPL
-#define TC_STREAM_EPL 8
-#endif
-#ifndef TC_STREAM_MINB
-#define TC_STREAM_MINB 1
-#endif
-#define STREAM_KERNEL k_stream<TC_STREAM_EPL, TC_STREAM_MINB>
+constexpr int STREAM_EPL = 8;
 
 struct Launch {
     int sms = 148;
-    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1;
+    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1;
     bool ready = false;
 };
 
@@ -841,12 +916,14 @@ tc_status launch_info(Launch& L) {
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_thread, k_thread, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_warp, k_warp, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_cta, k_cta, CTA_NT, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_stream, k_stream<STREAM_EPL>, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_merge, k_merge<STREAM_EPL>, 256, 0));
         c.occ_tasks = std::max(1, c.occ_tasks);
         c.occ_thread = std::max(1, c.occ_thread);
         c.occ_warp = std::max(1, c.occ_warp);
         c.occ_cta = std::max(1, c.occ_cta);
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_stream, STREAM_KERNEL, 256, 0));
         c.occ_stream = std::max(1, c.occ_stream);
+        c.occ_merge = std::max(1, c.occ_merge);
         c.ready = true;
     }
     L = c;
@@ -855,9 +932,26 @@ tc_status launch_info(Launch& L) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
-                      tc_census_t* out, uint32_t flags, cudaStream_t st) {
-    if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
+// Everything a census of a list of graphs needs that can be decided on the
+// host: resolved options, the graph (segment) table, capacities and the work
+// space layout.
+struct Layout {
+    tc_opts o;
+    int nseg = 0;
+    int64_t rows = 0;
+    uint64_t cap01 = 0, cap2 = 0;
+    std::vector<SegDev> segs;
+    std::vector<int64_t> pfx;
+    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_tl, o_ia, need;
+};
+
+// counters (uint32 words): [0..3] records per bin, [4] overflow flag,
+// [5] tile records, [8..9] row cursor (u64), [10..17] merged entries per bin
+// (u64), [20..23] cursors of the persistent merge queues
+constexpr int CTR_WORDS = 32;
+
+tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
+                      Layout& Lo) {
     tc_opts o;
     tc_opts_default(&o);
     if (opts_in) o = *opts_in;
@@ -867,153 +961,226 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         o.chunk > (o.split_cta ? TILE : WARP_LMAX))
         return fail(TC_ERR_ARG, "census: need 0 <= thr_thread <= thr_warp and 256 <= chunk <= "
                                 "1024 (warp tiles) or 3840 (split_cta = 1)");
-    // a warp holds both lists in shared memory: larger tasks go to CTA tiles
-    o.thr_warp = std::min(o.thr_warp, WARP_LMAX);
     if (o.stream_max < 0) return fail(TC_ERR_ARG, "census: stream_max < 0");
+    if (o.persistent && o.split_cta)
+        return fail(TC_ERR_ARG, "census: the persistent merge runs warp tiles (split_cta must be 0)");
+    // a warp holds both lists (or the short list) in shared memory
+    o.thr_warp = std::min(o.thr_warp, WARP_LMAX);
     o.stream_max = std::min(o.stream_max, STREAM_SMAX);
     const int nseg = (int)gidx.size();
-    std::vector<SegDev> segs((size_t)nseg);
-    std::vector<int64_t> pfx((size_t)nseg + 1, 0);
+    Lo.segs.assign((size_t)nseg, SegDev{});
+    Lo.pfx.assign((size_t)nseg + 1, 0);
     int64_t dyads = 0, merged = 0;
     for (int i = 0; i < nseg; ++i) {
         const int g = gidx[(size_t)i];
-        segs[(size_t)i].rb = set.voff[(size_t)g];
-        segs[(size_t)i].n = set.voff[(size_t)g + 1] - set.voff[(size_t)g];
-        segs[(size_t)i].slot = i;
-        segs[(size_t)i].pad = 0;
-        pfx[(size_t)i + 1] = pfx[(size_t)i] + segs[(size_t)i].n;
+        Lo.segs[(size_t)i].rb = set.voff[(size_t)g];
+        Lo.segs[(size_t)i].n = set.voff[(size_t)g + 1] - set.voff[(size_t)g];
+        Lo.segs[(size_t)i].slot = i;
+        Lo.segs[(size_t)i].pad = 0;
+        Lo.pfx[(size_t)i + 1] = Lo.pfx[(size_t)i] + Lo.segs[(size_t)i].n;
         dyads += set.stats[(size_t)g].dyads;
         merged += set.stats[(size_t)g].merged_entries;
     }
-    const int64_t rows = pfx[(size_t)nseg];
-    const uint64_t cap01 = (uint64_t)dyads + 1;
-    const uint64_t cap2 = (uint64_t)(merged / o.chunk) + (uint64_t)dyads + 1;
-    if (cap01 >= 0xffffffffull || cap2 >= 0xffffffffull)
+    Lo.o = o;
+    Lo.nseg = nseg;
+    Lo.rows = Lo.pfx[(size_t)nseg];
+    Lo.cap01 = (uint64_t)dyads + 1;
+    Lo.cap2 = (uint64_t)(merged / o.chunk) + (uint64_t)dyads + 1;
+    if (Lo.cap01 >= 0xffffffffull || Lo.cap2 >= 0xffffffffull)
         return fail(TC_ERR_UNSUPPORTED, "census: more than 2^32 tasks");
-    // work space layout
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
-    const size_t o_acc = take(sizeof(unsigned long long) * ACC * (size_t)nseg);
-    const size_t o_ctr = take(128);
-    const size_t o_seg = take(sizeof(SegDev) * (size_t)nseg);
-    const size_t o_pfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
-    const size_t o_out = take(sizeof(tc_census_t) * (size_t)nseg);
-    const size_t o_r0 = take(sizeof(uint4) * cap01);
-    const size_t o_r1 = take(sizeof(uint4) * cap01);
-    const size_t o_r2 = take(sizeof(uint4) * cap01);
-    const size_t o_r3 = take(sizeof(uint4) * cap01);
-    const size_t o_tl = take(sizeof(uint4) * cap2);
-    const size_t o_ia = take(sizeof(int32_t) * cap2);
-    const size_t need = off;
-    if (set.ws_bytes < need) {
-        dev_free(set.ws, st);
-        set.ws = nullptr;
-        set.ws_bytes = 0;
-        TC_CUDA(dev_alloc(&set.ws, need, st));
-        set.ws_bytes = need;
-    }
-    char* ws = (char*)set.ws;
-    unsigned long long* acc = (unsigned long long*)(ws + o_acc);
-    // counters: [0..3] records per bin, [4] overflow flag, [5] tile records,
-    // [8..9] row cursor (u64), [10..17] merged entries per bin (u64)
-    unsigned int* ctr = (unsigned int*)(ws + o_ctr);
-    SegDev* d_seg = (SegDev*)(ws + o_seg);
-    int64_t* d_pfx = (int64_t*)(ws + o_pfx);
-    tc_census_t* d_out = (flags & TC_OUT_DEVICE) ? out : (tc_census_t*)(ws + o_out);
+    Lo.o_acc = take(sizeof(unsigned long long) * ACC * (size_t)nseg);
+    Lo.o_ctr = take(sizeof(unsigned int) * CTR_WORDS);
+    Lo.o_seg = take(sizeof(SegDev) * (size_t)nseg);
+    Lo.o_pfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
+    Lo.o_out = take(sizeof(tc_census_t) * (size_t)nseg);
+    for (int b = 0; b < NBIN; ++b) Lo.o_r[b] = take(sizeof(uint4) * Lo.cap01);
+    Lo.o_tl = take(sizeof(uint4) * Lo.cap2);
+    Lo.o_ia = take(sizeof(int32_t) * Lo.cap2);
+    Lo.need = off;
+    return TC_OK;
+}
+
+// The graph table goes to the device once (a pageable copy: not part of a
+// captured graph).
+tc_status upload_layout(const Layout& Lo, char* ws, cudaStream_t st) {
+    TC_CUDA(cudaMemcpyAsync(ws + Lo.o_seg, Lo.segs.data(), sizeof(SegDev) * (size_t)Lo.nseg,
+                            cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaMemcpyAsync(ws + Lo.o_pfx, Lo.pfx.data(), sizeof(int64_t) * ((size_t)Lo.nseg + 1),
+                            cudaMemcpyHostToDevice, st));
+    return TC_OK;
+}
+
+// The census itself: one memset and the kernels, all on `st` (capturable).
+tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_census_t* d_out, cudaStream_t st,
+                         ProfileEvents* pe) {
+    const tc_opts& o = Lo.o;
+    unsigned long long* acc = (unsigned long long*)(ws + Lo.o_acc);
+    unsigned int* ctr = (unsigned int*)(ws + Lo.o_ctr);
+    const SegDev* d_seg = (const SegDev*)(ws + Lo.o_seg);
+    const int64_t* d_pfx = (const int64_t*)(ws + Lo.o_pfx);
     Bins bins;
-    bins.rec[0] = (uint4*)(ws + o_r0);
-    bins.rec[1] = (uint4*)(ws + o_r1);
-    bins.rec[2] = (uint4*)(ws + o_r2);
-    bins.rec[3] = (uint4*)(ws + o_r3);
-    bins.cap[0] = bins.cap[1] = bins.cap[2] = bins.cap[3] = (uint32_t)cap01;
-    uint4* d_tiles = (uint4*)(ws + o_tl);
+    for (int b = 0; b < NBIN; ++b) {
+        bins.rec[b] = (uint4*)(ws + Lo.o_r[b]);
+        bins.cap[b] = (uint32_t)Lo.cap01;
+    }
     bins.cnt = ctr;
     bins.overflow = (int*)(ctr + 4);
-    unsigned long long* cursor = (unsigned long long*)(ctr + 8);
     bins.entries = (unsigned long long*)(ctr + 10);
-    int32_t* d_ia = (int32_t*)(ws + o_ia);
-
-    TC_CUDA(cudaMemcpyAsync(d_seg, segs.data(), sizeof(SegDev) * (size_t)nseg, cudaMemcpyHostToDevice, st));
-    TC_CUDA(cudaMemcpyAsync(d_pfx, pfx.data(), sizeof(int64_t) * ((size_t)nseg + 1), cudaMemcpyHostToDevice, st));
-    TC_CUDA(cudaMemsetAsync(ws, 0, o_seg, st));  // accumulators + counters
-
+    unsigned long long* cursor = (unsigned long long*)(ctr + 8);
+    uint4* d_tiles = (uint4*)(ws + Lo.o_tl);
+    int32_t* d_ia = (int32_t*)(ws + Lo.o_ia);
+    const uint32_t cap2 = (uint32_t)Lo.cap2;
     Launch L;
     if (tc_status s = launch_info(L); s != TC_OK) return s;
-    BinParams bp{o.thr_thread, o.thr_warp, o.stream_max};
-    ProfileEvents* pe = nullptr;
-    if (o.profile) {
-        if (tc_status s = profile_events(&pe); s != TC_OK) return s;
-    }
+    const BinParams bp{o.thr_thread, o.thr_warp, o.stream_max};
     auto mark = [&](int k) {
         if (pe) cudaEventRecord(pe->ev[k], st);
     };
+    TC_CUDA(cudaMemsetAsync(ws, 0, Lo.o_seg, st));  // accumulators + counters
     mark(0);
-    if (rows > 0) {
-        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, nseg, rows, bp,
-                                                     bins, acc, cursor);
+    if (Lo.rows > 0) {
+        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
+                                                     bp, bins, acc, cursor);
         TC_CUDA(cudaGetLastError());
         mark(1);
         k_split<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], o.chunk,
-                                            d_tiles, d_ia, ctr + 5, (uint32_t)cap2, bins.overflow);
+                                            d_tiles, d_ia, ctr + 5, cap2, bins.overflow);
         TC_CUDA(cudaGetLastError());
         mark(2);
-        if (o.split_cta)
-            k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5,
-                                                        (uint32_t)cap2, o.chunk, acc);
-        else
-            k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5,
-                                                        (uint32_t)cap2, o.chunk, acc);
-        TC_CUDA(cudaGetLastError());
-        mark(3);
-        STREAM_KERNEL<<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[3], ctr + 3,
-                                                        bins.cap[3], acc);
-        TC_CUDA(cudaGetLastError());
-        mark(4);
-        k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], nullptr, ctr + 1,
-                                                            bins.cap[1], 0, acc);
-        TC_CUDA(cudaGetLastError());
-        mark(5);
-        k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
-                                                        bins.cap[0], acc);
-        TC_CUDA(cudaGetLastError());
+        if (o.persistent) {
+            MergeQueues q;
+            for (int b = 0; b < NBIN; ++b) {
+                q.rec[b] = bins.rec[b];
+                q.cap[b] = bins.cap[b];
+            }
+            q.cnt = ctr;
+            q.tiles = d_tiles;
+            q.ia = d_ia;
+            q.ntile = ctr + 5;
+            q.tile_cap = cap2;
+            q.tile = o.chunk;
+            q.cursor = ctr + 20;
+            k_merge<STREAM_EPL><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
+            TC_CUDA(cudaGetLastError());
+            mark(3);
+            mark(4);
+            mark(5);
+        } else {
+            if (o.split_cta)
+                k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5, cap2,
+                                                            o.chunk, acc);
+            else
+                k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5, cap2,
+                                                            o.chunk, acc);
+            TC_CUDA(cudaGetLastError());
+            mark(3);
+            k_stream<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[3],
+                                                                        ctr + 3, bins.cap[3], acc);
+            TC_CUDA(cudaGetLastError());
+            mark(4);
+            k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], nullptr, ctr + 1,
+                                                        bins.cap[1], 0, acc);
+            TC_CUDA(cudaGetLastError());
+            mark(5);
+            k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
+                                                            bins.cap[0], acc);
+            TC_CUDA(cudaGetLastError());
+        }
+    } else {
+        for (int k = 1; k <= 5; ++k) mark(k);
     }
     mark(6);
-    k_fold<<<(nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, nseg, d_out);
+    k_fold<<<(Lo.nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, Lo.nseg, d_out);
     TC_CUDA(cudaGetLastError());
     mark(7);
+    return TC_OK;
+}
+
+int census_launches(const Layout& Lo) {
+    if (Lo.rows == 0) return 1;
+    return Lo.o.persistent ? 4 : 7;
+}
+
+tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cudaStream_t st) {
+    unsigned int c[CTR_WORDS];
+    TC_CUDA(cudaMemcpyAsync(c, ws + Lo.o_ctr, sizeof c, cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    tc_profile_t& P = g_profile;
+    P = tc_profile_t{};
+    float ms[8] = {0};
+    for (int k = 0; k < 7; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
+    TC_CUDA(cudaEventElapsedTime(&ms[7], pe->ev[0], pe->ev[7]));
+    P.ms_tasks = ms[0];
+    P.ms_split = ms[1];
+    if (Lo.o.persistent) {
+        P.ms_merge = ms[2];
+    } else {
+        P.ms_tiles = ms[2];
+        P.ms_stream = ms[3];
+        P.ms_warp = ms[4];
+        P.ms_thread = ms[5];
+        P.ms_merge = ms[2] + ms[3] + ms[4] + ms[5];
+    }
+    P.ms_fold = ms[6];
+    P.ms_total = ms[7];
+    P.launches = census_launches(Lo);
+    for (int b = 0; b < NBIN; ++b) {
+        P.bin_tasks[b] = c[b];
+        P.bin_entries[b] = (int64_t)(((unsigned long long)c[10 + 2 * b + 1] << 32) | c[10 + 2 * b]);
+    }
+    P.chunks = c[5];
+    g_profile_valid = true;
+    return TC_OK;
+}
+
+tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
+                      tc_census_t* out, uint32_t flags, cudaStream_t st) {
+    if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
+    Layout Lo;
+    if (tc_status s = make_layout(set, gidx, opts_in, Lo); s != TC_OK) return s;
+    if (set.ws_bytes < Lo.need) {
+        dev_free(set.ws, st);
+        set.ws = nullptr;
+        set.ws_bytes = 0;
+        TC_CUDA(dev_alloc(&set.ws, Lo.need, st));
+        set.ws_bytes = Lo.need;
+    }
+    char* ws = (char*)set.ws;
+    tc_census_t* d_out = (flags & TC_OUT_DEVICE) ? out : (tc_census_t*)(ws + Lo.o_out);
+    ProfileEvents* pe = nullptr;
+    if (Lo.o.profile) {
+        if (tc_status s = profile_events(&pe); s != TC_OK) return s;
+    }
+    if (tc_status s = upload_layout(Lo, ws, st); s != TC_OK) return s;
+    if (tc_status s = enqueue_census(set, Lo, ws, d_out, st, pe); s != TC_OK) return s;
     if (pe) {
-        unsigned int c[18];
-        TC_CUDA(cudaMemcpyAsync(c, ctr, sizeof c, cudaMemcpyDeviceToHost, st));
-        TC_CUDA(cudaStreamSynchronize(st));
-        tc_profile_t& P = g_profile;
-        P = tc_profile_t{};
-        float ms[8] = {0};
-        for (int k = 0; k < 7; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
-        TC_CUDA(cudaEventElapsedTime(&ms[7], pe->ev[0], pe->ev[7]));
-        if (rows > 0) {
-            P.ms_tasks = ms[0];
-            P.ms_split = ms[1];
-            P.ms_tiles = ms[2];
-            P.ms_stream = ms[3];
-            P.ms_warp = ms[4];
-            P.ms_thread = ms[5];
-        }
-        P.ms_fold = ms[6];
-        P.ms_total = ms[7];
-        P.launches = rows > 0 ? 7 : 1;
-        for (int b = 0; b < NBIN; ++b) {
-            P.bin_tasks[b] = c[b];
-            P.bin_entries[b] = (int64_t)(((unsigned long long)c[10 + 2 * b + 1] << 32) | c[10 + 2 * b]);
-        }
-        P.chunks = c[5];
-        g_profile_valid = true;
+        if (tc_status s = read_profile(Lo, ws, pe, st); s != TC_OK) return s;
     }
     if (!(flags & TC_OUT_DEVICE)) {
         int ovf = 0;
-        TC_CUDA(cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * (size_t)nseg, cudaMemcpyDeviceToHost, st));
-        TC_CUDA(cudaMemcpyAsync(&ovf, bins.overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * (size_t)Lo.nseg, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaMemcpyAsync(&ovf, ws + Lo.o_ctr + 4 * sizeof(unsigned int), sizeof(int),
+                                cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         if (ovf) return fail(TC_ERR_CUDA, "census: task bin overflow (internal error)");
+    }
+    return TC_OK;
+}
+
+std::vector<int32_t> handle_indices(int32_t G, const tc_graph* gs) {
+    std::vector<int32_t> idx((size_t)G);
+    for (int32_t i = 0; i < G; ++i) idx[(size_t)i] = gs[i]->index;
+    return idx;
+}
+
+tc_status check_handles(int32_t G, const tc_graph* gs, const char* who) {
+    if (G < 0 || (G > 0 && !gs)) return fail(TC_ERR_ARG, std::string(who) + ": bad arguments");
+    for (int32_t i = 0; i < G; ++i) {
+        if (!gs[i]) return fail(TC_ERR_ARG, std::string(who) + ": null handle");
+        if (gs[i]->set != gs[0]->set)
+            return fail(TC_ERR_UNSUPPORTED, std::string(who) + ": handles come from different builds");
     }
     return TC_OK;
 }
@@ -1049,14 +1216,8 @@ tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts, 
     if (G < 0 || (G > 0 && (!gs || !out))) return tc::fail(TC_ERR_ARG, "tc_census_batched: bad arguments");
     if (G == 0) return TC_OK;
     try {
-        std::vector<int32_t> idx((size_t)G);
-        for (int32_t i = 0; i < G; ++i) {
-            if (!gs[i]) return tc::fail(TC_ERR_ARG, "tc_census_batched: null handle");
-            if (gs[i]->set != gs[0]->set)
-                return tc::fail(TC_ERR_UNSUPPORTED, "tc_census_batched: handles come from different builds");
-            idx[(size_t)i] = gs[i]->index;
-        }
-        return tc::census_impl(*gs[0]->set, idx, opts, out, flags, (cudaStream_t)stream);
+        if (tc_status s = tc::check_handles(G, gs, "tc_census_batched"); s != TC_OK) return s;
+        return tc::census_impl(*gs[0]->set, tc::handle_indices(G, gs), opts, out, flags, (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {
         return tc::fail(TC_ERR_OOM, "tc_census_batched: host allocation failed");
     } catch (...) {
@@ -1184,3 +1345,98 @@ extern "C" tc_status tc_census_csr_noalloc(int32_t n, const int64_t* row_ptr, co
         return tc::fail(TC_ERR_CUDA, "tc_census_csr_noalloc: unexpected exception");
     }
 }
+
+// ------------------------------------------------------------ batch plans --
+struct tc_plan_s {
+    std::shared_ptr<tc::GraphSet> set;
+    tc::Layout lo;
+    char* ws = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace tc {
+namespace {
+
+tc_status plan_create(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_census_t* out, cudaStream_t st,
+                      tc_plan* result) {
+    if (G < 1 || !gs || !out || !result) return fail(TC_ERR_ARG, "tc_plan_create: bad arguments");
+    if (tc_status s = check_handles(G, gs, "tc_plan_create"); s != TC_OK) return s;
+    if (opts && opts->profile) return fail(TC_ERR_ARG, "tc_plan_create: profile must be 0 in a plan");
+    std::unique_ptr<tc_plan_s> p(new tc_plan_s);
+    p->set = gs[0]->set;
+    if (tc_status s = make_layout(*p->set, handle_indices(G, gs), opts, p->lo); s != TC_OK) return s;
+    Launch L;
+    if (tc_status s = launch_info(L); s != TC_OK) return s;
+    TC_CUDA(dev_alloc((void**)&p->ws, p->lo.need, st));
+    struct Guard {
+        tc_plan_s* p;
+        cudaStream_t st;
+        bool ok = false;
+        ~Guard() {
+            if (!ok) {
+                cudaStreamSynchronize(st);
+                if (p->exec) cudaGraphExecDestroy(p->exec);
+                if (p->graph) cudaGraphDestroy(p->graph);
+                dev_free(p->ws, st);
+                cudaStreamSynchronize(st);
+            }
+        }
+    } guard{p.get(), st};
+    if (tc_status s = upload_layout(p->lo, p->ws, st); s != TC_OK) return s;
+    TC_CUDA(cudaStreamSynchronize(st));
+    cudaStream_t cap = nullptr;
+    TC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    tc_status s = TC_OK;
+    if (e == cudaSuccess) {
+        s = enqueue_census(*p->set, p->lo, p->ws, out, cap, nullptr);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (s == TC_OK && e2 != cudaSuccess) s = cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
+        p->graph = g;
+    } else {
+        s = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+    }
+    cudaStreamDestroy(cap);
+    if (s != TC_OK) return s;
+    TC_CUDA(cudaGraphInstantiate(&p->exec, p->graph, 0));
+    guard.ok = true;
+    *result = p.release();
+    return TC_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" {
+
+tc_status tc_plan_create(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_census_t* out, void* stream,
+                         tc_plan* plan) {
+    if (plan) *plan = nullptr;
+    try {
+        return tc::plan_create(G, gs, opts, out, (cudaStream_t)stream, plan);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_plan_create: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_plan_create: unexpected exception");
+    }
+}
+
+tc_status tc_plan_run(tc_plan plan, void* stream) {
+    if (!plan) return tc::fail(TC_ERR_ARG, "tc_plan_run: null plan");
+    TC_CUDA(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+    return TC_OK;
+}
+
+void tc_plan_free(tc_plan plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    tc::dev_free(plan->ws, 0);
+    cudaStreamSynchronize(0);
+    delete plan;
+}
+
+}  // extern "C"

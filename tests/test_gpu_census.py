@@ -24,10 +24,13 @@ BINS = {
     "stream_all": dict(thr_thread=0, thr_warp=0, stream_max=1024),
     "thread": dict(thr_thread=BIG, thr_warp=BIG),
     "warp": dict(thr_thread=0, thr_warp=BIG, stream_max=0),
-    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1, stream_max=0),
+    "separate": dict(persistent=0),
+    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1, stream_max=0, persistent=0),
     "wtile": dict(thr_thread=0, thr_warp=0, chunk=256, stream_max=0),
-    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1, stream_max=8),
+    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1, stream_max=8, persistent=0),
     "mixed": dict(thr_thread=8, thr_warp=40, chunk=512),
+    "persistent": dict(persistent=1),
+    "persistent_small": dict(persistent=1, thr_thread=8, thr_warp=64, chunk=256, stream_max=32),
 }
 
 
@@ -271,3 +274,49 @@ def test_repeated_calls_are_identical():
             assert tc.tc_census(g) == first
     finally:
         tc.tc_graph_free(g)
+
+
+def test_batch_plan_replays_match_oracle():
+    import torch
+    rng = np.random.default_rng(123)
+    arcs, ns = [], []
+    for k in range(40):
+        n = int(rng.integers(3, 300))
+        if k % 7 == 0:
+            s_, d_ = hub_graph(rng, max(n, 2600), 1, 2500, 2000, 0.2)
+            n = max(n, 2600)
+        else:
+            s_, d_ = rand_graph(rng, n, float(rng.choice([0.01, 0.05, 0.2])), 0.3)
+        arcs.append((s_, d_))
+        ns.append(n)
+    off = np.cumsum([0] + [a[0].size for a in arcs])
+    src = np.concatenate([a[0] for a in arcs]).astype(np.int32)
+    dst = np.concatenate([a[1] for a in arcs]).astype(np.int32)
+    want = [oracle.census(n, a[0], a[1], threads=THREADS) for n, a in zip(ns, arcs)]
+    gs = tc.tc_graph_build_batched(ns, off, src, dst)
+    try:
+        for name in ("default", "persistent", "persistent_small"):
+            out = torch.zeros(17 * len(gs), dtype=torch.int64, device="cuda")
+            plan = tc.tc_plan_create(gs, out, opts(name))
+            try:
+                for _ in range(2):
+                    out.zero_()
+                    tc.tc_plan_run(plan)
+                    torch.cuda.synchronize()
+                    words = out.cpu().tolist()
+                    got = [tc.census_from_device_words(words[17 * i:17 * i + 17]) for i in range(len(gs))]
+                    assert got == want, name
+            finally:
+                tc.tc_plan_free(plan)
+        # a plan over a reordered subset writes results in its own order
+        pick = [5, 0, 33, 7]
+        out = torch.zeros(17 * len(pick), dtype=torch.int64, device="cuda")
+        plan = tc.tc_plan_create([gs[i] for i in pick], out)
+        tc.tc_plan_run(plan)
+        torch.cuda.synchronize()
+        words = out.cpu().tolist()
+        tc.tc_plan_free(plan)
+        assert [tc.census_from_device_words(words[17 * i:17 * i + 17]) for i in range(4)] == [want[i] for i in pick]
+    finally:
+        for g in gs:
+            tc.tc_graph_free(g)
