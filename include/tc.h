@@ -246,6 +246,19 @@ tc_status tc_plan_create(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_
 tc_status tc_plan_run(tc_plan plan, void* stream);
 void tc_plan_free(tc_plan plan);
 
+/*
+ * tc_autotune -- pick census options for a list of graphs by measurement:
+ * coordinate descent over thr_thread, thr_warp, stream_max, chunk and
+ * persistent (two passes), each trial a full census timed with CUDA events
+ * on `stream` (best of two runs after a warm-up).  `base` (NULL = defaults)
+ * is the starting point; max_trials <= 0 means no limit.  *best receives the
+ * fastest options, *best_ms their time and *trials the number of options
+ * timed.  The counts never depend on the options, only the time does.
+ * Handles must come from one build, as for tc_census_batched.
+ */
+tc_status tc_autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t max_trials, void* stream,
+                      tc_opts* best, float* best_ms, int32_t* trials);
+
 /* Release a graph handle (synchronises the device first). NULL is a no-op. */
 void tc_graph_free(tc_graph g);
 

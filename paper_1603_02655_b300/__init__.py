@@ -37,7 +37,7 @@ TC_OUT_DEVICE = 2
 EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
            "tc_graph_export", "tc_census", "tc_census_batched", "tc_triad_type",
            "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile",
-           "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free")
+           "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free", "tc_autotune")
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
 
@@ -122,6 +122,8 @@ def load():
     lib.tc_plan_run.restype = ctypes.c_int
     lib.tc_plan_free.argtypes = [P]
     lib.tc_plan_free.restype = None
+    lib.tc_autotune.argtypes = [i32, P, P, i32, P, P, P, P]
+    lib.tc_autotune.restype = ctypes.c_int
     lib.tc_graph_free.argtypes = [P]
     lib.tc_graph_free.restype = None
     lib.tc_status_str.argtypes = [ctypes.c_int]
@@ -300,6 +302,67 @@ def tc_plan_run(plan: int, stream=None) -> None:
 def tc_plan_free(plan: int) -> None:
     if plan:
         load().tc_plan_free(plan)
+
+
+def tc_autotune(gs, base: TcOpts | None = None, max_trials: int = 0, stream=None):
+    """(best options, their census time in ms, options timed) for graphs gs."""
+    G = len(gs)
+    arr = (ctypes.c_void_p * max(G, 1))(*gs)
+    best = TcOpts()
+    ms = ctypes.c_float()
+    n = ctypes.c_int32()
+    pb = ctypes.byref(base) if base is not None else None
+    _check(load().tc_autotune(G, arr, pb, int(max_trials), _stream(stream), ctypes.byref(best),
+                              ctypes.byref(ms), ctypes.byref(n)), "tc_autotune")
+    return best, float(ms.value), int(n.value)
+
+
+TUNED_FIELDS = ("bin_mode", "thr_thread", "thr_warp", "chunk", "split_cta", "stream_max", "persistent")
+
+
+def graph_class(stats: list) -> str:
+    """Coarse class of a list of graphs for the autotune cache: count,
+    total merged entries, mean task length and largest degree (log2 buckets)."""
+    import math
+    G = len(stats)
+    merged = sum(s["merged_entries"] for s in stats)
+    dyads = sum(s["dyads"] for s in stats)
+    maxd = max((s["max_degree"] for s in stats), default=0)
+    lg = lambda x: int(round(math.log2(x))) if x > 0 else 0  # noqa: E731
+    return f"G{lg(G)}-m{lg(merged)}-t{lg(merged / dyads) if dyads else 0}-d{lg(maxd)}"
+
+
+def autotune(gs, cache_path: str | None = None, base: TcOpts | None = None, max_trials: int = 0,
+             stream=None, retune: bool = False) -> TcOpts:
+    """Autotuned census options for graphs gs, cached as JSON per device name
+    and graph class (default file: $TC_AUTOTUNE_CACHE or
+    ~/.cache/tc_b300/autotune.json)."""
+    import json
+    import torch
+    path = cache_path or os.environ.get("TC_AUTOTUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "tc_b300", "autotune.json")
+    dev = torch.cuda.get_device_name()
+    key = graph_class([tc_graph_stats(g) for g in gs])
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    hit = cache.get(dev, {}).get(key)
+    if hit and not retune:
+        return tc_opts_default(**{k: hit[k] for k in TUNED_FIELDS})
+    best, ms, trials = tc_autotune(gs, base, max_trials, stream)
+    entry = {k: int(getattr(best, k)) for k in TUNED_FIELDS}
+    entry.update(ms=ms, trials=trials)
+    cache.setdefault(dev, {})[key] = entry
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return best
 
 
 def tc_graph_free(g: int) -> None:

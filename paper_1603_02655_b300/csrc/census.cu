@@ -1440,3 +1440,102 @@ void tc_plan_free(tc_plan plan) {
 }
 
 }  // extern "C"
+
+// -------------------------------------------------------------- autotuner --
+// Coordinate descent over the binning and launch options: starting from
+// `base`, each option in turn takes the candidate value with the smallest
+// measured census time (CUDA events, best of two runs after one warm-up),
+// the others held at their current best.  Every trial computes the full
+// census; the counts do not depend on the options.
+namespace tc {
+namespace {
+
+tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t max_trials, cudaStream_t st,
+                   tc_opts* best, float* best_ms, int32_t* trials_out) {
+    if (G < 1 || !gs || !best) return fail(TC_ERR_ARG, "tc_autotune: bad arguments");
+    if (tc_status s = check_handles(G, gs, "tc_autotune"); s != TC_OK) return s;
+    GraphSet& set = *gs[0]->set;
+    const std::vector<int32_t> idx = handle_indices(G, gs);
+    tc_opts cur;
+    tc_opts_default(&cur);
+    if (base) cur = *base;
+    cur.profile = 0;
+    tc_census_t* d_out = nullptr;
+    TC_CUDA(dev_alloc((void**)&d_out, sizeof(tc_census_t) * (size_t)G, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TC_CUDA(cudaEventCreate(&e0));
+    TC_CUDA(cudaEventCreate(&e1));
+    struct Cleanup {
+        cudaEvent_t a, b;
+        tc_census_t* p;
+        cudaStream_t s;
+        ~Cleanup() {
+            cudaStreamSynchronize(s);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            dev_free(p, s);
+        }
+    } cleanup{e0, e1, d_out, st};
+    int trials = 0;
+    auto timeit = [&](const tc_opts& o, float& ms) -> tc_status {
+        float bestv = 3.4e38f;
+        for (int r = 0; r < 3; ++r) {
+            TC_CUDA(cudaEventRecord(e0, st));
+            if (tc_status s = census_impl(set, idx, &o, d_out, TC_OUT_DEVICE, st); s != TC_OK) return s;
+            TC_CUDA(cudaEventRecord(e1, st));
+            TC_CUDA(cudaEventSynchronize(e1));
+            float t = 0;
+            TC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            if (r > 0) bestv = std::min(bestv, t);
+        }
+        ms = bestv;
+        ++trials;
+        return TC_OK;
+    };
+    float cur_ms = 0;
+    if (tc_status s = timeit(cur, cur_ms); s != TC_OK) return s;
+    const int32_t thr_thread_c[] = {0, 16, 32, 48, 64, 96, 128, 192};
+    const int32_t thr_warp_c[] = {64, 128, 256, 512, 1024};
+    const int32_t stream_c[] = {0, 64, 256, 1024};
+    const int32_t chunk_c[] = {256, 512, 1024};
+    const int32_t pers_c[] = {0, 1};
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int field = 0; field < 5; ++field) {
+            const int32_t* cand = field == 0 ? thr_thread_c : field == 1 ? thr_warp_c : field == 2 ? stream_c
+                                : field == 3 ? chunk_c : pers_c;
+            const int nc = field == 0 ? 8 : field == 1 ? 5 : field == 2 ? 4 : field == 3 ? 3 : 2;
+            for (int k = 0; k < nc; ++k) {
+                if (max_trials > 0 && trials >= max_trials) break;
+                tc_opts o = cur;
+                int32_t* f = field == 0 ? &o.thr_thread : field == 1 ? &o.thr_warp : field == 2 ? &o.stream_max
+                           : field == 3 ? &o.chunk : &o.persistent;
+                if (*f == cand[k]) continue;
+                *f = cand[k];
+                if (o.thr_thread > o.thr_warp) continue;
+                if (o.persistent) o.split_cta = 0;
+                float ms = 0;
+                if (tc_status s = timeit(o, ms); s != TC_OK) return s;
+                if (ms < cur_ms) {
+                    cur = o;
+                    cur_ms = ms;
+                }
+            }
+        }
+    }
+    *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    if (trials_out) *trials_out = trials;
+    return TC_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" tc_status tc_autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t max_trials, void* stream,
+                                 tc_opts* best, float* best_ms, int32_t* trials) {
+    try {
+        return tc::autotune(G, gs, base, max_trials, (cudaStream_t)stream, best, best_ms, trials);
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_autotune: unexpected exception");
+    }
+}

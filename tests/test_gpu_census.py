@@ -320,3 +320,22 @@ def test_batch_plan_replays_match_oracle():
     finally:
         for g in gs:
             tc.tc_graph_free(g)
+
+
+def test_autotune_returns_valid_options_and_same_counts(tmp_path):
+    rng = np.random.default_rng(8)
+    src, dst = hub_graph(rng, 4000, 2, 2000, 15000, 0.3)
+    want = oracle.census(4000, src, dst, threads=THREADS)
+    g = tc.tc_graph_build(4000, src, dst)
+    try:
+        best, ms, trials = tc.tc_autotune([g], max_trials=12)
+        assert 1 <= trials <= 12 and ms > 0
+        assert 0 <= best.thr_thread <= best.thr_warp and 256 <= best.chunk <= 1024
+        assert tc.tc_census(g, best) == want
+        cache = tmp_path / "tune.json"
+        o1 = tc.autotune([g], cache_path=str(cache), max_trials=6)
+        o2 = tc.autotune([g], cache_path=str(cache), max_trials=6)  # served from the cache
+        assert [getattr(o1, k) for k in tc.TUNED_FIELDS] == [getattr(o2, k) for k in tc.TUNED_FIELDS]
+        assert tc.tc_census(g, o2) == want
+    finally:
+        tc.tc_graph_free(g)
