@@ -259,6 +259,48 @@ void tc_plan_free(tc_plan plan);
 tc_status tc_autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t max_trials, void* stream,
                       tc_opts* best, float* best_ms, int32_t* trials);
 
+/*
+ * Learned cost model for task binning (opts.bin_mode = TC_BIN_MLP): an MLP
+ * 8 -> 32 -> 32 -> 4 (ReLU) predicting log2 of the cycles a canonical-dyad
+ * task takes in each bin (0 thread, 1 warp, 2 split tiles, 3 streamed).
+ * Binning picks the cheapest eligible bin (a thread task costs 1/32 of a
+ * warp).  The thesis bins by the degree sum |N(u)|+|N(v)|-2 (Sec. 4.3.1):
+ * that rule remains the fallback while no model is installed.
+ * Parameters: float[TC_MLP_NPARAM] = W1[32][8] b1[32] W2[32][32] b2[32]
+ * W3[4][32] b3[4] (row = output neuron).  Features (float[8] per task,
+ * shorter list s first): log2(1+d_s)/20, log2(1+d_g)/20, their difference,
+ * log2(1+d_s+d_g)/20, mutual and out-only fractions of s and g.
+ *
+ *   tc_cost_sample      run the census with every eligible task forced into
+ *                       `bin`, recording {u, v, bin, cycles} (int32 x 4, u/v
+ *                       global rows) for tasks whose endpoint hash has
+ *                       (hash & mask) == 0, at most `cap` records into the
+ *                       device buffer `samples`; *n = records written.  Tiles
+ *                       of a split task record one line each (same u, v).
+ *   tc_cost_features    device features float[n][8] of tasks uv int32[n][2]
+ *                       (global rows of the graph's build).
+ *   tc_mlp_loss_grad    loss 1/n sum 0.5 (out[bin_i] - target_i)^2 and its
+ *                       FP32 gradient float[TC_MLP_NPARAM] (device buffers).
+ *   tc_mlp_train        `steps` Adam steps (lr, betas 0.9/0.999) on batches
+ *                       of `batch` samples drawn with SplitMix64(seed); *loss
+ *                       (device float) = loss over all n samples at the end.
+ *   tc_mlp_predict      out float[n][4] from feat, in FP32 or, with
+ *                       half_precision, the FP16 arithmetic binning uses.
+ *   tc_cost_model_load  install host parameters on the current device for
+ *                       TC_BIN_MLP (NULL uninstalls).
+ */
+#define TC_MLP_NPARAM 1476
+tc_status tc_cost_sample(int32_t G, const tc_graph* gs, int32_t bin, int32_t mask, int32_t cap,
+                         int32_t* samples, int32_t* n, void* stream);
+tc_status tc_cost_features(tc_graph g, const int32_t* uv, int32_t n, float* feat, void* stream);
+tc_status tc_mlp_loss_grad(const float* params, const float* feat, const int32_t* bin, const float* target,
+                           int32_t n, float* grad, float* loss, void* stream);
+tc_status tc_mlp_train(float* params, const float* feat, const int32_t* bin, const float* target, int32_t n,
+                       int32_t steps, int32_t batch, float lr, uint64_t seed, float* loss, void* stream);
+tc_status tc_mlp_predict(const float* params, const float* feat, int32_t n, int32_t half_precision, float* out,
+                         void* stream);
+tc_status tc_cost_model_load(const float* params);
+
 /* Release a graph handle (synchronises the device first). NULL is a no-op. */
 void tc_graph_free(tc_graph g);
 

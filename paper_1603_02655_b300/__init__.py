@@ -37,7 +37,10 @@ TC_OUT_DEVICE = 2
 EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
            "tc_graph_export", "tc_census", "tc_census_batched", "tc_triad_type",
            "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile",
-           "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free", "tc_autotune")
+           "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free", "tc_autotune",
+           "tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
+           "tc_cost_model_load")
+TC_MLP_NPARAM = 1476
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
 
@@ -124,6 +127,15 @@ def load():
     lib.tc_plan_free.restype = None
     lib.tc_autotune.argtypes = [i32, P, P, i32, P, P, P, P]
     lib.tc_autotune.restype = ctypes.c_int
+    lib.tc_cost_sample.argtypes = [i32, P, i32, i32, i32, P, P, P]
+    lib.tc_cost_features.argtypes = [P, P, i32, P, P]
+    lib.tc_mlp_loss_grad.argtypes = [P, P, P, P, i32, P, P, P]
+    lib.tc_mlp_train.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, P, P]
+    lib.tc_mlp_predict.argtypes = [P, P, i32, i32, P, P]
+    lib.tc_cost_model_load.argtypes = [P]
+    for name in ("tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
+                 "tc_cost_model_load"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.tc_graph_free.argtypes = [P]
     lib.tc_graph_free.restype = None
     lib.tc_status_str.argtypes = [ctypes.c_int]
@@ -363,6 +375,71 @@ def autotune(gs, cache_path: str | None = None, base: TcOpts | None = None, max_
         json.dump(cache, f, indent=1, sort_keys=True)
     os.replace(tmp, path)
     return best
+
+
+def tc_cost_sample(gs, bin_: int, mask: int, cap: int, stream=None):
+    """Instrumented census with every eligible task forced into bin `bin_`:
+    an int32 CUDA tensor [n, 4] of {u, v, bin, cycles} records."""
+    import torch
+    G = len(gs)
+    arr = (ctypes.c_void_p * max(G, 1))(*gs)
+    buf = torch.zeros((max(cap, 1), 4), dtype=torch.int32, device="cuda")
+    n = ctypes.c_int32()
+    _check(load().tc_cost_sample(G, arr, int(bin_), int(mask), int(cap), buf.data_ptr(), ctypes.byref(n),
+                                 _stream(stream)), "tc_cost_sample")
+    return buf[: n.value]
+
+
+def tc_cost_features(g: int, uv, stream=None):
+    """Features float32 CUDA tensor [n, 8] of tasks uv (int32 CUDA tensor [n, 2])."""
+    import torch
+    uv = uv.contiguous()
+    out = torch.empty((uv.shape[0], 8), dtype=torch.float32, device="cuda")
+    _check(load().tc_cost_features(g, uv.data_ptr(), int(uv.shape[0]), out.data_ptr(), _stream(stream)),
+           "tc_cost_features")
+    return out
+
+
+def tc_mlp_loss_grad(params, feat, bins, target, stream=None):
+    """(loss, gradient) of the cost-model loss; CUDA tensors in, FP32 out."""
+    import torch
+    grad = torch.empty(TC_MLP_NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(load().tc_mlp_loss_grad(params.data_ptr(), feat.data_ptr(), bins.data_ptr(), target.data_ptr(),
+                                   int(feat.shape[0]), grad.data_ptr(), loss.data_ptr(), _stream(stream)),
+           "tc_mlp_loss_grad")
+    return float(loss.item()), grad
+
+
+def tc_mlp_train(params, feat, bins, target, steps: int, batch: int, lr: float, seed: int = 1, stream=None):
+    """Adam steps on `params` (float32 CUDA tensor, updated in place); returns
+    the loss over all samples at the end."""
+    import torch
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(load().tc_mlp_train(params.data_ptr(), feat.data_ptr(), bins.data_ptr(), target.data_ptr(),
+                               int(feat.shape[0]), int(steps), int(batch), float(lr), int(seed),
+                               loss.data_ptr(), _stream(stream)), "tc_mlp_train")
+    return float(loss.item())
+
+
+def tc_mlp_predict(params, feat, half_precision: bool = True, stream=None):
+    import torch
+    out = torch.empty((feat.shape[0], 4), dtype=torch.float32, device="cuda")
+    _check(load().tc_mlp_predict(params.data_ptr(), feat.data_ptr(), int(feat.shape[0]), int(half_precision),
+                                 out.data_ptr(), _stream(stream)), "tc_mlp_predict")
+    return out
+
+
+def tc_cost_model_load(params) -> None:
+    """Install cost-model parameters (host float32, 1476 values) on the
+    current device for TC_BIN_MLP; None uninstalls."""
+    if params is None:
+        _check(load().tc_cost_model_load(None), "tc_cost_model_load")
+        return
+    a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    if a.size != TC_MLP_NPARAM:
+        raise ValueError(f"expected {TC_MLP_NPARAM} parameters")
+    _check(load().tc_cost_model_load(a.ctypes.data), "tc_cost_model_load")
 
 
 def tc_graph_free(g: int) -> None:

@@ -30,12 +30,38 @@
 #include <cstring>
 #include <mutex>
 
+#include "mlp.cuh"
 #include "tc_internal.cuh"
 
 namespace tc {
 namespace {
 
 constexpr int WARPS = 8;  // warps per 256-thread block
+constexpr int WARP_LMAX_T = 1024;   // = WARP_LMAX (whole-task warp bin limit)
+constexpr int STREAM_SMAX_T = 1024; // = STREAM_SMAX (short-list limit of the stream bin)
+
+// Per-task timing records of an instrumented census: tasks whose endpoint
+// hash has (hash & mask) == 0 append {u, v, bin, cycles}.
+struct Instr {
+    int4* buf;
+    unsigned int* count;
+    unsigned int cap;
+    unsigned int mask;
+};
+
+__device__ __forceinline__ bool sampled(const Instr* ins, uint32_t u, uint32_t v) {
+    uint32_t h = u * 0x9E3779B1u ^ (v * 0x85EBCA77u + 0x27d4eb2fu);
+    h ^= h >> 15;
+    h *= 0x2c1b3c6du;
+    h ^= h >> 12;
+    return (h & ins->mask) == 0;
+}
+
+__device__ __forceinline__ void record(const Instr* ins, uint32_t u, uint32_t v, int bin, long long cycles) {
+    const unsigned slot = atomicAdd(ins->count, 1u);
+    if (slot < ins->cap)
+        ins->buf[slot] = make_int4((int)u, (int)v, bin, (int)min(cycles, (long long)0x7fffffff));
+}
 
 thread_local tc_profile_t g_profile;
 thread_local bool g_profile_valid = false;
@@ -111,6 +137,8 @@ struct Bins {
 
 struct BinParams {
     int thr_thread, thr_warp, stream_max;
+    const __half2* mlp;     // packed FP16 cost model, or null for the degree-sum rule
+    const int32_t* vtag;    // per-vertex tag counts (model features)
 };
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
@@ -134,7 +162,8 @@ __device__ __forceinline__ int seg_of(const int64_t* pfx, int nseg, int64_t r) {
 // entries after k.  y > x: canonical dyad <x,y> (pre = t): add S into codes
 // pre+4t', n-|A|-|B| into the dyadic slot, emit the task.  y < x: row x is
 // B of dyad <y,x> (pre = swapped t): add S into codes pre+16t'.
-__global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_ptr,
+template <bool MLP>
+__global__ void __launch_bounds__(256, MLP ? 2 : 1) k_tasks(const int64_t* __restrict__ row_ptr,
                                                const uint32_t* __restrict__ adj,
                                                const int32_t* __restrict__ deg,
                                                const SegDev* __restrict__ seg,
@@ -147,6 +176,11 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
     const unsigned above = lane == 31 ? 0u : (full << (lane + 1));
     const unsigned below = (1u << lane) - 1u;
     constexpr int ROWS = 32;
+    __shared__ __align__(16) __half2 mlp_w[MLP ? MLPH_N + 2 : 1];
+    if (MLP) {
+        for (int k = threadIdx.x; k < MLPH_N; k += blockDim.x) mlp_w[k] = bp.mlp[k];
+        __syncthreads();
+    }
     int s = -1;
     int64_t rb = 0, n = 0, sp = 0;
     unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN];
@@ -236,9 +270,24 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                     const unsigned long long dy = (unsigned long long)(n - (int64_t)d - (int64_t)dv);
                     Dd[0] += pre_task == 3 ? 0ull : dy;
                     Dd[1] += pre_task == 3 ? dy : 0ull;
-                    bin = L <= bp.thr_thread ? 0
-                          : L <= bp.thr_warp ? 1
-                          : min(d, dv) <= bp.stream_max ? 3 : 2;
+                    if (!MLP || L <= bp.thr_thread) {
+                        bin = L <= bp.thr_thread ? 0
+                              : L <= bp.thr_warp ? 1
+                              : min(d, dv) <= bp.stream_max ? 3 : 2;
+                    } else {
+                        // learned binning: predicted log2 cycles per bin; a
+                        // thread task occupies 1/32 of a warp
+                        const int ds = min(d, dv), dg = max(d, dv);
+                        const bool xs = d <= dv;
+                        float f[MLP_IN], pr[MLP_OUT];
+                        task_features(ds, dg, bp.vtag + 3 * (xs ? x : rb + y), bp.vtag + 3 * (xs ? rb + y : x), f);
+                        mlp_predict_h(mlp_w, f, pr);
+                        float best = pr[0] - 5.0f;
+                        bin = 0;
+                        if (L <= WARP_LMAX_T && pr[1] < best) { best = pr[1]; bin = 1; }
+                        if (ds <= STREAM_SMAX_T && pr[3] < best) { best = pr[3]; bin = 3; }
+                        if (pr[2] < best) bin = 2;
+                    }
                 }
 #pragma unroll
                 for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
@@ -380,6 +429,7 @@ struct WarpHist {
     unsigned long long* acc;
     int tag;
     int lane;
+    const Instr* ins = nullptr;
     __device__ __forceinline__ void retag(int s) {
         if (s != tag) {
             flush_hist<WARPS>(hs, acc, tag, lane);
@@ -403,6 +453,7 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
     w.retag(__shfl_sync(0xffffffffu, s, 0));
     unsigned long long* h = (s == w.tag) ? w.hs : w.acc + (size_t)s * ACC;
     if (has) {
+        const long long t0 = w.ins ? clock64() : 0;
         uint32_t c = 0;
         const uint32_t pre = r.z & 3u;
         const int64_t rb = seg[s].rb;
@@ -430,6 +481,7 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
             }
         }
         if (c) atomicAdd(h + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+        if (w.ins && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 0, clock64() - t0);
     }
     __syncwarp();
 }
@@ -583,6 +635,7 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
                                           const uint4* __restrict__ rec, const int32_t* __restrict__ ia_start,
                                           unsigned i, unsigned nrec, int tile) {
     const int lane = w.lane;
+    const long long t0 = w.ins ? clock64() : 0;
     const uint4 r = rec[i];
     const int s = (int)(r.z >> 2);
     const uint32_t pre = r.z & 3u;
@@ -608,6 +661,8 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
     __syncwarp();
+    if (w.ins && lane == 0 && sampled(w.ins, r.x, r.y))
+        record(w.ins, r.x, r.y, ia_start ? 2 : 1, clock64() - t0);
 }
 
 __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_ptr,
@@ -652,6 +707,7 @@ __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const in
     constexpr int NQ = EPL / 4;  // 16-byte loads per lane per step
     const unsigned full = 0xffffffffu;
     const int lane = w.lane;
+    const long long t0 = w.ins ? clock64() : 0;
     const int s = (int)(r.z >> 2);
     const uint32_t pre = r.z & 3u;
     w.retag(s);
@@ -740,6 +796,7 @@ __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const in
     c = __reduce_add_sync(full, c);
     if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
     __syncwarp();
+    if (w.ins && lane == 0 && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 3, clock64() - t0);
 }
 
 template <int EPL>
@@ -777,6 +834,7 @@ struct MergeQueues {
     uint32_t tile_cap;
     int tile;
     unsigned int* cursor;         // [4] per-queue cursors, zeroed before launch
+    Instr ins;                    // per-task timing (ins.buf null: off)
 };
 
 template <int EPL>
@@ -788,7 +846,7 @@ __global__ void __launch_bounds__(256) k_merge(const int64_t* __restrict__ row_p
     __shared__ unsigned long long hs_all[WARPS][ACC];
     const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpHist w{hs_all[warp], acc, -1, lane};
+    WarpHist w{hs_all[warp], acc, -1, lane, q.ins.buf ? &q.ins : nullptr};
     for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
     __syncwarp();
     const unsigned n3 = min(q.cnt[3], q.cap[3]);
@@ -901,7 +959,7 @@ constexpr int STREAM_EPL = 8;
 
 struct Launch {
     int sms = 148;
-    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1;
+    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1, occ_tasks_mlp = 1;
     bool ready = false;
 };
 
@@ -912,7 +970,9 @@ tc_status launch_info(Launch& L) {
     Launch& c = cache[dev & 63];
     if (!c.ready) {
         TC_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks, k_tasks, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks, k_tasks<false>, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks_mlp, k_tasks<true>, 256, 0));
+        c.occ_tasks_mlp = std::max(1, c.occ_tasks_mlp);
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_thread, k_thread, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_warp, k_warp, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_cta, k_cta, CTA_NT, 0));
@@ -1014,7 +1074,7 @@ tc_status upload_layout(const Layout& Lo, char* ws, cudaStream_t st) {
 
 // The census itself: one memset and the kernels, all on `st` (capturable).
 tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_census_t* d_out, cudaStream_t st,
-                         ProfileEvents* pe) {
+                         ProfileEvents* pe, const Instr* ins = nullptr) {
     const tc_opts& o = Lo.o;
     unsigned long long* acc = (unsigned long long*)(ws + Lo.o_acc);
     unsigned int* ctr = (unsigned int*)(ws + Lo.o_ctr);
@@ -1034,15 +1094,20 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     const uint32_t cap2 = (uint32_t)Lo.cap2;
     Launch L;
     if (tc_status s = launch_info(L); s != TC_OK) return s;
-    const BinParams bp{o.thr_thread, o.thr_warp, o.stream_max};
+    const __half2* mlp = o.bin_mode == TC_BIN_MLP ? (const __half2*)cost_model_weights() : nullptr;
+    const BinParams bp{o.thr_thread, o.thr_warp, o.stream_max, mlp, set.vtag};
     auto mark = [&](int k) {
         if (pe) cudaEventRecord(pe->ev[k], st);
     };
     TC_CUDA(cudaMemsetAsync(ws, 0, Lo.o_seg, st));  // accumulators + counters
     mark(0);
     if (Lo.rows > 0) {
-        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
-                                                     bp, bins, acc, cursor);
+        if (mlp)
+            k_tasks<true><<<L.sms * L.occ_tasks_mlp, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx,
+                                                                  Lo.nseg, Lo.rows, bp, bins, acc, cursor);
+        else
+            k_tasks<false><<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx,
+                                                                Lo.nseg, Lo.rows, bp, bins, acc, cursor);
         TC_CUDA(cudaGetLastError());
         mark(1);
         k_split<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], o.chunk,
@@ -1062,6 +1127,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             q.tile_cap = cap2;
             q.tile = o.chunk;
             q.cursor = ctr + 20;
+            q.ins = ins ? *ins : Instr{nullptr, nullptr, 0, 0};
             k_merge<STREAM_EPL><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
             TC_CUDA(cudaGetLastError());
             mark(3);
@@ -1136,7 +1202,7 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
 }
 
 tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
-                      tc_census_t* out, uint32_t flags, cudaStream_t st) {
+                      tc_census_t* out, uint32_t flags, cudaStream_t st, const Instr* ins = nullptr) {
     if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
     Layout Lo;
     if (tc_status s = make_layout(set, gidx, opts_in, Lo); s != TC_OK) return s;
@@ -1154,7 +1220,7 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         if (tc_status s = profile_events(&pe); s != TC_OK) return s;
     }
     if (tc_status s = upload_layout(Lo, ws, st); s != TC_OK) return s;
-    if (tc_status s = enqueue_census(set, Lo, ws, d_out, st, pe); s != TC_OK) return s;
+    if (tc_status s = enqueue_census(set, Lo, ws, d_out, st, pe, ins); s != TC_OK) return s;
     if (pe) {
         if (tc_status s = read_profile(Lo, ws, pe, st); s != TC_OK) return s;
     }
@@ -1314,10 +1380,10 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
     bins.overflow = (int*)(s->ctr + 4);
     bins.entries = (unsigned long long*)(s->ctr + 10);
     unsigned long long* cursor = (unsigned long long*)(s->ctr + 8);
-    const BinParams bp{0x7fffffff, 0x7fffffff, 0};
+    const BinParams bp{0x7fffffff, 0x7fffffff, 0, nullptr, nullptr};
     if (n > 0) {
-        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
-                                                     s->acc, cursor);
+        k_tasks<false><<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp,
+                                                            bins, s->acc, cursor);
         TC_CUDA(cudaGetLastError());
         k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(row_ptr, adj, &s->seg, s->rec, s->ctr + 0,
                                                         bins.cap[0], s->acc);
@@ -1537,5 +1603,60 @@ extern "C" tc_status tc_autotune(int32_t G, const tc_graph* gs, const tc_opts* b
         return tc::autotune(G, gs, base, max_trials, (cudaStream_t)stream, best, best_ms, trials);
     } catch (...) {
         return tc::fail(TC_ERR_CUDA, "tc_autotune: unexpected exception");
+    }
+}
+
+// ------------------------------------------------------- cost sampling --
+namespace tc {
+namespace {
+
+tc_status cost_sample(int32_t G, const tc_graph* gs, int32_t bin, int32_t mask, int32_t cap, int32_t* samples,
+                      int32_t* n_out, cudaStream_t st) {
+    if (G < 1 || !gs || bin < 0 || bin > 3 || mask < 0 || cap < 0 || (cap > 0 && !samples) || !n_out)
+        return fail(TC_ERR_ARG, "tc_cost_sample: bad arguments");
+    if (tc_status s = check_handles(G, gs, "tc_cost_sample"); s != TC_OK) return s;
+    tc_opts o;
+    tc_opts_default(&o);
+    o.persistent = 1;
+    o.split_cta = 0;
+    if (bin == 0) {
+        o.thr_thread = 0x3fffffff;
+        o.thr_warp = 0x3fffffff;
+    } else if (bin == 1) {
+        o.thr_thread = 0;
+        o.thr_warp = WARP_LMAX;
+        o.stream_max = 0;
+    } else {
+        o.thr_thread = 0;
+        o.thr_warp = 0;
+        o.stream_max = bin == 3 ? STREAM_SMAX : 0;
+    }
+    unsigned int* count = nullptr;
+    TC_CUDA(dev_alloc((void**)&count, sizeof(unsigned int), st));
+    TC_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned int), st));
+    Instr ins{(int4*)samples, count, (unsigned)cap, (unsigned)mask};
+    tc_census_t* out = nullptr;
+    TC_CUDA(dev_alloc((void**)&out, sizeof(tc_census_t) * (size_t)G, st));
+    tc_status s = census_impl(*gs[0]->set, handle_indices(G, gs), &o, out, TC_OUT_DEVICE, st, &ins);
+    unsigned int n = 0;
+    if (s == TC_OK) {
+        TC_CUDA(cudaMemcpyAsync(&n, count, sizeof n, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+    }
+    dev_free(out, st);
+    dev_free(count, st);
+    *n_out = (int32_t)std::min<unsigned>(n, (unsigned)cap);
+    return s;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" tc_status tc_cost_sample(int32_t G, const tc_graph* gs, int32_t bin, int32_t mask, int32_t cap,
+                                    int32_t* samples, int32_t* n, void* stream) {
+    try {
+        return tc::cost_sample(G, gs, bin, mask, cap, samples, n, (cudaStream_t)stream);
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_cost_sample: unexpected exception");
     }
 }

@@ -60,6 +60,9 @@ struct GraphSet {
     ~GraphSet();
 };
 
+// Packed FP16 cost-model weights installed on the current device (or null).
+const void* cost_model_weights();
+
 }  // namespace tc
 
 struct tc_graph_s {
