@@ -260,6 +260,10 @@ def run_native(args, world, rank, local, pg):
         tc.tc_census(g, prof_opts, out=out, stream=stream)
         return g
 
+    learned = None
+    if args.mlp:
+        learned, prof_opts = train_and_compare(tc, [tc.tc_graph_build(arcs.n, src_d, dst_d)], prof_opts,
+                                               stream, free=True)
     tune = None
     if args.autotune:
         g = tc.tc_graph_build(arcs.n, src_d, dst_d)
@@ -377,6 +381,7 @@ def run_native(args, world, rank, local, pg):
                           "census_entries_per_s": stats["merged_entries"] / (np.mean(census_ms) / 1e3)},
             "roofline": roofline,
             "autotune": tune,
+            "learned_binning": learned,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
@@ -416,6 +421,9 @@ def run_batched(args, world, rank, local, pg):
     out = torch.zeros(17 * G, dtype=torch.int64, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    learned = None
+    if args.mlp:
+        learned, opts = train_and_compare(tc, gs, opts, stream, free=False)
     tune = None
     if args.autotune:
         t0 = time.perf_counter()
@@ -488,9 +496,59 @@ def run_batched(args, world, rank, local, pg):
             "speedup_vs_per_graph": float(np.min(per_ms)) / ms,
             "build_s": build_s, "generate_s": gen_s, "golden_checksums_match": gold_ok,
             "autotune": tune,
+            "learned_binning": learned,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
+
+
+def train_and_compare(tc, gs, opts, stream, free):
+    """Train the task-cost model on timings recorded on these graphs, install
+    it, and time the census with degree-sum binning and with learned binning
+    (best of 5 after 2 warm-ups each).  Returns (report, opts with learned
+    binning)."""
+    import torch
+    from paper_1603_02655_b300 import costmodel
+    t0 = time.perf_counter()
+    params, rep = costmodel.train_cost_model(gs, mask=63, steps=3000, stream=stream)
+    train_s = time.perf_counter() - t0
+    costmodel.install(params)
+
+    def best_ms(o):
+        out = torch.zeros(17 * len(gs), dtype=torch.int64, device="cuda")
+        ts = []
+        for k in range(7):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tc.tc_census_batched(gs, o, out=out, stream=stream)
+            c.record(stream)
+            torch.cuda.synchronize()
+            if k >= 2:
+                ts.append(a.elapsed_time(c))
+        return float(np.min(ts)), out.cpu().tolist()
+
+    heur = tc.tc_opts_default(**{k: getattr(opts, k) for k in tc.TUNED_FIELDS})
+    heur.bin_mode = tc.TC_BIN_HEURISTIC
+    learn = tc.tc_opts_default(**{k: getattr(opts, k) for k in tc.TUNED_FIELDS})
+    learn.bin_mode = tc.TC_BIN_MLP
+    h_ms, h_out = best_ms(heur)
+    l_ms, l_out = best_ms(learn)
+    bins_used = {}
+    for name, o in (("degree_sum", heur), ("learned", learn)):
+        o.profile = 1
+        tc.tc_census_batched(gs, o, stream=stream)
+        bins_used[name] = tc.tc_census_profile()["bin_tasks"]
+        o.profile = 0
+    assert h_out == l_out, "learned binning changed the counts"
+    learn.profile = opts.profile
+    report = {"census_ms_degree_sum": h_ms, "census_ms_learned": l_ms, "speedup": h_ms / l_ms,
+              "rmse_log2_cycles_mlp": rep["rmse_mlp"], "rmse_log2_cycles_degree_sum": rep["rmse_degree_sum"],
+              "samples": rep["samples"], "train_s": train_s,
+              "bin_tasks": bins_used}
+    if free:
+        for g in gs:
+            tc.tc_graph_free(g)
+    return report, learn
 
 
 def main():
@@ -503,6 +561,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--opts", default="", help="census options, e.g. thr_warp=512,stream_max=1024")
+    ap.add_argument("--mlp", action="store_true",
+                    help="train the learned cost model on the workload and bin with it")
     ap.add_argument("--autotune", type=int, default=0, metavar="TRIALS",
                     help="autotune the census options first (at most TRIALS timed options)")
     args = ap.parse_args()

@@ -263,8 +263,9 @@ tc_status tc_autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_
  * Learned cost model for task binning (opts.bin_mode = TC_BIN_MLP): an MLP
  * 8 -> 32 -> 32 -> 4 (ReLU) predicting log2 of the cycles a canonical-dyad
  * task takes in each bin (0 thread, 1 warp, 2 split tiles, 3 streamed).
- * Binning picks the cheapest eligible bin (a thread task costs 1/32 of a
- * warp).  The thesis bins by the degree sum |N(u)|+|N(v)|-2 (Sec. 4.3.1):
+ * The model decides the splitting of large tasks: every task above thr_warp
+ * is streamed by one warp or cut into tiles, whichever it predicts cheaper
+ * (k_route, FP16); smaller tasks keep the thr_thread / thr_warp rule.  The thesis bins by the degree sum |N(u)|+|N(v)|-2 (Sec. 4.3.1):
  * that rule remains the fallback while no model is installed.
  * Parameters: float[TC_MLP_NPARAM] = W1[32][8] b1[32] W2[32][32] b2[32]
  * W3[4][32] b3[4] (row = output neuron).  Features (float[8] per task,

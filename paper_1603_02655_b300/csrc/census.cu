@@ -37,8 +37,6 @@ namespace tc {
 namespace {
 
 constexpr int WARPS = 8;  // warps per 256-thread block
-constexpr int WARP_LMAX_T = 1024;   // = WARP_LMAX (whole-task warp bin limit)
-constexpr int STREAM_SMAX_T = 1024; // = STREAM_SMAX (short-list limit of the stream bin)
 
 // Per-task timing records of an instrumented census: tasks whose endpoint
 // hash has (hash & mask) == 0 append {u, v, bin, cycles}.
@@ -162,8 +160,7 @@ __device__ __forceinline__ int seg_of(const int64_t* pfx, int nseg, int64_t r) {
 // entries after k.  y > x: canonical dyad <x,y> (pre = t): add S into codes
 // pre+4t', n-|A|-|B| into the dyadic slot, emit the task.  y < x: row x is
 // B of dyad <y,x> (pre = swapped t): add S into codes pre+16t'.
-template <bool MLP>
-__global__ void __launch_bounds__(256, MLP ? 2 : 1) k_tasks(const int64_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_ptr,
                                                const uint32_t* __restrict__ adj,
                                                const int32_t* __restrict__ deg,
                                                const SegDev* __restrict__ seg,
@@ -176,11 +173,7 @@ __global__ void __launch_bounds__(256, MLP ? 2 : 1) k_tasks(const int64_t* __res
     const unsigned above = lane == 31 ? 0u : (full << (lane + 1));
     const unsigned below = (1u << lane) - 1u;
     constexpr int ROWS = 32;
-    __shared__ __align__(16) __half2 mlp_w[MLP ? MLPH_N + 2 : 1];
-    if (MLP) {
-        for (int k = threadIdx.x; k < MLPH_N; k += blockDim.x) mlp_w[k] = bp.mlp[k];
-        __syncthreads();
-    }
+
     int s = -1;
     int64_t rb = 0, n = 0, sp = 0;
     unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN];
@@ -270,24 +263,9 @@ __global__ void __launch_bounds__(256, MLP ? 2 : 1) k_tasks(const int64_t* __res
                     const unsigned long long dy = (unsigned long long)(n - (int64_t)d - (int64_t)dv);
                     Dd[0] += pre_task == 3 ? 0ull : dy;
                     Dd[1] += pre_task == 3 ? dy : 0ull;
-                    if (!MLP || L <= bp.thr_thread) {
-                        bin = L <= bp.thr_thread ? 0
-                              : L <= bp.thr_warp ? 1
-                              : min(d, dv) <= bp.stream_max ? 3 : 2;
-                    } else {
-                        // learned binning: predicted log2 cycles per bin; a
-                        // thread task occupies 1/32 of a warp
-                        const int ds = min(d, dv), dg = max(d, dv);
-                        const bool xs = d <= dv;
-                        float f[MLP_IN], pr[MLP_OUT];
-                        task_features(ds, dg, bp.vtag + 3 * (xs ? x : rb + y), bp.vtag + 3 * (xs ? rb + y : x), f);
-                        mlp_predict_h(mlp_w, f, pr);
-                        float best = pr[0] - 5.0f;
-                        bin = 0;
-                        if (L <= WARP_LMAX_T && pr[1] < best) { best = pr[1]; bin = 1; }
-                        if (ds <= STREAM_SMAX_T && pr[3] < best) { best = pr[3]; bin = 3; }
-                        if (pr[2] < best) bin = 2;
-                    }
+                    bin = L <= bp.thr_thread ? 0
+                          : L <= bp.thr_warp ? 1
+                          : min(d, dv) <= bp.stream_max ? 3 : 2;
                 }
 #pragma unroll
                 for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
@@ -317,6 +295,57 @@ __global__ void __launch_bounds__(256, MLP ? 2 : 1) k_tasks(const int64_t* __res
     for (int b = 0; b < NBIN; ++b) {
         const unsigned long long e = warp_sum64(Ee[b]);
         if (lane == 0 && e) atomicAdd(bins.entries + b, e);
+    }
+}
+
+// --------------------------------------------------------------- k_route --
+// Learned hub splitting: each task above the warp bin (collected in `cand`)
+// goes to the stream bin or is split into tiles, whichever the FP16 cost
+// model predicts cheaper (stream only when the shorter list fits a warp's
+// shared memory).
+__global__ void __launch_bounds__(256) k_route(const __half2* __restrict__ mlp, const int32_t* __restrict__ deg,
+                                               const int32_t* __restrict__ vtag, const uint4* __restrict__ cand,
+                                               const unsigned int* __restrict__ ncand_p, uint32_t cand_cap,
+                                               uint4* __restrict__ tiles_task, unsigned int* __restrict__ ntiles_task,
+                                               uint4* __restrict__ stream_task, unsigned int* __restrict__ nstream,
+                                               uint32_t cap, int stream_max, int* __restrict__ overflow) {
+    __shared__ __align__(16) __half2 w[MLPH_N + 2];
+    for (int k = threadIdx.x; k < MLPH_N; k += blockDim.x) w[k] = mlp[k];
+    __syncthreads();
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned n = min(*ncand_p, cand_cap);
+    for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const unsigned i = base + threadIdx.x;
+        const bool has = i < n;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        bool to_stream = false;
+        if (has) {
+            r = cand[i];
+            const int du = deg[r.x], dv = deg[r.y];
+            const int ds = min(du, dv), dg = max(du, dv);
+            const bool us = du <= dv;
+            float f[MLP_IN], pr[MLP_OUT];
+            task_features(ds, dg, vtag + 3 * (size_t)(us ? r.x : r.y), vtag + 3 * (size_t)(us ? r.y : r.x), f);
+            mlp_predict_h(w, f, pr);
+            to_stream = ds <= stream_max && pr[3] < pr[2];
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool mine = has && (k == 0 ? to_stream : !to_stream);
+            const unsigned m = __ballot_sync(full, mine);
+            if (!m) continue;
+            const int leader = __ffs(m) - 1;
+            unsigned at = 0;
+            if (lane == leader) at = atomicAdd(k == 0 ? nstream : ntiles_task, (unsigned)__popc(m));
+            at = __shfl_sync(full, at, leader);
+            if (mine) {
+                const unsigned idx = at + __popc(m & below);
+                if (idx < cap) (k == 0 ? stream_task : tiles_task)[idx] = r;
+                else atomicOr(overflow, 1);
+            }
+        }
     }
 }
 
@@ -959,7 +988,7 @@ constexpr int STREAM_EPL = 8;
 
 struct Launch {
     int sms = 148;
-    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1, occ_tasks_mlp = 1;
+    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1;
     bool ready = false;
 };
 
@@ -970,9 +999,7 @@ tc_status launch_info(Launch& L) {
     Launch& c = cache[dev & 63];
     if (!c.ready) {
         TC_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks, k_tasks<false>, 256, 0));
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks_mlp, k_tasks<true>, 256, 0));
-        c.occ_tasks_mlp = std::max(1, c.occ_tasks_mlp);
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tasks, k_tasks, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_thread, k_thread, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_warp, k_warp, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_cta, k_cta, CTA_NT, 0));
@@ -1002,7 +1029,7 @@ struct Layout {
     uint64_t cap01 = 0, cap2 = 0;
     std::vector<SegDev> segs;
     std::vector<int64_t> pfx;
-    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_tl, o_ia, need;
+    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, need;
 };
 
 // counters (uint32 words): [0..3] records per bin, [4] overflow flag,
@@ -1056,6 +1083,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.o_pfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
     Lo.o_out = take(sizeof(tc_census_t) * (size_t)nseg);
     for (int b = 0; b < NBIN; ++b) Lo.o_r[b] = take(sizeof(uint4) * Lo.cap01);
+    Lo.o_rt = o.bin_mode == TC_BIN_MLP ? take(sizeof(uint4) * Lo.cap01) : Lo.o_r[2];
     Lo.o_tl = take(sizeof(uint4) * Lo.cap2);
     Lo.o_ia = take(sizeof(int32_t) * Lo.cap2);
     Lo.need = off;
@@ -1095,22 +1123,29 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     Launch L;
     if (tc_status s = launch_info(L); s != TC_OK) return s;
     const __half2* mlp = o.bin_mode == TC_BIN_MLP ? (const __half2*)cost_model_weights() : nullptr;
-    const BinParams bp{o.thr_thread, o.thr_warp, o.stream_max, mlp, set.vtag};
+    // with a cost model, every task above the warp bin is first collected in
+    // bin 2 and then routed by k_route (stream bin or tiles)
+    const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, mlp, set.vtag};
+    uint4* split_tasks = (uint4*)(ws + Lo.o_rt);
     auto mark = [&](int k) {
         if (pe) cudaEventRecord(pe->ev[k], st);
     };
     TC_CUDA(cudaMemsetAsync(ws, 0, Lo.o_seg, st));  // accumulators + counters
     mark(0);
     if (Lo.rows > 0) {
-        if (mlp)
-            k_tasks<true><<<L.sms * L.occ_tasks_mlp, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx,
-                                                                  Lo.nseg, Lo.rows, bp, bins, acc, cursor);
-        else
-            k_tasks<false><<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx,
-                                                                Lo.nseg, Lo.rows, bp, bins, acc, cursor);
+        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
+                                                     bp, bins, acc, cursor);
         TC_CUDA(cudaGetLastError());
+        const unsigned int* nsplit = ctr + 2;
+        if (mlp) {
+            k_route<<<L.sms * 4, 256, 0, st>>>(mlp, set.deg, set.vtag, bins.rec[2], ctr + 2, bins.cap[2], split_tasks,
+                                               ctr + 6, bins.rec[3], ctr + 3, (uint32_t)Lo.cap01,
+                                               std::min(o.stream_max, STREAM_SMAX), bins.overflow);
+            TC_CUDA(cudaGetLastError());
+            nsplit = ctr + 6;
+        }
         mark(1);
-        k_split<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.adj, bins.rec[2], ctr + 2, bins.cap[2], o.chunk,
+        k_split<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.adj, split_tasks, nsplit, bins.cap[2], o.chunk,
                                             d_tiles, d_ia, ctr + 5, cap2, bins.overflow);
         TC_CUDA(cudaGetLastError());
         mark(2);
@@ -1166,7 +1201,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
 
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
-    return Lo.o.persistent ? 4 : 7;
+    const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
+    return (Lo.o.persistent ? 4 : 7) + route;
 }
 
 tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cudaStream_t st) {
@@ -1192,8 +1228,9 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     P.ms_fold = ms[6];
     P.ms_total = ms[7];
     P.launches = census_launches(Lo);
+    const bool routed = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights();
     for (int b = 0; b < NBIN; ++b) {
-        P.bin_tasks[b] = c[b];
+        P.bin_tasks[b] = (b == 2 && routed) ? c[6] : c[b];
         P.bin_entries[b] = (int64_t)(((unsigned long long)c[10 + 2 * b + 1] << 32) | c[10 + 2 * b]);
     }
     P.chunks = c[5];
@@ -1382,8 +1419,8 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
     unsigned long long* cursor = (unsigned long long*)(s->ctr + 8);
     const BinParams bp{0x7fffffff, 0x7fffffff, 0, nullptr, nullptr};
     if (n > 0) {
-        k_tasks<false><<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp,
-                                                            bins, s->acc, cursor);
+        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
+                                                     s->acc, cursor);
         TC_CUDA(cudaGetLastError());
         k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(row_ptr, adj, &s->seg, s->rec, s->ctr + 0,
                                                         bins.cap[0], s->acc);
