@@ -198,10 +198,53 @@ def oracle_sample_rate(arcs, seconds, threads=None):
     return done["entries"] / wall, threads, done["vertices"], done["entries"], wall
 
 
+def run_reference_batched(args, world):
+    """The oracle on a bounded sample of the batched workload's graphs, graphs
+    processed in parallel on the host threads (one graph per thread)."""
+    import oracle
+    import synth
+    b = synth.c4()
+    G = len(b)
+    threads = os.cpu_count() or 1
+    order = np.random.default_rng(4).permutation(G)
+    per_step_s = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates, walls, done_total = [], [], 0
+    k = 0
+    for i in range(args.warmup + args.steps):
+        graphs = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < per_step_s:  # whole graphs, all host threads each
+            a = b.graph(int(order[k % G]))
+            k += 1
+            og = oracle.Graph(a.n, a.src, a.dst)
+            og.census(threads)
+            og.close()
+            graphs += 1
+        wall = time.perf_counter() - t0
+        if i >= args.warmup:
+            rates.append(graphs / wall)
+            walls.append(wall)
+            done_total += graphs
+    value = float(np.mean(rates))
+    sample = (f"oracle census of {done_total} of the {G} c4 graphs (a fixed random order, each graph on "
+              f"all {threads} host threads, ~{per_step_s:.0f} s per step)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"c4: {WORKLOAD_DESC['c4']}", "graphs": G,
+                   "parallelism": f"host threads x{threads}"},
+        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def run_reference(args, world, rank, pg):
     import synth
     if rank != 0:
         return
+    if args.workload == "c4":
+        return run_reference_batched(args, world)
     arcs = synth.WORKLOADS[args.workload]()
     import oracle
     og = oracle.Graph(arcs.n, arcs.src, arcs.dst)
