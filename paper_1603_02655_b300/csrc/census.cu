@@ -472,6 +472,7 @@ struct WarpHist {
 // One thread per small task (32 consecutive tasks per warp item): a plain
 // two-pointer merge from global memory.  A lane whose task belongs to
 // another graph than the warp's histogram adds into global memory directly.
+template <bool INS>
 __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restrict__ row_ptr,
                                             const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
                                             const uint4* __restrict__ rec, unsigned base, unsigned ntask) {
@@ -482,7 +483,7 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
     w.retag(__shfl_sync(0xffffffffu, s, 0));
     unsigned long long* h = (s == w.tag) ? w.hs : w.acc + (size_t)s * ACC;
     if (has) {
-        const long long t0 = w.ins ? clock64() : 0;
+        const long long t0 = INS ? clock64() : 0;
         uint32_t c = 0;
         const uint32_t pre = r.z & 3u;
         const int64_t rb = seg[s].rb;
@@ -510,7 +511,7 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
             }
         }
         if (c) atomicAdd(h + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
-        if (w.ins && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 0, clock64() - t0);
+        if (INS && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 0, clock64() - t0);
     }
     __syncwarp();
 }
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(256) k_thread(const int64_t* __restrict__ row_
     __syncwarp();
     const unsigned ntask = min(*cnt, cap);
     for (unsigned base = (blockIdx.x * WARPS + warp) * 32u; base < ntask; base += gridDim.x * WARPS * 32u)
-        thread_item(w, row_ptr, adj, seg, rec, base, ntask);
+        thread_item<false>(w, row_ptr, adj, seg, rec, base, ntask);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -659,12 +660,13 @@ __device__ __forceinline__ uint32_t shared_elements(const uint32_t* sA, int na, 
 constexpr int WARP_LMAX = 1024;
 constexpr int WARP_BUF = WARP_LMAX + 16;  // words of shared memory per warp
 
+template <bool INS>
 __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int64_t* __restrict__ row_ptr,
                                           const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
                                           const uint4* __restrict__ rec, const int32_t* __restrict__ ia_start,
                                           unsigned i, unsigned nrec, int tile) {
     const int lane = w.lane;
-    const long long t0 = w.ins ? clock64() : 0;
+    const long long t0 = INS ? clock64() : 0;
     const uint4 r = rec[i];
     const int s = (int)(r.z >> 2);
     const uint32_t pre = r.z & 3u;
@@ -690,7 +692,7 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
     __syncwarp();
-    if (w.ins && lane == 0 && sampled(w.ins, r.x, r.y))
+    if (INS && lane == 0 && sampled(w.ins, r.x, r.y))
         record(w.ins, r.x, r.y, ia_start ? 2 : 1, clock64() - t0);
 }
 
@@ -709,7 +711,7 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
     __syncwarp();
     const unsigned ntask = min(*cnt, cap);
     for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
-        warp_item(w, sbuf[warp], row_ptr, adj, seg, rec, ia_start, i, ntask, tile);
+        warp_item<false>(w, sbuf[warp], row_ptr, adj, seg, rec, ia_start, i, ntask, tile);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -728,7 +730,7 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
 constexpr int STREAM_SMAX = 1024;
 static_assert(STREAM_SMAX + 8 <= WARP_BUF, "stream buffer fits the warp buffer");
 
-template <int EPL>
+template <int EPL, bool INS>
 __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const int64_t* __restrict__ row_ptr,
                                             const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
                                             const uint4 r) {
@@ -736,7 +738,7 @@ __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const in
     constexpr int NQ = EPL / 4;  // 16-byte loads per lane per step
     const unsigned full = 0xffffffffu;
     const int lane = w.lane;
-    const long long t0 = w.ins ? clock64() : 0;
+    const long long t0 = INS ? clock64() : 0;
     const int s = (int)(r.z >> 2);
     const uint32_t pre = r.z & 3u;
     w.retag(s);
@@ -825,7 +827,7 @@ __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const in
     c = __reduce_add_sync(full, c);
     if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
     __syncwarp();
-    if (w.ins && lane == 0 && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 3, clock64() - t0);
+    if (INS && lane == 0 && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 3, clock64() - t0);
 }
 
 template <int EPL>
@@ -843,7 +845,7 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
     __syncwarp();
     const unsigned ntask = min(*cnt, cap);
     for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
-        stream_item<EPL>(w, sbuf[warp], row_ptr, adj, seg, rec[i]);
+        stream_item<EPL, false>(w, sbuf[warp], row_ptr, adj, seg, rec[i]);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -866,7 +868,7 @@ struct MergeQueues {
     Instr ins;                    // per-task timing (ins.buf null: off)
 };
 
-template <int EPL>
+template <int EPL, bool INS>
 __global__ void __launch_bounds__(256) k_merge(const int64_t* __restrict__ row_ptr,
                                                const uint32_t* __restrict__ adj,
                                                const SegDev* __restrict__ seg, MergeQueues q,
@@ -875,7 +877,7 @@ __global__ void __launch_bounds__(256) k_merge(const int64_t* __restrict__ row_p
     __shared__ unsigned long long hs_all[WARPS][ACC];
     const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpHist w{hs_all[warp], acc, -1, lane, q.ins.buf ? &q.ins : nullptr};
+    WarpHist w{hs_all[warp], acc, -1, lane, INS ? &q.ins : nullptr};
     for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
     __syncwarp();
     const unsigned n3 = min(q.cnt[3], q.cap[3]);
@@ -895,10 +897,10 @@ __global__ void __launch_bounds__(256) k_merge(const int64_t* __restrict__ row_p
             if (at >= items[k]) break;
             const unsigned end = min(at + grab[k], items[k]);
             for (unsigned i = at; i < end; ++i) {
-                if (k == 0) stream_item<EPL>(w, sbuf[warp], row_ptr, adj, seg, q.rec[3][i]);
-                else if (k == 1) warp_item(w, sbuf[warp], row_ptr, adj, seg, q.tiles, q.ia, i, nt, q.tile);
-                else if (k == 2) warp_item(w, sbuf[warp], row_ptr, adj, seg, q.rec[1], nullptr, i, n1, 0);
-                else thread_item(w, row_ptr, adj, seg, q.rec[0], i * 32u, n0);
+                if (k == 0) stream_item<EPL, INS>(w, sbuf[warp], row_ptr, adj, seg, q.rec[3][i]);
+                else if (k == 1) warp_item<INS>(w, sbuf[warp], row_ptr, adj, seg, q.tiles, q.ia, i, nt, q.tile);
+                else if (k == 2) warp_item<INS>(w, sbuf[warp], row_ptr, adj, seg, q.rec[1], nullptr, i, n1, 0);
+                else thread_item<INS>(w, row_ptr, adj, seg, q.rec[0], i * 32u, n0);
             }
         }
     }
@@ -1004,7 +1006,7 @@ tc_status launch_info(Launch& L) {
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_warp, k_warp, 256, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_cta, k_cta, CTA_NT, 0));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_stream, k_stream<STREAM_EPL>, 256, 0));
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_merge, k_merge<STREAM_EPL>, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_merge, k_merge<STREAM_EPL, false>, 256, 0));
         c.occ_tasks = std::max(1, c.occ_tasks);
         c.occ_thread = std::max(1, c.occ_thread);
         c.occ_warp = std::max(1, c.occ_warp);
@@ -1163,7 +1165,10 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             q.tile = o.chunk;
             q.cursor = ctr + 20;
             q.ins = ins ? *ins : Instr{nullptr, nullptr, 0, 0};
-            k_merge<STREAM_EPL><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
+            if (ins)
+                k_merge<STREAM_EPL, true><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
+            else
+                k_merge<STREAM_EPL, false><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
             TC_CUDA(cudaGetLastError());
             mark(3);
             mark(4);
