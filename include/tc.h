@@ -84,13 +84,28 @@ typedef struct {
     int32_t split_cta;    /* 0: tiles of split tasks run one per warp;
                              1: one per 256-thread CTA */
     int32_t stream_max;   /* tasks above thr_warp whose shorter list has at most
-                             stream_max (capped at 1024) entries are streamed by
-                             one warp; the others are split into tiles */
+                             stream_max entries are streamed by one warp; the
+                             others are split into tiles.  Shorter lists of at
+                             most 1024 entries are staged whole and run in the
+                             main merge; longer ones ("hub" tasks) run in a
+                             separate launch that stages them 1024 at a time */
     int32_t persistent;   /* 1: the whole merge phase is one persistent launch
                              whose warps pull streamed tasks, tiles, warp tasks
                              and thread tasks from four queues (requires
                              split_cta = 0) */
-    int32_t reserved[4];  /* must be zero */
+    int32_t hub_ratio;    /* a hub task (shorter list above 1024 entries, within
+                             stream_max) is streamed when its longer list has at
+                             least hub_ratio times as many entries as the
+                             shorter one, else split into tiles; >= 0 (0 and 1
+                             stream every hub task) */
+    int32_t own_min;      /* a dyad whose higher-degree endpoint (its owner; equal
+                             degrees: the larger id) has degree d_h with
+                             own_min <= d_h <= 131072 is not merged: the
+                             owner's list is indexed by id buckets in shared
+                             memory (and copied there up to 16384 entries) and
+                             the other endpoint's list is looked up in it.
+                             0 disables */
+    int32_t reserved[2];  /* must be zero */
 } tc_opts;
 
 /* Per-kernel timing and binning of the calling thread's most recent
@@ -99,7 +114,9 @@ typedef struct {
     float ms_tasks;          /* task build + suffix-count terms (k_tasks) */
     float ms_split;          /* chunk start partitions (k_split) */
     float ms_tiles;          /* tiles of split tasks (k_warp or k_cta) */
-    float ms_stream;         /* streamed tasks (k_stream) */
+    float ms_stream;         /* streamed tasks (k_stream); with persistent = 1
+                                only the hub tasks */
+    float ms_owner;          /* owner tasks (k_owner) */
     float ms_warp;           /* whole tasks, one warp each (k_warp) */
     float ms_thread;         /* thread-per-task merges (k_thread) */
     float ms_merge;          /* the whole merge phase (all merge kernels, or k_merge) */
@@ -109,6 +126,15 @@ typedef struct {
     int64_t bin_tasks[4];    /* dyads per bin: thread, warp, split into tiles, streamed */
     int64_t bin_entries[4];  /* merged entries |N(u)|+|N(v)| per bin */
     int64_t chunks;          /* tile records of split tasks */
+    int64_t hub_tasks;       /* streamed tasks whose shorter list exceeds 1024
+                                (counted in bin_tasks[2]) */
+    int64_t hub_entries;     /* their merged entries (part of bin_entries[2]) */
+    int64_t owner_items;     /* owner work items (pieces of up to 1024 list
+                                positions) */
+    int64_t owner_tasks;     /* dyads it handled (in no bin) */
+    int64_t owner_entries;   /* their |N(u)|+|N(v)| */
+    int64_t owner_probes;    /* lookups: the non-owner endpoints' list lengths */
+    int64_t owner_staged;    /* owner-list entries staged */
 } tc_profile_t;
 
 tc_status tc_census_profile(tc_profile_t* out);

@@ -67,18 +67,22 @@ class TcOpts(ctypes.Structure):
                 ("thr_warp", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("split_cta", ctypes.c_int32),
                 ("stream_max", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("hub_ratio", ctypes.c_int32), ("own_min", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class TcProfile(ctypes.Structure):
     _fields_ = [("ms_tasks", ctypes.c_float), ("ms_split", ctypes.c_float),
-                ("ms_tiles", ctypes.c_float), ("ms_stream", ctypes.c_float),
+                ("ms_tiles", ctypes.c_float), ("ms_stream", ctypes.c_float), ("ms_owner", ctypes.c_float),
                 ("ms_warp", ctypes.c_float),
                 ("ms_thread", ctypes.c_float), ("ms_merge", ctypes.c_float),
                 ("ms_fold", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int32),
                 ("bin_tasks", ctypes.c_int64 * 4), ("bin_entries", ctypes.c_int64 * 4),
-                ("chunks", ctypes.c_int64)]
+                ("chunks", ctypes.c_int64), ("hub_tasks", ctypes.c_int64),
+                ("hub_entries", ctypes.c_int64), ("owner_items", ctypes.c_int64),
+                ("owner_tasks", ctypes.c_int64), ("owner_entries", ctypes.c_int64),
+                ("owner_probes", ctypes.c_int64), ("owner_staged", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -97,8 +97,10 @@ tc_status tc_opts_default(tc_opts* o) {
     o->thr_thread = 48;
     o->thr_warp = 1024;
     o->chunk = 1024;
-    o->stream_max = 1024;
+    o->stream_max = 1 << 30;
     o->persistent = 1;
+    o->hub_ratio = 1;
+    o->own_min = 0;
     return TC_OK;
 }
 

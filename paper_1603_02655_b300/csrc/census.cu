@@ -64,8 +64,10 @@ __device__ __forceinline__ void record(const Instr* ins, uint32_t u, uint32_t v,
 thread_local tc_profile_t g_profile;
 thread_local bool g_profile_valid = false;
 
+constexpr int NEV = 9;  // profile marks: start, after tasks, split, owners, and the merge kernels, fold
+
 struct ProfileEvents {
-    cudaEvent_t ev[8];
+    cudaEvent_t ev[NEV];
 };
 
 tc_status profile_events(ProfileEvents** out) {
@@ -75,7 +77,7 @@ tc_status profile_events(ProfileEvents** out) {
     TC_CUDA(cudaGetDevice(&dev));
     dev &= 63;
     if (!made[dev]) {
-        for (int k = 0; k < 8; ++k) TC_CUDA(cudaEventCreate(&pe[dev].ev[k]));
+        for (int k = 0; k < NEV; ++k) TC_CUDA(cudaEventCreate(&pe[dev].ev[k]));
         made[dev] = true;
     }
     *out = &pe[dev];
@@ -131,10 +133,29 @@ struct Bins {
     unsigned int* cnt;    // [NBIN] records appended per bin
     int* overflow;
     unsigned long long* entries;  // [NBIN] merged entries per bin
+    uint4* own;           // owner pieces {row, seg, piece, 0}: owners up to
+                          // OWN_CAP from the front, larger ones from the back
+    uint32_t own_cap;
+    unsigned int* own_cnt;        // [2] larger owners, smaller owners
+    unsigned long long* own_stat; // [4] tasks, merged entries, probes, staged entries
 };
 
+// Longest shorter list a streamed task stages whole in shared memory; longer
+// ones (hub tasks) run in a separate launch that stages it in pieces.
+constexpr int STREAM_SMAX = 1024;
+
+// Owner tasks: a dyad whose higher-degree endpoint (the owner; equal degrees:
+// the larger id) has degree in [own_min, OWN_MAX] is not merged; k_owner
+// indexes the owner's list in shared memory and looks the other endpoint's
+// list up in it.
+constexpr int OWN_CAP = 16384;   // owners up to this degree are staged whole
+constexpr int OWN_MAX = 131072;  // larger ones: bucket starts only
+// an owner's dyads are cut into pieces of this many list positions, one work
+// item each (so that several CTAs share a large owner)
+constexpr int OWN_PIECE = 1024;
+
 struct BinParams {
-    int thr_thread, thr_warp, stream_max;
+    int thr_thread, thr_warp, stream_max, own_min;
     const __half2* mlp;     // packed FP16 cost model, or null for the degree-sum rule
     const int32_t* vtag;    // per-vertex tag counts (model features)
 };
@@ -176,7 +197,7 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
 
     int s = -1;
     int64_t rb = 0, n = 0, sp = 0;
-    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN];
+    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN], Os[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
@@ -224,6 +245,20 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
             const int64_t x = rb + xl;
             const int64_t beg = row_ptr[x];
             const int d = deg[x];
+            if (bp.own_min > 0 && d >= bp.own_min && d <= OWN_MAX) {  // an owner: append its pieces
+                const bool large = d > OWN_CAP;
+                const int np = (d + OWN_PIECE - 1) / OWN_PIECE;
+                unsigned k = 0;
+                if (lane == 0) k = atomicAdd(bins.own_cnt + (large ? 0 : 1), (unsigned)np);
+                k = __shfl_sync(full, k, 0);
+                for (int p = lane; p < np; p += 32) {
+                    const unsigned i = k + (unsigned)p;
+                    if (i < bins.own_cap) bins.own[large ? bins.own_cap - 1 - i : i] =
+                        make_uint4((uint32_t)x, (uint32_t)s, (uint32_t)p, 0u);
+                    else atomicOr(bins.overflow, 1);
+                }
+                if (lane == 0) Os[3] += (unsigned long long)d * (unsigned long long)np;
+            }
             int c1 = 0, c2 = 0, c3 = 0;
             for (int cb = ((d - 1) >> 5) << 5; cb >= 0; cb -= 32) {
                 const int k = cb + lane;
@@ -263,9 +298,16 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                     const unsigned long long dy = (unsigned long long)(n - (int64_t)d - (int64_t)dv);
                     Dd[0] += pre_task == 3 ? 0ull : dy;
                     Dd[1] += pre_task == 3 ? dy : 0ull;
-                    bin = L <= bp.thr_thread ? 0
-                          : L <= bp.thr_warp ? 1
-                          : min(d, dv) <= bp.stream_max ? 3 : 2;
+                    const int dh = max(d, dv);
+                    if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
+                        Os[0] += 1;
+                        Os[1] += (unsigned long long)L;
+                        Os[2] += (unsigned long long)min(d, dv);
+                    } else {
+                        bin = L <= bp.thr_thread ? 0
+                              : L <= bp.thr_warp ? 1
+                              : min(d, dv) <= min(bp.stream_max, STREAM_SMAX) ? 3 : 2;
+                    }
                 }
 #pragma unroll
                 for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
@@ -295,6 +337,11 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
     for (int b = 0; b < NBIN; ++b) {
         const unsigned long long e = warp_sum64(Ee[b]);
         if (lane == 0 && e) atomicAdd(bins.entries + b, e);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned long long e = warp_sum64(Os[k]);
+        if (lane == 0 && e) atomicAdd(bins.own_stat + k, e);
     }
 }
 
@@ -329,7 +376,7 @@ __global__ void __launch_bounds__(256) k_route(const __half2* __restrict__ mlp, 
             float f[MLP_IN], pr[MLP_OUT];
             task_features(ds, dg, vtag + 3 * (size_t)(us ? r.x : r.y), vtag + 3 * (size_t)(us ? r.y : r.x), f);
             mlp_predict_h(w, f, pr);
-            to_stream = ds <= stream_max && pr[3] < pr[2];
+            to_stream = ds <= min(stream_max, STREAM_SMAX) && pr[3] < pr[2];
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -362,10 +409,19 @@ __global__ void __launch_bounds__(256) k_split(const int64_t* __restrict__ row_p
                                                int tile, uint4* __restrict__ tiles,
                                                int32_t* __restrict__ ia_out,
                                                unsigned int* __restrict__ ntile_p, uint32_t tile_cap,
-                                               int* __restrict__ overflow) {
+                                               int* __restrict__ overflow, int stream_max, int hub_ratio,
+                                               uint4* __restrict__ hub,
+                                               uint32_t hub_cap, const unsigned int* __restrict__ nstream_p,
+                                               unsigned int* __restrict__ nhub,
+                                               unsigned long long* __restrict__ hub_entries) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     const unsigned nt = min(*ntask_p, task_cap);
+    // hub tasks fill the stream-bin array from its end, below the streamed
+    // tasks already there (the two are disjoint sets of dyads)
+    const unsigned hub_room = hub_cap - min(*nstream_p, hub_cap);
+    unsigned long long he = 0;
     const unsigned warps = gridDim.x * (blockDim.x >> 5);
     for (unsigned w0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32u; w0 < nt; w0 += warps * 32u) {
         const unsigned i = w0 + lane;
@@ -378,7 +434,27 @@ __global__ void __launch_bounds__(256) k_split(const int64_t* __restrict__ row_p
             bb = row_ptr[r.y];
             b = row_ptr[r.y + 1] - bb;
         }
-        const unsigned ntl = has ? (unsigned)((a + b + tile - 1) / tile) : 0u;
+        // a hub task (shorter list within stream_max, longer list at least
+        // hub_ratio times longer) is streamed whole by the hub launch instead
+        // of being cut into tiles
+        const int64_t sh = min(a, b);
+        const bool to_hub = has && sh <= (int64_t)stream_max && max(a, b) >= (int64_t)hub_ratio * sh;
+        {
+            const unsigned m = __ballot_sync(full, to_hub);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned at = 0;
+                if (lane == leader) at = atomicAdd(nhub, (unsigned)__popc(m));
+                at = __shfl_sync(full, at, leader);
+                if (to_hub) {
+                    const unsigned idx = at + __popc(m & below);
+                    if (idx < hub_room) hub[hub_cap - 1 - idx] = r;
+                    else atomicOr(overflow, 1);
+                    he += (unsigned long long)(a + b);
+                }
+            }
+        }
+        const unsigned ntl = (has && !to_hub) ? (unsigned)((a + b + tile - 1) / tile) : 0u;
         unsigned incl = ntl;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -421,6 +497,8 @@ __global__ void __launch_bounds__(256) k_split(const int64_t* __restrict__ row_p
             }
         }
     }
+    he = warp_sum64(he);
+    if (lane == 0 && he) atomicAdd(hub_entries, he);
 }
 
 // ----------------------------------------------------- shared-element fix --
@@ -555,6 +633,30 @@ __device__ __forceinline__ int load_span(uint32_t* __restrict__ raw, const uint3
             x.y = a + 1 < lim ? x.y : SENT;
             x.z = a + 2 < lim ? x.z : SENT;
             x.w = a + 3 < lim ? x.w : SENT;
+        }
+        dst[m] = x;
+    }
+    return o;
+}
+
+// load_span for a list addressed by pointer, with 32-bit positions relative
+// to it: `count` words from p, those at relative index >= lim stored as the
+// sentinel.  Returns the span's offset in `raw`.
+__device__ __forceinline__ int load_span_p(uint32_t* __restrict__ raw, const uint32_t* __restrict__ p, int count,
+                                           int lim, int lane) {
+    const int o = (int)(((uintptr_t)p >> 2) & 3);
+    const uint4* src = reinterpret_cast<const uint4*>(p - o);
+    uint4* dst = reinterpret_cast<uint4*>(raw);
+    const int nq = (o + count + 3) >> 2;
+    const int lo = lim + o;  // limit relative to the aligned start
+    for (int m = lane; m < nq; m += 32) {
+        uint4 x = __ldg(src + m);
+        const int a = 4 * m;
+        if (a + 3 >= lo) {
+            x.x = a < lo ? x.x : SENT;
+            x.y = a + 1 < lo ? x.y : SENT;
+            x.z = a + 2 < lo ? x.z : SENT;
+            x.w = a + 3 < lo ? x.w : SENT;
         }
         dst[m] = x;
     }
@@ -727,7 +829,6 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
 // the first lane whose last key is not smaller (a 5-step search over the
 // lanes by shuffles).  Both lists are sorted, so each entry of S is placed in
 // exactly one step and every shared element is found once.
-constexpr int STREAM_SMAX = 1024;
 static_assert(STREAM_SMAX + 8 <= WARP_BUF, "stream buffer fits the warp buffer");
 
 template <int EPL, bool INS>
@@ -830,6 +931,7 @@ __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const in
     if (INS && lane == 0 && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 3, clock64() - t0);
 }
 
+// Stream-bin tasks, one per warp.
 template <int EPL>
 __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_ptr,
                                                 const uint32_t* __restrict__ adj,
@@ -846,6 +948,146 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
     const unsigned ntask = min(*cnt, cap);
     for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
         stream_item<EPL, false>(w, sbuf[warp], row_ptr, adj, seg, rec[i]);
+    __syncwarp();
+    flush_hist<WARPS>(w.hs, acc, w.tag, lane);
+}
+
+// ------------------------------------------------------------ hub items --
+// A streamed task whose shorter list S is longer than STREAM_SMAX (both
+// endpoints are hubs).  As a stream item, but S is staged STREAM_SMAX entries
+// at a time, each piece followed by a sentinel; when a piece is used up inside
+// a step of G the next one is staged and the same step is matched again.  Kept
+// out of the persistent merge so that its extra state does not cost that
+// kernel registers (occupancy).
+template <int EPL>
+__device__ __forceinline__ void hub_item(WarpHist& w, uint32_t* buf, const int64_t* __restrict__ row_ptr,
+                                            const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
+                                            const uint4 r) {
+    constexpr int STEP = 32 * EPL;
+    constexpr int NQ = EPL / 4;  // 16-byte loads per lane per step
+    const unsigned full = 0xffffffffu;
+    const int lane = w.lane;
+    const int s = (int)(r.z >> 2);
+    const uint32_t pre = r.z & 3u;
+    w.retag(s);
+    const int64_t rb = seg[s].rb;
+    const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
+    const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
+    const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+    const bool s_is_A = (ae - ab) <= (be - bb);
+    const uint32_t* Sp = adj + (s_is_A ? ab : bb);
+    const int nS = (int)(s_is_A ? ae - ab : be - bb);
+    // G from its 16-byte boundary: valid relative offsets [lead, glen)
+    const int64_t pG = s_is_A ? bb : ab;
+    const int lead = (int)(pG & 3);
+    const uint32_t* Gp = adj + (pG - lead);
+    const int glen = (int)((s_is_A ? be : ae) - (pG - lead));
+    // S is staged STREAM_SMAX entries at a time; chunk [sc, sc+cs) is followed
+    // by the sentinel in shared memory
+    int sc = 0, cs = min(nS, STREAM_SMAX);
+    const uint32_t* sS = buf + load_span_p(buf, Sp, cs + 1, cs, lane);
+    __syncwarp();
+    int js = 0;
+    uint32_t c = 0;
+    for (int off = 0; off < glen; off += STEP) {
+        const int e0 = off + EPL * lane;
+        uint32_t v[EPL];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4*>(Gp + e0) + q);
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+        uint32_t lane_last;
+        if (off < lead || off + STEP > glen) {  // first or last step: mask foreign entries
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) v[j] = (e0 + j >= lead && e0 + j < glen) ? v[j] : SENT;
+            lane_last = e0 + EPL - 1 < lead ? 0u : (e0 + EPL - 1 >= glen ? SENT : (v[EPL - 1] | 3u));
+        } else {
+            lane_last = v[EPL - 1] | 3u;
+        }
+        const uint32_t step_last = __shfl_sync(full, lane_last, 31);
+        for (;;) {
+            if (js == cs && sc + cs < nS) {  // chunk used up: stage the next, same step
+                __syncwarp();
+                sc += cs;
+                cs = min(nS - sc, STREAM_SMAX);
+                js = 0;
+                sS = buf + load_span_p(buf, Sp + sc, cs + 1, cs, lane);
+                __syncwarp();
+            }
+            const int jj = js + lane;
+            const uint32_t t = sS[min(jj, cs)];  // sS[cs] is the sentinel
+            const uint32_t tkey = t | 3u;
+            const bool inr = jj < cs && tkey <= step_last;
+            const unsigned m = __ballot_sync(full, inr);
+            if (m == 0) break;
+            const int k = __popc(m);
+            if (k <= 3) {
+                for (int q = 0; q < k; ++q) {
+                    const uint32_t tq = __shfl_sync(full, t, q);
+                    const uint32_t qkey = tq | 3u;
+                    uint32_t hit = SENT;
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j) hit = (v[j] | 3u) == qkey ? v[j] : hit;
+                    if (hit != SENT) {
+                        ++c;
+                        on_shared(w.hs, qkey >> 2, ul, vl, pre, s_is_A ? (tq & 3u) : (hit & 3u),
+                                  s_is_A ? (hit & 3u) : (tq & 3u));
+                    }
+                }
+                js += k;
+                if (js == cs && sc + cs < nS) continue;  // next chunk may lie in this step
+                break;  // the rest of S lies beyond this step
+            }
+            int own = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t x = __shfl_sync(full, lane_last, own + step - 1);
+                if (x < tkey) own += step;
+            }
+            own = min(own, 31);
+            uint32_t hit = SENT;
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) {
+                const uint32_t x = __shfl_sync(full, v[j], own);
+                hit = (x | 3u) == tkey ? x : hit;
+            }
+            if (inr && hit != SENT) {
+                ++c;
+                on_shared(w.hs, tkey >> 2, ul, vl, pre, s_is_A ? (t & 3u) : (hit & 3u),
+                          s_is_A ? (hit & 3u) : (t & 3u));
+            }
+            js += k;
+            if (k < 32 && !(js == cs && sc + cs < nS)) break;
+        }
+    }
+    c = __reduce_add_sync(full, c);
+    if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    __syncwarp();
+}
+
+
+// Hub tasks, one per warp; k_split stores them from the end of the
+// stream-bin array.
+template <int EPL>
+__global__ void __launch_bounds__(256) k_hub(const int64_t* __restrict__ row_ptr,
+                                             const uint32_t* __restrict__ adj,
+                                             const SegDev* __restrict__ seg,
+                                             const uint4* __restrict__ rec,
+                                             const unsigned int* __restrict__ cnt, uint32_t cap,
+                                             unsigned long long* __restrict__ acc) {
+    __shared__ __align__(16) uint32_t sbuf[WARPS][WARP_BUF];
+    __shared__ unsigned long long hs_all[WARPS][ACC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpHist w{hs_all[warp], acc, -1, lane};
+    for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
+    __syncwarp();
+    const unsigned ntask = min(*cnt, cap);
+    for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
+        hub_item<EPL>(w, sbuf[warp], row_ptr, adj, seg, rec[cap - 1 - i]);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -985,12 +1227,241 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
     out[seg[s].slot] = o;
 }
 
+// ---------------------------------------------------------------- owners --
+// Owner tasks (the IsNeighbour query of the method answered by a lookup in
+// the owner's list instead of a merge).  For an owner h of degree D the
+// neighbour ids are cut into 2^lB buckets by their high bits (2^lB ~ D, at
+// most 2^14), and a start table st[b] = entries of h's list in buckets below
+// b is built in shared memory.  Owners of degree up to OWN_CAP also have
+// their list copied there; a key is looked up by reading st[b], st[b+1] and
+// scanning the few entries between them (in shared memory, or in the list in
+// global memory for larger owners).  The dyads of h are the entries x of h's
+// list that h owns (deg x < D, or deg x = D and x < h); every entry w of x's
+// list is looked up, and each hit is a shared element of the dyad {h, x}.
+// Only the shared elements are handled here: the per-dyad suffix and dyadic
+// terms of every dyad come from k_tasks.
+constexpr int OWN_NT = 512;
+constexpr int OWN_WARPS = OWN_NT / 32;
+constexpr int OWN_LB = 14;  // at most 2^14 buckets
+constexpr size_t OWN_T_BYTES = sizeof(uint32_t) * OWN_CAP;
+constexpr size_t OWN_ST_BYTES = (sizeof(uint16_t) * (OWN_CAP + 2) + 15) / 16 * 16;
+constexpr size_t OWN_HS_BYTES = sizeof(unsigned long long) * OWN_WARPS * ACC;
+constexpr size_t OWN_SMEM = OWN_T_BYTES + OWN_ST_BYTES + OWN_HS_BYTES;
+static_assert(OWN_CAP <= 65535, "staged bucket starts are 16-bit");
+static_assert(OWN_CAP == 1 << OWN_LB, "a staged owner has at most 2^OWN_LB buckets");
+static_assert(sizeof(uint32_t) * ((1 << OWN_LB) + 1) <= OWN_T_BYTES + OWN_ST_BYTES,
+              "32-bit bucket starts of a large owner fit where a staged list goes");
+
+struct OwnArgs {
+    const int64_t* row_ptr;
+    const uint32_t* adj;
+    const int32_t* deg;
+    const SegDev* seg;
+    const uint4* list;       // Bins::own
+    uint32_t cap;            // Bins::own_cap
+    const unsigned* cnt;     // [2] pieces of larger, smaller owners
+    unsigned* cursor;        // [2]
+    unsigned long long* acc;
+};
+
+struct Owner {
+    int64_t rb, beg;  // graph's first row; start of the owner's list
+    uint32_t hl;      // owner's local id
+    uint32_t row;     // owner's global row
+    int D, lB, shift, s;  // degree, log2 buckets, key >> shift = bucket, graph
+    int p0, p1;           // list positions [p0, p1) whose dyads this item handles
+};
+
+__device__ __forceinline__ Owner owner_setup(const OwnArgs& a, uint4 rec) {
+    Owner o;
+    o.s = (int)rec.y;
+    o.rb = a.seg[o.s].rb;
+    const int64_t n = a.seg[o.s].n;
+    o.row = rec.x;
+    o.hl = (uint32_t)(rec.x - o.rb);
+    o.beg = a.row_ptr[rec.x];
+    o.D = (int)(a.row_ptr[rec.x + 1] - o.beg);
+    const int nbits = ceil_log2((int)min(n, (int64_t)1 << 30));
+    o.lB = min(ceil_log2(o.D), OWN_LB);
+    o.shift = max(0, nbits - o.lB);  // key >> shift < 2^lB
+    o.p0 = (int)rec.z * OWN_PIECE;
+    o.p1 = min(o.D, o.p0 + OWN_PIECE);
+    return o;
+}
+
+// Bucket starts st[0 .. 2^lB] of the owner's list (and, with STAGE, the list).
+template <typename ST, bool STAGE>
+__device__ __forceinline__ void owner_stage(const Owner& o, const uint32_t* __restrict__ G, uint32_t* T, ST* st) {
+    const int nb = 1 << o.lB;
+    for (int j = threadIdx.x; j < o.D; j += OWN_NT) {
+        const uint32_t e = __ldg(G + j);
+        if (STAGE) T[j] = e;
+        const int bj = (int)((e >> 2) >> o.shift);
+        const int bp = j == 0 ? -1 : (int)((__ldg(G + j - 1) >> 2) >> o.shift);
+        for (int b = bp + 1; b <= bj; ++b) st[b] = (ST)j;
+        if (j == o.D - 1)
+            for (int b = bj + 1; b <= nb; ++b) st[b] = (ST)o.D;
+    }
+}
+
+// Entry of the owner's list with key `key`, or SENT.
+template <typename ST>
+__device__ __forceinline__ uint32_t owner_probe(const Owner& o, const uint32_t* L, const ST* st, uint32_t key) {
+    const uint32_t b = key >> o.shift;
+    const int j1 = (int)st[b + 1];
+    for (int j = (int)st[b]; j < j1; ++j) {
+        const uint32_t e = L[j];
+        if ((e >> 2) >= key) return (e >> 2) == key ? e : SENT;
+    }
+    return SENT;
+}
+
+// The item's dyads, 32 list positions per warp step (pulled from `next`):
+// the lanes' dyads' lists are concatenated and walked OWN_U * 32 entries at a
+// time, each entry's dyad found by a search over the lanes' running lengths;
+// a lane first issues its OWN_U loads, then looks them up.
+constexpr int OWN_U = 8;
+
+template <typename ST>
+__device__ __forceinline__ void owner_tasks(WarpHist& w, const OwnArgs& a, const Owner& o, const uint32_t* L,
+                                            const ST* st, unsigned* next) {
+    const unsigned full = 0xffffffffu;
+    const int lane = w.lane;
+    const uint32_t* G = a.adj + o.beg;
+    uint32_t c012 = 0, c102 = 0;
+    for (;;) {
+        unsigned c = 0;
+        if (lane == 0) c = atomicAdd(next, 1u);
+        c = __shfl_sync(full, c, 0);
+        if (o.p0 + (int)(c * 32u) >= o.p1) break;
+        const int pos = o.p0 + (int)(c * 32u) + lane;
+        const bool valid = pos < o.p1;
+        const uint32_t e = valid ? __ldg(G + pos) : 0u;
+        const uint32_t x = e >> 2;
+        const int dx = valid ? a.deg[o.rb + x] : 0;
+        const bool owned = valid && (dx < o.D || (dx == o.D && x < o.hl));
+        const int len = owned ? dx : 0;
+        const int64_t sb = owned ? a.row_ptr[o.rb + x] : 0;
+        int incl = len;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const int v = __shfl_up_sync(full, incl, k);
+            if (lane >= k) incl += v;
+        }
+        const int total = __shfl_sync(full, incl, 31);
+        const int64_t sbx = sb - (incl - len);  // list start minus the lane's running offset
+        const uint32_t xe = (x << 2) | (e & 3u);
+        for (int f0 = 0; f0 < total; f0 += 32 * OWN_U) {
+            uint32_t se[OWN_U], xs[OWN_U];
+#pragma unroll
+            for (int k = 0; k < OWN_U; ++k) {
+                const int fi = f0 + 32 * k + lane;
+                int t = 0;  // first lane whose running length exceeds fi
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int v = __shfl_sync(full, incl, t + step - 1);
+                    if (v <= fi) t += step;
+                }
+                t = min(t, 31);
+                const int64_t bt = __shfl_sync(full, sbx, t);
+                xs[k] = __shfl_sync(full, xe, t);
+                se[k] = fi < total ? __ldg(a.adj + bt + fi) : SENT;
+            }
+#pragma unroll
+            for (int k = 0; k < OWN_U; ++k) {
+                if (se[k] == SENT) continue;
+                const uint32_t key = se[k] >> 2;
+                const uint32_t hit = owner_probe(o, L, st, key);
+                if (hit != SENT) {
+                    const uint32_t xt = xs[k] >> 2, et = xs[k] & 3u;
+                    const bool h_is_u = o.hl < xt;
+                    const uint32_t pre = h_is_u ? et : (((et & 1u) << 1) | (et >> 1));
+                    const uint32_t th = hit & 3u, tx = se[k] & 3u;
+                    on_shared(w.hs, key, h_is_u ? o.hl : xt, h_is_u ? xt : o.hl, pre, h_is_u ? th : tx,
+                              h_is_u ? tx : th);
+                    if (pre == 3) ++c102;
+                    else ++c012;
+                }
+            }
+        }
+    }
+    c012 = __reduce_add_sync(full, c012);
+    c102 = __reduce_add_sync(full, c102);
+    if (lane == 0) {
+        if (c012) atomicAdd(w.hs + 64, (unsigned long long)c012);
+        if (c102) atomicAdd(w.hs + 65, (unsigned long long)c102);
+    }
+    __syncwarp();
+}
+
+struct OwnCtl {
+    unsigned idx;   // item being processed
+    unsigned next;  // task-chunk cursor of the item
+    uint32_t row;   // owner indexed in shared memory (~0: none)
+    int seg;
+};
+
+// Persistent: first the pieces of owners above OWN_CAP (bucket starts in
+// shared memory, the list read from global memory), then the others (list
+// staged).  Consecutive pieces of one owner on a CTA reuse its index.
+__global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
+    extern __shared__ __align__(16) unsigned char own_smem[];
+    uint32_t* T = reinterpret_cast<uint32_t*>(own_smem);
+    uint16_t* st16 = reinterpret_cast<uint16_t*>(own_smem + OWN_T_BYTES);
+    uint32_t* st32 = reinterpret_cast<uint32_t*>(own_smem);
+    unsigned long long* hs_all = reinterpret_cast<unsigned long long*>(own_smem + OWN_T_BYTES + OWN_ST_BYTES);
+    __shared__ OwnCtl ctl;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpHist w{hs_all + (size_t)warp * ACC, a.acc, -1, lane};
+    for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
+    __syncwarp();
+    const unsigned nlarge = min(a.cnt[0], a.cap), nsmall = min(a.cnt[1], a.cap - nlarge);
+    if (threadIdx.x == 0) {
+        ctl.row = ~0u;
+        ctl.seg = -1;
+    }
+    for (int phase = 0; phase < 2; ++phase) {
+        const unsigned nitems = phase == 0 ? nlarge : nsmall;
+        if (threadIdx.x == 0) {  // the index in shared memory changes form between phases
+            ctl.row = ~0u;
+            ctl.seg = -1;
+        }
+        for (;;) {
+            if (threadIdx.x == 0) {
+                ctl.idx = atomicAdd(a.cursor + phase, 1u);
+                ctl.next = 0;
+            }
+            __syncthreads();
+            const unsigned idx = ctl.idx;
+            if (idx >= nitems) break;
+            const Owner o = owner_setup(a, a.list[phase == 0 ? a.cap - 1 - idx : idx]);
+            const uint32_t* G = a.adj + o.beg;
+            if (o.row != ctl.row || o.s != ctl.seg) {  // index the owner (unless the last item had it)
+                if (phase == 0) owner_stage<uint32_t, false>(o, G, T, st32);
+                else owner_stage<uint16_t, true>(o, G, T, st16);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    ctl.row = o.row;
+                    ctl.seg = o.s;
+                }
+            }
+            w.retag(o.s);
+            if (phase == 0) owner_tasks(w, a, o, G, st32, &ctl.next);
+            else owner_tasks(w, a, o, T, st16, &ctl.next);
+            __syncthreads();
+        }
+    }
+    __syncwarp();
+    flush_hist<WARPS>(w.hs, w.acc, w.tag, lane);
+}
+
 // ------------------------------------------------------------- host side --
 constexpr int STREAM_EPL = 8;
 
 struct Launch {
     int sms = 148;
     int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1;
+    int occ_owner = 1;
     bool ready = false;
 };
 
@@ -1013,6 +1484,9 @@ tc_status launch_info(Launch& L) {
         c.occ_cta = std::max(1, c.occ_cta);
         c.occ_stream = std::max(1, c.occ_stream);
         c.occ_merge = std::max(1, c.occ_merge);
+        TC_CUDA(cudaFuncSetAttribute(k_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OWN_SMEM));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_owner, k_owner, OWN_NT, OWN_SMEM));
+        c.occ_owner = std::max(1, c.occ_owner);
         c.ready = true;
     }
     L = c;
@@ -1031,13 +1505,18 @@ struct Layout {
     uint64_t cap01 = 0, cap2 = 0;
     std::vector<SegDev> segs;
     std::vector<int64_t> pfx;
-    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, need;
+    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, o_own, need;
+    uint32_t own_cap = 0;
 };
 
 // counters (uint32 words): [0..3] records per bin, [4] overflow flag,
 // [5] tile records, [8..9] row cursor (u64), [10..17] merged entries per bin
 // (u64), [20..23] cursors of the persistent merge queues
-constexpr int CTR_WORDS = 32;
+// Counter words: 0-3 bin records, 4 overflow, 5 tiles, 6 routed split tasks,
+// 7 hub tasks, 8-9 task-build row cursor, 10-17 bin entries, 20-23 merge
+// cursors, 24-25 hub entries, 26-27 owner cursors, 28-29 owner rows (larger,
+// smaller), 32-39 owner tasks, merged entries, probes, staged entries.
+constexpr int CTR_WORDS = 40;
 
 tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
                       Layout& Lo) {
@@ -1051,11 +1530,13 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         return fail(TC_ERR_ARG, "census: need 0 <= thr_thread <= thr_warp and 256 <= chunk <= "
                                 "1024 (warp tiles) or 3840 (split_cta = 1)");
     if (o.stream_max < 0) return fail(TC_ERR_ARG, "census: stream_max < 0");
+    if (o.hub_ratio < 0) return fail(TC_ERR_ARG, "census: hub_ratio < 0");
+    if (o.own_min < 0) return fail(TC_ERR_ARG, "census: own_min < 0");
     if (o.persistent && o.split_cta)
         return fail(TC_ERR_ARG, "census: the persistent merge runs warp tiles (split_cta must be 0)");
     // a warp holds both lists (or the short list) in shared memory
     o.thr_warp = std::min(o.thr_warp, WARP_LMAX);
-    o.stream_max = std::min(o.stream_max, STREAM_SMAX);
+
     const int nseg = (int)gidx.size();
     Lo.segs.assign((size_t)nseg, SegDev{});
     Lo.pfx.assign((size_t)nseg + 1, 0);
@@ -1088,6 +1569,9 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.o_rt = o.bin_mode == TC_BIN_MLP ? take(sizeof(uint4) * Lo.cap01) : Lo.o_r[2];
     Lo.o_tl = take(sizeof(uint4) * Lo.cap2);
     Lo.o_ia = take(sizeof(int32_t) * Lo.cap2);
+    // pieces: sum over owners of ceil(d / OWN_PIECE) <= rows + 2|U| / OWN_PIECE
+    Lo.own_cap = (uint32_t)std::min<int64_t>(Lo.rows + 2 * dyads / OWN_PIECE + 1, 0xffffffffll);
+    Lo.o_own = take(sizeof(uint4) * (o.own_min > 0 ? Lo.own_cap : 1));
     Lo.need = off;
     return TC_OK;
 }
@@ -1118,6 +1602,10 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     bins.cnt = ctr;
     bins.overflow = (int*)(ctr + 4);
     bins.entries = (unsigned long long*)(ctr + 10);
+    bins.own = (uint4*)(ws + Lo.o_own);
+    bins.own_cap = Lo.own_cap;
+    bins.own_cnt = ctr + 28;
+    bins.own_stat = (unsigned long long*)(ctr + 32);
     unsigned long long* cursor = (unsigned long long*)(ctr + 8);
     uint4* d_tiles = (uint4*)(ws + Lo.o_tl);
     int32_t* d_ia = (int32_t*)(ws + Lo.o_ia);
@@ -1127,7 +1615,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     const __half2* mlp = o.bin_mode == TC_BIN_MLP ? (const __half2*)cost_model_weights() : nullptr;
     // with a cost model, every task above the warp bin is first collected in
     // bin 2 and then routed by k_route (stream bin or tiles)
-    const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, mlp, set.vtag};
+    const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, o.own_min, mlp, set.vtag};
     uint4* split_tasks = (uint4*)(ws + Lo.o_rt);
     auto mark = [&](int k) {
         if (pe) cudaEventRecord(pe->ev[k], st);
@@ -1142,15 +1630,33 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         if (mlp) {
             k_route<<<L.sms * 4, 256, 0, st>>>(mlp, set.deg, set.vtag, bins.rec[2], ctr + 2, bins.cap[2], split_tasks,
                                                ctr + 6, bins.rec[3], ctr + 3, (uint32_t)Lo.cap01,
-                                               std::min(o.stream_max, STREAM_SMAX), bins.overflow);
+                                               o.stream_max, bins.overflow);
             TC_CUDA(cudaGetLastError());
             nsplit = ctr + 6;
         }
         mark(1);
+        // hub tasks: counted in ctr[7], entries in ctr[24..25], records at the
+        // end of the stream-bin array (with a cost model, what it sent to
+        // tiles stays there)
+        unsigned long long* hub_entries = (unsigned long long*)(ctr + 24);
         k_split<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.adj, split_tasks, nsplit, bins.cap[2], o.chunk,
-                                            d_tiles, d_ia, ctr + 5, cap2, bins.overflow);
+                                            d_tiles, d_ia, ctr + 5, cap2, bins.overflow, mlp ? 0 : o.stream_max,
+                                            o.hub_ratio,
+                                            bins.rec[3], bins.cap[3], ctr + 3, ctr + 7, hub_entries);
         TC_CUDA(cudaGetLastError());
         mark(2);
+        if (o.own_min > 0) {
+            const OwnArgs oa{set.row_ptr, set.adj, set.deg, d_seg, bins.own, bins.own_cap, ctr + 28, ctr + 26, acc};
+            k_owner<<<L.sms * L.occ_owner, OWN_NT, OWN_SMEM, st>>>(oa);
+            TC_CUDA(cudaGetLastError());
+        }
+        mark(3);
+        auto hub_launch = [&]() {
+            k_hub<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg,
+                                                                              bins.rec[3], ctr + 7, bins.cap[3],
+                                                                              acc);
+            return cudaGetLastError();
+        };
         if (o.persistent) {
             MergeQueues q;
             for (int b = 0; b < NBIN; ++b) {
@@ -1165,14 +1671,16 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             q.tile = o.chunk;
             q.cursor = ctr + 20;
             q.ins = ins ? *ins : Instr{nullptr, nullptr, 0, 0};
+            TC_CUDA(hub_launch());
+            mark(4);
             if (ins)
                 k_merge<STREAM_EPL, true><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
             else
                 k_merge<STREAM_EPL, false><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
             TC_CUDA(cudaGetLastError());
-            mark(3);
-            mark(4);
             mark(5);
+            mark(6);
+            mark(7);
         } else {
             if (o.split_cta)
                 k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5, cap2,
@@ -1181,33 +1689,34 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
                 k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5, cap2,
                                                             o.chunk, acc);
             TC_CUDA(cudaGetLastError());
-            mark(3);
-            k_stream<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[3],
-                                                                        ctr + 3, bins.cap[3], acc);
-            TC_CUDA(cudaGetLastError());
             mark(4);
+            k_stream<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg,
+                                                                               bins.rec[3], ctr + 3, bins.cap[3], acc);
+            TC_CUDA(cudaGetLastError());
+            TC_CUDA(hub_launch());
+            mark(5);
             k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], nullptr, ctr + 1,
                                                         bins.cap[1], 0, acc);
             TC_CUDA(cudaGetLastError());
-            mark(5);
+            mark(6);
             k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
                                                             bins.cap[0], acc);
             TC_CUDA(cudaGetLastError());
         }
     } else {
-        for (int k = 1; k <= 5; ++k) mark(k);
+        for (int k = 1; k <= 6; ++k) mark(k);
     }
-    mark(6);
+    mark(7);
     k_fold<<<(Lo.nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, Lo.nseg, d_out);
     TC_CUDA(cudaGetLastError());
-    mark(7);
+    mark(8);
     return TC_OK;
 }
 
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
-    return (Lo.o.persistent ? 4 : 7) + route;
+    return (Lo.o.persistent ? 5 : 8) + route + (Lo.o.own_min > 0 ? 1 : 0);
 }
 
 tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cudaStream_t st) {
@@ -1216,29 +1725,41 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     TC_CUDA(cudaStreamSynchronize(st));
     tc_profile_t& P = g_profile;
     P = tc_profile_t{};
-    float ms[8] = {0};
-    for (int k = 0; k < 7; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
-    TC_CUDA(cudaEventElapsedTime(&ms[7], pe->ev[0], pe->ev[7]));
+    // marks: 0 start, 1 tasks, 2 split, 3 owners, 4..7 merge kernels, 8 fold
+    float ms[NEV] = {0};
+    for (int k = 0; k + 1 < NEV; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
+    float total = 0;
+    TC_CUDA(cudaEventElapsedTime(&total, pe->ev[0], pe->ev[NEV - 1]));
     P.ms_tasks = ms[0];
     P.ms_split = ms[1];
+    P.ms_owner = ms[2];
     if (Lo.o.persistent) {
-        P.ms_merge = ms[2];
+        P.ms_stream = ms[3];          // hub tasks
+        P.ms_merge = ms[3] + ms[4];   // hub tasks + k_merge
     } else {
-        P.ms_tiles = ms[2];
-        P.ms_stream = ms[3];
-        P.ms_warp = ms[4];
-        P.ms_thread = ms[5];
-        P.ms_merge = ms[2] + ms[3] + ms[4] + ms[5];
+        P.ms_tiles = ms[3];
+        P.ms_stream = ms[4];
+        P.ms_warp = ms[5];
+        P.ms_thread = ms[6];
+        P.ms_merge = ms[3] + ms[4] + ms[5] + ms[6];
     }
-    P.ms_fold = ms[6];
-    P.ms_total = ms[7];
+    P.ms_fold = ms[7];
+    P.ms_total = total;
     P.launches = census_launches(Lo);
     const bool routed = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights();
+    auto u64 = [&](int w) { return (int64_t)(((unsigned long long)c[w + 1] << 32) | c[w]); };
     for (int b = 0; b < NBIN; ++b) {
         P.bin_tasks[b] = (b == 2 && routed) ? c[6] : c[b];
-        P.bin_entries[b] = (int64_t)(((unsigned long long)c[10 + 2 * b + 1] << 32) | c[10 + 2 * b]);
+        P.bin_entries[b] = u64(10 + 2 * b);
     }
     P.chunks = c[5];
+    P.hub_tasks = c[7];
+    P.hub_entries = u64(24);
+    P.owner_items = (int64_t)c[28] + c[29];
+    P.owner_tasks = u64(32);
+    P.owner_entries = u64(34);
+    P.owner_probes = u64(36);
+    P.owner_staged = u64(38);
     g_profile_valid = true;
     return TC_OK;
 }
@@ -1422,7 +1943,11 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
     bins.overflow = (int*)(s->ctr + 4);
     bins.entries = (unsigned long long*)(s->ctr + 10);
     unsigned long long* cursor = (unsigned long long*)(s->ctr + 8);
-    const BinParams bp{0x7fffffff, 0x7fffffff, 0, nullptr, nullptr};
+    bins.own = nullptr;
+    bins.own_cap = 0;
+    bins.own_cnt = nullptr;
+    bins.own_stat = nullptr;
+    const BinParams bp{0x7fffffff, 0x7fffffff, 0, 0, nullptr, nullptr};
     if (n > 0) {
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
                                                      s->acc, cursor);
@@ -1604,7 +2129,7 @@ tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t m
     if (tc_status s = timeit(cur, cur_ms); s != TC_OK) return s;
     const int32_t thr_thread_c[] = {0, 16, 32, 48, 64, 96, 128, 192};
     const int32_t thr_warp_c[] = {64, 128, 256, 512, 1024};
-    const int32_t stream_c[] = {0, 64, 256, 1024};
+    const int32_t stream_c[] = {0, 256, 1024, 1 << 30};
     const int32_t chunk_c[] = {256, 512, 1024};
     const int32_t pers_c[] = {0, 1};
     for (int pass = 0; pass < 2; ++pass) {
@@ -1671,7 +2196,7 @@ tc_status cost_sample(int32_t G, const tc_graph* gs, int32_t bin, int32_t mask, 
     } else {
         o.thr_thread = 0;
         o.thr_warp = 0;
-        o.stream_max = bin == 3 ? STREAM_SMAX : 0;
+        o.stream_max = bin == 3 ? (1 << 30) : 0;
     }
     unsigned int* count = nullptr;
     TC_CUDA(dev_alloc((void**)&count, sizeof(unsigned int), st));

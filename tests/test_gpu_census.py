@@ -22,6 +22,8 @@ BINS = {
     "default": {},
     "nostream": dict(stream_max=0),
     "stream_all": dict(thr_thread=0, thr_warp=0, stream_max=1024),
+    "stream_chunks": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30),
+    "hub_separate": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30, persistent=0),
     "thread": dict(thr_thread=BIG, thr_warp=BIG),
     "warp": dict(thr_thread=0, thr_warp=BIG, stream_max=0),
     "separate": dict(persistent=0),
@@ -31,6 +33,9 @@ BINS = {
     "mixed": dict(thr_thread=8, thr_warp=40, chunk=512),
     "persistent": dict(persistent=1),
     "persistent_small": dict(persistent=1, thr_thread=8, thr_warp=64, chunk=256, stream_max=32),
+    "owner_all": dict(own_min=1),
+    "owner_mid": dict(own_min=64, thr_thread=8, thr_warp=64),
+    "owner_sep": dict(own_min=32, persistent=0, stream_max=0),
 }
 
 
@@ -151,6 +156,91 @@ def test_hub_graphs_span_tiles_and_chunks(seed):
     want = oracle.census(n, src, dst, threads=THREADS)
     for name in BINS:
         assert gpu_census(n, src, dst, opts(name)) == want, name
+
+
+def test_hub_tasks_stage_short_list_in_pieces():
+    # hubs of exact degrees around the 1024-entry staging limit, all joined to
+    # one another: hub-hub dyads whose shorter list has 1024 entries run in the
+    # stream bin, longer ones (1025, 2048, 2049, 3500) in the hub launch, which
+    # stages the shorter list in 1024-entry pieces (the last one ragged)
+    rng = np.random.default_rng(7)
+    n = 6000
+    degs = [1023, 1024, 1025, 2048, 2049, 3500]
+    H = len(degs)
+    src, dst = [], []
+    for h, D in enumerate(degs):
+        nb = np.concatenate([np.delete(np.arange(H), h),
+                             rng.choice(np.arange(H, n), size=D - (H - 1), replace=False)])
+        out = rng.random(nb.size) < 0.5
+        src.append(np.where(out, h, nb))
+        dst.append(np.where(out, nb, h))
+    s = rng.integers(H, n, 20000)
+    d = rng.integers(H, n, 20000)
+    src.append(s)
+    dst.append(d)
+    src = np.concatenate(src).astype(np.int32)
+    dst = np.concatenate(dst).astype(np.int32)
+    want = oracle.census(n, src, dst, threads=THREADS)
+    for h, D in enumerate(degs):  # |N(h)|: distinct neighbours either way
+        assert np.unique(np.concatenate([dst[src == h], src[dst == h]])).size == D
+    hubs = sum(1 for i in range(H) for j in range(i + 1, H) if min(degs[i], degs[j]) > 1024)
+    for name in ("default", "separate", "stream_chunks", "hub_separate", "nostream"):
+        o = tc.tc_opts_default(profile=1, **BINS[name])
+        assert gpu_census(n, src, dst, o) == want, name
+        p = tc.tc_census_profile()
+        if o.stream_max > 1024:
+            assert p["hub_tasks"] == hubs, name
+            assert p["hub_entries"] > 0
+        else:
+            assert p["hub_tasks"] == 0, name
+
+
+def star_plus(rng, n, hub, leaves, extra):
+    """A hub joined to `leaves` (random directions, some mutual) plus random
+    arcs among the leaves."""
+    out = rng.random(leaves.size) < 0.5
+    mut = rng.random(leaves.size) < 0.2
+    src = [np.where(out, hub, leaves), leaves[mut]]
+    dst = [np.where(out, leaves, hub), np.full(mut.sum(), hub)]
+    src.append(rng.choice(leaves, extra))
+    dst.append(rng.choice(leaves, extra))
+    return np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32)
+
+
+def owner_profile(n, src, dst, **over):
+    o = tc.tc_opts_default(profile=1, **over)
+    c = gpu_census(n, src, dst, o)
+    return c, tc.tc_census_profile()
+
+
+def test_owner_large_and_skewed():
+    # owners above 16384 entries keep only 32-bit bucket starts in shared
+    # memory and read their list from global memory; two such hubs share
+    # neighbours (their dyad has both lists large)
+    rng = np.random.default_rng(11)
+    n = 200_000
+    leaves = rng.choice(n - 1, 40_000, replace=False)
+    s1, d1 = star_plus(rng, n, n - 1, leaves, 60_000)
+    leaves2 = np.concatenate([rng.choice(leaves, 10_000, replace=False),
+                              rng.choice(n - 1, 10_000, replace=False)])
+    leaves2 = np.unique(leaves2[leaves2 != 7])
+    s2, d2 = star_plus(rng, n, 7, leaves2, 0)
+    src, dst = np.concatenate([s1, s2, [7]]), np.concatenate([d1, d2, [n - 1]])
+    want = oracle.census(n, src, dst, threads=THREADS)
+    for own_min in (1, 1000, 20000):
+        c, p = owner_profile(n, src, dst, own_min=own_min)
+        assert c == want, own_min
+        assert p["owner_items"] >= 1 and p["owner_tasks"] > 0
+    # an owner whose neighbours all have small ids: they crowd into a few id
+    # buckets (long scans), which must stay exact
+    n = 1_000_000
+    s3, d3 = star_plus(rng, n, n - 1, np.arange(20_000), 50_000)
+    want = oracle.census(n, s3, d3, threads=THREADS)
+    c, p = owner_profile(n, s3, d3, own_min=1)
+    assert c == want
+    # with own_min = 1 every dyad is an owner task
+    assert p["owner_tasks"] == oracle.Graph(n, s3, d3).stats()["dyads"]
+    assert sum(p["bin_tasks"]) == 0
 
 
 def test_c1_matches_golden_and_brute():
