@@ -360,18 +360,22 @@ def run_native(args, world, rank, local, pg):
     # by k_hub, counted in bin 2) moved out of the kernel that would cut them
     pl = profs[-1]
     hub = pl["hub_entries"]
+    # k_owner reads, per owner dyad, the other endpoint's list (one lookup per
+    # entry) and, per work item, the owner's list: those are its bytes
+    own_bytes_entries = pl["owner_probes"] + pl["owner_staged"]
     if prof_opts.persistent:
-        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_hub": "ms_stream", "k_fold": "ms_fold"}
+        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_owner": "ms_owner", "k_hub": "ms_stream",
+                "k_fold": "ms_fold"}
         avg = {k: float(np.mean([p[f] for p in profs])) for k, f in kern.items()}
         avg["k_merge"] = float(np.mean([p["ms_merge"] - p["ms_stream"] for p in profs]))
-        merge_entries = {"k_merge": sum(pl["bin_entries"]) - hub, "k_hub": hub}
+        merge_entries = {"k_merge": sum(pl["bin_entries"]) - hub, "k_hub": hub, "k_owner": own_bytes_entries}
     else:
-        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_warp[tiles]": "ms_tiles",
+        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_owner": "ms_owner", "k_warp[tiles]": "ms_tiles",
                 "k_stream+k_hub": "ms_stream", "k_warp": "ms_warp", "k_thread": "ms_thread", "k_fold": "ms_fold"}
         avg = {k: float(np.mean([p[f] for p in profs])) for k, f in kern.items()}
         be = pl["bin_entries"]
         merge_entries = {"k_warp[tiles]": be[2] - hub, "k_stream+k_hub": be[3] + hub, "k_warp": be[1],
-                         "k_thread": be[0]}
+                         "k_thread": be[0], "k_owner": own_bytes_entries}
     top = max(merge_entries, key=lambda k: avg[k])
     entries_top = merge_entries[top]
     peak, peak_kind = peaks()
@@ -380,7 +384,12 @@ def run_native(args, world, rank, local, pg):
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": 4 * entries_top,
-                "ms_per_launch": avg[top]}
+                "bytes_per_unit": ("4 B per lookup plus 4 B per owner-list entry indexed" if top == "k_owner"
+                                   else "4 B per merged adjacency entry"),
+                "ms_per_launch": avg[top],
+                # the full-union merge work over the whole census (the paper's
+                # cost), as if every dyad were merged: an effective rate
+                "effective_frac": 4.0 * stats["merged_entries"] / (np.mean(census_ms) / 1e3) / 1e9 / peak}
     merge_ms = sum(avg[k] for k in merge_entries)
 
     # end to end through the public API from pinned host memory
@@ -429,6 +438,8 @@ def run_native(args, world, rank, local, pg):
                           "merge_ms": merge_ms, "kernel_ms": avg,
                           "bin_tasks": profs[-1]["bin_tasks"], "bin_entries": profs[-1]["bin_entries"],
                           "hub_tasks": profs[-1]["hub_tasks"], "hub_entries": hub,
+                          "owner": {k: pl[k] for k in ("owner_items", "owner_tasks", "owner_entries",
+                                                       "owner_probes", "owner_staged")},
                           "chunks": profs[-1]["chunks"],
                           "census_entries_per_s": stats["merged_entries"] / (np.mean(census_ms) / 1e3)},
             "roofline": roofline,

@@ -104,7 +104,7 @@ typedef struct {
                              owner's list is indexed by id buckets in shared
                              memory (and copied there up to 16384 entries) and
                              the other endpoint's list is looked up in it.
-                             0 disables */
+                             0 disables; default 128 */
     int32_t reserved[2];  /* must be zero */
 } tc_opts;
 

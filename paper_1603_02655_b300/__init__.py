@@ -333,7 +333,8 @@ def tc_autotune(gs, base: TcOpts | None = None, max_trials: int = 0, stream=None
     return best, float(ms.value), int(n.value)
 
 
-TUNED_FIELDS = ("bin_mode", "thr_thread", "thr_warp", "chunk", "split_cta", "stream_max", "persistent")
+TUNED_FIELDS = ("bin_mode", "thr_thread", "thr_warp", "chunk", "split_cta", "stream_max", "persistent",
+                "hub_ratio", "own_min")
 
 
 def graph_class(stats: list) -> str:
@@ -367,7 +368,7 @@ def autotune(gs, cache_path: str | None = None, base: TcOpts | None = None, max_
         except (OSError, ValueError):
             cache = {}
     hit = cache.get(dev, {}).get(key)
-    if hit and not retune:
+    if hit and not retune and all(k in hit for k in TUNED_FIELDS):
         return tc_opts_default(**{k: hit[k] for k in TUNED_FIELDS})
     best, ms, trials = tc_autotune(gs, base, max_trials, stream)
     entry = {k: int(getattr(best, k)) for k in TUNED_FIELDS}

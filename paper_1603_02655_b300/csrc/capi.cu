@@ -100,7 +100,7 @@ tc_status tc_opts_default(tc_opts* o) {
     o->stream_max = 1 << 30;
     o->persistent = 1;
     o->hub_ratio = 1;
-    o->own_min = 0;
+    o->own_min = 128;
     return TC_OK;
 }
 

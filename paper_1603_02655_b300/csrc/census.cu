@@ -148,11 +148,11 @@ constexpr int STREAM_SMAX = 1024;
 // the larger id) has degree in [own_min, OWN_MAX] is not merged; k_owner
 // indexes the owner's list in shared memory and looks the other endpoint's
 // list up in it.
-constexpr int OWN_CAP = 16384;   // owners up to this degree are staged whole
+constexpr int OWN_CAP = 15360;   // owners up to this degree are staged whole
 constexpr int OWN_MAX = 131072;  // larger ones: bucket starts only
 // an owner's dyads are cut into pieces of this many list positions, one work
 // item each (so that several CTAs share a large owner)
-constexpr int OWN_PIECE = 1024;
+constexpr int OWN_PIECE = 2048;
 
 struct BinParams {
     int thr_thread, thr_warp, stream_max, own_min;
@@ -1230,27 +1230,50 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 // ---------------------------------------------------------------- owners --
 // Owner tasks (the IsNeighbour query of the method answered by a lookup in
 // the owner's list instead of a merge).  For an owner h of degree D the
-// neighbour ids are cut into 2^lB buckets by their high bits (2^lB ~ D, at
-// most 2^14), and a start table st[b] = entries of h's list in buckets below
-// b is built in shared memory.  Owners of degree up to OWN_CAP also have
-// their list copied there; a key is looked up by reading st[b], st[b+1] and
-// scanning the few entries between them (in shared memory, or in the list in
-// global memory for larger owners).  The dyads of h are the entries x of h's
-// list that h owns (deg x < D, or deg x = D and x < h); every entry w of x's
-// list is looked up, and each hit is a shared element of the dyad {h, x}.
-// Only the shared elements are handled here: the per-dyad suffix and dyadic
-// terms of every dyad come from k_tasks.
+// neighbour ids are cut into 2^lB buckets by their high bits (2^lB ~ D), and
+// each bucket into 16 (owners up to OWN_CAP, whose list is also copied to
+// shared memory) or 32 (larger owners) sub-buckets by the next bits.  Shared
+// memory holds, per bucket, the start of its entries in h's list and a mask of
+// the sub-buckets that hold one.  A key whose sub-bucket bit is clear is
+// absent (one shared load, the common case); the others are queued per warp
+// and, 32 at a time, looked up by scanning their bucket's few entries (in
+// shared memory, or in the list in global memory for larger owners).  The dyads of h are the entries x of h's list that h owns
+// (deg x < D, or deg x = D and x < h); every entry w of x's list is looked
+// up, and each hit is a shared element of the dyad {h, x}.  Only the shared
+// elements are handled here: the per-dyad suffix and dyadic terms of every
+// dyad come from k_tasks.
+//
+// Work item: a piece of at most OWN_PIECE positions of h's list, taken
+// OWN_NT positions at a time.  Their owned dyads are compacted into a task
+// table (list start, id and tag, running offset of the concatenated lists),
+// and warps pull units of OWN_UNIT entries of the concatenation, so a long
+// list is shared by several warps.
 constexpr int OWN_NT = 512;
 constexpr int OWN_WARPS = OWN_NT / 32;
-constexpr int OWN_LB = 14;  // at most 2^14 buckets
+constexpr int OWN_LBS = 13;  // staged owners: at most 2^13 buckets
+constexpr int OWN_LBL = 13;  // larger owners: at most 2^13 buckets
+constexpr int OWN_U = 8;     // 32-entry blocks per unit
+constexpr int OWN_UNIT = 32 * OWN_U;
+constexpr size_t own_pad(size_t b) { return (b + 15) / 16 * 16; }
 constexpr size_t OWN_T_BYTES = sizeof(uint32_t) * OWN_CAP;
-constexpr size_t OWN_ST_BYTES = (sizeof(uint16_t) * (OWN_CAP + 2) + 15) / 16 * 16;
-constexpr size_t OWN_HS_BYTES = sizeof(unsigned long long) * OWN_WARPS * ACC;
-constexpr size_t OWN_SMEM = OWN_T_BYTES + OWN_ST_BYTES + OWN_HS_BYTES;
+constexpr size_t OWN_ST_BYTES = own_pad(sizeof(uint32_t) * ((1 << OWN_LBS) + 1));
+constexpr size_t OWN_HS_BYTES = sizeof(int32_t) * OWN_WARPS * ACC;
+constexpr size_t OWN_SB_BYTES = sizeof(int64_t) * OWN_NT;
+constexpr size_t OWN_XE_BYTES = sizeof(uint32_t) * OWN_NT;
+constexpr size_t OWN_PP_BYTES = own_pad(sizeof(int32_t) * (OWN_NT + 1));
+constexpr int OWN_QN = 64;  // per-warp queue of keys that passed the mask test
+constexpr size_t OWN_Q_BYTES = (sizeof(uint32_t) + sizeof(uint16_t)) * OWN_QN * OWN_WARPS;
+constexpr size_t OWN_SMEM =
+    OWN_T_BYTES + OWN_ST_BYTES + OWN_HS_BYTES + OWN_SB_BYTES + OWN_XE_BYTES + OWN_PP_BYTES + OWN_Q_BYTES;
+static_assert(OWN_NT <= 65536, "queued task indices are 16-bit");
+// staged owner: st[b] = start << 16 | sub-bucket mask, b in [0, 2^lB]
 static_assert(OWN_CAP <= 65535, "staged bucket starts are 16-bit");
-static_assert(OWN_CAP == 1 << OWN_LB, "a staged owner has at most 2^OWN_LB buckets");
-static_assert(sizeof(uint32_t) * ((1 << OWN_LB) + 1) <= OWN_T_BYTES + OWN_ST_BYTES,
-              "32-bit bucket starts of a large owner fit where a staged list goes");
+// larger owner: 32-bit starts [0, 2^lB] and 32-bit masks [0, 2^lB) in the
+// space of the staged list and table
+constexpr size_t OWN_LS_BYTES = own_pad(sizeof(uint32_t) * ((1 << OWN_LBL) + 1));
+static_assert(OWN_LS_BYTES + sizeof(uint32_t) * (1 << OWN_LBL) <= OWN_T_BYTES + OWN_ST_BYTES,
+              "a larger owner's starts and masks fit where a staged list goes");
+static_assert(OWN_PIECE % OWN_NT == 0, "an item is a whole number of task tables");
 
 struct OwnArgs {
     const int64_t* row_ptr;
@@ -1265,14 +1288,15 @@ struct OwnArgs {
 };
 
 struct Owner {
-    int64_t rb, beg;  // graph's first row; start of the owner's list
-    uint32_t hl;      // owner's local id
-    uint32_t row;     // owner's global row
+    int64_t rb, beg;      // graph's first row; start of the owner's list
+    uint32_t hl;          // owner's local id
+    uint32_t row;         // owner's global row
     int D, lB, shift, s;  // degree, log2 buckets, key >> shift = bucket, graph
+    int fsh, fmask;       // sub-bucket = (key >> fsh) & fmask
     int p0, p1;           // list positions [p0, p1) whose dyads this item handles
 };
 
-__device__ __forceinline__ Owner owner_setup(const OwnArgs& a, uint4 rec) {
+__device__ __forceinline__ Owner owner_setup(const OwnArgs& a, uint4 rec, int lbmax, int lsub) {
     Owner o;
     o.s = (int)rec.y;
     o.rb = a.seg[o.s].rb;
@@ -1282,124 +1306,271 @@ __device__ __forceinline__ Owner owner_setup(const OwnArgs& a, uint4 rec) {
     o.beg = a.row_ptr[rec.x];
     o.D = (int)(a.row_ptr[rec.x + 1] - o.beg);
     const int nbits = ceil_log2((int)min(n, (int64_t)1 << 30));
-    o.lB = min(ceil_log2(o.D), OWN_LB);
+    o.lB = min(ceil_log2(o.D), lbmax);
     o.shift = max(0, nbits - o.lB);  // key >> shift < 2^lB
+    const int sb = min(o.shift, lsub);
+    o.fsh = o.shift - sb;
+    o.fmask = (1 << sb) - 1;
     o.p0 = (int)rec.z * OWN_PIECE;
     o.p1 = min(o.D, o.p0 + OWN_PIECE);
     return o;
 }
 
-// Bucket starts st[0 .. 2^lB] of the owner's list (and, with STAGE, the list).
-template <typename ST, bool STAGE>
-__device__ __forceinline__ void owner_stage(const Owner& o, const uint32_t* __restrict__ G, uint32_t* T, ST* st) {
+// Index of the owner: bucket starts and sub-bucket masks (and, for a staged
+// owner, the list).  Starts first (every bucket b in [0, 2^lB] is written by
+// exactly one thread), then the masks by atomic OR.
+__device__ __forceinline__ int owner_sub(const Owner& o, uint32_t key) { return (int)((key >> o.fsh) & o.fmask); }
+
+template <bool STAGED>
+__device__ __forceinline__ void owner_index(const Owner& o, const uint32_t* __restrict__ G, uint32_t* T,
+                                            uint32_t* st, uint32_t* ls, uint32_t* lm) {
     const int nb = 1 << o.lB;
+    if (!STAGED)
+        for (int b = threadIdx.x; b < nb; b += OWN_NT) lm[b] = 0;
     for (int j = threadIdx.x; j < o.D; j += OWN_NT) {
         const uint32_t e = __ldg(G + j);
-        if (STAGE) T[j] = e;
+        if (STAGED) T[j] = e;
         const int bj = (int)((e >> 2) >> o.shift);
         const int bp = j == 0 ? -1 : (int)((__ldg(G + j - 1) >> 2) >> o.shift);
-        for (int b = bp + 1; b <= bj; ++b) st[b] = (ST)j;
+        for (int b = bp + 1; b <= bj; ++b) {
+            if (STAGED) st[b] = (uint32_t)j << 16;
+            else ls[b] = (uint32_t)j;
+        }
         if (j == o.D - 1)
-            for (int b = bj + 1; b <= nb; ++b) st[b] = (ST)o.D;
+            for (int b = bj + 1; b <= nb; ++b) {
+                if (STAGED) st[b] = (uint32_t)o.D << 16;
+                else ls[b] = (uint32_t)o.D;
+            }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < o.D; j += OWN_NT) {
+        const uint32_t key = __ldg(G + j) >> 2;
+        const int b = (int)(key >> o.shift);
+        const uint32_t bit = 1u << owner_sub(o, key);
+        atomicOr((STAGED ? st : lm) + b, bit);
     }
 }
 
 // Entry of the owner's list with key `key`, or SENT.
-template <typename ST>
-__device__ __forceinline__ uint32_t owner_probe(const Owner& o, const uint32_t* L, const ST* st, uint32_t key) {
+template <bool STAGED>
+__device__ __forceinline__ bool owner_maybe(const Owner& o, const uint32_t* st, const uint32_t* lm, uint32_t key) {
     const uint32_t b = key >> o.shift;
-    const int j1 = (int)st[b + 1];
-    for (int j = (int)st[b]; j < j1; ++j) {
+    return ((STAGED ? st[b] : lm[b]) >> owner_sub(o, key)) & 1u;
+}
+
+template <bool STAGED>
+__device__ __forceinline__ uint32_t owner_find(const Owner& o, const uint32_t* L, const uint32_t* st,
+                                               const uint32_t* ls, uint32_t key) {
+    const uint32_t b = key >> o.shift;
+    const int j0 = STAGED ? (int)(st[b] >> 16) : (int)ls[b];
+    const int j1 = STAGED ? (int)(st[b + 1] >> 16) : (int)ls[b + 1];
+    for (int j = j0; j < j1; ++j) {
         const uint32_t e = L[j];
         if ((e >> 2) >= key) return (e >> 2) == key ? e : SENT;
     }
     return SENT;
 }
 
-// The item's dyads, 32 list positions per warp step (pulled from `next`):
-// the lanes' dyads' lists are concatenated and walked OWN_U * 32 entries at a
-// time, each entry's dyad found by a search over the lanes' running lengths;
-// a lane first issues its OWN_U loads, then looks them up.
-constexpr int OWN_U = 8;
-
-template <typename ST>
-__device__ __forceinline__ void owner_tasks(WarpHist& w, const OwnArgs& a, const Owner& o, const uint32_t* L,
-                                            const ST* st, unsigned* next) {
-    const unsigned full = 0xffffffffu;
-    const int lane = w.lane;
-    const uint32_t* G = a.adj + o.beg;
-    uint32_t c012 = 0, c102 = 0;
-    for (;;) {
-        unsigned c = 0;
-        if (lane == 0) c = atomicAdd(next, 1u);
-        c = __shfl_sync(full, c, 0);
-        if (o.p0 + (int)(c * 32u) >= o.p1) break;
-        const int pos = o.p0 + (int)(c * 32u) + lane;
-        const bool valid = pos < o.p1;
-        const uint32_t e = valid ? __ldg(G + pos) : 0u;
-        const uint32_t x = e >> 2;
-        const int dx = valid ? a.deg[o.rb + x] : 0;
-        const bool owned = valid && (dx < o.D || (dx == o.D && x < o.hl));
-        const int len = owned ? dx : 0;
-        const int64_t sb = owned ? a.row_ptr[o.rb + x] : 0;
-        int incl = len;
-#pragma unroll
-        for (int k = 1; k < 32; k <<= 1) {
-            const int v = __shfl_up_sync(full, incl, k);
-            if (lane >= k) incl += v;
-        }
-        const int total = __shfl_sync(full, incl, 31);
-        const int64_t sbx = sb - (incl - len);  // list start minus the lane's running offset
-        const uint32_t xe = (x << 2) | (e & 3u);
-        for (int f0 = 0; f0 < total; f0 += 32 * OWN_U) {
-            uint32_t se[OWN_U], xs[OWN_U];
-#pragma unroll
-            for (int k = 0; k < OWN_U; ++k) {
-                const int fi = f0 + 32 * k + lane;
-                int t = 0;  // first lane whose running length exceeds fi
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int v = __shfl_sync(full, incl, t + step - 1);
-                    if (v <= fi) t += step;
-                }
-                t = min(t, 31);
-                const int64_t bt = __shfl_sync(full, sbx, t);
-                xs[k] = __shfl_sync(full, xe, t);
-                se[k] = fi < total ? __ldg(a.adj + bt + fi) : SENT;
-            }
-#pragma unroll
-            for (int k = 0; k < OWN_U; ++k) {
-                if (se[k] == SENT) continue;
-                const uint32_t key = se[k] >> 2;
-                const uint32_t hit = owner_probe(o, L, st, key);
-                if (hit != SENT) {
-                    const uint32_t xt = xs[k] >> 2, et = xs[k] & 3u;
-                    const bool h_is_u = o.hl < xt;
-                    const uint32_t pre = h_is_u ? et : (((et & 1u) << 1) | (et >> 1));
-                    const uint32_t th = hit & 3u, tx = se[k] & 3u;
-                    on_shared(w.hs, key, h_is_u ? o.hl : xt, h_is_u ? xt : o.hl, pre, h_is_u ? th : tx,
-                              h_is_u ? tx : th);
-                    if (pre == 3) ++c102;
-                    else ++c012;
-                }
-            }
-        }
+// A shared element w of dyad <u,v> (see k_tasks): corrections of the
+// suffix terms, into the warp's 32-bit histogram.
+__device__ __forceinline__ void on_shared32(int32_t* h, uint32_t w, uint32_t ul, uint32_t vl, uint32_t pre,
+                                            uint32_t tu, uint32_t tv) {
+    if (w > vl) {
+        atomicAdd(h + pre + 4 * tu, -1);
+        atomicAdd(h + pre + 16 * tv, -1);
+        atomicAdd(h + pre + 4 * tu + 16 * tv, 1);
+    } else if (w > ul) {
+        atomicAdd(h + pre + 16 * tv, -1);
     }
-    c012 = __reduce_add_sync(full, c012);
-    c102 = __reduce_add_sync(full, c102);
-    if (lane == 0) {
-        if (c012) atomicAdd(w.hs + 64, (unsigned long long)c012);
-        if (c102) atomicAdd(w.hs + 65, (unsigned long long)c102);
-    }
-    __syncwarp();
 }
+
+// Per-warp 32-bit histogram for one graph, added (sign-extended) into that
+// graph's 64-bit accumulators when the graph changes, at the end, and before
+// any slot could leave the int32 range (each shared element moves a slot by
+// at most 1).
+struct OwnHist {
+    int32_t* hs;
+    unsigned long long* acc;
+    int tag;
+    int lane;
+    unsigned pending;  // shared elements since the last flush
+    __device__ __forceinline__ void flush() {
+        if (tag >= 0)
+            for (int j = lane; j < ACC; j += 32) {
+                const int32_t v = hs[j];
+                if (v) atomicAdd(acc + (size_t)tag * ACC + j, (unsigned long long)(long long)v);
+                hs[j] = 0;
+            }
+        __syncwarp();
+        pending = 0;
+    }
+    __device__ __forceinline__ void retag(int s) {
+        if (s != tag || pending > (1u << 30)) {
+            flush();
+            tag = s;
+        }
+    }
+};
 
 struct OwnCtl {
     unsigned idx;   // item being processed
-    unsigned next;  // task-chunk cursor of the item
+    unsigned next;  // unit cursor of the item
     uint32_t row;   // owner indexed in shared memory (~0: none)
     int seg;
+    int ntask, total;
+    unsigned long long wsum[OWN_WARPS];
 };
+
+// The task table of positions [q0, q0 + OWN_NT) of the item: for their owned
+// dyads, in list order, tsb = start of the other endpoint's list, txe = its
+// id << 2 | the owner's tag for it, tpp = running offset of the concatenated
+// lists (tpp[ntask] = total).  One position per thread; one block-wide scan
+// of (count << 40 | length).
+__device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, int q0, const uint32_t* L,
+                                            int64_t* tsb, uint32_t* txe, int32_t* tpp, OwnCtl& ctl) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pos = q0 + (int)threadIdx.x;
+    const bool valid = pos < o.p1;
+    const uint32_t e = valid ? L[pos] : 0u;
+    const uint32_t x = e >> 2;
+    const int dx = valid ? a.deg[o.rb + x] : 0;
+    const bool owned = valid && (dx < o.D || (dx == o.D && x < o.hl));
+    const unsigned long long v = owned ? ((1ull << 40) | (unsigned long long)dx) : 0ull;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const unsigned long long t = __shfl_up_sync(full, incl, k);
+        if (lane >= k) incl += t;
+    }
+    if (lane == 31) ctl.wsum[warp] = incl;
+    __syncthreads();
+    unsigned long long ex = incl - v;
+    for (int w = 0; w < warp; ++w) ex += ctl.wsum[w];
+    if (owned) {
+        const int t = (int)(ex >> 40);
+        tsb[t] = a.row_ptr[o.rb + x];
+        txe[t] = (x << 2) | (e & 3u);
+        tpp[t] = (int)(ex & 0xffffffffffull);
+    }
+    if (threadIdx.x == OWN_NT - 1) {
+        ex += v;
+        ctl.ntask = (int)(ex >> 40);
+        ctl.total = (int)(ex & 0xffffffffffull);
+        tpp[ctl.ntask] = ctl.total;
+    }
+}
+
+// Per-warp queue of keys that passed the mask test: the list entry and its
+// task-table index, OWN_QN slots used as a ring.
+struct OwnQueue {
+    uint32_t* se;
+    uint16_t* q;
+    int head, n;  // warp-uniform
+};
+
+// Look up the 32 queued keys at the head (or the first `cnt`), one per lane.
+template <bool STAGED>
+__device__ __forceinline__ void owner_drain(OwnHist& w, OwnQueue& Q, int cnt, const Owner& o, const uint32_t* L,
+                                            const uint32_t* st, const uint32_t* ls, const uint32_t* txe,
+                                            uint32_t& c012, uint32_t& c102) {
+    __syncwarp();
+    const int lane = w.lane;
+    if (lane < cnt) {
+        const int slot = (Q.head + lane) & (OWN_QN - 1);
+        const uint32_t se = Q.se[slot];
+        const uint32_t key = se >> 2;
+        const uint32_t hit = owner_find<STAGED>(o, L, st, ls, key);
+        if (hit != SENT) {
+            const uint32_t xe = txe[Q.q[slot]];
+            const uint32_t xt = xe >> 2, et = xe & 3u;
+            const bool h_is_u = o.hl < xt;
+            const uint32_t pre = h_is_u ? et : (((et & 1u) << 1) | (et >> 1));
+            const uint32_t th = hit & 3u, tx = se & 3u;
+            on_shared32(w.hs, key, h_is_u ? o.hl : xt, h_is_u ? xt : o.hl, pre, h_is_u ? th : tx, h_is_u ? tx : th);
+            if (pre == 3) ++c102;
+            else ++c012;
+        }
+    }
+    __syncwarp();
+    Q.head = (Q.head + cnt) & (OWN_QN - 1);
+    Q.n -= cnt;
+}
+
+template <bool STAGED>
+__device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnArgs& a, const Owner& o,
+                                            const uint32_t* L, const uint32_t* st, const uint32_t* ls,
+                                            const uint32_t* lm, const int64_t* tsb, const uint32_t* txe,
+                                            const int32_t* tpp, int ntask, int total, unsigned* next) {
+    const unsigned full = 0xffffffffu;
+    const int lane = w.lane;
+    const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
+    uint32_t c012 = 0, c102 = 0;
+    for (;;) {
+        unsigned u = 0;
+        if (lane == 0) u = atomicAdd(next, 1u);
+        u = __shfl_sync(full, u, 0);
+        const int f0 = (int)u * OWN_UNIT;
+        if (f0 >= total) break;
+        // qb: last task starting at or before f0 - 1 (-1 when f0 = 0)
+        int qb = -1;
+        if (f0 > 0) {
+            int lo = 0, hi = ntask;  // count of tasks with start <= f0 - 1
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (tpp[mid] <= f0 - 1) lo = mid + 1;
+                else hi = mid;
+            }
+            qb = lo - 1;
+        }
+        const int kmax = min(OWN_U, (total - f0 + 31) >> 5);
+        uint32_t se[OWN_U];
+        int qk[OWN_U];
+#pragma unroll
+        for (int k = 0; k < OWN_U; ++k) {
+            se[k] = SENT;
+            qk[k] = 0;
+            if (k < kmax) {
+                const int base = f0 + 32 * k;
+                // tasks starting inside [base, base + 32): one bit each
+                const int j = qb + 1 + lane;
+                const int sj = j < ntask ? tpp[j] : 0x7fffffff;
+                const unsigned bit = sj < base + 32 ? 1u << (sj - base) : 0u;
+                const unsigned M = __reduce_or_sync(full, bit);
+                const int q = qb + __popc(M & upto);
+                const int f = base + lane;
+                if (f < total) {
+                    se[k] = __ldg(a.adj + tsb[q] + (f - tpp[q]));
+                    qk[k] = q;
+                }
+                qb = __shfl_sync(full, q, 31);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < OWN_U; ++k) {
+            if (k < kmax) {
+                const bool pass = se[k] != SENT && owner_maybe<STAGED>(o, st, lm, se[k] >> 2);
+                const unsigned m = __ballot_sync(full, pass);
+                if (pass) {
+                    const int slot = (Q.head + Q.n + __popc(m & (upto >> 1))) & (OWN_QN - 1);
+                    Q.se[slot] = se[k];
+                    Q.q[slot] = (uint16_t)qk[k];
+                }
+                Q.n += __popc(m);
+                if (Q.n >= 32) owner_drain<STAGED>(w, Q, 32, o, L, st, ls, txe, c012, c102);
+            }
+        }
+    }
+    if (Q.n > 0) owner_drain<STAGED>(w, Q, Q.n, o, L, st, ls, txe, c012, c102);  // the table changes next
+    c012 = __reduce_add_sync(full, c012);
+    c102 = __reduce_add_sync(full, c102);
+    if (lane == 0) {
+        if (c012) atomicAdd(w.hs + 64, (int)c012);
+        if (c102) atomicAdd(w.hs + 65, (int)c102);
+    }
+    w.pending += c012 + c102;
+    __syncwarp();
+}
 
 // Persistent: first the pieces of owners above OWN_CAP (bucket starts in
 // shared memory, the list read from global memory), then the others (list
@@ -1407,19 +1578,26 @@ struct OwnCtl {
 __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
     extern __shared__ __align__(16) unsigned char own_smem[];
     uint32_t* T = reinterpret_cast<uint32_t*>(own_smem);
-    uint16_t* st16 = reinterpret_cast<uint16_t*>(own_smem + OWN_T_BYTES);
-    uint32_t* st32 = reinterpret_cast<uint32_t*>(own_smem);
-    unsigned long long* hs_all = reinterpret_cast<unsigned long long*>(own_smem + OWN_T_BYTES + OWN_ST_BYTES);
+    uint32_t* st = reinterpret_cast<uint32_t*>(own_smem + OWN_T_BYTES);
+    uint32_t* ls = reinterpret_cast<uint32_t*>(own_smem);
+    uint32_t* lm = reinterpret_cast<uint32_t*>(own_smem + OWN_LS_BYTES);
+    unsigned char* p = own_smem + OWN_T_BYTES + OWN_ST_BYTES;
+    int32_t* hs_all = reinterpret_cast<int32_t*>(p);
+    p += OWN_HS_BYTES;
+    int64_t* tsb = reinterpret_cast<int64_t*>(p);
+    p += OWN_SB_BYTES;
+    uint32_t* txe = reinterpret_cast<uint32_t*>(p);
+    p += OWN_XE_BYTES;
+    int32_t* tpp = reinterpret_cast<int32_t*>(p);
+    p += OWN_PP_BYTES;
     __shared__ OwnCtl ctl;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpHist w{hs_all + (size_t)warp * ACC, a.acc, -1, lane};
+    OwnHist w{hs_all + (size_t)warp * ACC, a.acc, -1, lane, 0u};
+    OwnQueue Q{reinterpret_cast<uint32_t*>(p) + warp * OWN_QN,
+               reinterpret_cast<uint16_t*>(p + sizeof(uint32_t) * OWN_QN * OWN_WARPS) + warp * OWN_QN, 0, 0};
     for (int j = lane; j < ACC; j += 32) w.hs[j] = 0;
     __syncwarp();
     const unsigned nlarge = min(a.cnt[0], a.cap), nsmall = min(a.cnt[1], a.cap - nlarge);
-    if (threadIdx.x == 0) {
-        ctl.row = ~0u;
-        ctl.seg = -1;
-    }
     for (int phase = 0; phase < 2; ++phase) {
         const unsigned nitems = phase == 0 ? nlarge : nsmall;
         if (threadIdx.x == 0) {  // the index in shared memory changes form between phases
@@ -1434,25 +1612,33 @@ __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
             __syncthreads();
             const unsigned idx = ctl.idx;
             if (idx >= nitems) break;
-            const Owner o = owner_setup(a, a.list[phase == 0 ? a.cap - 1 - idx : idx]);
+            const Owner o = phase == 0 ? owner_setup(a, a.list[a.cap - 1 - idx], OWN_LBL, 5)
+                                       : owner_setup(a, a.list[idx], OWN_LBS, 4);
             const uint32_t* G = a.adj + o.beg;
-            if (o.row != ctl.row || o.s != ctl.seg) {  // index the owner (unless the last item had it)
-                if (phase == 0) owner_stage<uint32_t, false>(o, G, T, st32);
-                else owner_stage<uint16_t, true>(o, G, T, st16);
+            const bool restage = o.row != ctl.row || o.s != ctl.seg;
+            if (restage) {  // index the owner (unless the last item had it)
+                if (phase == 0) owner_index<false>(o, G, T, st, ls, lm);
+                else owner_index<true>(o, G, T, st, ls, lm);
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    ctl.row = o.row;
-                    ctl.seg = o.s;
-                }
+            }
+            if (threadIdx.x == 0 && restage) {  // all threads have compared
+                ctl.row = o.row;
+                ctl.seg = o.s;
             }
             w.retag(o.s);
-            if (phase == 0) owner_tasks(w, a, o, G, st32, &ctl.next);
-            else owner_tasks(w, a, o, T, st16, &ctl.next);
-            __syncthreads();
+            for (int q0 = o.p0; q0 < o.p1; q0 += OWN_NT) {
+                if (phase == 0) owner_table(a, o, q0, G, tsb, txe, tpp, ctl);
+                else owner_table(a, o, q0, T, tsb, txe, tpp, ctl);
+                if (threadIdx.x == 0) ctl.next = 0;
+                __syncthreads();
+                const int ntask = ctl.ntask, total = ctl.total;
+                if (phase == 0) owner_units<false>(w, Q, a, o, G, st, ls, lm, tsb, txe, tpp, ntask, total, &ctl.next);
+                else owner_units<true>(w, Q, a, o, T, st, ls, lm, tsb, txe, tpp, ntask, total, &ctl.next);
+                __syncthreads();
+            }
         }
     }
-    __syncwarp();
-    flush_hist<WARPS>(w.hs, w.acc, w.tag, lane);
+    w.flush();
 }
 
 // ------------------------------------------------------------- host side --
@@ -2127,21 +2313,30 @@ tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t m
     };
     float cur_ms = 0;
     if (tc_status s = timeit(cur, cur_ms); s != TC_OK) return s;
+    // coordinate descent over these fields, two passes; the owner threshold
+    // first (it decides which dyads reach the merge bins at all)
+    const int32_t own_c[] = {0, 64, 128, 256, 512, 1024, 4096};
     const int32_t thr_thread_c[] = {0, 16, 32, 48, 64, 96, 128, 192};
     const int32_t thr_warp_c[] = {64, 128, 256, 512, 1024};
     const int32_t stream_c[] = {0, 256, 1024, 1 << 30};
     const int32_t chunk_c[] = {256, 512, 1024};
     const int32_t pers_c[] = {0, 1};
+    struct Field {
+        int32_t tc_opts::*f;
+        const int32_t* cand;
+        int nc;
+    };
+    const Field fields[] = {{&tc_opts::own_min, own_c, 7},       {&tc_opts::thr_thread, thr_thread_c, 8},
+                            {&tc_opts::thr_warp, thr_warp_c, 5}, {&tc_opts::stream_max, stream_c, 4},
+                            {&tc_opts::chunk, chunk_c, 3},       {&tc_opts::persistent, pers_c, 2}};
     for (int pass = 0; pass < 2; ++pass) {
-        for (int field = 0; field < 5; ++field) {
-            const int32_t* cand = field == 0 ? thr_thread_c : field == 1 ? thr_warp_c : field == 2 ? stream_c
-                                : field == 3 ? chunk_c : pers_c;
-            const int nc = field == 0 ? 8 : field == 1 ? 5 : field == 2 ? 4 : field == 3 ? 3 : 2;
+        for (const Field& fd : fields) {
+            const int32_t* cand = fd.cand;
+            const int nc = fd.nc;
             for (int k = 0; k < nc; ++k) {
                 if (max_trials > 0 && trials >= max_trials) break;
                 tc_opts o = cur;
-                int32_t* f = field == 0 ? &o.thr_thread : field == 1 ? &o.thr_warp : field == 2 ? &o.stream_max
-                           : field == 3 ? &o.chunk : &o.persistent;
+                int32_t* f = &(o.*fd.f);
                 if (*f == cand[k]) continue;
                 *f = cand[k];
                 if (o.thr_thread > o.thr_warp) continue;

@@ -20,19 +20,20 @@ BIG = 1 << 30
 # chunk (tiny chunks: every task split), and small mixed thresholds
 BINS = {
     "default": {},
-    "nostream": dict(stream_max=0),
-    "stream_all": dict(thr_thread=0, thr_warp=0, stream_max=1024),
-    "stream_chunks": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30),
-    "hub_separate": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30, persistent=0),
-    "thread": dict(thr_thread=BIG, thr_warp=BIG),
-    "warp": dict(thr_thread=0, thr_warp=BIG, stream_max=0),
-    "separate": dict(persistent=0),
-    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1, stream_max=0, persistent=0),
-    "wtile": dict(thr_thread=0, thr_warp=0, chunk=256, stream_max=0),
-    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1, stream_max=8, persistent=0),
-    "mixed": dict(thr_thread=8, thr_warp=40, chunk=512),
-    "persistent": dict(persistent=1),
-    "persistent_small": dict(persistent=1, thr_thread=8, thr_warp=64, chunk=256, stream_max=32),
+    "no_owner": dict(own_min=0),
+    "nostream": dict(stream_max=0, own_min=0),
+    "stream_all": dict(thr_thread=0, thr_warp=0, stream_max=1024, own_min=0),
+    "stream_chunks": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30, own_min=0),
+    "hub_separate": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30, persistent=0, own_min=0),
+    "thread": dict(thr_thread=BIG, thr_warp=BIG, own_min=0),
+    "warp": dict(thr_thread=0, thr_warp=BIG, stream_max=0, own_min=0),
+    "separate": dict(persistent=0, own_min=0),
+    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1, stream_max=0, persistent=0, own_min=0),
+    "wtile": dict(thr_thread=0, thr_warp=0, chunk=256, stream_max=0, own_min=0),
+    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1, stream_max=8, persistent=0, own_min=0),
+    "mixed": dict(thr_thread=8, thr_warp=40, chunk=512, own_min=0),
+    "persistent": dict(persistent=1, own_min=0),
+    "persistent_small": dict(persistent=1, thr_thread=8, thr_warp=64, chunk=256, stream_max=32, own_min=0),
     "owner_all": dict(own_min=1),
     "owner_mid": dict(own_min=64, thr_thread=8, thr_warp=64),
     "owner_sep": dict(own_min=32, persistent=0, stream_max=0),
@@ -184,11 +185,13 @@ def test_hub_tasks_stage_short_list_in_pieces():
     for h, D in enumerate(degs):  # |N(h)|: distinct neighbours either way
         assert np.unique(np.concatenate([dst[src == h], src[dst == h]])).size == D
     hubs = sum(1 for i in range(H) for j in range(i + 1, H) if min(degs[i], degs[j]) > 1024)
-    for name in ("default", "separate", "stream_chunks", "hub_separate", "nostream"):
+    for name in ("default", "no_owner", "separate", "stream_chunks", "hub_separate", "nostream"):
         o = tc.tc_opts_default(profile=1, **BINS[name])
         assert gpu_census(n, src, dst, o) == want, name
         p = tc.tc_census_profile()
-        if o.stream_max > 1024:
+        if o.own_min > 0:  # the hubs own their dyads: looked up, not streamed
+            assert p["hub_tasks"] == 0 and p["owner_tasks"] > 0, name
+        elif o.stream_max > 1024:
             assert p["hub_tasks"] == hubs, name
             assert p["hub_entries"] > 0
         else:

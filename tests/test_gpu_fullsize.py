@@ -43,8 +43,8 @@ def test_single_graph_workloads_match_oracle(name):
         c = gold["census"]
         assert sum(c) == a.n * (a.n - 1) * (a.n - 2) // 6
         out = torch.zeros(17, dtype=torch.int64, device="cuda")
-        for o in (tc.tc_opts_default(), tc.tc_opts_default(persistent=0),
-                  tc.tc_opts_default(thr_warp=256, chunk=512, stream_max=256)):
+        for o in (tc.tc_opts_default(), tc.tc_opts_default(persistent=0), tc.tc_opts_default(own_min=0),
+                  tc.tc_opts_default(thr_warp=256, chunk=512, stream_max=256, own_min=1024)):
             tc.tc_census(g, o, out=out)
             torch.cuda.synchronize()
             assert tc.census_from_device_words(out.cpu().tolist()) == c
