@@ -133,7 +133,8 @@ typedef struct {
                                 positions) */
     int64_t owner_tasks;     /* dyads it handled (in no bin) */
     int64_t owner_entries;   /* their |N(u)|+|N(v)| */
-    int64_t owner_probes;    /* lookups: the non-owner endpoints' list lengths */
+    int64_t owner_probes;    /* lookups: entries of the non-owner endpoints'
+                                lists above min(u, v) */
     int64_t owner_staged;    /* owner-list entries staged */
 } tc_profile_t;
 

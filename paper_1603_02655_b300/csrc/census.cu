@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                     if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
                         Os[0] += 1;
                         Os[1] += (unsigned long long)L;
-                        Os[2] += (unsigned long long)min(d, dv);
+
                     } else {
                         bin = L <= bp.thr_thread ? 0
                               : L <= bp.thr_warp ? 1
@@ -588,7 +588,7 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
                 eB = ib < be ? __ldg(adj + ib) : SENT;
             }
         }
-        if (c) atomicAdd(h + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+        (void)c;  // shared elements: their dyadic share comes from the closed-triad counts (k_fold)
         if (INS && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 0, clock64() - t0);
     }
     __syncwarp();
@@ -789,10 +789,8 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
     uint32_t* rawB = raw + ((oA + na + 1 + 3) & ~3);
     const int oB = load_span<32>(rawB, adj, bb + js, nb + 1, min(bb + je + 1, be), lane);
     __syncwarp();
-    uint32_t c = shared_elements<32>(raw + oA, na, rawB + oB, nb, ia_start != nullptr, (uint32_t)(r.x - rb),
-                                     (uint32_t)(r.y - rb), pre, w.hs, lane);
-    c = __reduce_add_sync(0xffffffffu, c);
-    if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    shared_elements<32>(raw + oA, na, rawB + oB, nb, ia_start != nullptr, (uint32_t)(r.x - rb), (uint32_t)(r.y - rb),
+                        pre, w.hs, lane);
     __syncwarp();
     if (INS && lane == 0 && sampled(w.ins, r.x, r.y))
         record(w.ins, r.x, r.y, ia_start ? 2 : 1, clock64() - t0);
@@ -925,8 +923,7 @@ __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const in
             if (k < 32) break;
         }
     }
-    c = __reduce_add_sync(full, c);
-    if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    (void)c;
     __syncwarp();
     if (INS && lane == 0 && sampled(w.ins, r.x, r.y)) record(w.ins, r.x, r.y, 3, clock64() - t0);
 }
@@ -1064,8 +1061,7 @@ __device__ __forceinline__ void hub_item(WarpHist& w, uint32_t* buf, const int64
             if (k < 32 && !(js == cs && sc + cs < nS)) break;
         }
     }
-    c = __reduce_add_sync(full, c);
-    if (lane == 0 && c) atomicAdd(w.hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+    (void)c;
     __syncwarp();
 }
 
@@ -1195,10 +1191,8 @@ __global__ void __launch_bounds__(CTA_NT) k_cta(const int64_t* __restrict__ row_
         const int oA = load_span<CTA_NT>(rawA, adj, ab + is, na + 1, ab + ie, tid);
         const int oB = load_span<CTA_NT>(rawB, adj, bb + js, nb + 1, min(bb + je + 1, be), tid);
         __syncthreads();
-        uint32_t c = shared_elements<CTA_NT>(rawA + oA, na, rawB + oB, nb, true, (uint32_t)(r.x - rb),
-                                             (uint32_t)(r.y - rb), pre, hs, tid);
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0 && c) atomicAdd(hs + 64 + (pre == 3 ? 1 : 0), (unsigned long long)c);
+        shared_elements<CTA_NT>(rawA + oA, na, rawB + oB, nb, true, (uint32_t)(r.x - rb), (uint32_t)(r.y - rb), pre,
+                                hs, tid);
     }
     __syncthreads();
     if (tid < 32) flush_hist<1>(hs, acc, tag, lane);
@@ -1215,8 +1209,14 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 #pragma unroll
     for (int t = 0; t < 16; ++t) cnt[t] = 0;
     for (int code = 0; code < 64; ++code) cnt[triad_type(code)] += h[code];
-    cnt[1] += h[64];
-    cnt[2] += h[65];
+    // Slots 64/65 hold sum (n - |N(u)| - |N(v)|) over asymmetric / mutual
+    // dyads; the dyadic term n - |S| - 2 adds c_uv = |N(u) n N(v)| per dyad.
+    // A triad whose three pairs are all adjacent adds 1 to c_uv of each of
+    // its dyads, so sum_asym c_uv = 3(030T + 030C) + 2(120D + 120U + 120C)
+    // + 210 and sum_mutual c_uv = (120D + 120U + 120C) + 2 * 210 + 3 * 300.
+    const unsigned long long c120 = cnt[11] + cnt[12] + cnt[13];
+    cnt[1] += h[64] + 3 * (cnt[8] + cnt[9]) + 2 * c120 + cnt[14];
+    cnt[2] += h[65] + c120 + 2 * cnt[14] + 3 * cnt[15];
     const unsigned __int128 n = (unsigned __int128)(unsigned long long)seg[s].n;
     unsigned __int128 all = n >= 3 ? n * (n - 1) * (n - 2) / 6 : 0;
     for (int t = 1; t < 16; ++t) all -= cnt[t];
@@ -1285,6 +1285,7 @@ struct OwnArgs {
     const unsigned* cnt;     // [2] pieces of larger, smaller owners
     unsigned* cursor;        // [2]
     unsigned long long* acc;
+    unsigned long long* lookups;  // keys looked up (profile)
 };
 
 struct Owner {
@@ -1421,11 +1422,13 @@ struct OwnCtl {
     unsigned long long wsum[OWN_WARPS];
 };
 
-// The task table of positions [q0, q0 + OWN_NT) of the item: for their owned
-// dyads, in list order, tsb = start of the other endpoint's list, txe = its
-// id << 2 | the owner's tag for it, tpp = running offset of the concatenated
-// lists (tpp[ntask] = total).  One position per thread; one block-wide scan
-// of (count << 40 | length).
+// The task table of positions [q0, q0 + OWN_NT) of the item: for each owned
+// dyad {h, x}, in list order, the part of x's list above u = min(h, x) (a
+// shared element below both endpoints changes no triad code: its share of the
+// dyadic term comes from the closed-triad counts in k_fold).  tsb = start of
+// that part, txe = x << 2 | the owner's tag for x, tpp = running offset of
+// the concatenated parts (tpp[ntask] = total).  One position per thread; one
+// block-wide scan of (count << 40 | length).
 __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, int q0, const uint32_t* L,
                                             int64_t* tsb, uint32_t* txe, int32_t* tpp, OwnCtl& ctl) {
     const unsigned full = 0xffffffffu;
@@ -1436,7 +1439,21 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
     const uint32_t x = e >> 2;
     const int dx = valid ? a.deg[o.rb + x] : 0;
     const bool owned = valid && (dx < o.D || (dx == o.D && x < o.hl));
-    const unsigned long long v = owned ? ((1ull << 40) | (unsigned long long)dx) : 0ull;
+    int len = 0;
+    int64_t sb = 0;
+    if (owned) {
+        sb = a.row_ptr[o.rb + x];
+        const uint32_t u = min(o.hl, x);
+        int lo = 0, hi = dx;  // first entry of x's list above u
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((__ldg(a.adj + sb + mid) >> 2) <= u) lo = mid + 1;
+            else hi = mid;
+        }
+        len = dx - lo;
+        sb += lo;
+    }
+    const unsigned long long v = len > 0 ? ((1ull << 40) | (unsigned long long)len) : 0ull;
     unsigned long long incl = v;
 #pragma unroll
     for (int k = 1; k < 32; k <<= 1) {
@@ -1447,9 +1464,9 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
     __syncthreads();
     unsigned long long ex = incl - v;
     for (int w = 0; w < warp; ++w) ex += ctl.wsum[w];
-    if (owned) {
+    if (len > 0) {
         const int t = (int)(ex >> 40);
-        tsb[t] = a.row_ptr[o.rb + x];
+        tsb[t] = sb;
         txe[t] = (x << 2) | (e & 3u);
         tpp[t] = (int)(ex & 0xffffffffffull);
     }
@@ -1458,6 +1475,7 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
         ctl.ntask = (int)(ex >> 40);
         ctl.total = (int)(ex & 0xffffffffffull);
         tpp[ctl.ntask] = ctl.total;
+        if (ctl.total) atomicAdd(a.lookups, (unsigned long long)ctl.total);
     }
 }
 
@@ -1488,8 +1506,7 @@ __device__ __forceinline__ void owner_drain(OwnHist& w, OwnQueue& Q, int cnt, co
             const uint32_t pre = h_is_u ? et : (((et & 1u) << 1) | (et >> 1));
             const uint32_t th = hit & 3u, tx = se & 3u;
             on_shared32(w.hs, key, h_is_u ? o.hl : xt, h_is_u ? xt : o.hl, pre, h_is_u ? th : tx, h_is_u ? tx : th);
-            if (pre == 3) ++c102;
-            else ++c012;
+            ++c012;  // shared elements (for the flush bound)
         }
     }
     __syncwarp();
@@ -1562,13 +1579,7 @@ __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnAr
         }
     }
     if (Q.n > 0) owner_drain<STAGED>(w, Q, Q.n, o, L, st, ls, txe, c012, c102);  // the table changes next
-    c012 = __reduce_add_sync(full, c012);
-    c102 = __reduce_add_sync(full, c102);
-    if (lane == 0) {
-        if (c012) atomicAdd(w.hs + 64, (int)c012);
-        if (c102) atomicAdd(w.hs + 65, (int)c102);
-    }
-    w.pending += c012 + c102;
+    w.pending += __reduce_add_sync(full, c012 + c102);
     __syncwarp();
 }
 
@@ -1832,7 +1843,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         TC_CUDA(cudaGetLastError());
         mark(2);
         if (o.own_min > 0) {
-            const OwnArgs oa{set.row_ptr, set.adj, set.deg, d_seg, bins.own, bins.own_cap, ctr + 28, ctr + 26, acc};
+            const OwnArgs oa{set.row_ptr, set.adj, set.deg, d_seg, bins.own, bins.own_cap, ctr + 28, ctr + 26, acc,
+                             bins.own_stat + 2};
             k_owner<<<L.sms * L.occ_owner, OWN_NT, OWN_SMEM, st>>>(oa);
             TC_CUDA(cudaGetLastError());
         }

@@ -136,6 +136,34 @@ def test_random_graphs_vs_brute(seed):
     assert sum(b) == oracle.choose3(n)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_common_neighbour_sums_follow_closed_triads(seed):
+    # The CUDA path drops shared elements below both endpoints of a dyad and
+    # restores their dyadic share from the final counts: summed over the
+    # asymmetric (mutual) dyads, |N(u) n N(v)| equals the number of closed
+    # triads weighted by how many asymmetric (mutual) dyads each has.  Checked
+    # here by brute force on the oracle's adjacency and brute-force census.
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(4, 70))
+    src, dst = rand_graph(rng, n, float(rng.choice([0.05, 0.2, 0.6])), float(rng.choice([0.0, 0.3, 1.0])))
+    g = oracle.Graph(n, src, dst)
+    arcs = set(zip(src.tolist(), dst.tolist())) - {(i, i) for i in range(n)}
+    asym = mutual = 0
+    for u in range(n):
+        for v in range(u + 1, n):
+            a, b = (u, v) in arcs, (v, u) in arcs
+            if a or b:
+                c = g.common(u, v)
+                if a and b:
+                    mutual += c
+                else:
+                    asym += c
+    t = dict(zip(NAMES, oracle.brute_census(n, src, dst)))
+    c120 = t["120D"] + t["120U"] + t["120C"]
+    assert asym == 3 * (t["030T"] + t["030C"]) + 2 * c120 + t["210"]
+    assert mutual == c120 + 2 * t["210"] + 3 * t["300"]
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_random_graphs_vs_external(seed):
     rng = np.random.default_rng(100 + seed)
