@@ -1425,10 +1425,14 @@ struct OwnCtl {
 // The task table of positions [q0, q0 + OWN_NT) of the item: for each owned
 // dyad {h, x}, in list order, the part of x's list above u = min(h, x) (a
 // shared element below both endpoints changes no triad code: its share of the
-// dyadic term comes from the closed-triad counts in k_fold).  tsb = start of
-// that part, txe = x << 2 | the owner's tag for x, tpp = running offset of
-// the concatenated parts (tpp[ntask] = total).  One position per thread; one
-// block-wide scan of (count << 40 | length).
+// dyadic term comes from the closed-triad counts in k_fold).  The parts are
+// concatenated in "slots", each part widened to whole aligned 16-byte groups
+// of x's list (lead entries before it, trail after it, both < 4), so that
+// every 4 slots from a multiple of 4 are one aligned 16-byte load of one
+// list.  tsb = aligned word index << 4 | trail << 2 | lead, txe = x << 2 | the
+// owner's tag for x, tpp = first slot (tpp[ntask] = total slots).  One
+// position per thread; one block-wide scan of
+// (count << 54 | slots << 27 | lookups).
 __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, int q0, const uint32_t* L,
                                             int64_t* tsb, uint32_t* txe, int32_t* tpp, OwnCtl& ctl) {
     const unsigned full = 0xffffffffu;
@@ -1439,7 +1443,7 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
     const uint32_t x = e >> 2;
     const int dx = valid ? a.deg[o.rb + x] : 0;
     const bool owned = valid && (dx < o.D || (dx == o.D && x < o.hl));
-    int len = 0;
+    int len = 0, lead = 0, slots = 0;
     int64_t sb = 0;
     if (owned) {
         sb = a.row_ptr[o.rb + x];
@@ -1452,8 +1456,11 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
         }
         len = dx - lo;
         sb += lo;
+        lead = (int)(sb & 3);
+        slots = (lead + len + 3) & ~3;
     }
-    const unsigned long long v = len > 0 ? ((1ull << 40) | (unsigned long long)len) : 0ull;
+    const unsigned long long v =
+        len > 0 ? ((1ull << 54) | ((unsigned long long)slots << 27) | (unsigned long long)len) : 0ull;
     unsigned long long incl = v;
 #pragma unroll
     for (int k = 1; k < 32; k <<= 1) {
@@ -1465,17 +1472,19 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
     unsigned long long ex = incl - v;
     for (int w = 0; w < warp; ++w) ex += ctl.wsum[w];
     if (len > 0) {
-        const int t = (int)(ex >> 40);
-        tsb[t] = sb;
+        const int t = (int)(ex >> 54);
+        const int trail = slots - lead - len;
+        tsb[t] = ((sb - lead) << 4) | (int64_t)(trail << 2) | lead;
         txe[t] = (x << 2) | (e & 3u);
-        tpp[t] = (int)(ex & 0xffffffffffull);
+        tpp[t] = (int)((ex >> 27) & 0x7ffffff);
     }
     if (threadIdx.x == OWN_NT - 1) {
         ex += v;
-        ctl.ntask = (int)(ex >> 40);
-        ctl.total = (int)(ex & 0xffffffffffull);
+        ctl.ntask = (int)(ex >> 54);
+        ctl.total = (int)((ex >> 27) & 0x7ffffff);
         tpp[ctl.ntask] = ctl.total;
-        if (ctl.total) atomicAdd(a.lookups, (unsigned long long)ctl.total);
+        const unsigned long long lookups = ex & 0x7ffffff;
+        if (lookups) atomicAdd(a.lookups, lookups);
     }
 }
 
@@ -1529,53 +1538,54 @@ __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnAr
         u = __shfl_sync(full, u, 0);
         const int f0 = (int)u * OWN_UNIT;
         if (f0 >= total) break;
-        // qb: last task starting at or before f0 - 1 (-1 when f0 = 0)
-        int qb = -1;
-        if (f0 > 0) {
-            int lo = 0, hi = ntask;  // count of tasks with start <= f0 - 1
+        // this lane's 8 slots [s0, s0 + 8): two aligned 16-byte groups, each
+        // inside one dyad's part (parts are whole groups)
+        const int s0 = f0 + 8 * lane;
+        uint4 g[2];
+        int tq[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            g[k] = make_uint4(SENT, SENT, SENT, SENT);
+            tq[k] = 0;
+        }
+        if (s0 < total) {
+            int lo = 0, hi = ntask - 1;  // last dyad whose first slot is <= s0
             while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (tpp[mid] <= f0 - 1) lo = mid + 1;
-                else hi = mid;
+                const int mid = (lo + hi + 1) >> 1;
+                if (tpp[mid] <= s0) lo = mid;
+                else hi = mid - 1;
             }
-            qb = lo - 1;
-        }
-        const int kmax = min(OWN_U, (total - f0 + 31) >> 5);
-        uint32_t se[OWN_U];
-        int qk[OWN_U];
+            tq[0] = lo;
+            tq[1] = lo + (tpp[lo + 1] <= s0 + 4 ? 1 : 0);
 #pragma unroll
-        for (int k = 0; k < OWN_U; ++k) {
-            se[k] = SENT;
-            qk[k] = 0;
-            if (k < kmax) {
-                const int base = f0 + 32 * k;
-                // tasks starting inside [base, base + 32): one bit each
-                const int j = qb + 1 + lane;
-                const int sj = j < ntask ? tpp[j] : 0x7fffffff;
-                const unsigned bit = sj < base + 32 ? 1u << (sj - base) : 0u;
-                const unsigned M = __reduce_or_sync(full, bit);
-                const int q = qb + __popc(M & upto);
-                const int f = base + lane;
-                if (f < total) {
-                    se[k] = __ldg(a.adj + tsb[q] + (f - tpp[q]));
-                    qk[k] = q;
+            for (int k = 0; k < 2; ++k) {
+                const int sk = s0 + 4 * k;
+                if (sk < total) {
+                    const int64_t d = tsb[tq[k]];
+                    g[k] = __ldg(reinterpret_cast<const uint4*>(a.adj + (d >> 4) + (sk - tpp[tq[k]])));
+                    // slots of the group outside the part: the lead of its first
+                    // group, the trail of its last
+                    const int rel = sk - tpp[tq[k]];
+                    const int lead = (int)(d & 3), end = tpp[tq[k] + 1] - tpp[tq[k]] - (int)((d >> 2) & 3);
+                    if (rel + 0 < lead || rel + 0 >= end) g[k].x = SENT;
+                    if (rel + 1 < lead || rel + 1 >= end) g[k].y = SENT;
+                    if (rel + 2 < lead || rel + 2 >= end) g[k].z = SENT;
+                    if (rel + 3 < lead || rel + 3 >= end) g[k].w = SENT;
                 }
-                qb = __shfl_sync(full, q, 31);
             }
         }
+        const uint32_t se[8] = {g[0].x, g[0].y, g[0].z, g[0].w, g[1].x, g[1].y, g[1].z, g[1].w};
 #pragma unroll
-        for (int k = 0; k < OWN_U; ++k) {
-            if (k < kmax) {
-                const bool pass = se[k] != SENT && owner_maybe<STAGED>(o, st, lm, se[k] >> 2);
-                const unsigned m = __ballot_sync(full, pass);
-                if (pass) {
-                    const int slot = (Q.head + Q.n + __popc(m & (upto >> 1))) & (OWN_QN - 1);
-                    Q.se[slot] = se[k];
-                    Q.q[slot] = (uint16_t)qk[k];
-                }
-                Q.n += __popc(m);
-                if (Q.n >= 32) owner_drain<STAGED>(w, Q, 32, o, L, st, ls, txe, c012, c102);
+        for (int j = 0; j < 8; ++j) {
+            const bool pass = se[j] != SENT && owner_maybe<STAGED>(o, st, lm, se[j] >> 2);
+            const unsigned m = __ballot_sync(full, pass);
+            if (pass) {
+                const int slot = (Q.head + Q.n + __popc(m & (upto >> 1))) & (OWN_QN - 1);
+                Q.se[slot] = se[j];
+                Q.q[slot] = (uint16_t)tq[j >> 2];
             }
+            Q.n += __popc(m);
+            if (Q.n >= 32) owner_drain<STAGED>(w, Q, 32, o, L, st, ls, txe, c012, c102);
         }
     }
     if (Q.n > 0) owner_drain<STAGED>(w, Q, Q.n, o, L, st, ls, txe, c012, c102);  // the table changes next
