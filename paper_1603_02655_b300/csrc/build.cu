@@ -65,18 +65,32 @@ __global__ void k_heads(const uint64_t* __restrict__ k, int64_t N, int32_t* __re
     }
 }
 
+// One thread per sorted key; the first key of each (row, nbr) run writes the
+// entry with the OR of the run's tags, and counts it into its row's length
+// and the row's count of that tag (atomics aggregated over the warp's lanes
+// with the same row, resp. row and tag: sorted keys keep a row's entries in
+// neighbouring lanes).
 __global__ void k_write(const uint64_t* __restrict__ k, int64_t N, const int32_t* __restrict__ head,
                         const int32_t* __restrict__ pos, int sh, uint32_t nbr_mask,
-                        uint32_t* __restrict__ adj, unsigned long long* __restrict__ cnt) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (!head[i]) continue;
-        const uint64_t key = k[i] >> 2;
+                        uint32_t* __restrict__ adj, unsigned long long* __restrict__ cnt,
+                        int32_t* __restrict__ vtag) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < N; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;  // whole warps iterate together
+        const bool is_head = i < N && head[i];
+        uint64_t row = ~0ull;
         uint32_t tag = 0;
-        for (int64_t j = i; j < N && (k[j] >> 2) == key; ++j) tag |= (uint32_t)(k[j] & 3u);
-        const uint32_t nbr = (uint32_t)(key & nbr_mask);
-        adj[pos[i]] = (nbr << 2) | tag;
-        atomicAdd(&cnt[k[i] >> sh], 1ull);
+        if (is_head) {
+            const uint64_t key = k[i] >> 2;
+            for (int64_t j = i; j < N && (k[j] >> 2) == key; ++j) tag |= (uint32_t)(k[j] & 3u);
+            const uint32_t nbr = (uint32_t)(key & nbr_mask);
+            adj[pos[i]] = (nbr << 2) | tag;
+            row = k[i] >> sh;
+        }
+        const unsigned same_row = __match_any_sync(0xffffffffu, row);
+        const unsigned same_tag = __match_any_sync(0xffffffffu, (row << 2) | tag);
+        if (is_head && lane == __ffs(same_row) - 1) atomicAdd(&cnt[row], (unsigned long long)__popc(same_row));
+        if (is_head && lane == __ffs(same_tag) - 1) atomicAdd(&vtag[3 * row + tag - 1], __popc(same_tag));
     }
 }
 
@@ -86,61 +100,51 @@ __global__ void k_fill_sent(uint32_t* __restrict__ p, int64_t count) {
         p[i] = SENT;
 }
 
-// Warp per row: degree, per-row tag counts, and per-graph statistics
-// (accumulated per warp while its rows stay in one graph).
-__global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+// Thread per row: degree, and per-graph statistics from the row's degree and
+// tag counts (k_write counted the tags); a warp whose rows lie in one graph
+// adds its sums with one atomic each.
+__global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ vtag,
                            const int64_t* __restrict__ voff, int G, int64_t total_n,
-                           int32_t* __restrict__ deg, int32_t* __restrict__ vtag,
-                           unsigned long long* __restrict__ gstat /* [G][6] */,
-                           unsigned long long* __restrict__ cursor) {
+                           int32_t* __restrict__ deg, unsigned long long* __restrict__ gstat /* [G][6] */) {
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    constexpr int ROWS = 64;
-    int g = -1;
-    unsigned long long a_arcs = 0, a_deg = 0, a_mut = 0, a_sq = 0, a_max = 0;
-    auto flush = [&]() {
-        if (g >= 0 && lane == 0) {
-            unsigned long long* s = gstat + 6 * (size_t)g;
-            if (a_arcs) atomicAdd(s + 0, a_arcs);
-            if (a_deg) atomicAdd(s + 1, a_deg);
-            if (a_mut) atomicAdd(s + 2, a_mut);
-            if (a_sq) atomicAdd(s + 3, a_sq);
-            if (a_max) atomicMax(s + 4, a_max);
+    for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x; x0 < total_n; x0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = x0 + threadIdx.x;
+        const bool valid = x < total_n;
+        unsigned long long v[5] = {0, 0, 0, 0, 0};  // arcs, degree, 2 x mutual, degree^2, max degree
+        int g = 0;
+        if (valid) {
+            const unsigned long long d = (unsigned long long)(row_ptr[x + 1] - row_ptr[x]);
+            deg[x] = (int32_t)d;
+            const int c1 = vtag[3 * x], c3 = vtag[3 * x + 2];
+            v[0] = (unsigned long long)(c1 + c3);
+            v[1] = d;
+            v[2] = (unsigned long long)c3;
+            v[3] = d * d;
+            v[4] = d;
+            g = G == 1 ? 0 : find_graph(voff, G, x);
         }
-        a_arcs = a_deg = a_mut = a_sq = a_max = 0;
-    };
-    for (;;) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)ROWS);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if ((int64_t)base >= total_n) break;
-        const int64_t rend = min((int64_t)base + ROWS, total_n);
-        for (int64_t x = (int64_t)base; x < rend; ++x) {
-            const int gx = G == 1 ? 0 : find_graph(voff, G, x);
-            if (gx != g) { flush(); g = gx; }
-            const int64_t b = row_ptr[x], e = row_ptr[x + 1];
-            int c1 = 0, c2 = 0, c3 = 0;
-            for (int64_t k = b + lane; k < e + ((32 - ((e - b) & 31)) & 31); k += 32) {
-                const bool v = k < e;
-                const uint32_t t = v ? (adj[k] & 3u) : 0u;
-                c1 += __popc(__ballot_sync(0xffffffffu, t == 1));
-                c2 += __popc(__ballot_sync(0xffffffffu, t == 2));
-                c3 += __popc(__ballot_sync(0xffffffffu, t == 3));
+        const int g0 = __shfl_sync(full, g, 0);
+        if (__all_sync(full, !valid || g == g0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(full, v[q], o);
+                const unsigned long long t = __shfl_xor_sync(full, v[4], o);
+                v[4] = v[4] > t ? v[4] : t;
             }
-            const unsigned long long d = (unsigned long long)(e - b);
             if (lane == 0) {
-                deg[x] = (int32_t)d;
-                vtag[3 * x + 0] = c1;
-                vtag[3 * x + 1] = c2;
-                vtag[3 * x + 2] = c3;
+                unsigned long long* st = gstat + 6 * (size_t)g0;
+                for (int q = 0; q < 4; ++q)
+                    if (v[q]) atomicAdd(st + q, v[q]);
+                if (v[4]) atomicMax(st + 4, v[4]);
             }
-            a_arcs += (unsigned long long)(c1 + c3);
-            a_deg += d;
-            a_mut += (unsigned long long)c3;
-            a_sq += d * d;
-            a_max = a_max > d ? a_max : d;
+        } else if (valid) {
+            unsigned long long* st = gstat + 6 * (size_t)g;
+            for (int q = 0; q < 4; ++q)
+                if (v[q]) atomicAdd(st + q, v[q]);
+            if (v[4]) atomicMax(st + 4, v[4]);
         }
     }
-    flush();
 }
 
 int bits_for(uint64_t x) {  // smallest b with x < 2^b
@@ -212,6 +216,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     TC_CUDA(dev_alloc((void**)&set->adj, sizeof(uint32_t) * (size_t)(N + ADJ_PAD), st));
     TC_CUDA(dev_alloc((void**)&set->deg, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(dev_alloc((void**)&set->vtag, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
+    TC_CUDA(cudaMemsetAsync(set->vtag, 0, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
 
     Scratch S(st);
     int32_t *d_src = nullptr, *d_dst = nullptr;
@@ -228,19 +233,17 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     }
     int64_t *d_aoff = nullptr, *d_voff = nullptr;
     int* d_err = nullptr;
-    unsigned long long *d_cnt = nullptr, *d_gstat = nullptr, *d_cursor = nullptr;
+    unsigned long long *d_cnt = nullptr, *d_gstat = nullptr;
     TC_CUDA(S.get(&d_aoff, (size_t)G + 1));
     TC_CUDA(S.get(&d_voff, (size_t)G + 1));
     TC_CUDA(S.get(&d_err, 1));
     TC_CUDA(S.get(&d_cnt, (size_t)total_n + 1));
     TC_CUDA(S.get(&d_gstat, 6 * (size_t)G + 8));
-    TC_CUDA(S.get(&d_cursor, 1));
     TC_CUDA(cudaMemcpyAsync(d_aoff, aoff.data(), sizeof(int64_t) * ((size_t)G + 1), cudaMemcpyHostToDevice, st));
     TC_CUDA(cudaMemcpyAsync(d_voff, voff.data(), sizeof(int64_t) * ((size_t)G + 1), cudaMemcpyHostToDevice, st));
     TC_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     TC_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * ((size_t)total_n + 1), st));
     TC_CUDA(cudaMemsetAsync(d_gstat, 0, sizeof(unsigned long long) * (6 * (size_t)G + 8), st));
-    TC_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(unsigned long long), st));
 
     int32_t* d_pos = nullptr;
     int32_t nnz_host = 0;
@@ -268,7 +271,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         TC_CUDA(S.get((char**)&tmp2, scan_bytes));
         TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp2, scan_bytes, head, d_pos, (int)N, st));
         k_write<<<grid_for(N, 256), 256, 0, st>>>(ks, N, head, d_pos, sh, (uint32_t)((1ull << nb) - 1),
-                                                  set->adj, d_cnt);
+                                                  set->adj, d_cnt, set->vtag);
         TC_CUDA(cudaGetLastError());
         int32_t last_pos = 0, last_head = 0;
         TC_CUDA(cudaMemcpyAsync(&last_pos, d_pos + N - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -291,8 +294,8 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
                                                                         ADJ_PAD + (N - nnz_host));
     TC_CUDA(cudaGetLastError());
     if (total_n > 0) {
-        k_rowstats<<<grid_for(total_n * 32, 256), 256, 0, st>>>(set->row_ptr, set->adj, d_voff, G, total_n,
-                                                               set->deg, set->vtag, d_gstat, d_cursor);
+        k_rowstats<<<grid_for(total_n, 256), 256, 0, st>>>(set->row_ptr, set->vtag, d_voff, G, total_n,
+                                                          set->deg, d_gstat);
         TC_CUDA(cudaGetLastError());
     }
     std::vector<unsigned long long> gstat(6 * (size_t)G);

@@ -1252,8 +1252,8 @@ constexpr int OWN_NT = 512;
 constexpr int OWN_WARPS = OWN_NT / 32;
 constexpr int OWN_LBS = 13;  // staged owners: at most 2^13 buckets
 constexpr int OWN_LBL = 13;  // larger owners: at most 2^13 buckets
-constexpr int OWN_U = 8;     // 32-entry blocks per unit
-constexpr int OWN_UNIT = 32 * OWN_U;
+constexpr int OWN_G = 2;     // aligned 16-byte groups per lane per unit
+constexpr int OWN_UNIT = 32 * 4 * OWN_G;
 constexpr size_t own_pad(size_t b) { return (b + 15) / 16 * 16; }
 constexpr size_t OWN_T_BYTES = sizeof(uint32_t) * OWN_CAP;
 constexpr size_t OWN_ST_BYTES = own_pad(sizeof(uint32_t) * ((1 << OWN_LBS) + 1));
@@ -1538,13 +1538,13 @@ __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnAr
         u = __shfl_sync(full, u, 0);
         const int f0 = (int)u * OWN_UNIT;
         if (f0 >= total) break;
-        // this lane's 8 slots [s0, s0 + 8): two aligned 16-byte groups, each
-        // inside one dyad's part (parts are whole groups)
-        const int s0 = f0 + 8 * lane;
-        uint4 g[2];
-        int tq[2];
+        // this lane's 4 * OWN_G slots from s0: aligned 16-byte groups, each
+        // inside one dyad's part (parts are whole groups, at least one each)
+        const int s0 = f0 + 4 * OWN_G * lane;
+        uint4 g[OWN_G];
+        int tq[OWN_G];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < OWN_G; ++k) {
             g[k] = make_uint4(SENT, SENT, SENT, SENT);
             tq[k] = 0;
         }
@@ -1556,9 +1556,11 @@ __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnAr
                 else hi = mid - 1;
             }
             tq[0] = lo;
-            tq[1] = lo + (tpp[lo + 1] <= s0 + 4 ? 1 : 0);
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 1; k < OWN_G; ++k)
+                tq[k] = tq[k - 1] + (tq[k - 1] < ntask && tpp[tq[k - 1] + 1] <= s0 + 4 * k ? 1 : 0);
+#pragma unroll
+            for (int k = 0; k < OWN_G; ++k) {
                 const int sk = s0 + 4 * k;
                 if (sk < total) {
                     const int64_t d = tsb[tq[k]];
@@ -1574,9 +1576,16 @@ __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnAr
                 }
             }
         }
-        const uint32_t se[8] = {g[0].x, g[0].y, g[0].z, g[0].w, g[1].x, g[1].y, g[1].z, g[1].w};
+        uint32_t se[4 * OWN_G];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int k = 0; k < OWN_G; ++k) {
+            se[4 * k] = g[k].x;
+            se[4 * k + 1] = g[k].y;
+            se[4 * k + 2] = g[k].z;
+            se[4 * k + 3] = g[k].w;
+        }
+#pragma unroll
+        for (int j = 0; j < 4 * OWN_G; ++j) {
             const bool pass = se[j] != SENT && owner_maybe<STAGED>(o, st, lm, se[j] >> 2);
             const unsigned m = __ballot_sync(full, pass);
             if (pass) {
