@@ -100,12 +100,14 @@ __global__ void k_fill_sent(uint32_t* __restrict__ p, int64_t count) {
         p[i] = SENT;
 }
 
-// Thread per row: degree, and per-graph statistics from the row's degree and
-// tag counts (k_write counted the tags); a warp whose rows lie in one graph
-// adds its sums with one atomic each.
-__global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ vtag,
-                           const int64_t* __restrict__ voff, int G, int64_t total_n,
-                           int32_t* __restrict__ deg, unsigned long long* __restrict__ gstat /* [G][6] */) {
+// Thread per row: degree, the row's split (entries below the row's own id,
+// by binary search), and per-graph statistics from the row's degree and tag
+// counts (k_write counted the tags); a warp whose rows lie in one graph adds
+// its sums with one atomic each.
+__global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+                           const int32_t* __restrict__ vtag, const int64_t* __restrict__ voff, int G,
+                           int64_t total_n, int32_t* __restrict__ deg, int32_t* __restrict__ split,
+                           unsigned long long* __restrict__ gstat /* [G][6] */) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x; x0 < total_n; x0 += (int64_t)gridDim.x * blockDim.x) {
@@ -114,15 +116,24 @@ __global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const int32_t* _
         unsigned long long v[5] = {0, 0, 0, 0, 0};  // arcs, degree, 2 x mutual, degree^2, max degree
         int g = 0;
         if (valid) {
-            const unsigned long long d = (unsigned long long)(row_ptr[x + 1] - row_ptr[x]);
+            const int64_t b = row_ptr[x];
+            const unsigned long long d = (unsigned long long)(row_ptr[x + 1] - b);
             deg[x] = (int32_t)d;
+            g = G == 1 ? 0 : find_graph(voff, G, x);
+            const uint32_t xl = (uint32_t)(x - voff[g]);
+            int lo = 0, hi = (int)d;  // entries with neighbour id below x
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((adj[b + mid] >> 2) < xl) lo = mid + 1;
+                else hi = mid;
+            }
+            split[x] = lo;
             const int c1 = vtag[3 * x], c3 = vtag[3 * x + 2];
             v[0] = (unsigned long long)(c1 + c3);
             v[1] = d;
             v[2] = (unsigned long long)c3;
             v[3] = d * d;
             v[4] = d;
-            g = G == 1 ? 0 : find_graph(voff, G, x);
         }
         const int g0 = __shfl_sync(full, g, 0);
         if (__all_sync(full, !valid || g == g0)) {
@@ -217,6 +228,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     TC_CUDA(dev_alloc((void**)&set->deg, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(dev_alloc((void**)&set->vtag, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(cudaMemsetAsync(set->vtag, 0, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
+    TC_CUDA(dev_alloc((void**)&set->split, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
 
     Scratch S(st);
     int32_t *d_src = nullptr, *d_dst = nullptr;
@@ -294,8 +306,8 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
                                                                         ADJ_PAD + (N - nnz_host));
     TC_CUDA(cudaGetLastError());
     if (total_n > 0) {
-        k_rowstats<<<grid_for(total_n, 256), 256, 0, st>>>(set->row_ptr, set->vtag, d_voff, G, total_n,
-                                                          set->deg, d_gstat);
+        k_rowstats<<<grid_for(total_n, 256), 256, 0, st>>>(set->row_ptr, set->adj, set->vtag, d_voff, G,
+                                                          total_n, set->deg, set->split, d_gstat);
         TC_CUDA(cudaGetLastError());
     }
     std::vector<unsigned long long> gstat(6 * (size_t)G);

@@ -67,6 +67,7 @@ GraphSet::~GraphSet() {
     dev_free(adj, 0);
     dev_free(deg, 0);
     dev_free(vtag, 0);
+    dev_free(split, 0);
     dev_free(ws, 0);
     cudaStreamSynchronize(0);
 }

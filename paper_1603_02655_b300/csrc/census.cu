@@ -1279,6 +1279,7 @@ struct OwnArgs {
     const int64_t* row_ptr;
     const uint32_t* adj;
     const int32_t* deg;
+    const int32_t* split;    // per row: entries below the row's own id
     const SegDev* seg;
     const uint4* list;       // Bins::own
     uint32_t cap;            // Bins::own_cap
@@ -1447,13 +1448,17 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
     int64_t sb = 0;
     if (owned) {
         sb = a.row_ptr[o.rb + x];
-        const uint32_t u = min(o.hl, x);
-        int lo = 0, hi = dx;  // first entry of x's list above u
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((__ldg(a.adj + sb + mid) >> 2) <= u) lo = mid + 1;
-            else hi = mid;
-        }
+        // first entry of x's list above u = min(h, x): x's split when x < h,
+        // else found below the split (h < x is one of x's lower neighbours)
+        int lo = 0, hi = a.split[o.rb + x];
+        if (o.hl < x)
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((__ldg(a.adj + sb + mid) >> 2) <= o.hl) lo = mid + 1;
+                else hi = mid;
+            }
+        else
+            lo = hi;
         len = dx - lo;
         sb += lo;
         lead = (int)(sb & 3);
@@ -1862,8 +1867,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         TC_CUDA(cudaGetLastError());
         mark(2);
         if (o.own_min > 0) {
-            const OwnArgs oa{set.row_ptr, set.adj, set.deg, d_seg, bins.own, bins.own_cap, ctr + 28, ctr + 26, acc,
-                             bins.own_stat + 2};
+            const OwnArgs oa{set.row_ptr, set.adj, set.deg, set.split, d_seg, bins.own, bins.own_cap, ctr + 28,
+                             ctr + 26, acc, bins.own_stat + 2};
             k_owner<<<L.sms * L.occ_owner, OWN_NT, OWN_SMEM, st>>>(oa);
             TC_CUDA(cudaGetLastError());
         }
