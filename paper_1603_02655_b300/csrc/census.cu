@@ -1287,6 +1287,8 @@ struct OwnArgs {
     unsigned* cursor;        // [2]
     unsigned long long* acc;
     unsigned long long* lookups;  // keys looked up (profile)
+    int64_t* psb;            // per adjacency entry of an owner (k_owner_prep): start of the
+    int32_t* plen;           // other endpoint's list part above min(u, v), and its length
 };
 
 struct Owner {
@@ -1423,6 +1425,49 @@ struct OwnCtl {
     unsigned long long wsum[OWN_WARPS];
 };
 
+// For every position of every owner work item (a warp per item): whether the
+// owner owns the dyad with that neighbour x and, if so, where the part of x's
+// list above u = min(h, x) starts and how long it is (x's split when x < h,
+// else found by binary search below the split: h < x is one of x's lower
+// neighbours).  A flat pass, so these dependent loads overlap freely instead
+// of stalling k_owner between its barriers.
+__global__ void __launch_bounds__(256) k_owner_prep(OwnArgs a) {
+    const int lane = threadIdx.x & 31;
+    const unsigned nlarge = min(a.cnt[0], a.cap), nsmall = min(a.cnt[1], a.cap - nlarge);
+    const unsigned nitems = nlarge + nsmall;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nitems; i += warps) {
+        const uint4 rec = i < nsmall ? a.list[i] : a.list[a.cap - 1 - (i - nsmall)];
+        const int64_t rb = a.seg[rec.y].rb;
+        const uint32_t hl = (uint32_t)(rec.x - rb);
+        const int64_t beg = a.row_ptr[rec.x];
+        const int D = (int)(a.row_ptr[rec.x + 1] - beg);
+        const int p0 = (int)rec.z * OWN_PIECE, p1 = min(D, p0 + OWN_PIECE);
+        for (int pos = p0 + lane; pos < p1; pos += 32) {
+            const uint32_t x = __ldg(a.adj + beg + pos) >> 2;
+            const int dx = a.deg[rb + x];
+            int len = 0;
+            int64_t sb = 0;
+            if (dx < D || (dx == D && x < hl)) {
+                sb = a.row_ptr[rb + x];
+                int lo = 0, hi = a.split[rb + x];
+                if (hl < x)
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if ((__ldg(a.adj + sb + mid) >> 2) <= hl) lo = mid + 1;
+                        else hi = mid;
+                    }
+                else
+                    lo = hi;
+                len = dx - lo;
+                sb += lo;
+            }
+            a.psb[beg + pos] = sb;
+            a.plen[beg + pos] = len;
+        }
+    }
+}
+
 // The task table of positions [q0, q0 + OWN_NT) of the item: for each owned
 // dyad {h, x}, in list order, the part of x's list above u = min(h, x) (a
 // shared element below both endpoints changes no triad code: its share of the
@@ -1442,28 +1487,10 @@ __device__ __forceinline__ void owner_table(const OwnArgs& a, const Owner& o, in
     const bool valid = pos < o.p1;
     const uint32_t e = valid ? L[pos] : 0u;
     const uint32_t x = e >> 2;
-    const int dx = valid ? a.deg[o.rb + x] : 0;
-    const bool owned = valid && (dx < o.D || (dx == o.D && x < o.hl));
-    int len = 0, lead = 0, slots = 0;
-    int64_t sb = 0;
-    if (owned) {
-        sb = a.row_ptr[o.rb + x];
-        // first entry of x's list above u = min(h, x): x's split when x < h,
-        // else found below the split (h < x is one of x's lower neighbours)
-        int lo = 0, hi = a.split[o.rb + x];
-        if (o.hl < x)
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((__ldg(a.adj + sb + mid) >> 2) <= o.hl) lo = mid + 1;
-                else hi = mid;
-            }
-        else
-            lo = hi;
-        len = dx - lo;
-        sb += lo;
-        lead = (int)(sb & 3);
-        slots = (lead + len + 3) & ~3;
-    }
+    const int len = valid ? a.plen[o.beg + pos] : 0;
+    const int64_t sb = len > 0 ? a.psb[o.beg + pos] : 0;
+    const int lead = (int)(sb & 3);
+    const int slots = len > 0 ? (lead + len + 3) & ~3 : 0;
     const unsigned long long v =
         len > 0 ? ((1ull << 54) | ((unsigned long long)slots << 27) | (unsigned long long)len) : 0ull;
     unsigned long long incl = v;
@@ -1726,7 +1753,7 @@ struct Layout {
     uint64_t cap01 = 0, cap2 = 0;
     std::vector<SegDev> segs;
     std::vector<int64_t> pfx;
-    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, o_own, need;
+    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, need;
     uint32_t own_cap = 0;
 };
 
@@ -1793,6 +1820,11 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     // pieces: sum over owners of ceil(d / OWN_PIECE) <= rows + 2|U| / OWN_PIECE
     Lo.own_cap = (uint32_t)std::min<int64_t>(Lo.rows + 2 * dyads / OWN_PIECE + 1, 0xffffffffll);
     Lo.o_own = take(sizeof(uint4) * (o.own_min > 0 ? Lo.own_cap : 1));
+    // per adjacency entry of an owner: start and length of the other
+    // endpoint's list part (k_owner_prep)
+    const size_t nprep = o.own_min > 0 ? (size_t)std::max<int64_t>(set.nnz, 1) : 1;
+    Lo.o_psb = take(sizeof(int64_t) * nprep);
+    Lo.o_plen = take(sizeof(int32_t) * nprep);
     Lo.need = off;
     return TC_OK;
 }
@@ -1868,7 +1900,10 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         mark(2);
         if (o.own_min > 0) {
             const OwnArgs oa{set.row_ptr, set.adj, set.deg, set.split, d_seg, bins.own, bins.own_cap, ctr + 28,
-                             ctr + 26, acc, bins.own_stat + 2};
+                             ctr + 26, acc, bins.own_stat + 2, (int64_t*)(ws + Lo.o_psb),
+                             (int32_t*)(ws + Lo.o_plen)};
+            k_owner_prep<<<L.sms * 8, 256, 0, st>>>(oa);
+            TC_CUDA(cudaGetLastError());
             k_owner<<<L.sms * L.occ_owner, OWN_NT, OWN_SMEM, st>>>(oa);
             TC_CUDA(cudaGetLastError());
         }
@@ -1938,7 +1973,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
-    return (Lo.o.persistent ? 5 : 8) + route + (Lo.o.own_min > 0 ? 1 : 0);
+    return (Lo.o.persistent ? 5 : 8) + route + (Lo.o.own_min > 0 ? 2 : 0);
 }
 
 tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cudaStream_t st) {
