@@ -73,7 +73,7 @@ __global__ void k_heads(const uint64_t* __restrict__ k, int64_t N, int32_t* __re
 __global__ void k_write(const uint64_t* __restrict__ k, int64_t N, const int32_t* __restrict__ head,
                         const int32_t* __restrict__ pos, int sh, uint32_t nbr_mask,
                         uint32_t* __restrict__ adj, unsigned long long* __restrict__ cnt,
-                        int32_t* __restrict__ vtag) {
+                        int32_t* __restrict__ vtag, int32_t* __restrict__ arow) {
     const int lane = threadIdx.x & 31;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < N; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;  // whole warps iterate together
@@ -84,8 +84,9 @@ __global__ void k_write(const uint64_t* __restrict__ k, int64_t N, const int32_t
             const uint64_t key = k[i] >> 2;
             for (int64_t j = i; j < N && (k[j] >> 2) == key; ++j) tag |= (uint32_t)(k[j] & 3u);
             const uint32_t nbr = (uint32_t)(key & nbr_mask);
-            adj[pos[i]] = (nbr << 2) | tag;
             row = k[i] >> sh;
+            adj[pos[i]] = (nbr << 2) | tag;
+            arow[pos[i]] = (int32_t)row;
         }
         const unsigned same_row = __match_any_sync(0xffffffffu, row);
         const unsigned same_tag = __match_any_sync(0xffffffffu, (row << 2) | tag);
@@ -229,6 +230,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     TC_CUDA(dev_alloc((void**)&set->vtag, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(cudaMemsetAsync(set->vtag, 0, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(dev_alloc((void**)&set->split, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
+    TC_CUDA(dev_alloc((void**)&set->arow, sizeof(int32_t) * (size_t)std::max<int64_t>(N, 1), st));
 
     Scratch S(st);
     int32_t *d_src = nullptr, *d_dst = nullptr;
@@ -283,7 +285,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         TC_CUDA(S.get((char**)&tmp2, scan_bytes));
         TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp2, scan_bytes, head, d_pos, (int)N, st));
         k_write<<<grid_for(N, 256), 256, 0, st>>>(ks, N, head, d_pos, sh, (uint32_t)((1ull << nb) - 1),
-                                                  set->adj, d_cnt, set->vtag);
+                                                  set->adj, d_cnt, set->vtag, set->arow);
         TC_CUDA(cudaGetLastError());
         int32_t last_pos = 0, last_head = 0;
         TC_CUDA(cudaMemcpyAsync(&last_pos, d_pos + N - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -327,6 +329,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         s.asym = s.dyads - s.mutual;
         s.merged_entries = (int64_t)x[3];
         s.max_degree = (int64_t)x[4];
+        set->max_deg = std::max<int32_t>(set->max_deg, (int32_t)x[4]);
     }
     for (int32_t g = 0; g < G; ++g) {
         outs[g] = new tc_graph_s;

@@ -68,6 +68,7 @@ GraphSet::~GraphSet() {
     dev_free(deg, 0);
     dev_free(vtag, 0);
     dev_free(split, 0);
+    dev_free(arow, 0);
     dev_free(ws, 0);
     cudaStreamSynchronize(0);
 }

@@ -30,6 +30,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cub/device/device_scan.cuh>
+
 #include "mlp.cuh"
 #include "tc_internal.cuh"
 
@@ -119,6 +121,7 @@ __host__ __device__ __forceinline__ int triad_type(int code) {
 struct SegDev {
     int64_t rb;    // first global row of the graph (local id = global - rb)
     int64_t n;     // vertices
+    int64_t eb;    // first global adjacency entry of the graph
     int32_t slot;  // output index
     int32_t pad;
 };
@@ -340,6 +343,216 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+        const unsigned long long e = warp_sum64(Os[k]);
+        if (lane == 0 && e) atomicAdd(bins.own_stat + k, e);
+    }
+}
+
+// ---------------------------------------------------------- k_tasks_flat --
+// The same per-dyad terms as k_tasks, one adjacency entry per thread.  The
+// suffix counts of entry k in row x (entries after k with each tag) are the
+// row's tag totals (vtag, from the build) minus the row-local inclusive prefix
+// of one-hot tag words, itself the difference of a global inclusive scan at k
+// and before the row's first entry; the scan packs the three tags in 21-bit
+// fields, exact while every row has fewer than 2^21 entries (the difference
+// is taken modulo 2^64, so carries out of earlier rows cancel).
+constexpr int TAG_BITS = 21;
+constexpr unsigned long long TAG_MASK = (1ull << TAG_BITS) - 1;
+
+__global__ void k_onehot(const uint32_t* __restrict__ adj, int64_t nnz, unsigned long long* __restrict__ out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = __ldg(adj + k) & 3u;  // 1, 2 or 3
+        out[k] = 1ull << (TAG_BITS * (t - 1));
+    }
+}
+
+// Thread per row of the selected graphs: register each owner's work items.
+__global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
+                             const int64_t* __restrict__ pfx, int nseg, int64_t total_rows, int own_min,
+                             Bins bins) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int s = nseg == 1 ? 0 : seg_of(pfx, nseg, r);
+        const int64_t x = seg[s].rb + (r - pfx[s]);
+        const int d = deg[x];
+        if (d < own_min || d > OWN_MAX) continue;
+        const bool large = d > OWN_CAP;
+        const int np = (d + OWN_PIECE - 1) / OWN_PIECE;
+        const unsigned k = atomicAdd(bins.own_cnt + (large ? 0 : 1), (unsigned)np);
+        for (int p = 0; p < np; ++p) {
+            const unsigned i = k + (unsigned)p;
+            if (i < bins.own_cap) bins.own[large ? bins.own_cap - 1 - i : i] =
+                make_uint4((uint32_t)x, (uint32_t)s, (uint32_t)p, 0u);
+            else atomicOr(bins.overflow, 1);
+        }
+        atomicAdd(bins.own_stat + 3, (unsigned long long)d * (unsigned long long)np);
+    }
+}
+
+// Warps take runs of FLAT_RUN entries of the selected graphs' concatenated
+// adjacency (graph boundaries rarely fall inside one); lanes whose entry lies
+// in another graph than the warp's accumulators add directly.
+constexpr int FLAT_RUN = 2048;
+
+__global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ row_ptr,
+                                                    const uint32_t* __restrict__ adj,
+                                                    const int32_t* __restrict__ arow,
+                                                    const int32_t* __restrict__ deg,
+                                                    const int32_t* __restrict__ vtag,
+                                                    const unsigned long long* __restrict__ scan,
+                                                    const SegDev* __restrict__ seg,
+                                                    const int64_t* __restrict__ epfx, int nseg,
+                                                    int64_t total_entries, BinParams bp, Bins bins,
+                                                    unsigned long long* __restrict__ acc,
+                                                    unsigned long long* __restrict__ cursor) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const unsigned below = (1u << lane) - 1u;
+    int s = -1;  // graph of the warp's accumulators
+    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN], Os[2] = {0, 0};
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Aa[p][q] = Bb[p][q] = 0;
+    Dd[0] = Dd[1] = 0;
+#pragma unroll
+    for (int b = 0; b < NBIN; ++b) Ee[b] = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const unsigned long long a = warp_sum64(Aa[p][q]), b = warp_sum64(Bb[p][q]);
+                if (lane == 0 && s >= 0) {
+                    if (a) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 4 * (q + 1), a);
+                    if (b) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 16 * (q + 1), b);
+                }
+                Aa[p][q] = Bb[p][q] = 0;
+            }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const unsigned long long d = warp_sum64(Dd[q]);
+            if (lane == 0 && s >= 0 && d) atomicAdd(acc + (size_t)s * ACC + 64 + q, d);
+            Dd[q] = 0;
+        }
+    };
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)FLAT_RUN);
+        base = __shfl_sync(full, base, 0);
+        if ((int64_t)base >= total_entries) break;
+        const int64_t fend = min((int64_t)base + FLAT_RUN, total_entries);
+        int ls = nseg == 1 ? 0 : seg_of(epfx, nseg, (int64_t)base);  // lane's graph, stepped forward
+        for (int64_t f0 = (int64_t)base; f0 < fend; f0 += 32) {
+            const int64_t f = f0 + lane;
+            const bool valid = f < fend;
+            while (valid && ls + 1 < nseg && epfx[ls + 1] <= f) ++ls;
+            const int ws = __shfl_sync(full, ls, 0);
+            if (ws != s) {
+                flush();
+                s = ws;
+            }
+            const bool mine = ls == s;  // else this lane's entry belongs to a later graph
+            const SegDev sg = seg[ls];
+            const int64_t k = valid ? sg.eb + (f - epfx[ls]) : 0;
+            const uint32_t e = valid ? __ldg(adj + k) : 0u;
+            const int64_t x = valid ? (int64_t)arow[k] : 0;
+            const int64_t xl = x - sg.rb;
+            const uint32_t y = e >> 2;
+            const int t = (int)(e & 3u);
+            uint32_t S1 = 0, S2 = 0, S3 = 0;
+            int d = 0;
+            if (valid) {
+                const int64_t rs = row_ptr[x];
+                const unsigned long long I = scan[k] - (rs > 0 ? scan[rs - 1] : 0ull);
+                S1 = (uint32_t)vtag[3 * x] - (uint32_t)(I & TAG_MASK);
+                S2 = (uint32_t)vtag[3 * x + 1] - (uint32_t)((I >> TAG_BITS) & TAG_MASK);
+                S3 = (uint32_t)vtag[3 * x + 2] - (uint32_t)((I >> (2 * TAG_BITS)) & TAG_MASK);
+                d = deg[x];
+            }
+            const bool is_task = valid && (int64_t)y > xl;
+            const bool is_twin = valid && (int64_t)y < xl;
+            const int pre_task = t;
+            const int pre_twin = ((t & 1) << 1) | (t >> 1);
+            unsigned long long add[2][3][3];  // lanes of another graph add directly
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const bool ta = is_task && pre_task == p + 1;
+                const bool tb = is_twin && pre_twin == p + 1;
+                add[0][p][0] = ta ? S1 : 0ull;
+                add[0][p][1] = ta ? S2 : 0ull;
+                add[0][p][2] = ta ? S3 : 0ull;
+                add[1][p][0] = tb ? S1 : 0ull;
+                add[1][p][1] = tb ? S2 : 0ull;
+                add[1][p][2] = tb ? S3 : 0ull;
+            }
+            int L = 0;
+            int bin = -1;
+            unsigned long long dy = 0;
+            if (is_task) {
+                const int dv = deg[sg.rb + y];
+                L = d + dv;
+                dy = (unsigned long long)(sg.n - (int64_t)d - (int64_t)dv);
+                const int dh = max(d, dv);
+                if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
+                    Os[0] += 1;
+                    Os[1] += (unsigned long long)L;
+                } else {
+                    bin = L <= bp.thr_thread ? 0
+                          : L <= bp.thr_warp ? 1
+                          : min(d, dv) <= min(bp.stream_max, STREAM_SMAX) ? 3 : 2;
+                }
+            }
+            if (mine) {
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        Aa[p][q] += add[0][p][q];
+                        Bb[p][q] += add[1][p][q];
+                    }
+                Dd[0] += pre_task == 3 ? 0ull : dy;
+                Dd[1] += pre_task == 3 ? dy : 0ull;
+            } else if (valid) {
+                unsigned long long* h = acc + (size_t)ls * ACC;
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (add[0][p][q]) atomicAdd(h + (p + 1) + 4 * (q + 1), add[0][p][q]);
+                        if (add[1][p][q]) atomicAdd(h + (p + 1) + 16 * (q + 1), add[1][p][q]);
+                    }
+                if (dy) atomicAdd(h + 64 + (pre_task == 3 ? 1 : 0), dy);
+            }
+#pragma unroll
+            for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
+            const uint4 rec = make_uint4((uint32_t)x, (uint32_t)(sg.rb + y), ((uint32_t)ls << 2) | (uint32_t)pre_task, 0u);
+#pragma unroll
+            for (int b = 0; b < NBIN; ++b) {
+                const bool in = bin == b;
+                const unsigned mask = __ballot_sync(full, in);
+                if (mask) {
+                    const int leader = __ffs(mask) - 1;
+                    unsigned int at = 0;
+                    if (lane == leader) at = atomicAdd(bins.cnt + b, (unsigned)__popc(mask));
+                    at = __shfl_sync(full, at, leader);
+                    if (in) {
+                        const unsigned idx = at + __popc(mask & below);
+                        if (idx < bins.cap[b]) bins.rec[b][idx] = rec;
+                        else atomicOr(bins.overflow, 1);
+                    }
+                }
+            }
+        }
+    }
+    flush();
+#pragma unroll
+    for (int b = 0; b < NBIN; ++b) {
+        const unsigned long long e = warp_sum64(Ee[b]);
+        if (lane == 0 && e) atomicAdd(bins.entries + b, e);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
         const unsigned long long e = warp_sum64(Os[k]);
         if (lane == 0 && e) atomicAdd(bins.own_stat + k, e);
     }
@@ -1708,7 +1921,7 @@ constexpr int STREAM_EPL = 8;
 
 struct Launch {
     int sms = 148;
-    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1;
+    int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1, occ_flat = 1;
     int occ_owner = 1;
     bool ready = false;
 };
@@ -1732,6 +1945,8 @@ tc_status launch_info(Launch& L) {
         c.occ_cta = std::max(1, c.occ_cta);
         c.occ_stream = std::max(1, c.occ_stream);
         c.occ_merge = std::max(1, c.occ_merge);
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_flat, k_tasks_flat, 256, 0));
+        c.occ_flat = std::max(1, c.occ_flat);
         TC_CUDA(cudaFuncSetAttribute(k_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OWN_SMEM));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_owner, k_owner, OWN_NT, OWN_SMEM));
         c.occ_owner = std::max(1, c.occ_owner);
@@ -1753,7 +1968,12 @@ struct Layout {
     uint64_t cap01 = 0, cap2 = 0;
     std::vector<SegDev> segs;
     std::vector<int64_t> pfx;
-    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, need;
+    std::vector<int64_t> epfx;  // adjacency entries of the selected graphs, running
+    bool flat = false;          // per-entry task terms (k_tasks_flat)
+    int64_t entries = 0;
+    size_t scan_bytes = 0;      // CUB scan temporary storage
+    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, o_epfx,
+        o_scan, o_scantmp, need;
     uint32_t own_cap = 0;
 };
 
@@ -1788,11 +2008,16 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     const int nseg = (int)gidx.size();
     Lo.segs.assign((size_t)nseg, SegDev{});
     Lo.pfx.assign((size_t)nseg + 1, 0);
+    Lo.epfx.assign((size_t)nseg + 1, 0);
+    std::vector<int64_t> gent((size_t)set.G + 1, 0);  // first adjacency entry of each graph
+    for (int32_t g = 0; g < set.G; ++g) gent[(size_t)g + 1] = gent[(size_t)g] + 2 * set.stats[(size_t)g].dyads;
     int64_t dyads = 0, merged = 0;
     for (int i = 0; i < nseg; ++i) {
         const int g = gidx[(size_t)i];
         Lo.segs[(size_t)i].rb = set.voff[(size_t)g];
         Lo.segs[(size_t)i].n = set.voff[(size_t)g + 1] - set.voff[(size_t)g];
+        Lo.segs[(size_t)i].eb = gent[(size_t)g];
+        Lo.epfx[(size_t)i + 1] = Lo.epfx[(size_t)i] + 2 * set.stats[(size_t)g].dyads;
         Lo.segs[(size_t)i].slot = i;
         Lo.segs[(size_t)i].pad = 0;
         Lo.pfx[(size_t)i + 1] = Lo.pfx[(size_t)i] + Lo.segs[(size_t)i].n;
@@ -1825,6 +2050,16 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     const size_t nprep = o.own_min > 0 ? (size_t)std::max<int64_t>(set.nnz, 1) : 1;
     Lo.o_psb = take(sizeof(int64_t) * nprep);
     Lo.o_plen = take(sizeof(int32_t) * nprep);
+    // per-entry task terms need every row below 2^21 entries (packed tag scan)
+    Lo.entries = Lo.epfx[(size_t)nseg];
+    Lo.flat = set.arow != nullptr && set.max_deg < (1 << TAG_BITS) && set.nnz > 0;
+    Lo.o_epfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
+    Lo.scan_bytes = 0;
+    if (Lo.flat)
+        TC_CUDA(cub::DeviceScan::InclusiveSum(nullptr, Lo.scan_bytes, (unsigned long long*)nullptr,
+                                              (unsigned long long*)nullptr, (int)set.nnz, (cudaStream_t)0));
+    Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat ? (size_t)set.nnz : 1));
+    Lo.o_scantmp = take(std::max<size_t>(Lo.scan_bytes, 16));
     Lo.need = off;
     return TC_OK;
 }
@@ -1835,6 +2070,8 @@ tc_status upload_layout(const Layout& Lo, char* ws, cudaStream_t st) {
     TC_CUDA(cudaMemcpyAsync(ws + Lo.o_seg, Lo.segs.data(), sizeof(SegDev) * (size_t)Lo.nseg,
                             cudaMemcpyHostToDevice, st));
     TC_CUDA(cudaMemcpyAsync(ws + Lo.o_pfx, Lo.pfx.data(), sizeof(int64_t) * ((size_t)Lo.nseg + 1),
+                            cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaMemcpyAsync(ws + Lo.o_epfx, Lo.epfx.data(), sizeof(int64_t) * ((size_t)Lo.nseg + 1),
                             cudaMemcpyHostToDevice, st));
     return TC_OK;
 }
@@ -1876,8 +2113,23 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     TC_CUDA(cudaMemsetAsync(ws, 0, Lo.o_seg, st));  // accumulators + counters
     mark(0);
     if (Lo.rows > 0) {
-        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
-                                                     bp, bins, acc, cursor);
+        if (Lo.flat) {
+            unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
+            k_onehot<<<L.sms * 8, 256, 0, st>>>(set.adj, set.nnz, scan);
+            TC_CUDA(cudaGetLastError());
+            size_t sb = Lo.scan_bytes;
+            TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, scan, scan, (int)set.nnz, st));
+            if (bp.own_min > 0) {
+                k_owner_rows<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, bp.own_min, bins);
+                TC_CUDA(cudaGetLastError());
+            }
+            k_tasks_flat<<<L.sms * L.occ_flat, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, set.vtag, scan,
+                                                             d_seg, (const int64_t*)(ws + Lo.o_epfx), Lo.nseg,
+                                                             Lo.entries, bp, bins, acc, cursor);
+        } else {
+            k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg,
+                                                         Lo.rows, bp, bins, acc, cursor);
+        }
         TC_CUDA(cudaGetLastError());
         const unsigned int* nsplit = ctr + 2;
         if (mlp) {
@@ -1973,7 +2225,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
-    return (Lo.o.persistent ? 5 : 8) + route + (Lo.o.own_min > 0 ? 2 : 0);
+    const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 3 : 2) : 1;  // k_onehot, k_owner_rows, k_tasks_flat
+    return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0);
 }
 
 tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cudaStream_t st) {
@@ -2168,6 +2421,7 @@ __global__ void k_noalloc_init(NoallocLayout* s, const int64_t* __restrict__ row
     if (tid == 0) {
         s->seg.rb = 0;
         s->seg.n = n;
+        s->seg.eb = 0;
         s->seg.slot = 0;
         s->seg.pad = 0;
         s->pfx[0] = 0;

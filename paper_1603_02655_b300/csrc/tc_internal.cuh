@@ -50,6 +50,8 @@ struct GraphSet {
     int32_t* deg = nullptr;        // [total_n]
     int32_t* vtag = nullptr;       // [3 * total_n]: per vertex #out-only, #in-only, #mutual nbrs
     int32_t* split = nullptr;      // [total_n]: entries of row x below x (its first entry above x)
+    int32_t* arow = nullptr;       // [adj_cap]: global row of each adjacency entry
+    int32_t max_deg = 0;           // largest degree over all graphs
     std::vector<int64_t> voff;     // host [G+1]
     std::vector<tc_graph_stats_t> stats;  // host [G]
     int64_t max_n = 0;
