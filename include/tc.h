@@ -105,7 +105,10 @@ typedef struct {
                              memory (and copied there up to 16384 entries) and
                              the other endpoint's list is looked up in it.
                              0 disables; default 128 */
-    int32_t reserved[2];  /* must be zero */
+    int32_t row_tasks;    /* 1: compute the per-dyad terms with one warp per row
+                             (the path used anyway when a row has 2^21 or more
+                             entries); 0: one thread per adjacency entry */
+    int32_t reserved[1];  /* must be zero */
 } tc_opts;
 
 /* Per-kernel timing and binning of the calling thread's most recent

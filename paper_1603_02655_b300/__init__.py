@@ -68,7 +68,7 @@ class TcOpts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("split_cta", ctypes.c_int32),
                 ("stream_max", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("hub_ratio", ctypes.c_int32), ("own_min", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("row_tasks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class TcProfile(ctypes.Structure):

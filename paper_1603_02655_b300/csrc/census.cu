@@ -359,10 +359,15 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
 constexpr int TAG_BITS = 21;
 constexpr unsigned long long TAG_MASK = (1ull << TAG_BITS) - 1;
 
-__global__ void k_onehot(const uint32_t* __restrict__ adj, int64_t nnz, unsigned long long* __restrict__ out) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = __ldg(adj + k) & 3u;  // 1, 2 or 3
-        out[k] = 1ull << (TAG_BITS * (t - 1));
+// One-hot tag words of the selected graphs' entries, in the order of their
+// concatenation (position f; entry k = the graph's first entry + offset).
+__global__ void k_onehot(const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
+                         const int64_t* __restrict__ epfx, int nseg, int64_t total,
+                         unsigned long long* __restrict__ out) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+        const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
+        const uint32_t t = __ldg(adj + seg[s].eb + (f - epfx[s])) & 3u;  // 1, 2 or 3
+        out[f] = 1ull << (TAG_BITS * (t - 1));
     }
 }
 
@@ -463,8 +468,8 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
             uint32_t S1 = 0, S2 = 0, S3 = 0;
             int d = 0;
             if (valid) {
-                const int64_t rs = row_ptr[x];
-                const unsigned long long I = scan[k] - (rs > 0 ? scan[rs - 1] : 0ull);
+                const int64_t frs = epfx[ls] + (row_ptr[x] - sg.eb);  // the row's first entry, in scan order
+                const unsigned long long I = scan[f] - (frs > 0 ? scan[frs - 1] : 0ull);
                 S1 = (uint32_t)vtag[3 * x] - (uint32_t)(I & TAG_MASK);
                 S2 = (uint32_t)vtag[3 * x + 1] - (uint32_t)((I >> TAG_BITS) & TAG_MASK);
                 S3 = (uint32_t)vtag[3 * x + 2] - (uint32_t)((I >> (2 * TAG_BITS)) & TAG_MASK);
@@ -2052,13 +2057,14 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.o_plen = take(sizeof(int32_t) * nprep);
     // per-entry task terms need every row below 2^21 entries (packed tag scan)
     Lo.entries = Lo.epfx[(size_t)nseg];
-    Lo.flat = set.arow != nullptr && set.max_deg < (1 << TAG_BITS) && set.nnz > 0;
+    Lo.flat = !o.row_tasks && set.arow != nullptr && set.max_deg < (1 << TAG_BITS) && set.nnz > 0;
     Lo.o_epfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
     Lo.scan_bytes = 0;
+    Lo.flat = Lo.flat && Lo.entries > 0;
     if (Lo.flat)
         TC_CUDA(cub::DeviceScan::InclusiveSum(nullptr, Lo.scan_bytes, (unsigned long long*)nullptr,
-                                              (unsigned long long*)nullptr, (int)set.nnz, (cudaStream_t)0));
-    Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat ? (size_t)set.nnz : 1));
+                                              (unsigned long long*)nullptr, (int)Lo.entries, (cudaStream_t)0));
+    Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat ? (size_t)Lo.entries : 1));
     Lo.o_scantmp = take(std::max<size_t>(Lo.scan_bytes, 16));
     Lo.need = off;
     return TC_OK;
@@ -2115,10 +2121,11 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     if (Lo.rows > 0) {
         if (Lo.flat) {
             unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
-            k_onehot<<<L.sms * 8, 256, 0, st>>>(set.adj, set.nnz, scan);
+            const int64_t* d_epfx = (const int64_t*)(ws + Lo.o_epfx);
+            k_onehot<<<L.sms * 8, 256, 0, st>>>(set.adj, d_seg, d_epfx, Lo.nseg, Lo.entries, scan);
             TC_CUDA(cudaGetLastError());
             size_t sb = Lo.scan_bytes;
-            TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, scan, scan, (int)set.nnz, st));
+            TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, scan, scan, (int)Lo.entries, st));
             if (bp.own_min > 0) {
                 k_owner_rows<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, bp.own_min, bins);
                 TC_CUDA(cudaGetLastError());

@@ -37,6 +37,8 @@ BINS = {
     "owner_all": dict(own_min=1),
     "owner_mid": dict(own_min=64, thr_thread=8, thr_warp=64),
     "owner_sep": dict(own_min=32, persistent=0, stream_max=0),
+    "row_tasks": dict(row_tasks=1),
+    "row_tasks_merge": dict(row_tasks=1, own_min=0, thr_thread=8, thr_warp=64),
 }
 
 
