@@ -1686,6 +1686,44 @@ __global__ void __launch_bounds__(256) k_owner_prep(OwnArgs a) {
     }
 }
 
+// The same, one thread per adjacency entry of the census's graphs (entry k
+// of row h, found from the per-entry rows of the build): entries of rows that
+// are not owners are skipped.  Every lookup range is independent, so the
+// dependent loads of all of them overlap.
+__global__ void __launch_bounds__(256) k_owner_prep_flat(OwnArgs a, const int32_t* __restrict__ arow,
+                                                         const int64_t* __restrict__ epfx, int nseg,
+                                                         int64_t total, int own_min) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+        const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
+        const int64_t k = a.seg[s].eb + (f - epfx[s]);
+        const int64_t h = arow[k];
+        const int D = a.deg[h];
+        if (D < own_min || D > OWN_MAX) continue;
+        const int64_t rb = a.seg[s].rb;
+        const uint32_t hl = (uint32_t)(h - rb);
+        const uint32_t x = __ldg(a.adj + k) >> 2;
+        const int dx = a.deg[rb + x];
+        int len = 0;
+        int64_t sb = 0;
+        if (dx < D || (dx == D && x < hl)) {
+            sb = a.row_ptr[rb + x];
+            int lo = 0, hi = a.split[rb + x];
+            if (hl < x)
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((__ldg(a.adj + sb + mid) >> 2) <= hl) lo = mid + 1;
+                    else hi = mid;
+                }
+            else
+                lo = hi;
+            len = dx - lo;
+            sb += lo;
+        }
+        a.psb[k] = sb;
+        a.plen[k] = len;
+    }
+}
+
 // The task table of positions [q0, q0 + OWN_NT) of the item: for each owned
 // dyad {h, x}, in list order, the part of x's list above u = min(h, x) (a
 // shared element below both endpoints changes no triad code: its share of the
@@ -2161,7 +2199,11 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             const OwnArgs oa{set.row_ptr, set.adj, set.deg, set.split, d_seg, bins.own, bins.own_cap, ctr + 28,
                              ctr + 26, acc, bins.own_stat + 2, (int64_t*)(ws + Lo.o_psb),
                              (int32_t*)(ws + Lo.o_plen)};
-            k_owner_prep<<<L.sms * 8, 256, 0, st>>>(oa);
+            if (Lo.flat)
+                k_owner_prep_flat<<<L.sms * 16, 256, 0, st>>>(oa, set.arow, (const int64_t*)(ws + Lo.o_epfx), Lo.nseg,
+                                                              Lo.entries, o.own_min);
+            else
+                k_owner_prep<<<L.sms * 8, 256, 0, st>>>(oa);
             TC_CUDA(cudaGetLastError());
             k_owner<<<L.sms * L.occ_owner, OWN_NT, OWN_SMEM, st>>>(oa);
             TC_CUDA(cudaGetLastError());
