@@ -440,10 +440,9 @@ def run_native(args, world, rank, local, pg):
                        "step": "graph build + census, arc list resident in HBM",
                        "l2": "512 MB buffer written between timed steps (L2 flush)",
                        "parallelism": "single GPU" if world == 1 else f"replicas x{world}",
-                       "census_opts": {k: getattr(prof_opts, k) for k in
-                                       ("bin_mode", "thr_thread", "thr_warp", "chunk", "split_cta",
-                                        "stream_max", "persistent")}},
+                       "census_opts": {k: getattr(prof_opts, k) for k in tc.TUNED_FIELDS}},
             "breakdown": {"census_ms": float(np.mean(census_ms)), "build_ms": float(np.mean(build_ms)),
+                          "census_ms_steps": [round(float(x), 3) for x in census_ms],
                           "merge_ms": merge_ms, "kernel_ms": avg,
                           "bin_tasks": profs[-1]["bin_tasks"], "bin_entries": profs[-1]["bin_entries"],
                           "hub_tasks": profs[-1]["hub_tasks"], "hub_entries": hub,

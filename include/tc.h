@@ -278,8 +278,8 @@ void tc_plan_free(tc_plan plan);
 
 /*
  * tc_autotune -- pick census options for a list of graphs by measurement:
- * coordinate descent over thr_thread, thr_warp, stream_max, chunk and
- * persistent (two passes), each trial a full census timed with CUDA events
+ * coordinate descent over own_min, thr_thread, thr_warp, stream_max, chunk
+ * and persistent (two passes), each trial a full census timed with CUDA events
  * on `stream` (best of two runs after a warm-up).  `base` (NULL = defaults)
  * is the starting point; max_trials <= 0 means no limit.  *best receives the
  * fastest options, *best_ms their time and *trials the number of options

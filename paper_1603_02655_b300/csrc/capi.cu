@@ -96,8 +96,8 @@ tc_status tc_opts_default(tc_opts* o) {
     if (!o) return tc::fail(TC_ERR_ARG, "tc_opts_default: null");
     *o = tc_opts{};
     o->bin_mode = TC_BIN_HEURISTIC;
-    o->thr_thread = 48;
-    o->thr_warp = 1024;
+    o->thr_thread = 128;
+    o->thr_warp = 256;
     o->chunk = 1024;
     o->stream_max = 1 << 30;
     o->persistent = 1;
