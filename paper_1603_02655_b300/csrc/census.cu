@@ -15,17 +15,23 @@
 // regrouped; every per-dyad contribution is counted exactly once):
 //  * w only in A (tag_v = 0) is counted iff w > v, i.e. it is one of the
 //    entries of row u after v; w only in B (tag_u = 0) is counted iff w > u,
-//    i.e. one of the entries of row v after u.  k_tasks walks each row once,
-//    keeps suffix counts of the three tag values, and adds, per dyad, the
-//    counts of A after v into codes pre+4t and the counts of B after u into
-//    codes pre+16t, as if no element were shared, plus n - |A| - |B| into the
-//    dyadic slot.  It also emits the dyad as a task, binned by |A|+|B|.
-//  * The merge kernels stream A and B (the full lists: the union merge of the
-//    method) and find the shared elements w.  Each adds 1 to the dyadic slot
-//    (|S| shrinks by one) and corrects the classification: if w > v it was
-//    counted as pre+4tu and pre+16tv and is moved to pre+4tu+16tv; if
-//    u < w < v it was counted as pre+16tv and must not count at all.
-//  * k_fold maps the 64 codes onto the 16 MAN types and closes 003.
+//    i.e. one of the entries of row v after u.  The task pass (k_tasks_flat,
+//    one thread per adjacency entry, suffix counts from a tag scan; or
+//    k_tasks, one warp per row) adds, per dyad, the counts of A after v into
+//    codes pre+4t and the counts of B after u into codes pre+16t, as if no
+//    element were shared, plus n - |A| - |B| into the dyadic slot.  It emits
+//    the dyad as a task binned by |A|+|B|, unless its higher-degree endpoint
+//    owns it (owner lookups below).
+//  * The shared elements w correct the classification: if w > v the triad
+//    was counted as pre+4tu and pre+16tv and is moved to pre+4tu+16tv; if
+//    u < w < v it was counted as pre+16tv and must not count at all; a w
+//    below u changes nothing.  They are found by k_owner (the shorter list's
+//    entries above u looked up in an index of the owner's list) or by the
+//    merge kernels (k_merge, k_hub and the separate-launch items: both lists
+//    streamed).
+//  * |A n B| itself is never counted: summed over the dyads it is fixed by
+//    the closed-triad counts, which k_fold adds to the dyadic slots after
+//    mapping the 64 codes onto the 16 MAN types; k_fold closes 003.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
