@@ -485,18 +485,6 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
             const bool is_twin = valid && (int64_t)y < xl;
             const int pre_task = t;
             const int pre_twin = ((t & 1) << 1) | (t >> 1);
-            unsigned long long add[2][3][3];  // lanes of another graph add directly
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                const bool ta = is_task && pre_task == p + 1;
-                const bool tb = is_twin && pre_twin == p + 1;
-                add[0][p][0] = ta ? S1 : 0ull;
-                add[0][p][1] = ta ? S2 : 0ull;
-                add[0][p][2] = ta ? S3 : 0ull;
-                add[1][p][0] = tb ? S1 : 0ull;
-                add[1][p][1] = tb ? S2 : 0ull;
-                add[1][p][2] = tb ? S3 : 0ull;
-            }
             int L = 0;
             int bin = -1;
             unsigned long long dy = 0;
@@ -516,23 +504,25 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
             }
             if (mine) {
 #pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        Aa[p][q] += add[0][p][q];
-                        Bb[p][q] += add[1][p][q];
-                    }
+                for (int p = 0; p < 3; ++p) {
+                    const bool ta = is_task && pre_task == p + 1;
+                    const bool tb = is_twin && pre_twin == p + 1;
+                    Aa[p][0] += ta ? S1 : 0u;
+                    Aa[p][1] += ta ? S2 : 0u;
+                    Aa[p][2] += ta ? S3 : 0u;
+                    Bb[p][0] += tb ? S1 : 0u;
+                    Bb[p][1] += tb ? S2 : 0u;
+                    Bb[p][2] += tb ? S3 : 0u;
+                }
                 Dd[0] += pre_task == 3 ? 0ull : dy;
                 Dd[1] += pre_task == 3 ? dy : 0ull;
-            } else if (valid) {
+            } else if (valid && (is_task || is_twin)) {  // an entry of a later graph: add directly
                 unsigned long long* h = acc + (size_t)ls * ACC;
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (add[0][p][q]) atomicAdd(h + (p + 1) + 4 * (q + 1), add[0][p][q]);
-                        if (add[1][p][q]) atomicAdd(h + (p + 1) + 16 * (q + 1), add[1][p][q]);
-                    }
+                const int p = (is_task ? pre_task : pre_twin) - 1;
+                const int sh4 = is_task ? 4 : 16;
+                if (S1) atomicAdd(h + (p + 1) + sh4 * 1, (unsigned long long)S1);
+                if (S2) atomicAdd(h + (p + 1) + sh4 * 2, (unsigned long long)S2);
+                if (S3) atomicAdd(h + (p + 1) + sh4 * 3, (unsigned long long)S3);
                 if (dy) atomicAdd(h + 64 + (pre_task == 3 ? 1 : 0), dy);
             }
 #pragma unroll
