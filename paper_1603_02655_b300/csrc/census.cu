@@ -764,10 +764,25 @@ struct WarpHist {
 // One thread per small task (32 consecutive tasks per warp item): a plain
 // two-pointer merge from global memory.  A lane whose task belongs to
 // another graph than the warp's histogram adds into global memory directly.
+// Entries at or below u matter to no triad code (their dyadic share comes
+// from the closed-triad counts), so with `split` (entries of each row below
+// its own id) both lists start above u: u's own split point, and in v's list
+// the first entry above u, searched below v's split (u < v).
+__device__ __forceinline__ int first_above(const uint32_t* __restrict__ list, int n, uint32_t u) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((__ldg(list + mid) >> 2) <= u) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <bool INS>
 __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restrict__ row_ptr,
                                             const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
-                                            const uint4* __restrict__ rec, unsigned base, unsigned ntask) {
+                                            const int32_t* __restrict__ split, const uint4* __restrict__ rec,
+                                            unsigned base, unsigned ntask) {
     const unsigned ti = base + w.lane;
     const bool has = ti < ntask;
     const uint4 r = has ? rec[ti] : make_uint4(0, 0, 0, 0);
@@ -782,6 +797,10 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
         const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
         int64_t ia = row_ptr[r.x], ib = row_ptr[r.y];
         const int64_t ae = row_ptr[r.x + 1], be = row_ptr[r.y + 1];
+        if (split) {
+            ia += split[r.x];
+            ib += first_above(adj + ib, split[r.y], ul);
+        }
         uint32_t eA = ia < ae ? __ldg(adj + ia) : SENT;
         uint32_t eB = ib < be ? __ldg(adj + ib) : SENT;
         for (;;) {
@@ -811,6 +830,7 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
 __global__ void __launch_bounds__(256) k_thread(const int64_t* __restrict__ row_ptr,
                                                 const uint32_t* __restrict__ adj,
                                                 const SegDev* __restrict__ seg,
+                                                const int32_t* __restrict__ split,
                                                 const uint4* __restrict__ rec,
                                                 const unsigned int* __restrict__ cnt, uint32_t cap,
                                                 unsigned long long* __restrict__ acc) {
@@ -821,7 +841,7 @@ __global__ void __launch_bounds__(256) k_thread(const int64_t* __restrict__ row_
     __syncwarp();
     const unsigned ntask = min(*cnt, cap);
     for (unsigned base = (blockIdx.x * WARPS + warp) * 32u; base < ntask; base += gridDim.x * WARPS * 32u)
-        thread_item<false>(w, row_ptr, adj, seg, rec, base, ntask);
+        thread_item<false>(w, row_ptr, adj, seg, split, rec, base, ntask);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -979,8 +999,9 @@ constexpr int WARP_BUF = WARP_LMAX + 16;  // words of shared memory per warp
 template <bool INS>
 __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int64_t* __restrict__ row_ptr,
                                           const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
-                                          const uint4* __restrict__ rec, const int32_t* __restrict__ ia_start,
-                                          unsigned i, unsigned nrec, int tile) {
+                                          const int32_t* __restrict__ split, const uint4* __restrict__ rec,
+                                          const int32_t* __restrict__ ia_start, unsigned i, unsigned nrec,
+                                          int tile) {
     const int lane = w.lane;
     const long long t0 = INS ? clock64() : 0;
     const uint4 r = rec[i];
@@ -997,6 +1018,9 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
         ie = d1 == L ? ie : (int64_t)ia_start[min(i + 1, nrec - 1)];
         js = d0 - is;
         je = d1 - ie;
+    } else if (split) {  // a whole task: both lists from above u (see thread_item)
+        is = split[r.x];
+        js = first_above(adj + bb, split[r.y], (uint32_t)(r.x - rb));
     }
     const int na = (int)(ie - is), nb = (int)(je - js);
     const int oA = load_span<32>(raw, adj, ab + is, na + 1, ab + ie, lane);
@@ -1013,6 +1037,7 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
 __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_ptr,
                                               const uint32_t* __restrict__ adj,
                                               const SegDev* __restrict__ seg,
+                                              const int32_t* __restrict__ split,
                                               const uint4* __restrict__ rec,
                                               const int32_t* __restrict__ ia_start,
                                               const unsigned int* __restrict__ cnt, uint32_t cap,
@@ -1025,7 +1050,7 @@ __global__ void __launch_bounds__(256) k_warp(const int64_t* __restrict__ row_pt
     __syncwarp();
     const unsigned ntask = min(*cnt, cap);
     for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
-        warp_item<false>(w, sbuf[warp], row_ptr, adj, seg, rec, ia_start, i, ntask, tile);
+        warp_item<false>(w, sbuf[warp], row_ptr, adj, seg, split, rec, ia_start, i, ntask, tile);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -1317,6 +1342,7 @@ struct MergeQueues {
     uint32_t tile_cap;
     int tile;
     unsigned int* cursor;         // [4] per-queue cursors, zeroed before launch
+    const int32_t* split;         // per row: entries below its own id (whole tasks start above u)
     Instr ins;                    // per-task timing (ins.buf null: off)
 };
 
@@ -1350,9 +1376,11 @@ __global__ void __launch_bounds__(256) k_merge(const int64_t* __restrict__ row_p
             const unsigned end = min(at + grab[k], items[k]);
             for (unsigned i = at; i < end; ++i) {
                 if (k == 0) stream_item<EPL, INS>(w, sbuf[warp], row_ptr, adj, seg, q.rec[3][i]);
-                else if (k == 1) warp_item<INS>(w, sbuf[warp], row_ptr, adj, seg, q.tiles, q.ia, i, nt, q.tile);
-                else if (k == 2) warp_item<INS>(w, sbuf[warp], row_ptr, adj, seg, q.rec[1], nullptr, i, n1, 0);
-                else thread_item<INS>(w, row_ptr, adj, seg, q.rec[0], i * 32u, n0);
+                else if (k == 1)
+                    warp_item<INS>(w, sbuf[warp], row_ptr, adj, seg, q.split, q.tiles, q.ia, i, nt, q.tile);
+                else if (k == 2)
+                    warp_item<INS>(w, sbuf[warp], row_ptr, adj, seg, q.split, q.rec[1], nullptr, i, n1, 0);
+                else thread_item<INS>(w, row_ptr, adj, seg, q.split, q.rec[0], i * 32u, n0);
             }
         }
     }
@@ -2224,6 +2252,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             q.tile_cap = cap2;
             q.tile = o.chunk;
             q.cursor = ctr + 20;
+            q.split = set.split;
             q.ins = ins ? *ins : Instr{nullptr, nullptr, 0, 0};
             TC_CUDA(hub_launch());
             mark(4);
@@ -2240,8 +2269,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
                 k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5, cap2,
                                                             o.chunk, acc);
             else
-                k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5, cap2,
-                                                            o.chunk, acc);
+                k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split, d_tiles, d_ia,
+                                                            ctr + 5, cap2, o.chunk, acc);
             TC_CUDA(cudaGetLastError());
             mark(4);
             k_stream<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg,
@@ -2249,12 +2278,12 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             TC_CUDA(cudaGetLastError());
             TC_CUDA(hub_launch());
             mark(5);
-            k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[1], nullptr, ctr + 1,
-                                                        bins.cap[1], 0, acc);
+            k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split, bins.rec[1], nullptr,
+                                                        ctr + 1, bins.cap[1], 0, acc);
             TC_CUDA(cudaGetLastError());
             mark(6);
-            k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, bins.rec[0], ctr + 0,
-                                                            bins.cap[0], acc);
+            k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split, bins.rec[0],
+                                                            ctr + 0, bins.cap[0], acc);
             TC_CUDA(cudaGetLastError());
         }
     } else {
@@ -2508,7 +2537,7 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
                                                      s->acc, cursor);
         TC_CUDA(cudaGetLastError());
-        k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(row_ptr, adj, &s->seg, s->rec, s->ctr + 0,
+        k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(row_ptr, adj, &s->seg, nullptr, s->rec, s->ctr + 0,
                                                         bins.cap[0], s->acc);
         TC_CUDA(cudaGetLastError());
     }
