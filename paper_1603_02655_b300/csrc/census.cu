@@ -161,7 +161,7 @@ constexpr int OWN_CAP = 15360;   // owners up to this degree are staged whole
 constexpr int OWN_MAX = 131072;  // larger ones: bucket starts only
 // an owner's dyads are cut into pieces of this many list positions, one work
 // item each (so that several CTAs share a large owner)
-constexpr int OWN_PIECE = 2048;
+constexpr int OWN_PIECE = 1024;
 
 struct BinParams {
     int thr_thread, thr_warp, stream_max, own_min;
