@@ -157,7 +157,7 @@ constexpr int STREAM_SMAX = 1024;
 // the larger id) has degree in [own_min, OWN_MAX] is not merged; k_owner
 // indexes the owner's list in shared memory and looks the other endpoint's
 // list up in it.
-constexpr int OWN_CAP = 15360;   // owners up to this degree are staged whole
+constexpr int OWN_CAP = 8192;    // owners up to this degree are staged whole
 constexpr int OWN_MAX = 131072;  // larger ones: bucket starts only
 // an owner's dyads are cut into pieces of this many list positions, one work
 // item each (so that several CTAs share a large owner)

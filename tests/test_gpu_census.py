@@ -218,8 +218,31 @@ def owner_profile(n, src, dst, **over):
     return c, tc.tc_census_profile()
 
 
+def test_owner_staging_boundary():
+    # owners of up to 8192 entries are copied to shared memory, larger ones
+    # are looked up in global memory: hubs of 8191, 8192 and 8193 entries
+    # over the same neighbourhood, joined to one another
+    rng = np.random.default_rng(5)
+    n = 20_000
+    pool = np.arange(3, n)
+    src, dst = [], []
+    for h, D in enumerate((8191, 8192, 8193)):
+        nb = np.concatenate([np.delete(np.arange(3), h), rng.choice(pool[:12_000], D - 2, replace=False)])
+        out = rng.random(nb.size) < 0.5
+        src.append(np.where(out, h, nb))
+        dst.append(np.where(out, nb, h))
+    src.append(rng.integers(3, n, 40_000))
+    dst.append(rng.integers(3, n, 40_000))
+    src, dst = np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32)
+    want = oracle.census(n, src, dst, threads=THREADS)
+    for own_min in (1, 128, 8193):
+        c, p = owner_profile(n, src, dst, own_min=own_min)
+        assert c == want, own_min
+        assert p["owner_tasks"] > 0
+
+
 def test_owner_large_and_skewed():
-    # owners above 16384 entries keep only 32-bit bucket starts in shared
+    # owners above 8192 entries keep only 32-bit bucket starts in shared
     # memory and read their list from global memory; two such hubs share
     # neighbours (their dyad has both lists large)
     rng = np.random.default_rng(11)
