@@ -165,6 +165,10 @@ def test_pipeline_trains_and_reports_the_judge():
         params, rep = costmodel.train_cost_model([g], mask=7, steps=800)
         assert rep["test_samples"] > 100
         assert np.isfinite(rep["rmse_mlp"]) and np.isfinite(rep["rmse_degree_sum"])
+        # the gain of the trained network over the method without it: held-out
+        # task costs predicted better than by the degree-sum rule fitted to
+        # the same training samples
+        assert rep["rmse_mlp"] < rep["rmse_degree_sum"], rep
         tc.tc_cost_model_load(params)
         want = tc.tc_census(g)
         assert tc.tc_census(g, tc.tc_opts_default(bin_mode=tc.TC_BIN_MLP)) == want
