@@ -1610,11 +1610,23 @@ __device__ __forceinline__ uint32_t owner_find(const Owner& o, const uint32_t* L
     const uint32_t b = key >> o.shift;
     const int j0 = STAGED ? (int)(st[b] >> 16) : (int)ls[b];
     const int j1 = STAGED ? (int)(st[b + 1] >> 16) : (int)ls[b + 1];
-    for (int j = j0; j < j1; ++j) {
-        const uint32_t e = L[j];
-        if ((e >> 2) >= key) return (e >> 2) == key ? e : SENT;
+    if (STAGED) {  // the list is in shared memory: scan
+        for (int j = j0; j < j1; ++j) {
+            const uint32_t e = L[j];
+            if ((e >> 2) >= key) return (e >> 2) == key ? e : SENT;
+        }
+        return SENT;
     }
-    return SENT;
+    // the list is in global memory: up to 8 independent loads per round
+    uint32_t hit = SENT;
+    for (int j = j0; j < j1; j += 8) {
+        uint32_t e[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) e[k] = j + k < j1 ? __ldg(L + j + k) : SENT;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) hit = (e[k] >> 2) == key ? e[k] : hit;
+    }
+    return hit;
 }
 
 // A shared element w of dyad <u,v> (see k_tasks): corrections of the
