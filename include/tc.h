@@ -102,7 +102,7 @@ typedef struct {
                              degrees: the larger id) has degree d_h with
                              own_min <= d_h <= 131072 is not merged: the
                              owner's list is indexed by id buckets in shared
-                             memory (and copied there up to 8192 entries) and
+                             memory (and copied there up to 512 entries) and
                              the other endpoint's list is looked up in it.
                              0 disables; default 128 */
     int32_t row_tasks;    /* 1: compute the per-dyad terms with one warp per row

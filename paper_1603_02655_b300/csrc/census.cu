@@ -157,7 +157,7 @@ constexpr int STREAM_SMAX = 1024;
 // the larger id) has degree in [own_min, OWN_MAX] is not merged; k_owner
 // indexes the owner's list in shared memory and looks the other endpoint's
 // list up in it.
-constexpr int OWN_CAP = 8192;    // owners up to this degree are staged whole
+constexpr int OWN_CAP = 512;     // owners up to this degree are staged whole
 constexpr int OWN_MAX = 131072;  // larger ones: bucket starts only
 // an owner's dyads are cut into pieces of this many list positions, one work
 // item each (so that several CTAs share a large owner)
@@ -1492,7 +1492,7 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 // list is shared by several warps.
 constexpr int OWN_NT = 512;
 constexpr int OWN_WARPS = OWN_NT / 32;
-constexpr int OWN_LBS = 13;  // staged owners: at most 2^13 buckets
+constexpr int OWN_LBS = 9;   // staged owners: at most 2^9 buckets
 constexpr int OWN_LBL = 13;  // larger owners: at most 2^13 buckets
 constexpr int OWN_G = 2;     // aligned 16-byte groups per lane per unit
 constexpr int OWN_UNIT = 32 * 4 * OWN_G;
@@ -1505,16 +1505,20 @@ constexpr size_t OWN_XE_BYTES = sizeof(uint32_t) * OWN_NT;
 constexpr size_t OWN_PP_BYTES = own_pad(sizeof(int32_t) * (OWN_NT + 1));
 constexpr int OWN_QN = 64;  // per-warp queue of keys that passed the mask test
 constexpr size_t OWN_Q_BYTES = (sizeof(uint32_t) + sizeof(uint16_t)) * OWN_QN * OWN_WARPS;
+// the index region holds either a staged owner (list T, then its table st)
+// or a larger owner (32-bit starts ls, then masks lm)
+constexpr size_t OWN_LS_BYTES = own_pad(sizeof(uint32_t) * ((1 << OWN_LBL) + 1));
+constexpr size_t OWN_STAGED_BYTES = OWN_T_BYTES + OWN_ST_BYTES;
+constexpr size_t OWN_LARGE_BYTES = OWN_LS_BYTES + sizeof(uint32_t) * (1 << OWN_LBL);
+constexpr size_t OWN_IDX_BYTES = OWN_STAGED_BYTES > OWN_LARGE_BYTES ? OWN_STAGED_BYTES : OWN_LARGE_BYTES;
 constexpr size_t OWN_SMEM =
-    OWN_T_BYTES + OWN_ST_BYTES + OWN_HS_BYTES + OWN_SB_BYTES + OWN_XE_BYTES + OWN_PP_BYTES + OWN_Q_BYTES;
+    OWN_IDX_BYTES + OWN_HS_BYTES + OWN_SB_BYTES + OWN_XE_BYTES + OWN_PP_BYTES + OWN_Q_BYTES;
 static_assert(OWN_NT <= 65536, "queued task indices are 16-bit");
 // staged owner: st[b] = start << 16 | sub-bucket mask, b in [0, 2^lB]
 static_assert(OWN_CAP <= 65535, "staged bucket starts are 16-bit");
 // larger owner: 32-bit starts [0, 2^lB] and 32-bit masks [0, 2^lB) in the
 // space of the staged list and table
-constexpr size_t OWN_LS_BYTES = own_pad(sizeof(uint32_t) * ((1 << OWN_LBL) + 1));
-static_assert(OWN_LS_BYTES + sizeof(uint32_t) * (1 << OWN_LBL) <= OWN_T_BYTES + OWN_ST_BYTES,
-              "a larger owner's starts and masks fit where a staged list goes");
+static_assert(OWN_CAP <= (1 << OWN_LBS), "a staged owner has at most one entry per bucket on average");
 static_assert(OWN_PIECE % OWN_NT == 0, "an item is a whole number of task tables");
 
 struct OwnArgs {
@@ -1935,7 +1939,7 @@ __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
     uint32_t* st = reinterpret_cast<uint32_t*>(own_smem + OWN_T_BYTES);
     uint32_t* ls = reinterpret_cast<uint32_t*>(own_smem);
     uint32_t* lm = reinterpret_cast<uint32_t*>(own_smem + OWN_LS_BYTES);
-    unsigned char* p = own_smem + OWN_T_BYTES + OWN_ST_BYTES;
+    unsigned char* p = own_smem + OWN_IDX_BYTES;
     int32_t* hs_all = reinterpret_cast<int32_t*>(p);
     p += OWN_HS_BYTES;
     int64_t* tsb = reinterpret_cast<int64_t*>(p);

@@ -219,14 +219,14 @@ def owner_profile(n, src, dst, **over):
 
 
 def test_owner_staging_boundary():
-    # owners of up to 8192 entries are copied to shared memory, larger ones
-    # are looked up in global memory: hubs of 8191, 8192 and 8193 entries
+    # owners of up to 512 entries are copied to shared memory, larger ones
+    # are looked up in global memory: hubs of 511, 512 and 513 entries
     # over the same neighbourhood, joined to one another
     rng = np.random.default_rng(5)
     n = 20_000
     pool = np.arange(3, n)
     src, dst = [], []
-    for h, D in enumerate((8191, 8192, 8193)):
+    for h, D in enumerate((511, 512, 513)):
         nb = np.concatenate([np.delete(np.arange(3), h), rng.choice(pool[:12_000], D - 2, replace=False)])
         out = rng.random(nb.size) < 0.5
         src.append(np.where(out, h, nb))
@@ -235,14 +235,14 @@ def test_owner_staging_boundary():
     dst.append(rng.integers(3, n, 40_000))
     src, dst = np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32)
     want = oracle.census(n, src, dst, threads=THREADS)
-    for own_min in (1, 128, 8193):
+    for own_min in (1, 128, 513):
         c, p = owner_profile(n, src, dst, own_min=own_min)
         assert c == want, own_min
         assert p["owner_tasks"] > 0
 
 
 def test_owner_large_and_skewed():
-    # owners above 8192 entries keep only 32-bit bucket starts in shared
+    # owners above 512 entries keep only 32-bit bucket starts in shared
     # memory and read their list from global memory; two such hubs share
     # neighbours (their dyad has both lists large)
     rng = np.random.default_rng(11)
