@@ -1851,59 +1851,73 @@ __device__ __forceinline__ void owner_drain(OwnHist& w, OwnQueue& Q, int cnt, co
     Q.n -= cnt;
 }
 
+// Grab the warp's next unit of OWN_UNIT slots and issue this lane's loads:
+// 4 * OWN_G slots from s0 in aligned 16-byte groups, each inside one dyad's
+// part (parts are whole groups, at least one each).  keep has bit i set for
+// slot i when it lies inside its part (not the lead of the part's first group
+// or the trail of its last); tqp holds the group's task index in 16-bit
+// fields.  Returns the unit's first slot.
+__device__ __forceinline__ int owner_issue(const OwnArgs& a, const int64_t* tsb, const int32_t* tpp, int ntask,
+                                           int total, unsigned* next, int lane, uint4 (&g)[OWN_G], uint32_t& tqp,
+                                           uint32_t& keep) {
+    unsigned u = 0;
+    if (lane == 0) u = atomicAdd(next, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    const int f0 = (int)u * OWN_UNIT;
+    const int s0 = f0 + 4 * OWN_G * lane;
+    tqp = 0;
+    keep = 0;
+#pragma unroll
+    for (int k = 0; k < OWN_G; ++k) g[k] = make_uint4(SENT, SENT, SENT, SENT);
+    if (s0 < total) {
+        int lo = 0, hi = ntask - 1;  // last dyad whose first slot is <= s0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tpp[mid] <= s0) lo = mid;
+            else hi = mid - 1;
+        }
+        int t = lo;
+#pragma unroll
+        for (int k = 0; k < OWN_G; ++k) {
+            const int sk = s0 + 4 * k;
+            if (k > 0 && tpp[t + 1] <= sk) ++t;  // t + 1 <= ntask: tpp[ntask] = total
+            if (sk < total) {
+                const int64_t d = tsb[t];
+                const int p = tpp[t];
+                const int rel = sk - p;
+                g[k] = __ldg(reinterpret_cast<const uint4*>(a.adj + (d >> 4) + rel));
+                const int lead = (int)(d & 3), end = tpp[t + 1] - p - (int)((d >> 2) & 3);
+                // slots rel .. rel+3 inside [lead, end)
+                const int lo4 = max(lead - rel, 0), hi4 = min(end - rel, 4);
+                const uint32_t bits = hi4 > lo4 ? ((1u << hi4) - 1u) & ~((1u << lo4) - 1u) : 0u;
+                keep |= bits << (4 * k);
+                tqp |= (uint32_t)t << (16 * k);
+            }
+        }
+    }
+    return f0;
+}
+
+// Units of the current task table, pulled by the warp one at a time; the
+// next unit's loads are issued before the current unit is filtered, so they
+// are in flight meanwhile.
 template <bool STAGED>
 __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnArgs& a, const Owner& o,
                                             const uint32_t* L, const uint32_t* st, const uint32_t* ls,
                                             const uint32_t* lm, const int64_t* tsb, const uint32_t* txe,
                                             const int32_t* tpp, int ntask, int total, unsigned* next) {
+    static_assert(OWN_G <= 2, "task indices of a lane's groups are packed in 16-bit fields of one word");
     const unsigned full = 0xffffffffu;
     const int lane = w.lane;
     const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
     uint32_t c012 = 0, c102 = 0;
-    for (;;) {
-        unsigned u = 0;
-        if (lane == 0) u = atomicAdd(next, 1u);
-        u = __shfl_sync(full, u, 0);
-        const int f0 = (int)u * OWN_UNIT;
-        if (f0 >= total) break;
-        // this lane's 4 * OWN_G slots from s0: aligned 16-byte groups, each
-        // inside one dyad's part (parts are whole groups, at least one each)
-        const int s0 = f0 + 4 * OWN_G * lane;
-        uint4 g[OWN_G];
-        int tq[OWN_G];
-#pragma unroll
-        for (int k = 0; k < OWN_G; ++k) {
-            g[k] = make_uint4(SENT, SENT, SENT, SENT);
-            tq[k] = 0;
-        }
-        if (s0 < total) {
-            int lo = 0, hi = ntask - 1;  // last dyad whose first slot is <= s0
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (tpp[mid] <= s0) lo = mid;
-                else hi = mid - 1;
-            }
-            tq[0] = lo;
-#pragma unroll
-            for (int k = 1; k < OWN_G; ++k)
-                tq[k] = tq[k - 1] + (tq[k - 1] < ntask && tpp[tq[k - 1] + 1] <= s0 + 4 * k ? 1 : 0);
-#pragma unroll
-            for (int k = 0; k < OWN_G; ++k) {
-                const int sk = s0 + 4 * k;
-                if (sk < total) {
-                    const int64_t d = tsb[tq[k]];
-                    g[k] = __ldg(reinterpret_cast<const uint4*>(a.adj + (d >> 4) + (sk - tpp[tq[k]])));
-                    // slots of the group outside the part: the lead of its first
-                    // group, the trail of its last
-                    const int rel = sk - tpp[tq[k]];
-                    const int lead = (int)(d & 3), end = tpp[tq[k] + 1] - tpp[tq[k]] - (int)((d >> 2) & 3);
-                    if (rel + 0 < lead || rel + 0 >= end) g[k].x = SENT;
-                    if (rel + 1 < lead || rel + 1 >= end) g[k].y = SENT;
-                    if (rel + 2 < lead || rel + 2 >= end) g[k].z = SENT;
-                    if (rel + 3 < lead || rel + 3 >= end) g[k].w = SENT;
-                }
-            }
-        }
+    uint4 g[OWN_G];
+    uint32_t tqp, keep;
+    int f0 = owner_issue(a, tsb, tpp, ntask, total, next, lane, g, tqp, keep);
+    while (f0 < total) {
+        uint4 gn[OWN_G];
+        uint32_t tqn, keepn;
+        const int f0n = owner_issue(a, tsb, tpp, ntask, total, next, lane, gn, tqn, keepn);
         uint32_t se[4 * OWN_G];
 #pragma unroll
         for (int k = 0; k < OWN_G; ++k) {
@@ -1914,16 +1928,21 @@ __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnAr
         }
 #pragma unroll
         for (int j = 0; j < 4 * OWN_G; ++j) {
-            const bool pass = se[j] != SENT && owner_maybe<STAGED>(o, st, lm, se[j] >> 2);
+            const bool pass = ((keep >> j) & 1u) && owner_maybe<STAGED>(o, st, lm, se[j] >> 2);
             const unsigned m = __ballot_sync(full, pass);
             if (pass) {
                 const int slot = (Q.head + Q.n + __popc(m & (upto >> 1))) & (OWN_QN - 1);
                 Q.se[slot] = se[j];
-                Q.q[slot] = (uint16_t)tq[j >> 2];
+                Q.q[slot] = (uint16_t)(tqp >> (16 * (j >> 2)));
             }
             Q.n += __popc(m);
             if (Q.n >= 32) owner_drain<STAGED>(w, Q, 32, o, L, st, ls, txe, c012, c102);
         }
+#pragma unroll
+        for (int k = 0; k < OWN_G; ++k) g[k] = gn[k];
+        tqp = tqn;
+        keep = keepn;
+        f0 = f0n;
     }
     if (Q.n > 0) owner_drain<STAGED>(w, Q, Q.n, o, L, st, ls, txe, c012, c102);  // the table changes next
     w.pending += __reduce_add_sync(full, c012 + c102);
