@@ -25,10 +25,13 @@
 //  * The shared elements w correct the classification: if w > v the triad
 //    was counted as pre+4tu and pre+16tv and is moved to pre+4tu+16tv; if
 //    u < w < v it was counted as pre+16tv and must not count at all; a w
-//    below u changes nothing.  They are found by k_owner (the shorter list's
-//    entries above u looked up in an index of the owner's list) or by the
-//    merge kernels (k_merge, k_hub and the separate-launch items: both lists
-//    streamed).
+//    below u changes nothing.  In a triangle a < b < c the first case is
+//    dyad <a,b> with w = c, the second dyad <a,c> with w = b, both fixed by
+//    the three tags of the triangle, so both corrections are made when dyad
+//    <a,b> finds c: only shared elements above v are searched for.  They are
+//    found by k_owner (the shorter list's entries above v looked up in an
+//    index of the owner's list) or by the merge kernels (k_merge, k_hub and
+//    the separate-launch items: both lists streamed).
 //  * |A n B| itself is never counted: summed over the dyads it is fixed by
 //    the closed-triad counts, which k_fold adds to the dyadic slots after
 //    mapping the 64 codes onto the 16 MAN types; k_fold closes 003.
@@ -716,16 +719,22 @@ __global__ void __launch_bounds__(256) k_split(const int64_t* __restrict__ row_p
 }
 
 // ----------------------------------------------------- shared-element fix --
-// w is in both N(u) and N(v) (tags tu, tv).  Move its contribution from the
-// single-list codes to the joint code (w > v), or drop it (u < w < v).
+// w is in both N(u) and N(v) (tags tu, tv), u < v < w: the triangle {u,v,w}
+// is handled once, by its lowest dyad <u,v>.  For <u,v> its contribution
+// moves from the single-list codes pre+4tu and pre+16tv to the joint code;
+// for <u,w>, whose middle vertex is v, the single-list code tu + 16 tag_w(v)
+// (tag_w(v): tv with its two bits swapped) must not count.  A shared w below
+// v is left to the dyad of the triangle's two lowest vertices.
+__device__ __forceinline__ uint32_t tag_swap(uint32_t t) { return ((t & 1u) << 1) | (t >> 1); }
+
 __device__ __forceinline__ void on_shared(unsigned long long* h, uint32_t w, uint32_t ul, uint32_t vl,
                                           uint32_t pre, uint32_t tu, uint32_t tv) {
+    (void)ul;
     if (w > vl) {
         atomicAdd(h + pre + 4 * tu, ~0ull);
         atomicAdd(h + pre + 16 * tv, ~0ull);
         atomicAdd(h + pre + 4 * tu + 16 * tv, 1ull);
-    } else if (w > ul) {
-        atomicAdd(h + pre + 16 * tv, ~0ull);
+        atomicAdd(h + tu + 16 * tag_swap(tv), ~0ull);
     }
 }
 
@@ -764,10 +773,10 @@ struct WarpHist {
 // One thread per small task (32 consecutive tasks per warp item): a plain
 // two-pointer merge from global memory.  A lane whose task belongs to
 // another graph than the warp's histogram adds into global memory directly.
-// Entries at or below u matter to no triad code (their dyadic share comes
-// from the closed-triad counts), so with `split` (entries of each row below
-// its own id) both lists start above u: u's own split point, and in v's list
-// the first entry above u, searched below v's split (u < v).
+// Only shared elements above v change a code through this dyad (on_shared),
+// so with `split` (entries of each row below its own id) both lists start
+// above v: v's own split point, and in u's list the first entry above v,
+// searched above u's split (u < v).
 __device__ __forceinline__ int first_above(const uint32_t* __restrict__ list, int n, uint32_t u) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -798,8 +807,9 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
         int64_t ia = row_ptr[r.x], ib = row_ptr[r.y];
         const int64_t ae = row_ptr[r.x + 1], be = row_ptr[r.y + 1];
         if (split) {
-            ia += split[r.x];
-            ib += first_above(adj + ib, split[r.y], ul);
+            const int su = split[r.x];
+            ia += su + first_above(adj + ia + su, (int)(ae - ia) - su, vl);
+            ib += split[r.y];
         }
         uint32_t eA = ia < ae ? __ldg(adj + ia) : SENT;
         uint32_t eB = ib < be ? __ldg(adj + ib) : SENT;
@@ -1018,9 +1028,10 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
         ie = d1 == L ? ie : (int64_t)ia_start[min(i + 1, nrec - 1)];
         js = d0 - is;
         je = d1 - ie;
-    } else if (split) {  // a whole task: both lists from above u (see thread_item)
-        is = split[r.x];
-        js = first_above(adj + bb, split[r.y], (uint32_t)(r.x - rb));
+    } else if (split) {  // a whole task: both lists from above v (see thread_item)
+        const int su = split[r.x];
+        is = su + first_above(adj + ab + su, (int)ie - su, (uint32_t)(r.y - rb));
+        js = split[r.y];
     }
     const int na = (int)(ie - is), nb = (int)(je - js);
     const int oA = load_span<32>(raw, adj, ab + is, na + 1, ab + ie, lane);
@@ -1342,7 +1353,7 @@ struct MergeQueues {
     uint32_t tile_cap;
     int tile;
     unsigned int* cursor;         // [4] per-queue cursors, zeroed before launch
-    const int32_t* split;         // per row: entries below its own id (whole tasks start above u)
+    const int32_t* split;         // per row: entries below its own id (whole tasks start above v)
     Instr ins;                    // per-task timing (ins.buf null: off)
 };
 
@@ -1633,23 +1644,22 @@ __device__ __forceinline__ uint32_t owner_find(const Owner& o, const uint32_t* L
     return hit;
 }
 
-// A shared element w of dyad <u,v> (see k_tasks): corrections of the
-// suffix terms, into the warp's 32-bit histogram.
-__device__ __forceinline__ void on_shared32(int32_t* h, uint32_t w, uint32_t ul, uint32_t vl, uint32_t pre,
-                                            uint32_t tu, uint32_t tv) {
+// A shared element w > v of dyad <u,v> (see on_shared): corrections of the
+// suffix terms of <u,v> and <u,w>, into the warp's 32-bit histogram.
+__device__ __forceinline__ void on_shared32(int32_t* h, uint32_t w, uint32_t vl, uint32_t pre, uint32_t tu,
+                                            uint32_t tv) {
     if (w > vl) {
         atomicAdd(h + pre + 4 * tu, -1);
         atomicAdd(h + pre + 16 * tv, -1);
         atomicAdd(h + pre + 4 * tu + 16 * tv, 1);
-    } else if (w > ul) {
-        atomicAdd(h + pre + 16 * tv, -1);
+        atomicAdd(h + tu + 16 * tag_swap(tv), -1);
     }
 }
 
 // Per-warp 32-bit histogram for one graph, added (sign-extended) into that
 // graph's 64-bit accumulators when the graph changes, at the end, and before
 // any slot could leave the int32 range (each shared element moves a slot by
-// at most 1).
+// at most 2, and a work item adds fewer than 2^28 shared elements per warp).
 struct OwnHist {
     int32_t* hs;
     unsigned long long* acc;
@@ -1667,7 +1677,7 @@ struct OwnHist {
         pending = 0;
     }
     __device__ __forceinline__ void retag(int s) {
-        if (s != tag || pending > (1u << 30)) {
+        if (s != tag || pending > (1u << 29)) {
             flush();
             tag = s;
         }
@@ -1685,8 +1695,8 @@ struct OwnCtl {
 
 // For every position of every owner work item (a warp per item): whether the
 // owner owns the dyad with that neighbour x and, if so, where the part of x's
-// list above u = min(h, x) starts and how long it is (x's split when x < h,
-// else found by binary search below the split: h < x is one of x's lower
+// list above v = max(h, x) starts and how long it is (x's split when h < x,
+// else found by binary search above the split: h > x is one of x's upper
 // neighbours).  A flat pass, so these dependent loads overlap freely instead
 // of stalling k_owner between its barriers.
 __global__ void __launch_bounds__(256) k_owner_prep(OwnArgs a) {
@@ -1708,15 +1718,13 @@ __global__ void __launch_bounds__(256) k_owner_prep(OwnArgs a) {
             int64_t sb = 0;
             if (dx < D || (dx == D && x < hl)) {
                 sb = a.row_ptr[rb + x];
-                int lo = 0, hi = a.split[rb + x];
-                if (hl < x)
+                int lo = a.split[rb + x], hi = dx;
+                if (hl > x)  // h is one of x's upper neighbours: start after it
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
                         if ((__ldg(a.adj + sb + mid) >> 2) <= hl) lo = mid + 1;
                         else hi = mid;
                     }
-                else
-                    lo = hi;
                 len = dx - lo;
                 sb += lo;
             }
@@ -1747,15 +1755,13 @@ __global__ void __launch_bounds__(256) k_owner_prep_flat(OwnArgs a, const int32_
         int64_t sb = 0;
         if (dx < D || (dx == D && x < hl)) {
             sb = a.row_ptr[rb + x];
-            int lo = 0, hi = a.split[rb + x];
-            if (hl < x)
+            int lo = a.split[rb + x], hi = dx;
+            if (hl > x)  // h is one of x's upper neighbours: start after it
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if ((__ldg(a.adj + sb + mid) >> 2) <= hl) lo = mid + 1;
                     else hi = mid;
                 }
-            else
-                lo = hi;
             len = dx - lo;
             sb += lo;
         }
@@ -1765,9 +1771,10 @@ __global__ void __launch_bounds__(256) k_owner_prep_flat(OwnArgs a, const int32_
 }
 
 // The task table of positions [q0, q0 + OWN_NT) of the item: for each owned
-// dyad {h, x}, in list order, the part of x's list above u = min(h, x) (a
-// shared element below both endpoints changes no triad code: its share of the
-// dyadic term comes from the closed-triad counts in k_fold).  The parts are
+// dyad {h, x}, in list order, the part of x's list above v = max(h, x) (a
+// shared element below v is handled by another dyad of its triangle, see
+// on_shared; its share of the dyadic term comes from the closed-triad counts
+// in k_fold).  The parts are
 // concatenated in "slots", each part widened to whole aligned 16-byte groups
 // of x's list (lead entries before it, trail after it, both < 4), so that
 // every 4 slots from a multiple of 4 are one aligned 16-byte load of one
@@ -1842,7 +1849,7 @@ __device__ __forceinline__ void owner_drain(OwnHist& w, OwnQueue& Q, int cnt, co
             const bool h_is_u = o.hl < xt;
             const uint32_t pre = h_is_u ? et : (((et & 1u) << 1) | (et >> 1));
             const uint32_t th = hit & 3u, tx = se & 3u;
-            on_shared32(w.hs, key, h_is_u ? o.hl : xt, h_is_u ? xt : o.hl, pre, h_is_u ? th : tx, h_is_u ? tx : th);
+            on_shared32(w.hs, key, h_is_u ? xt : o.hl, pre, h_is_u ? th : tx, h_is_u ? tx : th);
             ++c012;  // shared elements (for the flush bound)
         }
     }
