@@ -140,7 +140,7 @@ struct SegDev {
 constexpr int NBIN = 4;
 
 struct Bins {
-    uint4* rec[NBIN];     // {u global, v global, seg<<2 | pre, 0}
+    uint4* rec[NBIN];     // {u global, v global, seg<<2 | pre, position in u's list after v}
     uint32_t cap[NBIN];
     unsigned int* cnt;    // [NBIN] records appended per bin
     int* overflow;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
 #pragma unroll
                 for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
                 const uint4 rec = make_uint4((uint32_t)x, (uint32_t)(rb + y),
-                                             ((uint32_t)s << 2) | (uint32_t)pre_task, 0u);
+                                             ((uint32_t)s << 2) | (uint32_t)pre_task, (uint32_t)(k + 1));
 #pragma unroll
                 for (int b = 0; b < NBIN; ++b) {
                     const bool mine = bin == b;
@@ -476,8 +476,10 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
             const int t = (int)(e & 3u);
             uint32_t S1 = 0, S2 = 0, S3 = 0;
             int d = 0;
+            int64_t rp = 0;
             if (valid) {
-                const int64_t frs = epfx[ls] + (row_ptr[x] - sg.eb);  // the row's first entry, in scan order
+                rp = row_ptr[x];
+                const int64_t frs = epfx[ls] + (rp - sg.eb);  // the row's first entry, in scan order
                 const unsigned long long I = scan[f] - (frs > 0 ? scan[frs - 1] : 0ull);
                 S1 = (uint32_t)vtag[3 * x] - (uint32_t)(I & TAG_MASK);
                 S2 = (uint32_t)vtag[3 * x + 1] - (uint32_t)((I >> TAG_BITS) & TAG_MASK);
@@ -530,7 +532,8 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
             }
 #pragma unroll
             for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
-            const uint4 rec = make_uint4((uint32_t)x, (uint32_t)(sg.rb + y), ((uint32_t)ls << 2) | (uint32_t)pre_task, 0u);
+            const uint4 rec = make_uint4((uint32_t)x, (uint32_t)(sg.rb + y), ((uint32_t)ls << 2) | (uint32_t)pre_task,
+                                         (uint32_t)(k - rp + 1));
 #pragma unroll
             for (int b = 0; b < NBIN; ++b) {
                 const bool in = bin == b;
@@ -775,18 +778,8 @@ struct WarpHist {
 // another graph than the warp's histogram adds into global memory directly.
 // Only shared elements above v change a code through this dyad (on_shared),
 // so with `split` (entries of each row below its own id) both lists start
-// above v: v's own split point, and in u's list the first entry above v,
-// searched above u's split (u < v).
-__device__ __forceinline__ int first_above(const uint32_t* __restrict__ list, int n, uint32_t u) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((__ldg(list + mid) >> 2) <= u) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
+// above v: v's own split point, and in u's list the entry after v, whose
+// position the task record carries in .w (the task pass knows it).
 template <bool INS>
 __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restrict__ row_ptr,
                                             const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
@@ -807,8 +800,7 @@ __device__ __forceinline__ void thread_item(WarpHist& w, const int64_t* __restri
         int64_t ia = row_ptr[r.x], ib = row_ptr[r.y];
         const int64_t ae = row_ptr[r.x + 1], be = row_ptr[r.y + 1];
         if (split) {
-            const int su = split[r.x];
-            ia += su + first_above(adj + ia + su, (int)(ae - ia) - su, vl);
+            ia += r.w;
             ib += split[r.y];
         }
         uint32_t eA = ia < ae ? __ldg(adj + ia) : SENT;
@@ -1029,8 +1021,7 @@ __device__ __forceinline__ void warp_item(WarpHist& w, uint32_t* raw, const int6
         js = d0 - is;
         je = d1 - ie;
     } else if (split) {  // a whole task: both lists from above v (see thread_item)
-        const int su = split[r.x];
-        is = su + first_above(adj + ab + su, (int)ie - su, (uint32_t)(r.y - rb));
+        is = r.w;
         js = split[r.y];
     }
     const int na = (int)(ie - is), nb = (int)(je - js);
@@ -1082,7 +1073,7 @@ static_assert(STREAM_SMAX + 8 <= WARP_BUF, "stream buffer fits the warp buffer")
 template <int EPL, bool INS>
 __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const int64_t* __restrict__ row_ptr,
                                             const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
-                                            const uint4 r) {
+                                            const int32_t* __restrict__ split, const uint4 r) {
     constexpr int STEP = 32 * EPL;
     constexpr int NQ = EPL / 4;  // 16-byte loads per lane per step
     const unsigned full = 0xffffffffu;
@@ -1093,8 +1084,9 @@ __device__ __forceinline__ void stream_item(WarpHist& w, uint32_t* buf, const in
     w.retag(s);
     const int64_t rb = seg[s].rb;
     const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
-    const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
-    const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+    // both lists from above v (see thread_item)
+    const int64_t ab = row_ptr[r.x] + (split ? r.w : 0), ae = row_ptr[r.x + 1];
+    const int64_t bb = row_ptr[r.y] + (split ? split[r.y] : 0), be = row_ptr[r.y + 1];
     const bool s_is_A = (ae - ab) <= (be - bb);
     const int64_t pS = s_is_A ? ab : bb;
     const int nS = (int)(s_is_A ? ae - ab : be - bb);
@@ -1183,6 +1175,7 @@ template <int EPL>
 __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_ptr,
                                                 const uint32_t* __restrict__ adj,
                                                 const SegDev* __restrict__ seg,
+                                                const int32_t* __restrict__ split,
                                                 const uint4* __restrict__ rec,
                                                 const unsigned int* __restrict__ cnt, uint32_t cap,
                                                 unsigned long long* __restrict__ acc) {
@@ -1194,7 +1187,7 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
     __syncwarp();
     const unsigned ntask = min(*cnt, cap);
     for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
-        stream_item<EPL, false>(w, sbuf[warp], row_ptr, adj, seg, rec[i]);
+        stream_item<EPL, false>(w, sbuf[warp], row_ptr, adj, seg, split, rec[i]);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -1209,7 +1202,7 @@ __global__ void __launch_bounds__(256) k_stream(const int64_t* __restrict__ row_
 template <int EPL>
 __device__ __forceinline__ void hub_item(WarpHist& w, uint32_t* buf, const int64_t* __restrict__ row_ptr,
                                             const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
-                                            const uint4 r) {
+                                            const int32_t* __restrict__ split, const uint4 r) {
     constexpr int STEP = 32 * EPL;
     constexpr int NQ = EPL / 4;  // 16-byte loads per lane per step
     const unsigned full = 0xffffffffu;
@@ -1219,8 +1212,9 @@ __device__ __forceinline__ void hub_item(WarpHist& w, uint32_t* buf, const int64
     w.retag(s);
     const int64_t rb = seg[s].rb;
     const uint32_t ul = (uint32_t)(r.x - rb), vl = (uint32_t)(r.y - rb);
-    const int64_t ab = row_ptr[r.x], ae = row_ptr[r.x + 1];
-    const int64_t bb = row_ptr[r.y], be = row_ptr[r.y + 1];
+    // both lists from above v (see thread_item)
+    const int64_t ab = row_ptr[r.x] + (split ? r.w : 0), ae = row_ptr[r.x + 1];
+    const int64_t bb = row_ptr[r.y] + (split ? split[r.y] : 0), be = row_ptr[r.y + 1];
     const bool s_is_A = (ae - ab) <= (be - bb);
     const uint32_t* Sp = adj + (s_is_A ? ab : bb);
     const int nS = (int)(s_is_A ? ae - ab : be - bb);
@@ -1322,6 +1316,7 @@ template <int EPL>
 __global__ void __launch_bounds__(256) k_hub(const int64_t* __restrict__ row_ptr,
                                              const uint32_t* __restrict__ adj,
                                              const SegDev* __restrict__ seg,
+                                             const int32_t* __restrict__ split,
                                              const uint4* __restrict__ rec,
                                              const unsigned int* __restrict__ cnt, uint32_t cap,
                                              unsigned long long* __restrict__ acc) {
@@ -1333,7 +1328,7 @@ __global__ void __launch_bounds__(256) k_hub(const int64_t* __restrict__ row_ptr
     __syncwarp();
     const unsigned ntask = min(*cnt, cap);
     for (unsigned i = blockIdx.x * WARPS + warp; i < ntask; i += gridDim.x * WARPS)
-        hub_item<EPL>(w, sbuf[warp], row_ptr, adj, seg, rec[cap - 1 - i]);
+        hub_item<EPL>(w, sbuf[warp], row_ptr, adj, seg, split, rec[cap - 1 - i]);
     __syncwarp();
     flush_hist<WARPS>(w.hs, acc, w.tag, lane);
 }
@@ -1386,7 +1381,7 @@ __global__ void __launch_bounds__(256) k_merge(const int64_t* __restrict__ row_p
             if (at >= items[k]) break;
             const unsigned end = min(at + grab[k], items[k]);
             for (unsigned i = at; i < end; ++i) {
-                if (k == 0) stream_item<EPL, INS>(w, sbuf[warp], row_ptr, adj, seg, q.rec[3][i]);
+                if (k == 0) stream_item<EPL, INS>(w, sbuf[warp], row_ptr, adj, seg, q.split, q.rec[3][i]);
                 else if (k == 1)
                     warp_item<INS>(w, sbuf[warp], row_ptr, adj, seg, q.split, q.tiles, q.ia, i, nt, q.tile);
                 else if (k == 2)
@@ -2276,7 +2271,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         }
         mark(3);
         auto hub_launch = [&]() {
-            k_hub<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg,
+            k_hub<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split,
                                                                               bins.rec[3], ctr + 7, bins.cap[3],
                                                                               acc);
             return cudaGetLastError();
@@ -2315,7 +2310,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
                                                             ctr + 5, cap2, o.chunk, acc);
             TC_CUDA(cudaGetLastError());
             mark(4);
-            k_stream<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg,
+            k_stream<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split,
                                                                                bins.rec[3], ctr + 3, bins.cap[3], acc);
             TC_CUDA(cudaGetLastError());
             TC_CUDA(hub_launch());
