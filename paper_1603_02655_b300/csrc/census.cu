@@ -1494,8 +1494,8 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 // Work item: a piece of at most OWN_PIECE positions of h's list, taken
 // OWN_NT positions at a time.  Their owned dyads are compacted into a task
 // table (list start, id and tag, running offset of the concatenated lists),
-// and warps pull units of OWN_UNIT entries of the concatenation, so a long
-// list is shared by several warps.
+// and each warp takes an equal range of the concatenation, OWN_UNIT entries
+// at a time, so a long list is shared by several warps.
 constexpr int OWN_NT = 512;
 constexpr int OWN_WARPS = OWN_NT / 32;
 constexpr int OWN_LBS = 9;   // staged owners: at most 2^9 buckets
@@ -1681,7 +1681,6 @@ struct OwnHist {
 
 struct OwnCtl {
     unsigned idx;   // item being processed
-    unsigned next;  // unit cursor of the item
     uint32_t row;   // owner indexed in shared memory (~0: none)
     int seg;
     int ntask, total;
@@ -1853,73 +1852,79 @@ __device__ __forceinline__ void owner_drain(OwnHist& w, OwnQueue& Q, int cnt, co
     Q.n -= cnt;
 }
 
-// Grab the warp's next unit of OWN_UNIT slots and issue this lane's loads:
-// 4 * OWN_G slots from s0 in aligned 16-byte groups, each inside one dyad's
-// part (parts are whole groups, at least one each).  keep has bit i set for
-// slot i when it lies inside its part (not the lead of the part's first group
-// or the trail of its last); tqp holds the group's task index in 16-bit
-// fields.  Returns the unit's first slot.
-__device__ __forceinline__ int owner_issue(const OwnArgs& a, const int64_t* tsb, const int32_t* tpp, int ntask,
-                                           int total, unsigned* next, int lane, uint4 (&g)[OWN_G], uint32_t& tqp,
-                                           uint32_t& keep) {
-    unsigned u = 0;
-    if (lane == 0) u = atomicAdd(next, 1u);
-    u = __shfl_sync(0xffffffffu, u, 0);
-    const int f0 = (int)u * OWN_UNIT;
+// Issue this lane's loads for the unit of OWN_UNIT slots at f0 of the warp's
+// range [f0, hi): 4 * OWN_G slots from s0 in aligned 16-byte groups, each
+// inside one dyad's part (parts are whole groups, at least one each).  keep
+// has bit i set for slot i when it lies inside its part (not the lead of the
+// part's first group or the trail of its last); tqp holds the group's task
+// index in 16-bit fields.  t is the lane's task: the last dyad whose first
+// slot is <= the lane's previous group, advanced here (slots only grow).
+__device__ __forceinline__ void owner_issue(const OwnArgs& a, const int64_t* tsb, const int32_t* tpp, int f0, int hi,
+                                            int lane, int& t, uint4 (&g)[OWN_G], uint32_t& tqp, uint32_t& keep) {
     const int s0 = f0 + 4 * OWN_G * lane;
     tqp = 0;
     keep = 0;
 #pragma unroll
     for (int k = 0; k < OWN_G; ++k) g[k] = make_uint4(SENT, SENT, SENT, SENT);
-    if (s0 < total) {
-        int lo = 0, hi = ntask - 1;  // last dyad whose first slot is <= s0
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tpp[mid] <= s0) lo = mid;
-            else hi = mid - 1;
-        }
-        int t = lo;
 #pragma unroll
-        for (int k = 0; k < OWN_G; ++k) {
-            const int sk = s0 + 4 * k;
-            if (k > 0 && tpp[t + 1] <= sk) ++t;  // t + 1 <= ntask: tpp[ntask] = total
-            if (sk < total) {
-                const int64_t d = tsb[t];
-                const int p = tpp[t];
-                const int rel = sk - p;
-                g[k] = __ldg(reinterpret_cast<const uint4*>(a.adj + (d >> 4) + rel));
-                const int lead = (int)(d & 3), end = tpp[t + 1] - p - (int)((d >> 2) & 3);
-                // slots rel .. rel+3 inside [lead, end)
-                const int lo4 = max(lead - rel, 0), hi4 = min(end - rel, 4);
-                const uint32_t bits = hi4 > lo4 ? ((1u << hi4) - 1u) & ~((1u << lo4) - 1u) : 0u;
-                keep |= bits << (4 * k);
-                tqp |= (uint32_t)t << (16 * k);
-            }
+    for (int k = 0; k < OWN_G; ++k) {
+        const int sk = s0 + 4 * k;
+        if (sk < hi) {
+            while (tpp[t + 1] <= sk) ++t;  // ends below ntask: tpp[ntask] = total > sk
+            const int64_t d = tsb[t];
+            const int p = tpp[t];
+            const int rel = sk - p;
+            g[k] = __ldg(reinterpret_cast<const uint4*>(a.adj + (d >> 4) + rel));
+            const int lead = (int)(d & 3), end = tpp[t + 1] - p - (int)((d >> 2) & 3);
+            // slots rel .. rel+3 inside [lead, end)
+            const int lo4 = max(lead - rel, 0), hi4 = min(end - rel, 4);
+            const uint32_t bits = hi4 > lo4 ? ((1u << hi4) - 1u) & ~((1u << lo4) - 1u) : 0u;
+            keep |= bits << (4 * k);
+            tqp |= (uint32_t)t << (16 * k);
         }
     }
-    return f0;
 }
 
-// Units of the current task table, pulled by the warp one at a time; the
+// Units of the current task table.  Each warp takes an equal range of the
+// table's slots (whole groups), a unit of OWN_UNIT slots at a time; a lane
+// finds its first dyad by binary search and then only steps forward.  The
 // next unit's loads are issued before the current unit is filtered, so they
 // are in flight meanwhile.
 template <bool STAGED>
 __device__ __forceinline__ void owner_units(OwnHist& w, OwnQueue& Q, const OwnArgs& a, const Owner& o,
                                             const uint32_t* L, const uint32_t* st, const uint32_t* ls,
                                             const uint32_t* lm, const int64_t* tsb, const uint32_t* txe,
-                                            const int32_t* tpp, int ntask, int total, unsigned* next) {
+                                            const int32_t* tpp, int ntask, int total) {
     static_assert(OWN_G <= 2, "task indices of a lane's groups are packed in 16-bit fields of one word");
     const unsigned full = 0xffffffffu;
     const int lane = w.lane;
     const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
     uint32_t c012 = 0, c102 = 0;
+    const int warp = (int)(threadIdx.x >> 5);
+    const int lo = (int)(((int64_t)total * warp / OWN_WARPS) & ~(int64_t)3);
+    const int hi = warp == OWN_WARPS - 1 ? total : (int)(((int64_t)total * (warp + 1) / OWN_WARPS) & ~(int64_t)3);
+    int t = 0;
+    {
+        const int s0 = lo + 4 * OWN_G * lane;
+        if (s0 < hi) {
+            int l = 0, h = ntask - 1;  // last dyad whose first slot is <= s0
+            while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (tpp[mid] <= s0) l = mid;
+                else h = mid - 1;
+            }
+            t = l;
+        }
+    }
     uint4 g[OWN_G];
     uint32_t tqp, keep;
-    int f0 = owner_issue(a, tsb, tpp, ntask, total, next, lane, g, tqp, keep);
-    while (f0 < total) {
+    int f0 = lo;
+    owner_issue(a, tsb, tpp, f0, hi, lane, t, g, tqp, keep);
+    while (f0 < hi) {
         uint4 gn[OWN_G];
         uint32_t tqn, keepn;
-        const int f0n = owner_issue(a, tsb, tpp, ntask, total, next, lane, gn, tqn, keepn);
+        const int f0n = f0 + OWN_UNIT;
+        owner_issue(a, tsb, tpp, f0n, hi, lane, t, gn, tqn, keepn);
         uint32_t se[4 * OWN_G];
 #pragma unroll
         for (int k = 0; k < OWN_G; ++k) {
@@ -1986,7 +1991,6 @@ __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
         for (;;) {
             if (threadIdx.x == 0) {
                 ctl.idx = atomicAdd(a.cursor + phase, 1u);
-                ctl.next = 0;
             }
             __syncthreads();
             const unsigned idx = ctl.idx;
@@ -2008,11 +2012,10 @@ __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
             for (int q0 = o.p0; q0 < o.p1; q0 += OWN_NT) {
                 if (phase == 0) owner_table(a, o, q0, G, tsb, txe, tpp, ctl);
                 else owner_table(a, o, q0, T, tsb, txe, tpp, ctl);
-                if (threadIdx.x == 0) ctl.next = 0;
                 __syncthreads();
                 const int ntask = ctl.ntask, total = ctl.total;
-                if (phase == 0) owner_units<false>(w, Q, a, o, G, st, ls, lm, tsb, txe, tpp, ntask, total, &ctl.next);
-                else owner_units<true>(w, Q, a, o, T, st, ls, lm, tsb, txe, tpp, ntask, total, &ctl.next);
+                if (phase == 0) owner_units<false>(w, Q, a, o, G, st, ls, lm, tsb, txe, tpp, ntask, total);
+                else owner_units<true>(w, Q, a, o, T, st, ls, lm, tsb, txe, tpp, ntask, total);
                 __syncthreads();
             }
         }
