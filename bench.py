@@ -161,32 +161,77 @@ def barrier(pg):
 
 # ------------------------------------------------------------ CPU oracle arm
 
-def oracle_sample_rate(arcs, seconds, threads=None):
-    """Run the oracle census on disjoint vertex ranges (ids are a random
-    permutation, so a range of low endpoints is a random sample of dyads) for
-    about `seconds` of wall time on `threads` host threads."""
+def vertex_costs(arcs):
+    """Merged entries (d_u + d_v summed over the canonical dyads <u,v>, u < v)
+    charged to each vertex as the dyads' lower endpoint: sample sizing only."""
+    n = arcs.n
+    s = arcs.src.astype(np.int64)
+    d = arcs.dst.astype(np.int64)
+    keep = s != d
+    u = np.minimum(s[keep], d[keep])
+    v = np.maximum(s[keep], d[keep])
+    key = np.unique(u * n + v)
+    u = key // n
+    v = key - u * n
+    deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
+    return np.bincount(u, weights=(deg[u] + deg[v]).astype(np.float64), minlength=n)
+
+
+def cost_ranges(cost, target, cap, rng):
+    """Consecutive vertex ranges of about `target` merged entries each (a
+    heavier vertex forms a range of its own), in random order; ranges above
+    `cap` are left out.  Returns [(a, b, entries)], and the number left out."""
+    cc = np.cumsum(cost)
+    cuts = np.unique(np.searchsorted(cc, np.arange(target, cc[-1], target), side="right"))
+    bounds = np.concatenate([[0], cuts[(cuts > 0) & (cuts < cost.size)], [cost.size]])
+    csum = np.concatenate([[0.0], cc])
+    out, skipped = [], 0
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        c = csum[b] - csum[a]
+        if c > cap:
+            skipped += 1
+        elif c > 0:
+            out.append((int(a), int(b), float(c)))
+    order = rng.permutation(len(out))
+    return [out[k] for k in order], skipped
+
+
+def oracle_sample_rate(arcs, seconds, threads=None, cost=None, seed=0):
+    """Run the oracle census on random disjoint vertex ranges (the dyads whose
+    lower endpoint lies in a range) on `threads` host threads, the ranges
+    chosen by their merged entries so that the run takes about `seconds` of
+    wall time.  A range whose entries one thread could not finish within that
+    time (a hub as lower endpoint) is left out."""
     import oracle
     threads = threads or os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    cost = vertex_costs(arcs) if cost is None else cost
     og = oracle.Graph(arcs.n, arcs.src, arcs.dst)
-    n = arcs.n
-    # calibrate on one small range
-    r0 = max(1, n // 20000)
-    t = time.perf_counter()
-    _, e0 = og.census_range(0, r0)
-    dt = max(time.perf_counter() - t, 1e-4)
-    per_vertex = dt / r0
-    total_vertices = int(min(n, max(threads, seconds * threads / per_vertex)))
-    step = max(1, total_vertices // (threads * 8))
-    ranges = [(a, min(a + step, total_vertices)) for a in range(r0, total_vertices, step)]
+    # calibrate the single-thread rate on ~0.25 s of small ranges
+    cal, _ = cost_ranges(cost, 2e5, 2e7, rng)
+    e_cal, t = 0, time.perf_counter()
+    for a, b, _ in cal:
+        e_cal += og.census_range(a, b)[1]
+        if time.perf_counter() - t > 0.25:
+            break
+    rate1 = max(e_cal, 1) / max(time.perf_counter() - t, 1e-4)
+    budget = seconds * threads * rate1
+    ranges, skipped = cost_ranges(cost, budget / (threads * 16), seconds * rate1, rng)
+    take, acc = [], 0.0
+    for r in ranges:
+        if acc >= budget:
+            break
+        take.append(r)
+        acc += r[2]
     lock = threading.Lock()
-    done = {"entries": e0, "vertices": r0}
+    done = {"entries": 0, "vertices": 0}
 
     def work():
         while True:
             with lock:
-                if not ranges:
+                if not take:
                     return
-                a, b = ranges.pop()
+                a, b, _ = take.pop()
             _, e = og.census_range(a, b)
             with lock:
                 done["entries"] += e
@@ -198,9 +243,9 @@ def oracle_sample_rate(arcs, seconds, threads=None):
         th.start()
     for th in pool:
         th.join()
-    wall = time.perf_counter() - t + dt
+    wall = time.perf_counter() - t
     og.close()
-    return done["entries"] / wall, threads, done["vertices"], done["entries"], wall
+    return done["entries"] / max(wall, 1e-9), threads, done["vertices"], done["entries"], wall, skipped
 
 
 def run_reference_batched(args, world):
@@ -257,15 +302,17 @@ def run_reference(args, world, rank, pg):
     threads = os.cpu_count() or 1
     per_step_s = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
     rates, walls = [], []
+    cost = vertex_costs(arcs)
     for i in range(args.warmup + args.steps):
-        rate, thr, verts, ents, wall = oracle_sample_rate(arcs, per_step_s, threads)
+        rate, thr, verts, ents, wall, skipped = oracle_sample_rate(arcs, per_step_s, threads, cost, seed=i)
         if i >= args.warmup:
             rates.append(rate)
             walls.append(wall)
     value = float(np.mean(rates))
-    sample = (f"oracle census of the canonical dyads whose lower endpoint lies in disjoint vertex "
-              f"ranges (~{per_step_s:.0f} s per step on {threads} host threads) of workload "
-              f"{args.workload}; rate = merged entries processed / wall time")
+    sample = (f"oracle census of the canonical dyads whose lower endpoint lies in random disjoint vertex "
+              f"ranges sized by their merged entries (~{per_step_s:.0f} s per step on {threads} host "
+              f"threads; ranges one thread could not finish in that time, {skipped} of them, left "
+              f"out) of workload {args.workload}; rate = merged entries processed / wall time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
@@ -427,11 +474,12 @@ def run_native(args, world, rank, local, pg):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, thr, verts, ents, wall = oracle_sample_rate(arcs, args.cpu_seconds)
+        rate, thr, verts, ents, wall, skipped = oracle_sample_rate(arcs, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"oracle census of the canonical dyads with lower endpoint in {verts} of "
-                         f"{arcs.n} vertices ({ents:.3e} merged entries, {wall:.1f} s on {thr} "
-                         f"host threads)"}
+                         f"{arcs.n} vertices, random ranges sized by merged entries ({ents:.3e} "
+                         f"merged entries, {wall:.1f} s on {thr} host threads; {skipped} ranges "
+                         f"too heavy for one thread in that time left out)"}
 
     if rank == 0:
         line = {
