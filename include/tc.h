@@ -57,6 +57,21 @@ typedef struct {
     uint64_t count003_hi;
 } tc_census_t;
 
+/* Census by the 64 labelled triad codes (the non-isomorphic census of Sec.
+ * 2.2: Fig. "Triad Code Algorithm" without its TriadTable step).  Code =
+ * e(u,v) + 2e(v,u) + 4e(u,w) + 8e(w,u) + 16e(v,w) + 32e(w,v), where <u,v>
+ * (u < v, adjacent) is the canonical dyad that counts the triad and w its
+ * third vertex: a connected triad is counted by the dyad for which w passes
+ * the canonical test of Fig. "Subquadratic Triad Census Algorithm"; a triad
+ * with a single adjacent pair u < v has code e(u,v) + 2e(v,u) (the dyadic
+ * term); code 0 is the null triad, C(n,3) minus all others, 128-bit like
+ * tc_census_t (count[0] low, count0_hi high 64 bits).  Mapping the codes by
+ * the isomorphism table gives tc_census_t. */
+typedef struct {
+    uint64_t count[64];
+    uint64_t count0_hi;
+} tc_census64_t;
+
 /* Statistics of a built graph (per graph of a batched build). */
 typedef struct {
     int64_t n;              /* vertices */
@@ -214,6 +229,15 @@ tc_status tc_census(tc_graph g, const tc_opts* opts, tc_census_t* out, uint32_t 
  */
 tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts,
                             tc_census_t* out, uint32_t flags, void* stream);
+
+/*
+ * tc_census_codes / tc_census_codes_batched -- the 64-code census of one
+ * graph, or of G graphs of one build (out[i] for gs[i]); arguments, memory
+ * and errors as tc_census / tc_census_batched.
+ */
+tc_status tc_census_codes(tc_graph g, const tc_opts* opts, tc_census64_t* out, uint32_t flags, void* stream);
+tc_status tc_census_codes_batched(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_census64_t* out,
+                                  uint32_t flags, void* stream);
 
 /*
  * tc_census_csr_noalloc -- the census of a graph the caller already holds in

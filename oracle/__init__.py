@@ -58,6 +58,9 @@ def _get():
         lib.oracle_census_range.argtypes = [P, i32, i32, P, P]
         lib.oracle_census_range.restype = u64
         lib.oracle_census.argtypes = [P, i32, P, P]
+        lib.oracle_brute_codes.argtypes = [i32, i64, P, P, P]
+        lib.oracle_brute_codes.restype = ctypes.c_int
+        lib.oracle_census_codes.argtypes = [P, P, P]
         _lib = lib
     return _lib
 
@@ -87,6 +90,19 @@ def brute_census(n: int, src, dst) -> list[int]:
     out = np.zeros(16, dtype=np.uint64)
     if _get().oracle_brute(int(n), s.size, _p(s), _p(d), _p(out)) != 0:
         raise ValueError("oracle_brute: bad arguments")
+    return [int(x) for x in out]
+
+
+def brute_census_codes(n: int, src, dst) -> list[int]:
+    """O(n^3) 64-code census by definition (n <= 4096); raises if some triple
+    is not counted exactly once."""
+    s, d = _arcs(src, dst)
+    out = np.zeros(64, dtype=np.uint64)
+    r = _get().oracle_brute_codes(int(n), s.size, _p(s), _p(d), _p(out))
+    if r == -2:
+        raise AssertionError("oracle_brute_codes: a triple is not counted exactly once")
+    if r != 0:
+        raise ValueError("oracle_brute_codes: bad arguments")
     return [int(x) for x in out]
 
 
@@ -129,6 +145,13 @@ class Graph:
         _get().oracle_census(self._h, int(threads), _p(lo), _p(hi))
         return _join(lo, hi)
 
+    def census_codes(self) -> list[int]:
+        """64-code census (Fig. "Triad Code Algorithm" without TriadTable)."""
+        lo = np.zeros(64, dtype=np.uint64)
+        hi = np.zeros(64, dtype=np.uint64)
+        _get().oracle_census_codes(self._h, _p(lo), _p(hi))
+        return _join(lo, hi)
+
     def census_range(self, u_begin: int, u_end: int):
         """Types 1..15 from canonical dyads with u in [u_begin, u_end) (no 003
         closure); returns (counts, merged entries processed)."""
@@ -142,6 +165,14 @@ def census(n: int, src, dst, threads: int = 1) -> list[int]:
     g = Graph(n, src, dst)
     try:
         return g.census(threads)
+    finally:
+        g.close()
+
+
+def census_codes(n: int, src, dst) -> list[int]:
+    g = Graph(n, src, dst)
+    try:
+        return g.census_codes()
     finally:
         g.close()
 

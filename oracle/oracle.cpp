@@ -14,6 +14,9 @@
  *                       naming rules of Sec. 2.2 (the thesis does not print
  *                       the table; its figure of the 16 types is lost).
  *   oracle_brute        O(n^3) definition: classify every vertex triple.
+ *   oracle_brute_codes  O(n^3) 64-code census: each triple given to the dyad
+ *                       and third vertex that count it (canonical test).
+ *   oracle_census_codes the 64-code (non-isomorphic) census of the same loop.
  *   oracle_census_*     the algorithm of Sec. 2.2, Fig. "Subquadratic Triad
  *                       Census Algorithm", with the v0.4 pre-computed dyad part
  *                       of Sec. 4.2.4 (Fig. "Modified TriadCode Algorithm").
@@ -220,6 +223,40 @@ uint64_t census_range(const OGraph& g, int32_t ub, int32_t ue, u128 cnt[16]) {
     return entries;
 }
 
+/* The same loop in the non-isomorphic mode of Fig. "Triad Code Algorithm"
+ * (the code itself, no TriadTable): the dyadic term goes to code pre (a
+ * triad whose only arcs join u and v), every counted w to its 6-bit code.
+ * Adds into c[64] (index 0 untouched). */
+void census_codes_range(const OGraph& g, int32_t ub, int32_t ue, u128 c[64]) {
+    const int64_t n = g.n;
+    std::vector<int32_t> S;
+    for (int32_t u = ub; u < ue; ++u) {
+        auto nu_b = g.nbr.begin() + g.nptr[u], nu_e = g.nbr.begin() + g.nptr[u + 1];
+        for (auto it = nu_b; it != nu_e; ++it) {
+            const int32_t v = *it;
+            if (!(u < v)) continue;                         /* canonical dyad */
+            auto nv_b = g.nbr.begin() + g.nptr[v], nv_e = g.nbr.begin() + g.nptr[v + 1];
+            S.clear();
+            std::set_union(nu_b, nu_e, nv_b, nv_e, std::back_inserter(S));
+            S.erase(std::remove_if(S.begin(), S.end(),
+                                   [&](int32_t x) { return x == u || x == v; }),
+                    S.end());
+            const int pre = (is_edge(g, u, v) ? 1 : 0) + 2 * (is_edge(g, v, u) ? 1 : 0);
+            c[pre] += (u128)(uint64_t)(n - (int64_t)S.size() - 2);
+            for (int32_t w : S) {
+                if (v < w || (w < v && u < w && !is_neighbour(g, u, w))) {
+                    int code = pre;
+                    code += 4 * (is_edge(g, u, w) ? 1 : 0);
+                    code += 8 * (is_edge(g, w, u) ? 1 : 0);
+                    code += 16 * (is_edge(g, v, w) ? 1 : 0);
+                    code += 32 * (is_edge(g, w, v) ? 1 : 0);
+                    c[code] += 1;
+                }
+            }
+        }
+    }
+}
+
 void close_null(int64_t n, u128 cnt[16]) {
     u128 sum = 0;
     for (int t = 1; t < 16; ++t) sum += cnt[t];
@@ -262,6 +299,51 @@ int oracle_brute(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                 int code = e(i, j) + 2 * e(j, i) + 4 * e(i, k) + 8 * e(k, i) +
                            16 * e(j, k) + 32 * e(k, j);
                 out[T[code]]++;
+            }
+    return 0;
+}
+
+/* O(n^3) 64-code census by definition: every triple i<j<k is given to the
+ * canonical dyad <u,v> (u < v adjacent) and third vertex w that count it --
+ * the only adjacent pair when w is isolated from both (code pre), else the
+ * pair for which w passes the canonical test v < w or (u < w < v and w not
+ * a neighbour of u) -- and its code is taken with that labelling; a triple
+ * without arcs has code 0.  Returns 0, -1 on bad arguments (n > 4096, id out
+ * of range), -2 if some triple is counted other than exactly once. */
+int oracle_brute_codes(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, uint64_t out[64]) {
+    if (n < 0 || n > 4096 || m < 0) return -1;
+    std::vector<uint8_t> adj((size_t)n * (size_t)n, 0);
+    for (int64_t i = 0; i < m; ++i) {
+        int32_t s = src[i], d = dst[i];
+        if (s < 0 || s >= n || d < 0 || d >= n) return -1;
+        if (s != d) adj[(size_t)s * n + d] = 1;
+    }
+    auto e = [&](int a, int b) { return (int)adj[(size_t)a * n + b]; };
+    auto nb = [&](int a, int b) { return e(a, b) || e(b, a); };
+    for (int t = 0; t < 64; ++t) out[t] = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            for (int k = j + 1; k < n; ++k) {
+                const int uvw[3][3] = {{i, j, k}, {i, k, j}, {j, k, i}};
+                int counted = 0, any = 0;
+                for (const auto& t : uvw) {
+                    const int u = t[0], v = t[1], w = t[2];
+                    if (!nb(u, v)) continue;
+                    any = 1;
+                    const int pre = e(u, v) + 2 * e(v, u);
+                    if (!nb(u, w) && !nb(v, w)) {
+                        out[pre]++;
+                        ++counted;
+                    } else if (v < w || (u < w && w < v && !nb(u, w))) {
+                        out[pre + 4 * e(u, w) + 8 * e(w, u) + 16 * e(v, w) + 32 * e(w, v)]++;
+                        ++counted;
+                    }
+                }
+                if (!any) {
+                    out[0]++;
+                    ++counted;
+                }
+                if (counted != 1) return -2;
             }
     return 0;
 }
@@ -375,6 +457,21 @@ void oracle_census(const void* gp, int32_t threads, uint64_t lo[16], uint64_t hi
         for (int k = 0; k < 16; ++k) cnt[k] += local[(size_t)t][k];
     close_null(g.n, cnt);
     store(cnt, lo, hi);
+}
+
+/* 64-code census (sequential), 128-bit per code; code 0 = C(n,3) minus all
+ * others. */
+void oracle_census_codes(const void* gp, uint64_t lo[64], uint64_t hi[64]) {
+    const OGraph& g = *(const OGraph*)gp;
+    u128 c[64] = {0};
+    census_codes_range(g, 0, g.n, c);
+    u128 sum = 0;
+    for (int t = 1; t < 64; ++t) sum += c[t];
+    c[0] = choose3(g.n) - sum;
+    for (int t = 0; t < 64; ++t) {
+        lo[t] = (uint64_t)c[t];
+        hi[t] = (uint64_t)(c[t] >> 64);
+    }
 }
 
 } // extern "C"

@@ -5,14 +5,16 @@ step of the census runs in the library's CUDA kernels.  Entry points keep the
 C names:
 
     tc_graph_build, tc_graph_build_batched, tc_graph_stats, tc_graph_export,
-    tc_census, tc_census_batched, tc_graph_free, tc_opts_default,
+    tc_census, tc_census_batched, tc_census_codes, tc_census_codes_batched,
+    tc_graph_free, tc_opts_default,
     tc_triad_type, tc_status_str, tc_last_error
 
 Host inputs are numpy arrays (or anything ``np.asarray`` accepts); device
 inputs are CUDA torch tensors (their ``data_ptr`` is passed with the
 TC_DEVICE_PTRS flag).  Census results come back as lists of 16 Python ints in
 MAN order (003 012 102 021D 021U 021C 111D 111U 030T 030C 201 120D 120U 120C
-210 300), the 003 count rebuilt from its two 64-bit halves.
+210 300), the 003 count rebuilt from its two 64-bit halves; the 64-code
+census (tc_census_codes) as lists of 64 ints indexed by the labelled code.
 
 There is no CPU fallback: if ``libtc.so`` is missing, ``load()`` raises.
 """
@@ -39,7 +41,7 @@ EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_gr
            "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile",
            "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free", "tc_autotune",
            "tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
-           "tc_cost_model_load")
+           "tc_cost_model_load", "tc_census_codes", "tc_census_codes_batched")
 TC_MLP_NPARAM = 1476
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
@@ -51,6 +53,15 @@ class TcCensus(ctypes.Structure):
     def to_list(self) -> list[int]:
         c = [int(x) for x in self.count]
         c[0] |= int(self.count003_hi) << 64
+        return c
+
+
+class TcCensus64(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64 * 64), ("count0_hi", ctypes.c_uint64)]
+
+    def to_list(self) -> list[int]:
+        c = [int(x) for x in self.count]
+        c[0] |= int(self.count0_hi) << 64
         return c
 
 
@@ -117,6 +128,8 @@ def load():
     lib.tc_graph_export.argtypes = [P, P, P]
     lib.tc_census.argtypes = [P, P, P, u32, P]
     lib.tc_census_batched.argtypes = [i32, P, P, P, u32, P]
+    lib.tc_census_codes.argtypes = [P, P, P, u32, P]
+    lib.tc_census_codes_batched.argtypes = [i32, P, P, P, u32, P]
     lib.tc_triad_type.argtypes = [ctypes.c_int]
     lib.tc_triad_type.restype = ctypes.c_int
     lib.tc_census_profile.argtypes = [P]
@@ -147,7 +160,8 @@ def load():
     lib.tc_last_error.argtypes = []
     lib.tc_last_error.restype = ctypes.c_char_p
     for name in ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
-                 "tc_graph_export", "tc_census", "tc_census_batched"):
+                 "tc_graph_export", "tc_census", "tc_census_batched", "tc_census_codes",
+                 "tc_census_codes_batched"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -279,6 +293,32 @@ def tc_census_batched(gs, opts: TcOpts | None = None, out=None, stream=None):
     _check(lib.tc_census_batched(G, arr, po, out.data_ptr(), TC_OUT_DEVICE, _stream(stream)),
            "tc_census_batched")
     return out
+
+
+def tc_census_codes(g: int, opts: TcOpts | None = None, out=None, stream=None):
+    """64-code census of one graph.  Without `out`: host result, a list of 64
+    ints (index = labelled code).  With `out` (a CUDA tensor of >= 65 int64):
+    asynchronous device result."""
+    lib = load()
+    po = ctypes.byref(opts) if opts is not None else None
+    if out is None:
+        c = TcCensus64()
+        _check(lib.tc_census_codes(g, po, ctypes.byref(c), 0, _stream(stream)), "tc_census_codes")
+        return c.to_list()
+    _check(lib.tc_census_codes(g, po, out.data_ptr(), TC_OUT_DEVICE, _stream(stream)), "tc_census_codes")
+    return out
+
+
+def tc_census_codes_batched(gs, opts: TcOpts | None = None, stream=None):
+    """64-code censuses of graphs `gs` (handles of one batched build), host
+    result: one list of 64 ints per graph."""
+    lib = load()
+    G = len(gs)
+    arr = (ctypes.c_void_p * max(G, 1))(*gs)
+    po = ctypes.byref(opts) if opts is not None else None
+    res = (TcCensus64 * max(G, 1))()
+    _check(lib.tc_census_codes_batched(G, arr, po, res, 0, _stream(stream)), "tc_census_codes_batched")
+    return [res[i].to_list() for i in range(G)]
 
 
 def tc_census_profile() -> dict:

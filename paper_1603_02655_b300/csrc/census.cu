@@ -209,12 +209,12 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
 
     int s = -1;
     int64_t rb = 0, n = 0, sp = 0;
-    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN], Os[4] = {0, 0, 0, 0};
+    unsigned long long Aa[3][3], Bb[3][3], Dd[3], Ee[NBIN], Os[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int q = 0; q < 3; ++q) Aa[p][q] = Bb[p][q] = 0;
-    Dd[0] = Dd[1] = 0;
+    Dd[0] = Dd[1] = Dd[2] = 0;
 #pragma unroll
     for (int b = 0; b < NBIN; ++b) Ee[b] = 0;
 
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                 Aa[p][q] = Bb[p][q] = 0;
             }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < 3; ++q) {
             unsigned long long d = warp_sum64(Dd[q]);
             if (lane == 0 && s >= 0 && d) atomicAdd(acc + (size_t)s * ACC + 64 + q, d);
             Dd[q] = 0;
@@ -308,8 +308,8 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                     const int dv = deg[rb + y];
                     L = d + dv;
                     const unsigned long long dy = (unsigned long long)(n - (int64_t)d - (int64_t)dv);
-                    Dd[0] += pre_task == 3 ? 0ull : dy;
-                    Dd[1] += pre_task == 3 ? dy : 0ull;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) Dd[q] += pre_task == q + 1 ? dy : 0ull;
                     const int dh = max(d, dv);
                     if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
                         Os[0] += 1;
@@ -408,7 +408,7 @@ __global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __re
 // in another graph than the warp's accumulators add directly.
 constexpr int FLAT_RUN = 2048;
 
-__global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(256, 3) k_tasks_flat(const int64_t* __restrict__ row_ptr,
                                                     const uint32_t* __restrict__ adj,
                                                     const int32_t* __restrict__ arow,
                                                     const int32_t* __restrict__ deg,
@@ -423,12 +423,12 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
     const unsigned full = 0xffffffffu;
     const unsigned below = (1u << lane) - 1u;
     int s = -1;  // graph of the warp's accumulators
-    unsigned long long Aa[3][3], Bb[3][3], Dd[2], Ee[NBIN], Os[2] = {0, 0};
+    unsigned long long Aa[3][3], Bb[3][3], Dd[3], Ee[NBIN], Os[2] = {0, 0};
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int q = 0; q < 3; ++q) Aa[p][q] = Bb[p][q] = 0;
-    Dd[0] = Dd[1] = 0;
+    Dd[0] = Dd[1] = Dd[2] = 0;
 #pragma unroll
     for (int b = 0; b < NBIN; ++b) Ee[b] = 0;
     auto flush = [&]() {
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
                 Aa[p][q] = Bb[p][q] = 0;
             }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < 3; ++q) {
             const unsigned long long d = warp_sum64(Dd[q]);
             if (lane == 0 && s >= 0 && d) atomicAdd(acc + (size_t)s * ACC + 64 + q, d);
             Dd[q] = 0;
@@ -519,8 +519,8 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
                     Bb[p][1] += tb ? S2 : 0u;
                     Bb[p][2] += tb ? S3 : 0u;
                 }
-                Dd[0] += pre_task == 3 ? 0ull : dy;
-                Dd[1] += pre_task == 3 ? dy : 0ull;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Dd[q] += (is_task && pre_task == q + 1) ? dy : 0ull;
             } else if (valid && (is_task || is_twin)) {  // an entry of a later graph: add directly
                 unsigned long long* h = acc + (size_t)ls * ACC;
                 const int p = (is_task ? pre_task : pre_twin) - 1;
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(256) k_tasks_flat(const int64_t* __restrict__ 
                 if (S1) atomicAdd(h + (p + 1) + sh4 * 1, (unsigned long long)S1);
                 if (S2) atomicAdd(h + (p + 1) + sh4 * 2, (unsigned long long)S2);
                 if (S3) atomicAdd(h + (p + 1) + sh4 * 3, (unsigned long long)S3);
-                if (dy) atomicAdd(h + 64 + (pre_task == 3 ? 1 : 0), dy);
+                if (dy) atomicAdd(h + 63 + pre_task, dy);
             }
 #pragma unroll
             for (int b = 0; b < NBIN; ++b) Ee[b] += bin == b ? (unsigned long long)L : 0ull;
@@ -1449,7 +1449,7 @@ __global__ void __launch_bounds__(CTA_NT) k_cta(const int64_t* __restrict__ row_
 // ---------------------------------------------------------------- k_fold --
 // 64 codes -> 16 MAN types; 003 = C(n,3) - the rest, in 128-bit (Sec. 2.2).
 __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev* __restrict__ seg, int nseg,
-                       tc_census_t* __restrict__ out) {
+                       tc_census_t* __restrict__ out, tc_census64_t* __restrict__ codes) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     const unsigned long long* h = acc + (size_t)s * ACC;
@@ -1457,14 +1457,14 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
 #pragma unroll
     for (int t = 0; t < 16; ++t) cnt[t] = 0;
     for (int code = 0; code < 64; ++code) cnt[triad_type(code)] += h[code];
-    // Slots 64/65 hold sum (n - |N(u)| - |N(v)|) over asymmetric / mutual
-    // dyads; the dyadic term n - |S| - 2 adds c_uv = |N(u) n N(v)| per dyad.
-    // A triad whose three pairs are all adjacent adds 1 to c_uv of each of
-    // its dyads, so sum_asym c_uv = 3(030T + 030C) + 2(120D + 120U + 120C)
-    // + 210 and sum_mutual c_uv = (120D + 120U + 120C) + 2 * 210 + 3 * 300.
+    // Slots 64..66 hold sum (n - |N(u)| - |N(v)|) over the dyads with
+    // pre = 1, 2, 3; the dyadic term n - |S| - 2 adds c_uv = |N(u) n N(v)|
+    // per dyad.  A triad whose three pairs are all adjacent adds 1 to c_uv of
+    // each of its dyads, so sum_asym c_uv = 3(030T + 030C) + 2(120D + 120U +
+    // 120C) + 210 and sum_mutual c_uv = (120D + 120U + 120C) + 2 * 210 + 3 * 300.
     const unsigned long long c120 = cnt[11] + cnt[12] + cnt[13];
-    cnt[1] += h[64] + 3 * (cnt[8] + cnt[9]) + 2 * c120 + cnt[14];
-    cnt[2] += h[65] + c120 + 2 * cnt[14] + 3 * cnt[15];
+    cnt[1] += h[64] + h[65] + 3 * (cnt[8] + cnt[9]) + 2 * c120 + cnt[14];
+    cnt[2] += h[66] + c120 + 2 * cnt[14] + 3 * cnt[15];
     const unsigned __int128 n = (unsigned __int128)(unsigned long long)seg[s].n;
     unsigned __int128 all = n >= 3 ? n * (n - 1) * (n - 2) / 6 : 0;
     for (int t = 1; t < 16; ++t) all -= cnt[t];
@@ -1473,6 +1473,27 @@ __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev*
     o.count003_hi = (uint64_t)(all >> 64);
     for (int t = 1; t < 16; ++t) o.count[t] = cnt[t];
     out[seg[s].slot] = o;
+    if (codes) {
+        // the 64 labelled codes (Fig. "Triad Code Algorithm" without the
+        // TriadTable step): a connected triad keeps the code of the dyad that
+        // counts it; a triad with one adjacent pair has code pre, counted by
+        // the dyadic term.  Its c_uv share per pre value: a closed triad is
+        // counted with u < v < w, so its three dyads, in canonical order, have
+        // pre values pre, t_u(w), t_v(w).
+        tc_census64_t c;
+        unsigned long long dy[3] = {h[64], h[65], h[66]};
+        for (int code = 0; code < 64; ++code) {
+            c.count[code] = h[code];
+            const int p = code & 3, tu = (code >> 2) & 3, tv = (code >> 4) & 3;
+            if (tu && tv)
+                for (int q = 1; q <= 3; ++q)
+                    dy[q - 1] += h[code] * (unsigned long long)((p == q) + (tu == q) + (tv == q));
+        }
+        for (int q = 1; q <= 3; ++q) c.count[q] += dy[q - 1];
+        c.count[0] = (uint64_t)all;
+        c.count0_hi = (uint64_t)(all >> 64);
+        codes[seg[s].slot] = c;
+    }
 }
 
 // ---------------------------------------------------------------- owners --
@@ -2079,7 +2100,7 @@ struct Layout {
     bool flat = false;          // per-entry task terms (k_tasks_flat)
     int64_t entries = 0;
     size_t scan_bytes = 0;      // CUB scan temporary storage
-    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, o_epfx,
+    size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_codes, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, o_epfx,
         o_scan, o_scantmp, need;
     uint32_t own_cap = 0;
 };
@@ -2145,6 +2166,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.o_seg = take(sizeof(SegDev) * (size_t)nseg);
     Lo.o_pfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
     Lo.o_out = take(sizeof(tc_census_t) * (size_t)nseg);
+    Lo.o_codes = take(sizeof(tc_census64_t) * (size_t)nseg);
     for (int b = 0; b < NBIN; ++b) Lo.o_r[b] = take(sizeof(uint4) * Lo.cap01);
     Lo.o_rt = o.bin_mode == TC_BIN_MLP ? take(sizeof(uint4) * Lo.cap01) : Lo.o_r[2];
     Lo.o_tl = take(sizeof(uint4) * Lo.cap2);
@@ -2186,7 +2208,7 @@ tc_status upload_layout(const Layout& Lo, char* ws, cudaStream_t st) {
 
 // The census itself: one memset and the kernels, all on `st` (capturable).
 tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_census_t* d_out, cudaStream_t st,
-                         ProfileEvents* pe, const Instr* ins = nullptr) {
+                         ProfileEvents* pe, const Instr* ins = nullptr, tc_census64_t* d_codes = nullptr) {
     const tc_opts& o = Lo.o;
     unsigned long long* acc = (unsigned long long*)(ws + Lo.o_acc);
     unsigned int* ctr = (unsigned int*)(ws + Lo.o_ctr);
@@ -2330,7 +2352,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         for (int k = 1; k <= 6; ++k) mark(k);
     }
     mark(7);
-    k_fold<<<(Lo.nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, Lo.nseg, d_out);
+    k_fold<<<(Lo.nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, Lo.nseg, d_out, d_codes);
     TC_CUDA(cudaGetLastError());
     mark(8);
     return TC_OK;
@@ -2388,8 +2410,11 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     return TC_OK;
 }
 
+// out and/or codes (either may be null): one record per graph, host memory
+// or, with TC_OUT_DEVICE, device memory.
 tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
-                      tc_census_t* out, uint32_t flags, cudaStream_t st, const Instr* ins = nullptr) {
+                      tc_census_t* out, uint32_t flags, cudaStream_t st, const Instr* ins = nullptr,
+                      tc_census64_t* codes = nullptr) {
     if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
     Layout Lo;
     if (tc_status s = make_layout(set, gidx, opts_in, Lo); s != TC_OK) return s;
@@ -2401,19 +2426,25 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         set.ws_bytes = Lo.need;
     }
     char* ws = (char*)set.ws;
-    tc_census_t* d_out = (flags & TC_OUT_DEVICE) ? out : (tc_census_t*)(ws + Lo.o_out);
+    const bool dev = (flags & TC_OUT_DEVICE) != 0;
+    tc_census_t* d_out = dev && out ? out : (tc_census_t*)(ws + Lo.o_out);
+    tc_census64_t* d_codes = !codes ? nullptr : dev ? codes : (tc_census64_t*)(ws + Lo.o_codes);
     ProfileEvents* pe = nullptr;
     if (Lo.o.profile) {
         if (tc_status s = profile_events(&pe); s != TC_OK) return s;
     }
     if (tc_status s = upload_layout(Lo, ws, st); s != TC_OK) return s;
-    if (tc_status s = enqueue_census(set, Lo, ws, d_out, st, pe, ins); s != TC_OK) return s;
+    if (tc_status s = enqueue_census(set, Lo, ws, d_out, st, pe, ins, d_codes); s != TC_OK) return s;
     if (pe) {
         if (tc_status s = read_profile(Lo, ws, pe, st); s != TC_OK) return s;
     }
-    if (!(flags & TC_OUT_DEVICE)) {
+    if (!dev) {
         int ovf = 0;
-        TC_CUDA(cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * (size_t)Lo.nseg, cudaMemcpyDeviceToHost, st));
+        if (out)
+            TC_CUDA(cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * (size_t)Lo.nseg, cudaMemcpyDeviceToHost, st));
+        if (codes)
+            TC_CUDA(cudaMemcpyAsync(codes, d_codes, sizeof(tc_census64_t) * (size_t)Lo.nseg, cudaMemcpyDeviceToHost,
+                                    st));
         TC_CUDA(cudaMemcpyAsync(&ovf, ws + Lo.o_ctr + 4 * sizeof(unsigned int), sizeof(int),
                                 cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
@@ -2475,6 +2506,33 @@ tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts, 
         return tc::fail(TC_ERR_OOM, "tc_census_batched: host allocation failed");
     } catch (...) {
         return tc::fail(TC_ERR_CUDA, "tc_census_batched: unexpected exception");
+    }
+}
+
+tc_status tc_census_codes(tc_graph g, const tc_opts* opts, tc_census64_t* out, uint32_t flags, void* stream) {
+    if (!g || !out) return tc::fail(TC_ERR_ARG, "tc_census_codes: null argument");
+    try {
+        std::vector<int32_t> idx{g->index};
+        return tc::census_impl(*g->set, idx, opts, nullptr, flags, (cudaStream_t)stream, nullptr, out);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_census_codes: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_census_codes: unexpected exception");
+    }
+}
+
+tc_status tc_census_codes_batched(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_census64_t* out,
+                                  uint32_t flags, void* stream) {
+    if (G < 0 || (G > 0 && (!gs || !out))) return tc::fail(TC_ERR_ARG, "tc_census_codes_batched: bad arguments");
+    if (G == 0) return TC_OK;
+    try {
+        if (tc_status s = tc::check_handles(G, gs, "tc_census_codes_batched"); s != TC_OK) return s;
+        return tc::census_impl(*gs[0]->set, tc::handle_indices(G, gs), opts, nullptr, flags, (cudaStream_t)stream,
+                               nullptr, out);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_census_codes_batched: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_census_codes_batched: unexpected exception");
     }
 }
 
@@ -2581,7 +2639,7 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
                                                         bins.cap[0], s->acc);
         TC_CUDA(cudaGetLastError());
     }
-    k_fold<<<1, 128, 0, st>>>(s->acc, &s->seg, 1, out);
+    k_fold<<<1, 128, 0, st>>>(s->acc, &s->seg, 1, out, nullptr);
     TC_CUDA(cudaGetLastError());
     int ovf = 0;
     TC_CUDA(cudaMemcpyAsync(&ovf, s->ctr + 4, sizeof(int), cudaMemcpyDeviceToHost, st));

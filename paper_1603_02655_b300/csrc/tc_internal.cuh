@@ -18,8 +18,9 @@ constexpr uint32_t SENT = 0xFFFFFFFFu;
 // Sentinel words stored after the adjacency array so that vector loads of a
 // merge window may run past the last row.
 constexpr int64_t ADJ_PAD = 8192;
-// Accumulator slots per graph: 64 triad codes + dyadic 012 + dyadic 102.
-constexpr int ACC = 66;
+// Accumulator slots per graph: 64 triad codes, then the dyadic sums
+// n - |N(u)| - |N(v)| over the dyads with pre = 1, 2, 3 (slots 64, 65, 66).
+constexpr int ACC = 67;
 
 // ---------------------------------------------------------------- errors --
 tc_status fail(tc_status s, const std::string& msg);

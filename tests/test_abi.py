@@ -57,6 +57,9 @@ def test_argument_errors_need_no_device(lib):
     assert lib.tc_census(None, None, None, 0, None) == tc.TC_ERR_ARG
     assert lib.tc_census_batched(-1, None, None, None, 0, None) == tc.TC_ERR_ARG
     assert lib.tc_census_batched(0, None, None, None, 0, None) == tc.TC_OK
+    assert lib.tc_census_codes(None, None, None, 0, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_codes_batched(-1, None, None, None, 0, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_codes_batched(0, None, None, None, 0, None) == tc.TC_OK
     assert lib.tc_graph_stats(None, None) == tc.TC_ERR_ARG
     assert lib.tc_opts_default(None) == tc.TC_ERR_ARG
     assert "null" in tc.tc_last_error() or tc.tc_last_error()

@@ -134,6 +134,50 @@ def test_all_4096_four_vertex_digraphs_batched():
             tc.tc_graph_free(g)
 
 
+def fold(codes):
+    T = oracle.triad_table()
+    out = [0] * 16
+    for c, k in enumerate(codes):
+        out[T[c]] += k
+    return out
+
+
+def test_codes_match_oracle():
+    rng = np.random.default_rng(21)
+    graphs = [(40, *rand_graph(rng, 40, 0.15, 0.3)), (300, *rand_graph(rng, 300, 0.03, 0.5)),
+              (3000, *hub_graph(rng, 3000, 3, 900, 20000, 0.2))]
+    for n, src, dst in graphs:
+        want = oracle.census_codes(n, src, dst)
+        g = tc.tc_graph_build(n, src, dst)
+        try:
+            for name in ("default", "owner_all", "no_owner", "row_tasks", "cta", "stream_all"):
+                got = tc.tc_census_codes(g, opts(name))
+                assert got == want, (n, name)
+                assert fold(got) == tc.tc_census(g, opts(name)), (n, name)
+        finally:
+            tc.tc_graph_free(g)
+
+
+def test_codes_batched_all_64_triads():
+    bits = {(0, 1): 1, (1, 0): 2, (0, 2): 4, (2, 0): 8, (1, 2): 16, (2, 1): 32}
+    src, dst, off, want = [], [], [0], []
+    for c in range(64):
+        arcs = [ab for ab, b in bits.items() if c & b]
+        s = [a for a, _ in arcs]
+        d = [b for _, b in arcs]
+        src += s
+        dst += d
+        off.append(len(src))
+        want.append(oracle.brute_census_codes(3, s, d))
+    gs = tc.tc_graph_build_batched([3] * 64, off, src, dst)
+    try:
+        for name in ("default", "owner_all", "thread"):
+            assert tc.tc_census_codes_batched(gs, opts(name)) == want, name
+    finally:
+        for g in gs:
+            tc.tc_graph_free(g)
+
+
 # ------------------------------------------------------------ random graphs
 
 @pytest.mark.parametrize("seed", range(6))
@@ -236,6 +280,35 @@ def test_owner_staging_boundary():
     src, dst = np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32)
     want = oracle.census(n, src, dst, threads=THREADS)
     for own_min in (1, 128, 513):
+        c, p = owner_profile(n, src, dst, own_min=own_min)
+        assert c == want, own_min
+        assert p["owner_tasks"] > 0
+
+
+def test_owner_structured_ids():
+    # owners whose neighbour ids share their low bits (stride 64: every key in
+    # few id buckets) or are consecutive, joined to one another, plus owners
+    # of 1 to 4 entries
+    rng = np.random.default_rng(17)
+    n = 70_000
+    strided = np.arange(64, 64 * 1000, 64)
+    run = np.arange(60_000, 63_000)
+    src = [np.zeros(strided.size, np.int64), np.full(run.size, 1)]
+    dst = [strided, run]
+    for hub, nb in ((0, run[::3]), (1, strided[::2])):  # shared neighbours
+        src.append(np.full(nb.size, hub))
+        dst.append(nb)
+    src.append([0, 5, 6, 7, 7, 9, 9, 9])
+    dst.append([1, 6, 7, 5, 8, 10, 11, 12])
+    src.append(rng.integers(2, n, 30_000))
+    dst.append(rng.integers(2, n, 30_000))
+    src, dst = np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    flip = rng.random(src.size) < 0.3
+    src, dst = np.where(flip, dst, src), np.where(flip, src, dst)
+    want = oracle.census(n, src, dst, threads=THREADS)
+    for own_min in (1, 128):
         c, p = owner_profile(n, src, dst, own_min=own_min)
         assert c == want, own_min
         assert p["owner_tasks"] > 0

@@ -7,6 +7,7 @@ import os
 
 import pytest
 
+import oracle
 import synth
 import paper_1603_02655_b300 as tc
 from paper_1603_02655_b300 import build as tcbuild
@@ -49,6 +50,15 @@ def test_single_graph_workloads_match_oracle(name):
             torch.cuda.synchronize()
             assert tc.census_from_device_words(out.cpu().tolist()) == c
         assert tc.tc_census(g) == c  # host output path
+        # the 64-code census maps onto the golden 16-type census, and the
+        # connected codes agree between the owner and merge-only paths
+        T = oracle.triad_table()
+        codes = tc.tc_census_codes(g)
+        folded = [0] * 16
+        for code, k in enumerate(codes):
+            folded[T[code]] += k
+        assert folded == c
+        assert tc.tc_census_codes(g, tc.tc_opts_default(own_min=0)) == codes
     finally:
         tc.tc_graph_free(g)
 

@@ -294,3 +294,74 @@ def test_gnp_counts_match_expectation():
         tol = 18 * math.sqrt(exp[t]) + 0.02 * exp[t] + 5
         assert abs(c[t] - exp[t]) <= tol, (NAMES[t], c[t], exp[t])
     check_invariants(a.n, a.src, a.dst, c)
+
+
+# ------------------------------------------------------ 64-code census (f1)
+
+def fold(codes):
+    T = oracle.triad_table()
+    out = [0] * 16
+    for c, k in enumerate(codes):
+        out[T[c]] += k
+    return out
+
+
+def one_hot(n, **codes):
+    out = [0] * 64
+    for c, k in codes.items():
+        out[int(c[1:])] = k
+    return out
+
+
+def test_codes_hand_cases():
+    # worked by hand from Fig. "Triad Code Algorithm" and the canonical test
+    cases = [
+        # path 0->1->2: <0,1> with w = 2 > v counts it: 1 + 16 e(1,2) = 17
+        (3, [(0, 1), (1, 2)], dict(c17=1)),
+        # single arc: the dyadic term of <1,2>, code pre
+        (3, [(1, 2)], dict(c1=1)),
+        (3, [(2, 1)], dict(c2=1)),
+        (3, [(0, 1), (1, 0)], dict(c3=1)),
+        # transitive triangle: <0,1> with w = 2: 1 + 4 e(0,2) + 16 e(1,2) = 21
+        (3, [(0, 1), (1, 2), (0, 2)], dict(c21=1)),
+        # 0->2->1: <0,2> with w = 1 (0 < 1 < 2, 1 not a neighbour of 0):
+        # pre 1 + 16 e(2,1) = 17; <1,2> with w = 0 < u does not count
+        (3, [(0, 2), (2, 1)], dict(c17=1)),
+        # one arc among four vertices: two dyadic triads, two null ones
+        (4, [(0, 1)], dict(c0=2, c1=2)),
+    ]
+    for n, arcs, want in cases:
+        src = np.array([a for a, _ in arcs], dtype=np.int32)
+        dst = np.array([b for _, b in arcs], dtype=np.int32)
+        got = oracle.brute_census_codes(n, src, dst)
+        assert got == one_hot(n, **want), (arcs, [i for i, k in enumerate(got) if k])
+        assert oracle.census_codes(n, src, dst) == got
+
+
+def test_codes_all_64_triads_and_4096_four_vertex_digraphs():
+    for c in range(64):
+        arcs = code_arcs(c)
+        src = np.array([a for a, _ in arcs], dtype=np.int32)
+        dst = np.array([b for _, b in arcs], dtype=np.int32)
+        b = oracle.brute_census_codes(3, src, dst)
+        assert fold(b) == oracle.brute_census(3, src, dst), c
+        assert oracle.census_codes(3, src, dst) == b, c
+    pairs = [(a, b) for a in range(4) for b in range(4) if a != b]
+    for mask in range(1 << 12):
+        arcs = [pairs[k] for k in range(12) if mask >> k & 1]
+        src = np.array([a for a, _ in arcs], dtype=np.int32)
+        dst = np.array([b for _, b in arcs], dtype=np.int32)
+        b = oracle.brute_census_codes(4, src, dst)
+        assert fold(b) == oracle.brute_census(4, src, dst), mask
+        assert oracle.census_codes(4, src, dst) == b, mask
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_codes_random_graphs_vs_brute(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(10, 40))
+    s, d = np.nonzero(rng.random((n, n)) < rng.uniform(0.05, 0.4))
+    b = oracle.brute_census_codes(n, s, d)
+    assert oracle.census_codes(n, s, d) == b
+    assert fold(b) == oracle.census(n, s, d)
+    assert sum(b) == math.comb(n, 3)
