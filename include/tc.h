@@ -160,6 +160,9 @@ tc_status tc_census_profile(tc_profile_t* out);
 
 /* tc_graph_build flags */
 #define TC_DEVICE_PTRS 1u   /* src/dst (and arc offsets) are device pointers */
+#define TC_UNDIRECTED 4u    /* each pair src[i], dst[i] is an undirected edge: both
+                               arcs (a mutual dyad), the input mode of a Pajek
+                               *Edges section (Sec. 5.1.1 reads both kinds) */
 /* tc_census / tc_census_batched flags */
 #define TC_OUT_DEVICE 2u    /* out is device memory: the call only enqueues work
                                on `stream` and returns without synchronising */
@@ -172,8 +175,9 @@ tc_status tc_opts_default(tc_opts* o);
  * (the CRS "adjacency array" of Sec. 2.5.1 / 5.1.1, with the thesis's separate
  * edge and neighbour arrays folded into one list).
  *   n          vertex count, 0 <= n < 2^30.
- *   src, dst   m arc endpoints (arc src[i] -> dst[i]), int32, host memory or,
- *              with TC_DEVICE_PTRS, device memory.  Not retained.
+ *   src, dst   m arc endpoints (arc src[i] -> dst[i]; with TC_UNDIRECTED
+ *              the edge src[i] -- dst[i]), int32, host memory or, with
+ *              TC_DEVICE_PTRS, device memory.  Not retained.
  *   m          number of arcs, >= 0.
  *   stream     stream the build runs on; the call synchronises it before
  *              returning (it reads back the graph statistics).
@@ -186,6 +190,28 @@ tc_status tc_opts_default(tc_opts* o);
  */
 tc_status tc_graph_build(int32_t n, const int32_t* src, const int32_t* dst, int64_t m,
                          uint32_t flags, void* stream, tc_graph* out);
+
+/*
+ * tc_graph_build_text -- a graph from a network file in the Pajek-style text
+ * format the thesis reads (Sec. 3.1, "Implementation details": the order of
+ * the graph, optional labelled vertex lines, then arcs of a directed or edges
+ * of an undirected graph told apart by the section keyword; Sec. 5.1.1:
+ * 0- or 1-based ids), parsed on the device, then built as tc_graph_build.
+ *   text, bytes  the file's bytes (host memory or, with TC_DEVICE_PTRS,
+ *                device memory; not retained), bytes < 2^31.
+ *   id_base      0 or 1 (Pajek files are 1-based).
+ * Lines: "*Vertices n" (required, once; its vertex lines are skipped),
+ * "*Arcs" (lines "a b ...": arc a->b, further tokens such as weights are
+ * ignored), "*Edges" ("a b ...": both arcs), "*Arcslist" / "*Edgeslist"
+ * ("a b c ...": a->b, a->c, ... / edges); keywords case-insensitive; lines
+ * starting with '%' and blank lines are skipped; '\r' counts as a blank.
+ * Errors: TC_ERR_ARG (no or repeated *Vertices, data before any header, a
+ * malformed header or arc line, bad id_base), TC_ERR_UNSUPPORTED (other
+ * sections such as *Matrix, n >= 2^30, >= 2^30 arcs, text >= 2 GB),
+ * TC_ERR_ID_RANGE (an id outside [base, base + n)), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+tc_status tc_graph_build_text(const char* text, int64_t bytes, int32_t id_base, uint32_t flags, void* stream,
+                              tc_graph* out);
 
 /*
  * tc_graph_build_batched -- build G independent graphs in one pass.

@@ -34,6 +34,7 @@ TYPE_NAMES = ("003", "012", "102", "021D", "021U", "021C", "111D", "111U",
 TC_OK, TC_ERR_ARG, TC_ERR_ID_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED = range(7)
 TC_BIN_HEURISTIC, TC_BIN_MLP = 0, 1
 TC_DEVICE_PTRS = 1
+TC_UNDIRECTED = 4
 TC_OUT_DEVICE = 2
 
 EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_graph_stats",
@@ -41,7 +42,8 @@ EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_gr
            "tc_graph_free", "tc_status_str", "tc_last_error", "tc_census_profile",
            "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free", "tc_autotune",
            "tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
-           "tc_cost_model_load", "tc_census_codes", "tc_census_codes_batched")
+           "tc_cost_model_load", "tc_census_codes", "tc_census_codes_batched",
+           "tc_graph_build_text")
 TC_MLP_NPARAM = 1476
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
@@ -129,6 +131,8 @@ def load():
     lib.tc_census.argtypes = [P, P, P, u32, P]
     lib.tc_census_batched.argtypes = [i32, P, P, P, u32, P]
     lib.tc_census_codes.argtypes = [P, P, P, u32, P]
+    lib.tc_graph_build_text.argtypes = [P, i64, i32, u32, P, P]
+    lib.tc_graph_build_text.restype = ctypes.c_int
     lib.tc_census_codes_batched.argtypes = [i32, P, P, P, u32, P]
     lib.tc_triad_type.argtypes = [ctypes.c_int]
     lib.tc_triad_type.restype = ctypes.c_int
@@ -216,8 +220,9 @@ def tc_opts_default(**over) -> TcOpts:
     return o
 
 
-def tc_graph_build(n: int, src, dst, stream=None) -> int:
-    """Build one graph; returns the opaque handle (an int)."""
+def tc_graph_build(n: int, src, dst, stream=None, undirected: bool = False) -> int:
+    """Build one graph; returns the opaque handle (an int).  With
+    `undirected`, each pair is an edge (both arcs)."""
     ps, ks, ds = _arr(src, np.int32)
     pd, kd, dd = _arr(dst, np.int32)
     if ds != dd:
@@ -226,13 +231,31 @@ def tc_graph_build(n: int, src, dst, stream=None) -> int:
     if m != int(kd.numel() if dd else kd.size):
         raise ValueError("src and dst differ in length")
     h = ctypes.c_void_p()
-    st = load().tc_graph_build(int(n), ps if m else None, pd if m else None, m,
-                               TC_DEVICE_PTRS if ds else 0, _stream(stream), ctypes.byref(h))
+    flags = (TC_DEVICE_PTRS if ds else 0) | (TC_UNDIRECTED if undirected else 0)
+    st = load().tc_graph_build(int(n), ps if m else None, pd if m else None, m, flags, _stream(stream),
+                               ctypes.byref(h))
     _check(st, "tc_graph_build")
     return h.value
 
 
-def tc_graph_build_batched(ns, arc_off, src, dst, stream=None) -> list[int]:
+def tc_graph_build_text(text, id_base: int = 1, stream=None) -> int:
+    """Build one graph from a Pajek-style network file's contents (bytes or
+    str on the host, or a CUDA uint8 tensor), parsed on the device."""
+    if isinstance(text, str):
+        text = text.encode()
+    h = ctypes.c_void_p()
+    if isinstance(text, (bytes, bytearray)):
+        buf = ctypes.create_string_buffer(bytes(text), len(text))
+        st = load().tc_graph_build_text(ctypes.cast(buf, ctypes.c_void_p), len(text), int(id_base), 0,
+                                        _stream(stream), ctypes.byref(h))
+    else:  # a CUDA tensor of bytes
+        st = load().tc_graph_build_text(text.data_ptr(), int(text.numel()), int(id_base), TC_DEVICE_PTRS,
+                                        _stream(stream), ctypes.byref(h))
+    _check(st, "tc_graph_build_text")
+    return h.value
+
+
+def tc_graph_build_batched(ns, arc_off, src, dst, stream=None, undirected: bool = False) -> list[int]:
     """Build G graphs (ids local to each graph); returns G handles."""
     ns = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
     off = np.ascontiguousarray(np.asarray(arc_off, dtype=np.int64))
@@ -244,8 +267,8 @@ def tc_graph_build_batched(ns, arc_off, src, dst, stream=None) -> list[int]:
     if ds != dd:
         raise TypeError("src and dst must both be host or both be device arrays")
     out = (ctypes.c_void_p * G)()
-    st = load().tc_graph_build_batched(G, ns.ctypes.data, off.ctypes.data, ps, pd,
-                                       TC_DEVICE_PTRS if ds else 0, _stream(stream), out)
+    flags = (TC_DEVICE_PTRS if ds else 0) | (TC_UNDIRECTED if undirected else 0)
+    st = load().tc_graph_build_batched(G, ns.ctypes.data, off.ctypes.data, ps, pd, flags, _stream(stream), out)
     _check(st, "tc_graph_build_batched")
     return [out[i] for i in range(G)]
 

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtc.so")
-SOURCES = ["capi.cu", "build.cu", "census.cu", "mlp.cu"]
+SOURCES = ["capi.cu", "build.cu", "census.cu", "mlp.cu", "pajek.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -39,7 +39,8 @@ __device__ __forceinline__ int find_graph(const int64_t* off, int G, int64_t i) 
 
 __global__ void k_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
                        const int64_t* __restrict__ arc_off, const int64_t* __restrict__ voff,
-                       int G, int sh, uint64_t* __restrict__ keys, int* __restrict__ err) {
+                       int G, int sh, uint32_t tag_out, uint32_t tag_in, uint64_t* __restrict__ keys,
+                       int* __restrict__ err) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int g = G == 1 ? 0 : find_graph(arc_off, G, i);
@@ -49,8 +50,8 @@ __global__ void k_keys(const int32_t* __restrict__ src, const int32_t* __restric
         if (s < 0 || s >= n || d < 0 || d >= n) {
             atomicOr(err, 1);
         } else if (s != d) {
-            k1 = ((uint64_t)(base + s) << sh) | ((uint64_t)d << 2) | 1u;  // row s: arc s->d
-            k2 = ((uint64_t)(base + d) << sh) | ((uint64_t)s << 2) | 2u;  // row d: arc s->d seen from d
+            k1 = ((uint64_t)(base + s) << sh) | ((uint64_t)d << 2) | tag_out;  // row s: arc s->d
+            k2 = ((uint64_t)(base + d) << sh) | ((uint64_t)s << 2) | tag_in;   // row d: arc s->d seen from d
         }
         keys[2 * i] = k1;
         keys[2 * i + 1] = k2;
@@ -193,7 +194,8 @@ int grid_for(int64_t work, int threads) {
 tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const int32_t* src,
                      const int32_t* dst, uint32_t flags, cudaStream_t st, tc_graph* outs) {
     if (G < 1 || !ns || !arc_off || !outs) return fail(TC_ERR_ARG, "graph build: null argument or G < 1");
-    if (flags & ~TC_DEVICE_PTRS) return fail(TC_ERR_ARG, "graph build: unknown flag");
+    if (flags & ~(TC_DEVICE_PTRS | TC_UNDIRECTED)) return fail(TC_ERR_ARG, "graph build: unknown flag");
+    const bool undirected = (flags & TC_UNDIRECTED) != 0;  // an edge is both arcs
     std::vector<int64_t> voff((size_t)G + 1, 0), aoff((size_t)G + 1, 0);
     int64_t max_n = 0;
     for (int32_t g = 0; g < G; ++g) {
@@ -268,7 +270,8 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         TC_CUDA(S.get(&k1, (size_t)N));
         TC_CUDA(S.get(&head, (size_t)N));
         TC_CUDA(S.get(&d_pos, (size_t)N));
-        k_keys<<<grid_for(m, 256), 256, 0, st>>>(d_src, d_dst, m, d_aoff, d_voff, G, sh, k0, d_err);
+        k_keys<<<grid_for(m, 256), 256, 0, st>>>(d_src, d_dst, m, d_aoff, d_voff, G, sh, undirected ? 3u : 1u,
+                                                 undirected ? 3u : 2u, k0, d_err);
         TC_CUDA(cudaGetLastError());
         cub::DoubleBuffer<uint64_t> db(k0, k1);
         size_t tmp_bytes = 0;

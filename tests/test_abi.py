@@ -60,6 +60,11 @@ def test_argument_errors_need_no_device(lib):
     assert lib.tc_census_codes(None, None, None, 0, None) == tc.TC_ERR_ARG
     assert lib.tc_census_codes_batched(-1, None, None, None, 0, None) == tc.TC_ERR_ARG
     assert lib.tc_census_codes_batched(0, None, None, None, 0, None) == tc.TC_OK
+    assert lib.tc_graph_build_text(None, 0, 1, 0, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_graph_build_text(b"*Vertices 3\n", 12, 2, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG
+    assert lib.tc_graph_build_text(b"*Vertices 3\n", 12, 1, 0x80, None, ctypes.byref(h)) == tc.TC_ERR_ARG
+    assert lib.tc_graph_build_text(None, 0, 1, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG  # empty file
+    assert lib.tc_graph_build(5, None, None, 0, 0x80 | tc.TC_UNDIRECTED, None, ctypes.byref(h)) == tc.TC_ERR_ARG
     assert lib.tc_graph_stats(None, None) == tc.TC_ERR_ARG
     assert lib.tc_opts_default(None) == tc.TC_ERR_ARG
     assert "null" in tc.tc_last_error() or tc.tc_last_error()
