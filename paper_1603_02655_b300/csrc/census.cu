@@ -1523,6 +1523,9 @@ constexpr int OWN_LBS = 9;   // staged owners: at most 2^9 buckets
 constexpr int OWN_LBL = 13;  // larger owners: at most 2^13 buckets
 constexpr int OWN_G = 2;     // aligned 16-byte groups per lane per unit
 constexpr int OWN_UNIT = 32 * 4 * OWN_G;
+// consecutive items a CTA takes at a time from the larger owners (pieces of
+// one owner are consecutive, so the CTA indexes it once for all of them)
+constexpr unsigned OWN_GRAB = 2;
 constexpr size_t own_pad(size_t b) { return (b + 15) / 16 * 16; }
 constexpr size_t OWN_T_BYTES = sizeof(uint32_t) * OWN_CAP;
 constexpr size_t OWN_ST_BYTES = own_pad(sizeof(uint32_t) * ((1 << OWN_LBS) + 1));
@@ -2009,13 +2012,15 @@ __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
             ctl.row = ~0u;
             ctl.seg = -1;
         }
+        const unsigned grab = phase == 0 ? OWN_GRAB : 1u;
         for (;;) {
             if (threadIdx.x == 0) {
-                ctl.idx = atomicAdd(a.cursor + phase, 1u);
+                ctl.idx = atomicAdd(a.cursor + phase, grab);
             }
             __syncthreads();
-            const unsigned idx = ctl.idx;
-            if (idx >= nitems) break;
+            const unsigned idx0 = ctl.idx;
+            if (idx0 >= nitems) break;
+            for (unsigned idx = idx0; idx < min(idx0 + grab, nitems); ++idx) {
             const Owner o = phase == 0 ? owner_setup(a, a.list[a.cap - 1 - idx], OWN_LBL, 5)
                                        : owner_setup(a, a.list[idx], OWN_LBS, 4);
             const uint32_t* G = a.adj + o.beg;
@@ -2038,6 +2043,7 @@ __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
                 if (phase == 0) owner_units<false>(w, Q, a, o, G, st, ls, lm, tsb, txe, tpp, ntask, total);
                 else owner_units<true>(w, Q, a, o, T, st, ls, lm, tsb, txe, tpp, ntask, total);
                 __syncthreads();
+            }
             }
         }
     }
