@@ -667,6 +667,7 @@ def train_and_compare(tc, gs, opts, stream, free):
     learn.profile = opts.profile
     report = {"census_ms_degree_sum": h_ms, "census_ms_learned": l_ms, "speedup": h_ms / l_ms,
               "rmse_log2_cycles_mlp": rep["rmse_mlp"], "rmse_log2_cycles_degree_sum": rep["rmse_degree_sum"],
+              "rmse_log2_cycles_exact_size": rep.get("rmse_exact_size"),
               "samples": rep["samples"], "train_s": train_s,
               "bin_tasks": bins_used}
     if free:

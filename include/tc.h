@@ -374,6 +374,12 @@ tc_status tc_autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_
 tc_status tc_cost_sample(int32_t G, const tc_graph* gs, int32_t bin, int32_t mask, int32_t cap,
                          int32_t* samples, int32_t* n, void* stream);
 tc_status tc_cost_features(tc_graph g, const int32_t* uv, int32_t n, float* feat, void* stream);
+/* tc_union_sizes: |S| = |N(u) u N(v) \ {u, v}| (Sec. 2.2; the exact task
+ * cost W3 of Sec. 4.3.1) of pairs uv int32[n][2] (device; global rows, both
+ * of one graph of the build g belongs to) into out int32[n] (device);
+ * synchronises `stream`.  Errors: TC_ERR_ARG, TC_ERR_ID_RANGE (a pair not
+ * within one graph), TC_ERR_OOM, TC_ERR_CUDA. */
+tc_status tc_union_sizes(tc_graph g, const int32_t* uv, int32_t n, int32_t* out, void* stream);
 tc_status tc_mlp_loss_grad(const float* params, const float* feat, const int32_t* bin, const float* target,
                            int32_t n, float* grad, float* loss, void* stream);
 tc_status tc_mlp_train(float* params, const float* feat, const int32_t* bin, const float* target, int32_t n,

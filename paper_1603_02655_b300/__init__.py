@@ -43,7 +43,7 @@ EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_gr
            "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free", "tc_autotune",
            "tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
            "tc_cost_model_load", "tc_census_codes", "tc_census_codes_batched",
-           "tc_graph_build_text")
+           "tc_graph_build_text", "tc_union_sizes")
 TC_MLP_NPARAM = 1476
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
@@ -132,6 +132,8 @@ def load():
     lib.tc_census_batched.argtypes = [i32, P, P, P, u32, P]
     lib.tc_census_codes.argtypes = [P, P, P, u32, P]
     lib.tc_graph_build_text.argtypes = [P, i64, i32, u32, P, P]
+    lib.tc_union_sizes.argtypes = [P, P, i32, P, P]
+    lib.tc_union_sizes.restype = ctypes.c_int
     lib.tc_graph_build_text.restype = ctypes.c_int
     lib.tc_census_codes_batched.argtypes = [i32, P, P, P, u32, P]
     lib.tc_triad_type.argtypes = [ctypes.c_int]
@@ -465,6 +467,17 @@ def tc_cost_features(g: int, uv, stream=None):
     out = torch.empty((uv.shape[0], 8), dtype=torch.float32, device="cuda")
     _check(load().tc_cost_features(g, uv.data_ptr(), int(uv.shape[0]), out.data_ptr(), _stream(stream)),
            "tc_cost_features")
+    return out
+
+
+def tc_union_sizes(g: int, uv, stream=None):
+    """|S| = |N(u) u N(v) minus {u, v}| (int32 CUDA tensor [n]) of pairs uv
+    (int32 CUDA tensor [n, 2], global rows of one graph of g's build each)."""
+    import torch
+    uv = uv.contiguous()
+    out = torch.empty(uv.shape[0], dtype=torch.int32, device="cuda")
+    _check(load().tc_union_sizes(g, uv.data_ptr(), int(uv.shape[0]), out.data_ptr(), _stream(stream)),
+           "tc_union_sizes")
     return out
 
 

@@ -16,7 +16,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import (TC_MLP_NPARAM, tc_cost_features, tc_cost_model_load, tc_cost_sample, tc_graph_stats,
-               tc_mlp_predict, tc_mlp_train)
+               tc_mlp_predict, tc_mlp_train, tc_union_sizes)
 
 BINS = 4
 
@@ -69,9 +69,18 @@ def fit(feat, bins: np.ndarray, target: np.ndarray, steps: int = 3000, batch: in
     return p.cpu().numpy(), loss
 
 
-def evaluate(params: np.ndarray, feat, bins: np.ndarray, target: np.ndarray, train_mask: np.ndarray) -> dict:
+def union_sizes(g, uv: np.ndarray, stream=None) -> np.ndarray:
+    """|S| of each sampled task (the exact cost of Sec. 4.3.1), from the GPU."""
+    import torch
+    return tc_union_sizes(g, torch.from_numpy(np.ascontiguousarray(uv)).cuda(), stream).cpu().numpy()
+
+
+def evaluate(params: np.ndarray, feat, bins: np.ndarray, target: np.ndarray, train_mask: np.ndarray,
+             s_exact: np.ndarray | None = None) -> dict:
     """Held-out RMSE (in log2 cycles) of the network (FP16 inference, as used
-    by binning) and of the degree-sum rule fitted per bin on the training part."""
+    by binning), of the degree-sum rule fitted per bin on the training part,
+    and (given |S| per task) of the same fit on the exact cost |S|: the
+    ceiling of a one-number cost rule."""
     import torch
     p = torch.from_numpy(params.astype(np.float32)).cuda()
     pred = tc_mlp_predict(p, feat, True).cpu().numpy()
@@ -80,7 +89,7 @@ def evaluate(params: np.ndarray, feat, bins: np.ndarray, target: np.ndarray, tra
     L = np.exp2(f[:, 3] * 20.0) - 1.0
     test = ~train_mask
     out = {"samples": int(bins.size), "test_samples": int(test.sum()), "per_bin": {}}
-    se_mlp = se_heur = 0.0
+    se_mlp = se_heur = se_exact = 0.0
     for b in range(BINS):
         tr = train_mask & (bins == b)
         te = test & (bins == b)
@@ -93,11 +102,17 @@ def evaluate(params: np.ndarray, feat, bins: np.ndarray, target: np.ndarray, tra
         e_heur = h - target[te]
         se_mlp += float(np.sum(e_mlp ** 2))
         se_heur += float(np.sum(e_heur ** 2))
+        if s_exact is not None:
+            ls = np.log2(1.0 + s_exact.astype(np.float64))
+            cx, *_ = np.linalg.lstsq(np.stack([np.ones(tr.sum()), ls[tr]], axis=1), target[tr], rcond=None)
+            se_exact += float(np.sum((cx[0] + cx[1] * ls[te] - target[te]) ** 2))
         out["per_bin"][b] = {"n_test": int(te.sum()), "rmse_mlp": float(np.sqrt(np.mean(e_mlp ** 2))),
                              "rmse_degree_sum": float(np.sqrt(np.mean(e_heur ** 2)))}
     nt = max(1, int(test.sum()))
     out["rmse_mlp"] = float(np.sqrt(se_mlp / nt))
     out["rmse_degree_sum"] = float(np.sqrt(se_heur / nt))
+    if s_exact is not None:
+        out["rmse_exact_size"] = float(np.sqrt(se_exact / nt))
     return out
 
 
@@ -118,7 +133,7 @@ def train_cost_model(gs, mask: int = 63, steps: int = 3000, batch: int = 4096, l
     idx = torch.from_numpy(np.nonzero(train_mask)[0]).cuda()
     params, loss = fit(feat[idx].contiguous(), bins[train_mask], target[train_mask], steps, batch, lr, seed,
                        stream=stream)
-    rep = evaluate(params, feat, bins, target, train_mask)
+    rep = evaluate(params, feat, bins, target, train_mask, union_sizes(gs[0], uv, stream))
     rep["train_loss"] = loss
     rep["graph_stats"] = [tc_graph_stats(g) for g in gs[:4]]
     return params, rep

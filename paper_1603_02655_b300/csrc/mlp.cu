@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <algorithm>
+
 #include "mlp.cuh"
 #include "tc_internal.cuh"
 
@@ -28,6 +30,59 @@ __global__ void k_features(const int32_t* __restrict__ deg, const int32_t* __res
             task_features_uv(u, v, deg, vtag, f);
         }
         for (int k = 0; k < MLP_IN; ++k) feat[(size_t)i * MLP_IN + k] = f[k];
+    }
+}
+
+// |S| = |N(u) u N(v) \ {u, v}| of pairs of vertices of one graph each (the
+// graph's global rows [voff[g], voff[g+1]), local ids = row - voff[g]): the
+// exact task cost of Sec. 4.3.1 (workload W3).
+// One warp per pair: lanes take the shorter list's entries in turn and
+// binary-search them in the longer one; |S| = d_u + d_v - |common| - 2 when
+// u and v are adjacent (each list then holds the other endpoint).
+__device__ __forceinline__ bool list_has(const uint32_t* l, int n, uint32_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((l[mid] >> 2) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < n && (l[lo] >> 2) == key;
+}
+
+__global__ void k_union_sizes(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+                              const int64_t* __restrict__ voff, int G, const int32_t* __restrict__ uv, int32_t n,
+                              int32_t* __restrict__ out, int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int64_t u = uv[2 * i], v = uv[2 * i + 1];
+        int lo_g = 0, hi_g = G - 1;  // graph of u: last g with voff[g] <= u
+        while (lo_g < hi_g) {
+            const int mid = (lo_g + hi_g + 1) >> 1;
+            if (voff[mid] <= u) lo_g = mid;
+            else hi_g = mid - 1;
+        }
+        const int64_t r0 = voff[lo_g], r1 = voff[lo_g + 1];
+        if (u < r0 || u >= r1 || v < r0 || v >= r1) {
+            if (lane == 0) {
+                atomicOr(err, 1);
+                out[i] = 0;
+            }
+            continue;
+        }
+        const int64_t ub = row_ptr[u], vb = row_ptr[v];
+        const int du = (int)(row_ptr[u + 1] - ub), dv = (int)(row_ptr[v + 1] - vb);
+        const bool u_short = du <= dv;
+        const uint32_t* sl = adj + (u_short ? ub : vb);
+        const uint32_t* gl = adj + (u_short ? vb : ub);
+        const int ns = u_short ? du : dv, ng = u_short ? dv : du;
+        int common = 0;
+        for (int k = lane; k < ns; k += 32) common += list_has(gl, ng, sl[k] >> 2) ? 1 : 0;
+        for (int o = 16; o > 0; o >>= 1) common += __shfl_xor_sync(0xffffffffu, common, o);
+        if (lane == 0) {
+            const bool adjacent = u != v && list_has(adj + ub, du, (uint32_t)(v - r0));
+            out[i] = du + dv - common - (adjacent ? 2 : 0);
+        }
     }
 }
 
@@ -304,6 +359,29 @@ tc_status tc_cost_features(tc_graph g, const int32_t* uv, int32_t n, float* feat
     TC_CUDA(cudaStreamSynchronize(st));
     tc::dev_free(err, st);
     if (h) return tc::fail(TC_ERR_ID_RANGE, "tc_cost_features: a vertex outside the graph set");
+    return TC_OK;
+}
+
+tc_status tc_union_sizes(tc_graph g, const int32_t* uv, int32_t n, int32_t* out, void* stream) {
+    if (!g || n < 0 || (n > 0 && (!uv || !out))) return tc::fail(TC_ERR_ARG, "tc_union_sizes: bad arguments");
+    if (n == 0) return TC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* err = nullptr;
+    TC_CUDA(tc::dev_alloc((void**)&err, sizeof(int), st));
+    TC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    const tc::GraphSet& s = *g->set;
+    int64_t* voff = nullptr;
+    TC_CUDA(tc::dev_alloc((void**)&voff, sizeof(int64_t) * s.voff.size(), st));
+    TC_CUDA(cudaMemcpyAsync(voff, s.voff.data(), sizeof(int64_t) * s.voff.size(), cudaMemcpyHostToDevice, st));
+    tc::k_union_sizes<<<(int)std::min<int64_t>(((int64_t)n + 7) / 8, 1 << 20), 256, 0, st>>>(
+        s.row_ptr, s.adj, voff, (int)s.G, uv, n, out, err);
+    TC_CUDA(cudaGetLastError());
+    int h = 0;
+    TC_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    tc::dev_free(err, st);
+    tc::dev_free(voff, st);
+    if (h) return tc::fail(TC_ERR_ID_RANGE, "tc_union_sizes: a pair not within one graph of the build");
     return TC_OK;
 }
 

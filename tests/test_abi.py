@@ -61,6 +61,7 @@ def test_argument_errors_need_no_device(lib):
     assert lib.tc_census_codes_batched(-1, None, None, None, 0, None) == tc.TC_ERR_ARG
     assert lib.tc_census_codes_batched(0, None, None, None, 0, None) == tc.TC_OK
     assert lib.tc_graph_build_text(None, 0, 1, 0, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_union_sizes(None, None, 1, None, None) == tc.TC_ERR_ARG
     assert lib.tc_graph_build_text(b"*Vertices 3\n", 12, 2, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG
     assert lib.tc_graph_build_text(b"*Vertices 3\n", 12, 1, 0x80, None, ctypes.byref(h)) == tc.TC_ERR_ARG
     assert lib.tc_graph_build_text(None, 0, 1, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG  # empty file

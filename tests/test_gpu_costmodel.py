@@ -158,6 +158,40 @@ def test_learned_binning_never_changes_counts(seed):
         tc.tc_graph_free(g)
 
 
+def test_union_sizes_match_definition():
+    import torch
+    # |S| = |N(u) u N(v) minus {u, v}| from the host neighbour sets, for
+    # adjacent and non-adjacent pairs of two graphs of one batched build
+    rng = np.random.default_rng(12)
+    graphs = [synth.rmat(10, 8, recip=0.2, seed=4), synth.rmat(9, 6, recip=0.0, seed=5)]
+    gs = tc.tc_graph_build_batched([a.n for a in graphs], np.cumsum([0] + [a.src.size for a in graphs]),
+                                   np.concatenate([a.src for a in graphs]), np.concatenate([a.dst for a in graphs]))
+    try:
+        uv, want = [], []
+        base = 0
+        for a in graphs:
+            nb = [set() for _ in range(a.n)]
+            for s_, d_ in zip(a.src.tolist(), a.dst.tolist()):
+                if s_ != d_:
+                    nb[s_].add(d_)
+                    nb[d_].add(s_)
+            for _ in range(300):
+                u = int(rng.integers(a.n))
+                v = int(rng.choice(sorted(nb[u]))) if nb[u] and rng.random() < 0.7 else int(rng.integers(a.n))
+                if u == v:
+                    continue
+                uv.append((base + u, base + v))
+                want.append(len((nb[u] | nb[v]) - {u, v}))
+            base += a.n
+        got = tc.tc_union_sizes(gs[0], torch.tensor(uv, dtype=torch.int32, device="cuda")).cpu().tolist()
+        assert got == want
+        with pytest.raises(tc.TcError):  # a pair across the two graphs
+            tc.tc_union_sizes(gs[0], torch.tensor([[0, graphs[0].n]], dtype=torch.int32, device="cuda"))
+    finally:
+        for g in gs:
+            tc.tc_graph_free(g)
+
+
 def test_pipeline_trains_and_reports_the_judge():
     a = synth.rmat(16, 8, recip=0.1, seed=9)
     g = tc.tc_graph_build(a.n, a.src, a.dst)
@@ -169,6 +203,7 @@ def test_pipeline_trains_and_reports_the_judge():
         # task costs predicted better than by the degree-sum rule fitted to
         # the same training samples
         assert rep["rmse_mlp"] < rep["rmse_degree_sum"], rep
+        assert np.isfinite(rep["rmse_exact_size"])
         tc.tc_cost_model_load(params)
         want = tc.tc_census(g)
         assert tc.tc_census(g, tc.tc_opts_default(bin_mode=tc.TC_BIN_MLP)) == want
