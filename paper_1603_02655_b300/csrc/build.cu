@@ -70,11 +70,12 @@ __global__ void k_heads(const uint64_t* __restrict__ k, int64_t N, int32_t* __re
 // entry with the OR of the run's tags, and counts it into its row's length
 // and the row's count of that tag (atomics aggregated over the warp's lanes
 // with the same row, resp. row and tag: sorted keys keep a row's entries in
-// neighbouring lanes).
+// neighbouring lanes).  With first_up (one graph: local id = row), the
+// row's first entry above its own id records its position there.
 __global__ void k_write(const uint64_t* __restrict__ k, int64_t N, const int32_t* __restrict__ head,
                         const int32_t* __restrict__ pos, int sh, uint32_t nbr_mask,
                         uint32_t* __restrict__ adj, unsigned long long* __restrict__ cnt,
-                        int32_t* __restrict__ vtag, int32_t* __restrict__ arow) {
+                        int32_t* __restrict__ vtag, int32_t* __restrict__ arow, int32_t* __restrict__ first_up) {
     const int lane = threadIdx.x & 31;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < N; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;  // whole warps iterate together
@@ -88,6 +89,10 @@ __global__ void k_write(const uint64_t* __restrict__ k, int64_t N, const int32_t
             row = k[i] >> sh;
             adj[pos[i]] = (nbr << 2) | tag;
             arow[pos[i]] = (int32_t)row;
+            if (first_up && (uint64_t)nbr > row) {
+                const uint64_t pk = i == 0 ? ~0ull : k[i - 1];
+                if ((pk >> sh) != row || (uint64_t)((uint32_t)((pk >> 2) & nbr_mask)) < row) first_up[row] = pos[i];
+            }
         }
         const unsigned same_row = __match_any_sync(0xffffffffu, row);
         const unsigned same_tag = __match_any_sync(0xffffffffu, (row << 2) | tag);
@@ -102,8 +107,9 @@ __global__ void k_fill_sent(uint32_t* __restrict__ p, int64_t count) {
         p[i] = SENT;
 }
 
-// Thread per row: degree, the row's split (entries below the row's own id,
-// by binary search), and per-graph statistics from the row's degree and tag
+// Thread per row: degree, the row's split (entries below the row's own id:
+// from the first entry above it that k_write recorded for one graph, else by
+// binary search), and per-graph statistics from the row's degree and tag
 // counts (k_write counted the tags); a warp whose rows lie in one graph adds
 // its sums with one atomic each.
 __global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
@@ -122,14 +128,19 @@ __global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const uint32_t* 
             const unsigned long long d = (unsigned long long)(row_ptr[x + 1] - b);
             deg[x] = (int32_t)d;
             g = G == 1 ? 0 : find_graph(voff, G, x);
-            const uint32_t xl = (uint32_t)(x - voff[g]);
-            int lo = 0, hi = (int)d;  // entries with neighbour id below x
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((adj[b + mid] >> 2) < xl) lo = mid + 1;
-                else hi = mid;
+            if (G == 1) {  // k_write recorded the first entry above x (or -1: none)
+                const int32_t fu = split[x];
+                split[x] = fu < 0 ? (int32_t)d : (int32_t)(fu - b);
+            } else {
+                const uint32_t xl = (uint32_t)(x - voff[g]);
+                int lo = 0, hi = (int)d;  // entries with neighbour id below x
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((adj[b + mid] >> 2) < xl) lo = mid + 1;
+                    else hi = mid;
+                }
+                split[x] = lo;
             }
-            split[x] = lo;
             const int c1 = vtag[3 * x], c3 = vtag[3 * x + 2];
             v[0] = (unsigned long long)(c1 + c3);
             v[1] = d;
@@ -232,6 +243,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     TC_CUDA(dev_alloc((void**)&set->vtag, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(cudaMemsetAsync(set->vtag, 0, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(dev_alloc((void**)&set->split, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
+    TC_CUDA(cudaMemsetAsync(set->split, 0xFF, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(dev_alloc((void**)&set->arow, sizeof(int32_t) * (size_t)std::max<int64_t>(N, 1), st));
 
     Scratch S(st);
@@ -288,7 +300,8 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         TC_CUDA(S.get((char**)&tmp2, scan_bytes));
         TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp2, scan_bytes, head, d_pos, (int)N, st));
         k_write<<<grid_for(N, 256), 256, 0, st>>>(ks, N, head, d_pos, sh, (uint32_t)((1ull << nb) - 1),
-                                                  set->adj, d_cnt, set->vtag, set->arow);
+                                                  set->adj, d_cnt, set->vtag, set->arow,
+                                                  G == 1 ? set->split : nullptr);
         TC_CUDA(cudaGetLastError());
         int32_t last_pos = 0, last_head = 0;
         TC_CUDA(cudaMemcpyAsync(&last_pos, d_pos + N - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
