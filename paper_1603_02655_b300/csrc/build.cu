@@ -7,12 +7,19 @@
 // IsEdge and IsNeighbour from the tags of the merge instead of searching.
 //
 // Steps (all on the device, on the caller's stream):
-//   1 keys: each arc x->y emits (row x, nbr y, bit0) and (row y, nbr x, bit1);
-//     self-loops emit a sentinel key that sorts last; ids are range-checked.
-//   2 one radix sort of the 64-bit keys (library primitive: CUB).
-//   3 run heads over (row, nbr); exclusive scan gives each run its slot.
-//   4 each run writes one entry with the OR of its tags and counts its row.
-//   5 scan of the row counts -> row_ptr; per-row tag counts and per-graph
+//   1 keys: each arc x->y emits one canonical key (row min(x,y), nbr
+//     max(x,y), tag seen from the lower endpoint); self-loops emit a sentinel
+//     key that sorts last; ids are range-checked.
+//   2 a radix sort of the 64-bit keys (library primitive: CUB): each dyad
+//     once, in (lower, higher) order.
+//   3 run heads over (lower, higher); an exclusive scan numbers the dyads.
+//   4 each run is a dyad (the OR of its tags): its upper entry (row lower) in
+//     dyad order, its lower entry (row higher) for the next sort; per-row
+//     counts of upper and lower entries and of tags.
+//   5 a stable radix sort of the lower entries by row (32-bit keys, the
+//     library again): each row's lower entries by ascending neighbour.
+//   6 scans of the counts -> row_ptr; each row is its lower entries, then its
+//     upper ones (so a row's split point is its lower count); per-graph
 //     statistics (arcs, dyads, mutual, merged entries = sum d^2, max degree).
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
@@ -37,24 +44,24 @@ __device__ __forceinline__ int find_graph(const int64_t* off, int G, int64_t i) 
     return lo;
 }
 
-__global__ void k_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                       const int64_t* __restrict__ arc_off, const int64_t* __restrict__ voff,
-                       int G, int sh, uint32_t tag_out, uint32_t tag_in, uint64_t* __restrict__ keys,
-                       int* __restrict__ err) {
+__global__ void k_dyad_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                            const int64_t* __restrict__ arc_off, const int64_t* __restrict__ voff, int G, int sh,
+                            bool undirected, uint64_t* __restrict__ keys, int* __restrict__ err) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int g = G == 1 ? 0 : find_graph(arc_off, G, i);
         const int64_t base = voff[g], n = voff[g + 1] - base;
         const int32_t s = src[i], d = dst[i];
-        uint64_t k1 = KEY_SENT, k2 = KEY_SENT;
+        uint64_t k = KEY_SENT;
         if (s < 0 || s >= n || d < 0 || d >= n) {
             atomicOr(err, 1);
         } else if (s != d) {
-            k1 = ((uint64_t)(base + s) << sh) | ((uint64_t)d << 2) | tag_out;  // row s: arc s->d
-            k2 = ((uint64_t)(base + d) << sh) | ((uint64_t)s << 2) | tag_in;   // row d: arc s->d seen from d
+            const int32_t lo = min(s, d), hi = max(s, d);
+            // tag seen from the lower endpoint: bit0 = arc lo->hi, bit1 = hi->lo
+            const uint32_t tag = undirected ? 3u : (s < d ? 1u : 2u);
+            k = ((uint64_t)(base + lo) << sh) | ((uint64_t)hi << 2) | tag;
         }
-        keys[2 * i] = k1;
-        keys[2 * i + 1] = k2;
+        keys[i] = k;
     }
 }
 
@@ -66,38 +73,76 @@ __global__ void k_heads(const uint64_t* __restrict__ k, int64_t N, int32_t* __re
     }
 }
 
-// One thread per sorted key; the first key of each (row, nbr) run writes the
-// entry with the OR of the run's tags, and counts it into its row's length
-// and the row's count of that tag (atomics aggregated over the warp's lanes
-// with the same row, resp. row and tag: sorted keys keep a row's entries in
-// neighbouring lanes).  With first_up (one graph: local id = row), the
-// row's first entry above its own id records its position there.
-__global__ void k_write(const uint64_t* __restrict__ k, int64_t N, const int32_t* __restrict__ head,
-                        const int32_t* __restrict__ pos, int sh, uint32_t nbr_mask,
-                        uint32_t* __restrict__ adj, unsigned long long* __restrict__ cnt,
-                        int32_t* __restrict__ vtag, int32_t* __restrict__ arow, int32_t* __restrict__ first_up) {
+__device__ __forceinline__ uint32_t tag_swap(uint32_t t) { return ((t & 1u) << 1) | (t >> 1); }
+
+// One thread per sorted key; the first key of each (lower, higher) run is a
+// dyad <u,v> with the OR of the run's tags: dyad j gets the upper entry
+// (row u, v << 2 | tag) and the lower entry (row v, u << 2 | swapped tag).
+// Counts per row: upper and lower entries, entries of each tag (atomics
+// aggregated over a warp's lanes with the same row u, resp. row u and tag:
+// sorted keys keep them in neighbouring lanes).
+__global__ void k_dyads(const uint64_t* __restrict__ k, int64_t M, const int32_t* __restrict__ head,
+                        const int32_t* __restrict__ dpos, int sh, uint32_t nbr_mask, const int64_t* __restrict__ voff,
+                        int G, int32_t* __restrict__ up_row, uint32_t* __restrict__ up_val,
+                        uint32_t* __restrict__ lo_key, uint32_t* __restrict__ lo_val, int32_t* __restrict__ cnt_up,
+                        int32_t* __restrict__ cnt_lo, int32_t* __restrict__ vtag) {
     const int lane = threadIdx.x & 31;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < N; i0 += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < M; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;  // whole warps iterate together
-        const bool is_head = i < N && head[i];
-        uint64_t row = ~0ull;
+        const bool is_head = i < M && head[i];
+        uint64_t u = ~0ull;
         uint32_t tag = 0;
         if (is_head) {
             const uint64_t key = k[i] >> 2;
-            for (int64_t j = i; j < N && (k[j] >> 2) == key; ++j) tag |= (uint32_t)(k[j] & 3u);
-            const uint32_t nbr = (uint32_t)(key & nbr_mask);
-            row = k[i] >> sh;
-            adj[pos[i]] = (nbr << 2) | tag;
-            arow[pos[i]] = (int32_t)row;
-            if (first_up && (uint64_t)nbr > row) {
-                const uint64_t pk = i == 0 ? ~0ull : k[i - 1];
-                if ((pk >> sh) != row || (uint64_t)((uint32_t)((pk >> 2) & nbr_mask)) < row) first_up[row] = pos[i];
-            }
+            for (int64_t j = i; j < M && (k[j] >> 2) == key; ++j) tag |= (uint32_t)(k[j] & 3u);
+            u = k[i] >> sh;
+            const uint32_t vl = (uint32_t)(key & nbr_mask);
+            const int64_t base = G == 1 ? 0 : voff[find_graph(voff, G, (int64_t)u)];
+            const uint64_t v = (uint64_t)base + vl;
+            const uint32_t ul = (uint32_t)(u - (uint64_t)base);
+            const int32_t j = dpos[i];
+            up_row[j] = (int32_t)u;
+            up_val[j] = (vl << 2) | tag;
+            lo_key[j] = (uint32_t)v;
+            lo_val[j] = (ul << 2) | tag_swap(tag);
+            atomicAdd(&cnt_lo[v], 1);
+            atomicAdd(&vtag[3 * v + tag_swap(tag) - 1], 1);
         }
-        const unsigned same_row = __match_any_sync(0xffffffffu, row);
-        const unsigned same_tag = __match_any_sync(0xffffffffu, (row << 2) | tag);
-        if (is_head && lane == __ffs(same_row) - 1) atomicAdd(&cnt[row], (unsigned long long)__popc(same_row));
-        if (is_head && lane == __ffs(same_tag) - 1) atomicAdd(&vtag[3 * row + tag - 1], __popc(same_tag));
+        const unsigned same_row = __match_any_sync(0xffffffffu, u);
+        const unsigned same_tag = __match_any_sync(0xffffffffu, (u << 2) | tag);
+        if (is_head && lane == __ffs(same_row) - 1) atomicAdd(&cnt_up[u], __popc(same_row));
+        if (is_head && lane == __ffs(same_tag) - 1) atomicAdd(&vtag[3 * u + tag - 1], __popc(same_tag));
+    }
+}
+
+__global__ void k_row_counts(const int32_t* __restrict__ cnt_lo, const int32_t* __restrict__ cnt_up, int64_t n,
+                             unsigned long long* __restrict__ cnt) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        cnt[x] = (unsigned long long)(cnt_lo[x] + cnt_up[x]);
+}
+
+// Lower entries (sorted by row, then neighbour) to the front of their rows;
+// lpre = exclusive scan of the lower counts (each row's first sorted entry).
+__global__ void k_place_lo(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val, int64_t D,
+                           const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ lpre,
+                           uint32_t* __restrict__ adj, int32_t* __restrict__ arow) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < D; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = key[j];
+        const int64_t p = row_ptr[v] + (j - lpre[v]);
+        adj[p] = val[j];
+        arow[p] = (int32_t)v;
+    }
+}
+
+// Upper entries (in dyad order: by row, then neighbour) after the lower ones.
+__global__ void k_place_up(const int32_t* __restrict__ row, const uint32_t* __restrict__ val, int64_t D,
+                           const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cnt_lo,
+                           const int32_t* __restrict__ upre, uint32_t* __restrict__ adj, int32_t* __restrict__ arow) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < D; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = row[j];
+        const int64_t p = row_ptr[u] + cnt_lo[u] + (j - upre[u]);
+        adj[p] = val[j];
+        arow[p] = u;
     }
 }
 
@@ -107,14 +152,11 @@ __global__ void k_fill_sent(uint32_t* __restrict__ p, int64_t count) {
         p[i] = SENT;
 }
 
-// Thread per row: degree, the row's split (entries below the row's own id:
-// from the first entry above it that k_write recorded for one graph, else by
-// binary search), and per-graph statistics from the row's degree and tag
-// counts (k_write counted the tags); a warp whose rows lie in one graph adds
+// Thread per row: degree, and per-graph statistics from the row's degree and tag
+// counts (k_dyads counted the tags); a warp whose rows lie in one graph adds
 // its sums with one atomic each.
-__global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
-                           const int32_t* __restrict__ vtag, const int64_t* __restrict__ voff, int G,
-                           int64_t total_n, int32_t* __restrict__ deg, int32_t* __restrict__ split,
+__global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ vtag,
+                           const int64_t* __restrict__ voff, int G, int64_t total_n, int32_t* __restrict__ deg,
                            unsigned long long* __restrict__ gstat /* [G][6] */) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -128,19 +170,6 @@ __global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const uint32_t* 
             const unsigned long long d = (unsigned long long)(row_ptr[x + 1] - b);
             deg[x] = (int32_t)d;
             g = G == 1 ? 0 : find_graph(voff, G, x);
-            if (G == 1) {  // k_write recorded the first entry above x (or -1: none)
-                const int32_t fu = split[x];
-                split[x] = fu < 0 ? (int32_t)d : (int32_t)(fu - b);
-            } else {
-                const uint32_t xl = (uint32_t)(x - voff[g]);
-                int lo = 0, hi = (int)d;  // entries with neighbour id below x
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if ((adj[b + mid] >> 2) < xl) lo = mid + 1;
-                    else hi = mid;
-                }
-                split[x] = lo;
-            }
             const int c1 = vtag[3 * x], c3 = vtag[3 * x + 2];
             v[0] = (unsigned long long)(c1 + c3);
             v[1] = d;
@@ -194,6 +223,17 @@ struct Scratch {
     }
 };
 
+// out = exclusive scan of in (count < 2^31 items, sums < 2^31).
+tc_status scan_i32(Scratch& S, const int32_t* in, int32_t* out, int64_t count, cudaStream_t st) {
+    if (count <= 0) return TC_OK;
+    size_t bytes = 0;
+    TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, (int)count, st));
+    void* tmp = nullptr;
+    TC_CUDA(S.get((char**)&tmp, bytes));
+    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, in, out, (int)count, st));
+    return TC_OK;
+}
+
 int grid_for(int64_t work, int threads) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -243,7 +283,8 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     TC_CUDA(dev_alloc((void**)&set->vtag, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(cudaMemsetAsync(set->vtag, 0, sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(dev_alloc((void**)&set->split, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
-    TC_CUDA(cudaMemsetAsync(set->split, 0xFF, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
+    // split = the row's lower count, counted by k_dyads
+    TC_CUDA(cudaMemsetAsync(set->split, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
     TC_CUDA(dev_alloc((void**)&set->arow, sizeof(int32_t) * (size_t)std::max<int64_t>(N, 1), st));
 
     Scratch S(st);
@@ -273,44 +314,54 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     TC_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * ((size_t)total_n + 1), st));
     TC_CUDA(cudaMemsetAsync(d_gstat, 0, sizeof(unsigned long long) * (6 * (size_t)G + 8), st));
 
-    int32_t* d_pos = nullptr;
-    int32_t nnz_host = 0;
-    if (N > 0) {
+    int64_t nnz_host = 0;
+    int32_t* cnt_up = nullptr;
+    TC_CUDA(S.get(&cnt_up, (size_t)std::max<int64_t>(total_n, 1)));
+    TC_CUDA(cudaMemsetAsync(cnt_up, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(total_n, 1), st));
+    int64_t D = 0;
+    int32_t* up_row = nullptr;
+    uint32_t *up_val = nullptr, *lk[2] = {nullptr, nullptr}, *lv[2] = {nullptr, nullptr};
+    if (m > 0) {
         uint64_t *k0 = nullptr, *k1 = nullptr;
-        int32_t* head = nullptr;
-        TC_CUDA(S.get(&k0, (size_t)N));
-        TC_CUDA(S.get(&k1, (size_t)N));
-        TC_CUDA(S.get(&head, (size_t)N));
-        TC_CUDA(S.get(&d_pos, (size_t)N));
-        k_keys<<<grid_for(m, 256), 256, 0, st>>>(d_src, d_dst, m, d_aoff, d_voff, G, sh, undirected ? 3u : 1u,
-                                                 undirected ? 3u : 2u, k0, d_err);
+        int32_t *head = nullptr, *dpos = nullptr;
+        TC_CUDA(S.get(&k0, (size_t)m));
+        TC_CUDA(S.get(&k1, (size_t)m));
+        TC_CUDA(S.get(&head, (size_t)m));
+        TC_CUDA(S.get(&dpos, (size_t)m));
+        k_dyad_keys<<<grid_for(m, 256), 256, 0, st>>>(d_src, d_dst, m, d_aoff, d_voff, G, sh, undirected, k0, d_err);
         TC_CUDA(cudaGetLastError());
         cub::DoubleBuffer<uint64_t> db(k0, k1);
         size_t tmp_bytes = 0;
-        TC_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, db, (int)N, 2, sh + rb, st));
+        TC_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, db, (int)m, 2, sh + rb, st));
         void* tmp = nullptr;
         TC_CUDA(S.get((char**)&tmp, tmp_bytes));
-        TC_CUDA(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, db, (int)N, 2, sh + rb, st));
+        TC_CUDA(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, db, (int)m, 2, sh + rb, st));
         const uint64_t* ks = db.Current();
-        k_heads<<<grid_for(N, 256), 256, 0, st>>>(ks, N, head);
+        k_heads<<<grid_for(m, 256), 256, 0, st>>>(ks, m, head);
         TC_CUDA(cudaGetLastError());
-        size_t scan_bytes = 0;
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, head, d_pos, (int)N, st));
-        void* tmp2 = nullptr;
-        TC_CUDA(S.get((char**)&tmp2, scan_bytes));
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp2, scan_bytes, head, d_pos, (int)N, st));
-        k_write<<<grid_for(N, 256), 256, 0, st>>>(ks, N, head, d_pos, sh, (uint32_t)((1ull << nb) - 1),
-                                                  set->adj, d_cnt, set->vtag, set->arow,
-                                                  G == 1 ? set->split : nullptr);
-        TC_CUDA(cudaGetLastError());
+        if (tc_status s2 = scan_i32(S, head, dpos, m, st); s2 != TC_OK) return s2;
         int32_t last_pos = 0, last_head = 0;
-        TC_CUDA(cudaMemcpyAsync(&last_pos, d_pos + N - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        TC_CUDA(cudaMemcpyAsync(&last_head, head + N - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaMemcpyAsync(&last_pos, dpos + m - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaMemcpyAsync(&last_head, head + m - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
-        nnz_host = last_pos + last_head;
+        D = (int64_t)last_pos + last_head;
+        TC_CUDA(S.get(&up_row, (size_t)D));
+        TC_CUDA(S.get(&up_val, (size_t)D));
+        for (int b = 0; b < 2; ++b) {
+            TC_CUDA(S.get(&lk[b], (size_t)D));
+            TC_CUDA(S.get(&lv[b], (size_t)D));
+        }
+        k_dyads<<<grid_for(m, 256), 256, 0, st>>>(ks, m, head, dpos, sh, (uint32_t)((1ull << nb) - 1), d_voff, G,
+                                                  up_row, up_val, lk[0], lv[0], cnt_up, set->split, set->vtag);
+        TC_CUDA(cudaGetLastError());
     }
+    nnz_host = 2 * D;
     set->nnz = nnz_host;
     // row_ptr = exclusive scan of the row counts (total_n + 1 items, last count 0)
+    if (total_n > 0) {
+        k_row_counts<<<grid_for(total_n, 256), 256, 0, st>>>(set->split, cnt_up, total_n, d_cnt);
+        TC_CUDA(cudaGetLastError());
+    }
     {
         size_t scan_bytes = 0;
         TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, d_cnt,
@@ -320,12 +371,33 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, scan_bytes, d_cnt,
                                               (unsigned long long*)set->row_ptr, (int)(total_n + 1), st));
     }
+    if (D > 0) {
+        // lower entries sorted by row (stable: the dyad order keeps each row's
+        // lower neighbours ascending)
+        cub::DoubleBuffer<uint32_t> dk(lk[0], lk[1]), dv(lv[0], lv[1]);
+        size_t tmp_bytes = 0;
+        TC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, dk, dv, (int)D, 0, rb, st));
+        void* tmp = nullptr;
+        TC_CUDA(S.get((char**)&tmp, tmp_bytes));
+        TC_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, dk, dv, (int)D, 0, rb, st));
+        int32_t *lpre = nullptr, *upre = nullptr;
+        TC_CUDA(S.get(&lpre, (size_t)total_n));
+        TC_CUDA(S.get(&upre, (size_t)total_n));
+        if (tc_status s2 = scan_i32(S, set->split, lpre, total_n, st); s2 != TC_OK) return s2;
+        if (tc_status s2 = scan_i32(S, cnt_up, upre, total_n, st); s2 != TC_OK) return s2;
+        k_place_lo<<<grid_for(D, 256), 256, 0, st>>>(dk.Current(), dv.Current(), D, set->row_ptr, lpre, set->adj,
+                                                     set->arow);
+        TC_CUDA(cudaGetLastError());
+        k_place_up<<<grid_for(D, 256), 256, 0, st>>>(up_row, up_val, D, set->row_ptr, set->split, upre, set->adj,
+                                                     set->arow);
+        TC_CUDA(cudaGetLastError());
+    }
     k_fill_sent<<<grid_for(ADJ_PAD + (N - nnz_host), 256), 256, 0, st>>>(set->adj + nnz_host,
                                                                         ADJ_PAD + (N - nnz_host));
     TC_CUDA(cudaGetLastError());
     if (total_n > 0) {
-        k_rowstats<<<grid_for(total_n, 256), 256, 0, st>>>(set->row_ptr, set->adj, set->vtag, d_voff, G,
-                                                          total_n, set->deg, set->split, d_gstat);
+        k_rowstats<<<grid_for(total_n, 256), 256, 0, st>>>(set->row_ptr, set->vtag, d_voff, G, total_n, set->deg,
+                                                          d_gstat);
         TC_CUDA(cudaGetLastError());
     }
     std::vector<unsigned long long> gstat(6 * (size_t)G);
