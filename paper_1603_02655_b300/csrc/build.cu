@@ -154,12 +154,48 @@ __global__ void k_fill_sent(uint32_t* __restrict__ p, int64_t count) {
 
 // Thread per row: degree, and per-graph statistics from the row's degree and tag
 // counts (k_dyads counted the tags); a warp whose rows lie in one graph adds
-// its sums with one atomic each.
+// its sums with one atomic each (one graph: a block adds its sums once).
 __global__ void k_rowstats(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ vtag,
                            const int64_t* __restrict__ voff, int G, int64_t total_n, int32_t* __restrict__ deg,
                            unsigned long long* __restrict__ gstat /* [G][6] */) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    if (G == 1) {  // one graph: per-thread sums, then one atomic per block and statistic
+        unsigned long long v[5] = {0, 0, 0, 0, 0};  // arcs, degree, 2 x mutual, degree^2, max degree
+        for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total_n;
+             x += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t b = row_ptr[x];
+            const unsigned long long d = (unsigned long long)(row_ptr[x + 1] - b);
+            deg[x] = (int32_t)d;
+            const int c1 = vtag[3 * x], c3 = vtag[3 * x + 2];
+            v[0] += (unsigned long long)(c1 + c3);
+            v[1] += d;
+            v[2] += (unsigned long long)c3;
+            v[3] += d * d;
+            v[4] = v[4] > d ? v[4] : d;
+        }
+        __shared__ unsigned long long part[5][32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(full, v[q], o);
+            const unsigned long long t = __shfl_xor_sync(full, v[4], o);
+            v[4] = v[4] > t ? v[4] : t;
+        }
+        const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        if (lane == 0)
+            for (int q = 0; q < 5; ++q) part[q][warp] = v[q];
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            const int q = threadIdx.x;
+            unsigned long long a = 0;
+            for (int w = 0; w < nw; ++w) a = q == 4 ? (a > part[q][w] ? a : part[q][w]) : a + part[q][w];
+            if (a) {
+                if (q == 4) atomicMax(gstat + 4, a);
+                else atomicAdd(gstat + q, a);
+            }
+        }
+        return;
+    }
     for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x; x0 < total_n; x0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t x = x0 + threadIdx.x;
         const bool valid = x < total_n;
