@@ -96,11 +96,11 @@ tc_status tc_opts_default(tc_opts* o) {
     if (!o) return tc::fail(TC_ERR_ARG, "tc_opts_default: null");
     *o = tc_opts{};
     o->bin_mode = TC_BIN_HEURISTIC;
-    o->thr_thread = 128;
+    o->thr_thread = 192;
     o->thr_warp = 256;
     o->chunk = 1024;
     o->stream_max = 1 << 30;
-    o->persistent = 1;
+    o->persistent = 0;
     o->hub_ratio = 1;
     o->own_min = 128;
     return TC_OK;
