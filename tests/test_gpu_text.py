@@ -114,3 +114,19 @@ def test_errors(text, status):
     with pytest.raises(tc.TcError) as e:
         tc.tc_graph_build_text(text, 1)
     assert e.value.status == status
+
+
+def test_tiny_and_empty_inputs():
+    # n < 3: every count 0; an order without arcs: all triads null; a section
+    # header without lines; the 64-code census agrees
+    for text, n in (("*Vertices 0\n", 0), ("*Vertices 2\n*Arcs\n1 2\n", 2), ("*Vertices 5\n*Arcs\n", 5),
+                    ("*Vertices 4\n*Edges\n% nothing\n\n", 4)):
+        g = tc.tc_graph_build_text(text, 1)
+        try:
+            want = [0] * 16
+            want[0] = n * (n - 1) * (n - 2) // 6 if n >= 3 else 0
+            assert tc.tc_census(g) == want, text
+            codes = tc.tc_census_codes(g)
+            assert codes[0] == want[0] and sum(codes[1:]) == 0, text
+        finally:
+            tc.tc_graph_free(g)
