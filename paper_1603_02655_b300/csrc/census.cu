@@ -408,7 +408,7 @@ __global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __re
 // in another graph than the warp's accumulators add directly.
 constexpr int FLAT_RUN = 2048;
 
-__global__ void __launch_bounds__(256, 3) k_tasks_flat(const int64_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict__ row_ptr,
                                                     const uint32_t* __restrict__ adj,
                                                     const int32_t* __restrict__ arow,
                                                     const int32_t* __restrict__ deg,
