@@ -406,7 +406,7 @@ __global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __re
 // Warps take runs of FLAT_RUN entries of the selected graphs' concatenated
 // adjacency (graph boundaries rarely fall inside one); lanes whose entry lies
 // in another graph than the warp's accumulators add directly.
-constexpr int FLAT_RUN = 2048;
+constexpr int FLAT_RUN = 1024;
 
 __global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict__ row_ptr,
                                                     const uint32_t* __restrict__ adj,
