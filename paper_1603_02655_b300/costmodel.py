@@ -8,7 +8,7 @@
    predicting log2(cycles) per bin.
 4. `evaluate`: held-out error of the network against the degree-sum rule of
    the thesis (Sec. 4.3.1: cost |N(u)|+|N(v)|-2), fitted per bin as
-   log2(cycles) ~ a + b log2(|N(u)|+|N(v)|) -- the judge of the network.
+   log2(cycles) ~ a + b log2(|N(u)|+|N(v)|) -- the yardstick of the network.
 5. `install`: FP16 weights used by census binning (bin_mode = TC_BIN_MLP).
 """
 from __future__ import annotations

@@ -192,7 +192,7 @@ def test_union_sizes_match_definition():
             tc.tc_graph_free(g)
 
 
-def test_pipeline_trains_and_reports_the_judge():
+def test_pipeline_trains_and_reports_its_gain():
     a = synth.rmat(16, 8, recip=0.1, seed=9)
     g = tc.tc_graph_build(a.n, a.src, a.dst)
     try:
