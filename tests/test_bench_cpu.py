@@ -66,3 +66,38 @@ def test_max_over_ranks_gloo():
         assert p.exitcode == 0
     res = dict(q.get() for _ in range(2))
     assert res == {0: 11.0, 1: 11.0}
+
+
+def test_oracle_sample_ranges_are_sized_and_bounded():
+    # the CPU-baseline sample: vertex costs = merged entries charged to each
+    # lower endpoint; ranges of about the target cost, heavy ones left out,
+    # and a timed sample that stays near its time budget
+    import time
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    a = synth.rmat(12, 8, recip=0.1, seed=3)
+    cost = bench.vertex_costs(a)
+    s, d = a.src.astype(np.int64), a.dst.astype(np.int64)
+    keep = s != d
+    u, v = np.minimum(s[keep], d[keep]), np.maximum(s[keep], d[keep])
+    pairs = np.unique(u * a.n + v)
+    deg = np.bincount(pairs // a.n, minlength=a.n) + np.bincount(pairs % a.n, minlength=a.n)
+    assert cost.sum() == float((deg.astype(np.int64) ** 2).sum())  # sum over dyads of d_u + d_v
+    rng = np.random.default_rng(0)
+    target, cap = cost.sum() / 50, cost.sum() / 10
+    ranges, skipped = bench.cost_ranges(cost, target, cap, rng)
+    covered = np.zeros(a.n, bool)
+    for lo, hi, c in ranges:
+        assert 0 <= lo < hi <= a.n and 0 < c <= cap
+        assert abs(c - cost[lo:hi].sum()) < 1e-6 * max(1.0, c)
+        assert not covered[lo:hi].any()
+        covered[lo:hi] = True
+    every, none = bench.cost_ranges(cost, target, float("inf"), np.random.default_rng(0))
+    assert none == 0 and skipped == sum(1 for r in every if r[2] > cap)
+    assert len(ranges) + skipped == len(every)
+    t = time.perf_counter()
+    rate, threads, verts, ents, wall, _ = bench.oracle_sample_rate(a, 1.0, threads=2, cost=cost)
+    assert rate > 0 and ents > 0 and verts > 0 and threads == 2
+    assert time.perf_counter() - t < 60
