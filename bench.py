@@ -196,7 +196,7 @@ def cost_ranges(cost, target, cap, rng):
     return [out[k] for k in order], skipped
 
 
-def oracle_sample_rate(arcs, seconds, threads=None, cost=None, seed=0):
+def oracle_sample_rate(arcs, seconds, threads=None, cost=None, seed=0, og=None):
     """Run the oracle census on random disjoint vertex ranges (the dyads whose
     lower endpoint lies in a range) on `threads` host threads, the ranges
     chosen by their merged entries so that the run takes about `seconds` of
@@ -206,7 +206,9 @@ def oracle_sample_rate(arcs, seconds, threads=None, cost=None, seed=0):
     threads = threads or os.cpu_count() or 1
     rng = np.random.default_rng(seed)
     cost = vertex_costs(arcs) if cost is None else cost
-    og = oracle.Graph(arcs.n, arcs.src, arcs.dst)
+    own = og is None  # an oracle graph built here is freed here
+    if own:
+        og = oracle.Graph(arcs.n, arcs.src, arcs.dst)
     # calibrate the single-thread rate on ~0.25 s of small ranges
     cal, _ = cost_ranges(cost, 2e5, 2e7, rng)
     e_cal, t = 0, time.perf_counter()
@@ -244,7 +246,8 @@ def oracle_sample_rate(arcs, seconds, threads=None, cost=None, seed=0):
     for th in pool:
         th.join()
     wall = time.perf_counter() - t
-    og.close()
+    if own:
+        og.close()
     return done["entries"] / max(wall, 1e-9), threads, done["vertices"], done["entries"], wall, skipped
 
 
@@ -304,7 +307,7 @@ def run_reference(args, world, rank, pg):
     rates, walls = [], []
     cost = vertex_costs(arcs)
     for i in range(args.warmup + args.steps):
-        rate, thr, verts, ents, wall, skipped = oracle_sample_rate(arcs, per_step_s, threads, cost, seed=i)
+        rate, thr, verts, ents, wall, skipped = oracle_sample_rate(arcs, per_step_s, threads, cost, seed=i, og=og)
         if i >= args.warmup:
             rates.append(rate)
             walls.append(wall)
