@@ -39,7 +39,7 @@ WORKLOAD_DESC = {
     "c4": "4096 graphs, n log-uniform in [64, 65536], even G(n,p) mean out-degree U(4,32), odd R-MAT edge factor 8, reciprocity U(0,0.5), seed 4",
     "c5": "Chung-Lu n=2^22 gamma 2.1 mean total degree 16 max 1e5 reciprocity 0.15, seed 5",
 }
-OWN_BUILD_KERNELS = 5   # k_keys k_heads k_write k_fill_sent k_rowstats (plus CUB sort/scan)
+OWN_BUILD_KERNELS = 8   # k_dyad_keys k_heads k_dyads k_row_counts k_place_lo k_place_up k_fill_sent k_rowstats (plus CUB sort/scan)
 FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
 
