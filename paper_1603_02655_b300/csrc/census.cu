@@ -40,6 +40,8 @@
 #include <mutex>
 
 #include <cub/device/device_scan.cuh>
+#include <thrust/iterator/counting_iterator.h>
+#include <thrust/iterator/transform_iterator.h>
 
 #include "mlp.cuh"
 #include "tc_internal.cuh"
@@ -368,17 +370,21 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
 constexpr int TAG_BITS = 21;
 constexpr unsigned long long TAG_MASK = (1ull << TAG_BITS) - 1;
 
-// One-hot tag words of the selected graphs' entries, in the order of their
-// concatenation (position f; entry k = the graph's first entry + offset).
-__global__ void k_onehot(const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
-                         const int64_t* __restrict__ epfx, int nseg, int64_t total,
-                         unsigned long long* __restrict__ out) {
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+// The one-hot tag word of entry f of the selected graphs' entries (in the
+// order of their concatenation; entry k = the graph's first entry + offset),
+// computed as the scan reads it (no array of words is written).
+struct OneHot {
+    const uint32_t* adj;
+    const SegDev* seg;
+    const int64_t* epfx;
+    int nseg;
+    __device__ unsigned long long operator()(int64_t f) const {
         const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
         const uint32_t t = __ldg(adj + seg[s].eb + (f - epfx[s])) & 3u;  // 1, 2 or 3
-        out[f] = 1ull << (TAG_BITS * (t - 1));
+        return 1ull << (TAG_BITS * (t - 1));
     }
-}
+};
+using OneHotIt = thrust::transform_iterator<OneHot, thrust::counting_iterator<int64_t>, unsigned long long>;
 
 // Thread per row of the selected graphs: register each owner's work items.
 __global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
@@ -2192,8 +2198,9 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.scan_bytes = 0;
     Lo.flat = Lo.flat && Lo.entries > 0;
     if (Lo.flat)
-        TC_CUDA(cub::DeviceScan::InclusiveSum(nullptr, Lo.scan_bytes, (unsigned long long*)nullptr,
-                                              (unsigned long long*)nullptr, (int)Lo.entries, (cudaStream_t)0));
+        TC_CUDA(cub::DeviceScan::InclusiveSum(
+            nullptr, Lo.scan_bytes, OneHotIt(thrust::counting_iterator<int64_t>(0), OneHot{nullptr, nullptr, nullptr, 1}),
+            (unsigned long long*)nullptr, (int)Lo.entries, (cudaStream_t)0));
     Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat ? (size_t)Lo.entries : 1));
     Lo.o_scantmp = take(std::max<size_t>(Lo.scan_bytes, 16));
     Lo.need = off;
@@ -2252,10 +2259,9 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         if (Lo.flat) {
             unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
             const int64_t* d_epfx = (const int64_t*)(ws + Lo.o_epfx);
-            k_onehot<<<L.sms * 8, 256, 0, st>>>(set.adj, d_seg, d_epfx, Lo.nseg, Lo.entries, scan);
-            TC_CUDA(cudaGetLastError());
             size_t sb = Lo.scan_bytes;
-            TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, scan, scan, (int)Lo.entries, st));
+            const OneHotIt words(thrust::counting_iterator<int64_t>(0), OneHot{set.adj, d_seg, d_epfx, Lo.nseg});
+            TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, words, scan, (int)Lo.entries, st));
             if (bp.own_min > 0) {
                 k_owner_rows<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, bp.own_min, bins);
                 TC_CUDA(cudaGetLastError());
@@ -2367,7 +2373,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
-    const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 3 : 2) : 1;  // k_onehot, k_owner_rows, k_tasks_flat
+    const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 2 : 1) : 1;  // k_owner_rows, k_tasks_flat
     return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0);
 }
 
