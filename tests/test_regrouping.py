@@ -33,20 +33,16 @@ def swap(t):
 CASES = [(1, 8, 0.3), (2, 12, 0.4), (3, 15, 0.25), (4, 20, 0.5), (5, 10, 0.8), (6, 25, 0.15)]
 
 
-@pytest.mark.parametrize("seed,n,p", CASES)
-def test_suffix_terms_plus_triangle_corrections_give_the_codes(seed, n, p):
-    tag, nb, _, _ = digraph(seed, n, p)
-    want = [0] * 64
+def regrouped(tag, nb, n, drop=None):
+    """Per-code counts from the suffix terms and the once-per-triangle
+    corrections; `drop` names one correction to leave out (a planted
+    mistake the test must notice)."""
     got = [0] * 64
     for u in range(n):
         for v in nb[u]:
             if v <= u:
                 continue
             pre = tag(u, v)
-            S = (set(nb[u]) | set(nb[v])) - {u, v}
-            for w in S:  # the canonical test and the code, as defined
-                if v < w or (u < w < v and w not in nb[u]):
-                    want[pre + 4 * tag(u, w) + 16 * tag(v, w)] += 1
             for w in nb[u]:  # suffix of A after v, as if tag_v(w) = 0
                 if w > v:
                     got[pre + 4 * tag(u, w)] += 1
@@ -56,11 +52,41 @@ def test_suffix_terms_plus_triangle_corrections_give_the_codes(seed, n, p):
             for w in set(nb[u]) & set(nb[v]):  # each triangle once, by its lowest dyad
                 if w > v:
                     tu, tv = tag(u, w), tag(v, w)
-                    got[pre + 4 * tu] -= 1
-                    got[pre + 16 * tv] -= 1
-                    got[pre + 4 * tu + 16 * tv] += 1
-                    got[tu + 16 * swap(tv)] -= 1  # dyad <u,w>, middle vertex v
-    assert got == want
+                    if drop != "a":
+                        got[pre + 4 * tu] -= 1
+                    if drop != "b":
+                        got[pre + 16 * tv] -= 1
+                    if drop != "joint":
+                        got[pre + 4 * tu + 16 * tv] += 1
+                    if drop != "middle":
+                        got[tu + 16 * swap(tv)] -= 1  # dyad <u,w>, middle vertex v
+    return got
+
+
+def defined(tag, nb, n):
+    want = [0] * 64
+    for u in range(n):
+        for v in nb[u]:
+            if v <= u:
+                continue
+            pre = tag(u, v)
+            S = (set(nb[u]) | set(nb[v])) - {u, v}
+            for w in S:  # the canonical test and the code, as defined
+                if v < w or (u < w < v and w not in nb[u]):
+                    want[pre + 4 * tag(u, w) + 16 * tag(v, w)] += 1
+    return want
+
+
+@pytest.mark.parametrize("drop", ["a", "b", "joint", "middle"])
+def test_each_correction_is_needed(drop):
+    tag, nb, _, _ = digraph(4, 20, 0.5)
+    assert regrouped(tag, nb, 20, drop) != defined(tag, nb, 20)
+
+
+@pytest.mark.parametrize("seed,n,p", CASES)
+def test_suffix_terms_plus_triangle_corrections_give_the_codes(seed, n, p):
+    tag, nb, _, _ = digraph(seed, n, p)
+    assert regrouped(tag, nb, n) == defined(tag, nb, n)
 
 
 @pytest.mark.parametrize("seed,n,p", CASES)
