@@ -123,8 +123,24 @@ typedef struct {
     int32_t row_tasks;    /* 1: compute the per-dyad terms with one warp per row
                              (the path used anyway when a row has 2^21 or more
                              entries); 0: one thread per adjacency entry */
-    int32_t reserved[1];  /* must be zero */
+    int32_t tri_path;     /* how the shared neighbours of the dyads (the
+                             triangles) are found:
+                             TC_TRI_FORWARD (0, default): each triangle once,
+                             from degree-ranked forward lists (vertices ranked
+                             by (floor(log2 degree), id); a dyad's owner is its
+                             higher-ranked endpoint);
+                             TC_TRI_MERGE (1): per-dyad owner lookups and merge
+                             bins, tuned by the fields above (own_min,
+                             thr_thread, thr_warp, chunk, stream_max, hub_ratio,
+                             persistent, split_cta, bin_mode) */
+    int32_t fwd_big;      /* TC_TRI_FORWARD: owners with at least fwd_big forward
+                             neighbours (and at most 2^17 vertices ranked above
+                             them) get a CTA and an exact tag map of their
+                             forward list in shared memory; the others a
+                             binary search per lookup.  >= 1; default 32 */
 } tc_opts;
+
+enum { TC_TRI_FORWARD = 0, TC_TRI_MERGE = 1 };
 
 /* Per-kernel timing and binning of the calling thread's most recent
  * tc_census / tc_census_batched call made with opts.profile = 1. */
@@ -134,7 +150,7 @@ typedef struct {
     float ms_tiles;          /* tiles of split tasks (k_warp or k_cta) */
     float ms_stream;         /* streamed tasks (k_stream); with persistent = 1
                                 only the hub tasks */
-    float ms_owner;          /* owner tasks (k_owner) */
+    float ms_owner;          /* owner lookups (k_owner alone) */
     float ms_warp;           /* whole tasks, one warp each (k_warp) */
     float ms_thread;         /* thread-per-task merges (k_thread) */
     float ms_merge;          /* the whole merge phase (all merge kernels, or k_merge) */
@@ -152,8 +168,20 @@ typedef struct {
     int64_t owner_tasks;     /* dyads it handled (in no bin) */
     int64_t owner_entries;   /* their |N(u)|+|N(v)| */
     int64_t owner_probes;    /* lookups: entries of the non-owner endpoints'
-                                lists above min(u, v) */
+                                lists above max(u, v) */
     int64_t owner_staged;    /* owner-list entries staged */
+    /* TC_TRI_FORWARD (the merge-path fields above are then zero): */
+    float ms_forward;        /* vertex ranks, forward lists and dyad records */
+    float ms_tri_map;        /* lookups of tag-map owners (k_tri_big) */
+    float ms_tri_search;     /* lookups of the other owners (k_tri_small) */
+    float ms_owner_prep;     /* TC_TRI_MERGE: the owner dyads' lookup ranges
+                                (k_owner_prep), not part of ms_owner */
+    int64_t fwd_entries;     /* forward-list entries (= dyads) */
+    int64_t map_items;       /* tag-map work items (pieces of <= 1024 dyads) */
+    int64_t map_lookups;     /* suffix entries looked up in tag maps */
+    int64_t map_triangles;   /* triangles found there */
+    int64_t search_lookups;  /* suffix entries looked up by binary search */
+    int64_t search_triangles;
 } tc_profile_t;
 
 tc_status tc_census_profile(tc_profile_t* out);
@@ -193,8 +221,8 @@ tc_status tc_graph_build(int32_t n, const int32_t* src, const int32_t* dst, int6
 
 /*
  * tc_graph_build_text -- a graph from a network file in the Pajek-style text
- * format the thesis reads (Sec. 3.1, "Implementation details": the order of
- * the graph, optional labelled vertex lines, then arcs of a directed or edges
+ * format the thesis reads (Sec. 4.2.1, "Implementation details": the order
+ * of the graph, optional labelled vertex lines, then arcs of a directed or edges
  * of an undirected graph told apart by the section keyword; Sec. 5.1.1:
  * 0- or 1-based ids), parsed on the device, then built as tc_graph_build.
  *   text, bytes  the file's bytes (host memory or, with TC_DEVICE_PTRS,
@@ -282,18 +310,26 @@ tc_status tc_census_codes_batched(int32_t G, const tc_graph* gs, const tc_opts* 
  *            be copied out with tc_graph_export).  No padding is required.
  *   nnz      row_ptr[n] (= 2 * dyads), with nnz/2 <= TC_NOALLOC_MAX_DYADS.
  *   out      device tc_census_t, written by the call.
- *   stream   the work runs on it; the call synchronises it before returning
- *            (it reads back a capacity check).
+ *   stream   the work runs on it.  The call synchronises it twice (it reads
+ *            back the CSR checks, then a capacity check), so it must never be
+ *            made while `stream` is being captured into a CUDA graph: it then
+ *            returns TC_ERR_ARG before enqueuing anything.
  * Scratch: a fixed area of about 5 MB compiled into the library as a static
  * device array; every GPU that loads the library holds it until the process
- * exits.  The first call on a device looks up its device address (set-up);
- * make that first call before any stream capture.  All calls share the one
- * area and it keeps the previous call's contents (the call clears what must
- * start at zero), so calls that overlap on the GPU -- from two streams or two
- * host threads -- race: serialise them.
- * Errors: TC_ERR_ARG (null pointers, negative or odd nnz), TC_ERR_UNSUPPORTED
- * (n or nnz/2 beyond the maxima, or the CSR holds more dyads than nnz/2),
- * TC_ERR_CUDA.
+ * exits.  Each call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing; the first call on a
+ * device loads the library's kernels there), so the address stays right
+ * after the caller resets the device.  All calls share the one area and it
+ * keeps the previous call's contents (the call clears what must start at
+ * zero), so calls that overlap on the GPU -- from two streams or two host
+ * threads -- race: serialise them.
+ * Checks made on the device before any census kernel runs: row_ptr[0] == 0,
+ * row_ptr[n] == nnz, no row offset decreases, every neighbour id < n.
+ * Errors: TC_ERR_ARG (null pointers, negative or odd nnz, row offsets that
+ * fail the checks, a capturing stream), TC_ERR_ID_RANGE (a neighbour id
+ * outside [0, n)), TC_ERR_UNSUPPORTED (n or nnz/2 beyond the maxima, or the
+ * CSR lists more canonical dyads than nnz/2, i.e. it is not symmetric; the
+ * census is then not written correctly), TC_ERR_CUDA.
  */
 #define TC_NOALLOC_MAX_N 262144
 #define TC_NOALLOC_MAX_DYADS 262144

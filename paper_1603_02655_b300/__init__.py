@@ -33,6 +33,7 @@ TYPE_NAMES = ("003", "012", "102", "021D", "021U", "021C", "111D", "111U",
 
 TC_OK, TC_ERR_ARG, TC_ERR_ID_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED = range(7)
 TC_BIN_HEURISTIC, TC_BIN_MLP = 0, 1
+TC_TRI_FORWARD, TC_TRI_MERGE = 0, 1
 TC_DEVICE_PTRS = 1
 TC_UNDIRECTED = 4
 TC_OUT_DEVICE = 2
@@ -81,7 +82,7 @@ class TcOpts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("split_cta", ctypes.c_int32),
                 ("stream_max", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("hub_ratio", ctypes.c_int32), ("own_min", ctypes.c_int32),
-                ("row_tasks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("row_tasks", ctypes.c_int32), ("tri_path", ctypes.c_int32), ("fwd_big", ctypes.c_int32)]
 
 
 class TcProfile(ctypes.Structure):
@@ -95,7 +96,12 @@ class TcProfile(ctypes.Structure):
                 ("chunks", ctypes.c_int64), ("hub_tasks", ctypes.c_int64),
                 ("hub_entries", ctypes.c_int64), ("owner_items", ctypes.c_int64),
                 ("owner_tasks", ctypes.c_int64), ("owner_entries", ctypes.c_int64),
-                ("owner_probes", ctypes.c_int64), ("owner_staged", ctypes.c_int64)]
+                ("owner_probes", ctypes.c_int64), ("owner_staged", ctypes.c_int64),
+                ("ms_forward", ctypes.c_float), ("ms_tri_map", ctypes.c_float),
+                ("ms_tri_search", ctypes.c_float), ("ms_owner_prep", ctypes.c_float),
+                ("fwd_entries", ctypes.c_int64), ("map_items", ctypes.c_int64),
+                ("map_lookups", ctypes.c_int64), ("map_triangles", ctypes.c_int64),
+                ("search_lookups", ctypes.c_int64), ("search_triangles", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -356,7 +362,22 @@ def tc_census_profile() -> dict:
 def tc_census_csr_noalloc(n: int, row_ptr, adj, nnz: int, out, stream=None):
     """Census of a caller-held device CSR (row_ptr int64[n+1], adj 32-bit
     [nnz] CUDA tensors) into `out` (CUDA int64 tensor of >= 17 words), using
-    only the library's fixed scratch area: no device allocation."""
+    only the library's fixed scratch area: no device allocation.  The
+    tensors are checked here (device, dtype, contiguity, length) so that the
+    kernels never read or write past them."""
+    def need(ok, what):
+        if not ok:
+            raise TcError(TC_ERR_ARG, "tc_census_csr_noalloc: " + what)
+    import torch
+    need(int(n) >= 0 and int(nnz) >= 0, "negative size")
+    for name, t, dts in (("row_ptr", row_ptr, (torch.int64,)), ("adj", adj, (torch.int32, torch.uint32)),
+                         ("out", out, (torch.int64, torch.uint64))):
+        need(isinstance(t, torch.Tensor) and t.is_cuda, f"{name} must be a CUDA tensor")
+        need(t.dtype in dts, f"{name} has dtype {t.dtype}")
+        need(t.is_contiguous(), f"{name} must be contiguous")
+    need(row_ptr.numel() >= int(n) + 1, "row_ptr holds fewer than n+1 offsets")
+    need(adj.numel() >= int(nnz), "adj holds fewer than nnz entries")
+    need(out.numel() >= 17, "out holds fewer than 17 words")
     p_adj = adj.data_ptr() if nnz else None
     st = load().tc_census_csr_noalloc(int(n), row_ptr.data_ptr(), p_adj, int(nnz), out.data_ptr(),
                                       _stream(stream))
@@ -399,7 +420,7 @@ def tc_autotune(gs, base: TcOpts | None = None, max_trials: int = 0, stream=None
 
 
 TUNED_FIELDS = ("bin_mode", "thr_thread", "thr_warp", "chunk", "split_cta", "stream_max", "persistent",
-                "hub_ratio", "own_min")
+                "hub_ratio", "own_min", "tri_path", "fwd_big")
 
 
 def graph_class(stats: list) -> str:

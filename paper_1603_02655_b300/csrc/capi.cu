@@ -103,6 +103,8 @@ tc_status tc_opts_default(tc_opts* o) {
     o->persistent = 0;
     o->hub_ratio = 1;
     o->own_min = 128;
+    o->tri_path = TC_TRI_FORWARD;
+    o->fwd_big = 32;
     return TC_OK;
 }
 

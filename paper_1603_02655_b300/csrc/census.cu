@@ -77,7 +77,10 @@ __device__ __forceinline__ void record(const Instr* ins, uint32_t u, uint32_t v,
 thread_local tc_profile_t g_profile;
 thread_local bool g_profile_valid = false;
 
-constexpr int NEV = 9;  // profile marks: start, after tasks, split, owners, and the merge kernels, fold
+// profile marks: start, after the task pass, k_split (forward path: the
+// forward lists), the owner prep (k_tri_big), k_owner (k_tri_small), the
+// four merge kernels, k_fold
+constexpr int NEV = 10;
 
 struct ProfileEvents {
     cudaEvent_t ev[NEV];
@@ -172,6 +175,7 @@ struct BinParams {
     int thr_thread, thr_warp, stream_max, own_min;
     const __half2* mlp;     // packed FP16 cost model, or null for the degree-sum rule
     const int32_t* vtag;    // per-vertex tag counts (model features)
+    int fwd;                // 1: the triangles come from the forward lists: emit no task
 };
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
             const int64_t x = rb + xl;
             const int64_t beg = row_ptr[x];
             const int d = deg[x];
-            if (bp.own_min > 0 && d >= bp.own_min && d <= OWN_MAX) {  // an owner: append its pieces
+            if (!bp.fwd && bp.own_min > 0 && d >= bp.own_min && d <= OWN_MAX) {  // an owner: append its pieces
                 const bool large = d > OWN_CAP;
                 const int np = (d + OWN_PIECE - 1) / OWN_PIECE;
                 unsigned k = 0;
@@ -313,7 +317,8 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
 #pragma unroll
                     for (int q = 0; q < 3; ++q) Dd[q] += pre_task == q + 1 ? dy : 0ull;
                     const int dh = max(d, dv);
-                    if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
+                    if (bp.fwd) {
+                    } else if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
                         Os[0] += 1;
                         Os[1] += (unsigned long long)L;
 
@@ -504,7 +509,8 @@ __global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict
                 L = d + dv;
                 dy = (unsigned long long)(sg.n - (int64_t)d - (int64_t)dv);
                 const int dh = max(d, dv);
-                if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
+                if (bp.fwd) {
+                } else if (bp.own_min > 0 && dh >= bp.own_min && dh <= OWN_MAX) {  // owner task
                     Os[0] += 1;
                     Os[1] += (unsigned long long)L;
                 } else {
@@ -2056,13 +2062,15 @@ __global__ void __launch_bounds__(OWN_NT, 2) k_owner(OwnArgs a) {
     w.flush();
 }
 
+#include "forward.cuh"
+
 // ------------------------------------------------------------- host side --
 constexpr int STREAM_EPL = 8;
 
 struct Launch {
     int sms = 148;
     int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1, occ_flat = 1;
-    int occ_owner = 1;
+    int occ_owner = 1, occ_tri_big = 1, occ_tri_small = 1;
     bool ready = false;
 };
 
@@ -2090,6 +2098,11 @@ tc_status launch_info(Launch& L) {
         TC_CUDA(cudaFuncSetAttribute(k_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OWN_SMEM));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_owner, k_owner, OWN_NT, OWN_SMEM));
         c.occ_owner = std::max(1, c.occ_owner);
+        TC_CUDA(cudaFuncSetAttribute(k_tri_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TB_SMEM));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_big, k_tri_big, TB_NT, TB_SMEM));
+        c.occ_tri_big = std::max(1, c.occ_tri_big);
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_small, k_tri_small, 256, 0));
+        c.occ_tri_small = std::max(1, c.occ_tri_small);
         c.ready = true;
     }
     L = c;
@@ -2115,6 +2128,14 @@ struct Layout {
     size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_codes, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, o_epfx,
         o_scan, o_scantmp, need;
     uint32_t own_cap = 0;
+    // forward path (tri_path = TC_TRI_FORWARD)
+    bool fwd = false;
+    int nb = 0;            // blocks of the rank computation
+    int64_t dyads = 0;     // canonical dyads of the selection
+    uint32_t item_cap = 0;
+    size_t fscan_bytes = 0;
+    size_t o_hist, o_hex, o_co, o_rank, o_perm, o_fs, o_fptr, o_nown, o_tptr, o_tcur, o_fid, o_fwd, o_trec, o_items,
+        o_fscantmp;
 };
 
 // counters (uint32 words): [0..3] records per bin, [4] overflow flag,
@@ -2124,7 +2145,9 @@ struct Layout {
 // 7 hub tasks, 8-9 task-build row cursor, 10-17 bin entries, 20-23 merge
 // cursors, 24-25 hub entries, 26-27 owner cursors, 28-29 owner rows (larger,
 // smaller), 32-39 owner tasks, merged entries, probes, staged entries.
-constexpr int CTR_WORDS = 40;
+// Forward path: 40 tag-map items, 42-43 work cursors, 44-51 lookups and
+// triangles of each lookup form (u64).
+constexpr int CTR_WORDS = 64;
 
 tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
                       Layout& Lo) {
@@ -2142,6 +2165,8 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     if (o.own_min < 0) return fail(TC_ERR_ARG, "census: own_min < 0");
     if (o.persistent && o.split_cta)
         return fail(TC_ERR_ARG, "census: the persistent merge runs warp tiles (split_cta must be 0)");
+    if (o.tri_path != TC_TRI_FORWARD && o.tri_path != TC_TRI_MERGE) return fail(TC_ERR_ARG, "census: unknown tri_path");
+    if (o.fwd_big < 1) return fail(TC_ERR_ARG, "census: fwd_big < 1");
     // a warp holds both lists (or the short list) in shared memory
     o.thr_warp = std::min(o.thr_warp, WARP_LMAX);
 
@@ -2179,10 +2204,24 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.o_pfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
     Lo.o_out = take(sizeof(tc_census_t) * (size_t)nseg);
     Lo.o_codes = take(sizeof(tc_census64_t) * (size_t)nseg);
-    for (int b = 0; b < NBIN; ++b) Lo.o_r[b] = take(sizeof(uint4) * Lo.cap01);
-    Lo.o_rt = o.bin_mode == TC_BIN_MLP ? take(sizeof(uint4) * Lo.cap01) : Lo.o_r[2];
-    Lo.o_tl = take(sizeof(uint4) * Lo.cap2);
-    Lo.o_ia = take(sizeof(int32_t) * Lo.cap2);
+    // per-entry task terms need every row below 2^21 entries (packed tag scan)
+    Lo.entries = Lo.epfx[(size_t)nseg];
+    // the forward path needs the per-entry rows and fewer than 2^31 entries
+    // (its scans count in int32); otherwise the merge path runs
+    Lo.fwd = o.tri_path == TC_TRI_FORWARD && set.arow != nullptr && Lo.rows > 0 && Lo.entries > 0 &&
+             Lo.entries < ((int64_t)1 << 31);
+    Lo.dyads = dyads;
+    // merge-path bins, tiles and owner tables (one record each when unused)
+    const uint64_t c01 = Lo.fwd ? 1 : Lo.cap01, c2 = Lo.fwd ? 1 : Lo.cap2;
+    for (int b = 0; b < NBIN; ++b) Lo.o_r[b] = take(sizeof(uint4) * c01);
+    Lo.o_rt = o.bin_mode == TC_BIN_MLP ? take(sizeof(uint4) * c01) : Lo.o_r[2];
+    Lo.o_tl = take(sizeof(uint4) * c2);
+    Lo.o_ia = take(sizeof(int32_t) * c2);
+    if (Lo.fwd) {
+        Lo.cap01 = Lo.cap2 = 1;
+        o.own_min = 0;
+        Lo.o.own_min = 0;
+    }
     // pieces: sum over owners of ceil(d / OWN_PIECE) <= rows + 2|U| / OWN_PIECE
     Lo.own_cap = (uint32_t)std::min<int64_t>(Lo.rows + 2 * dyads / OWN_PIECE + 1, 0xffffffffll);
     Lo.o_own = take(sizeof(uint4) * (o.own_min > 0 ? Lo.own_cap : 1));
@@ -2191,8 +2230,6 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     const size_t nprep = o.own_min > 0 ? (size_t)std::max<int64_t>(set.nnz, 1) : 1;
     Lo.o_psb = take(sizeof(int64_t) * nprep);
     Lo.o_plen = take(sizeof(int32_t) * nprep);
-    // per-entry task terms need every row below 2^21 entries (packed tag scan)
-    Lo.entries = Lo.epfx[(size_t)nseg];
     Lo.flat = !o.row_tasks && set.arow != nullptr && set.max_deg < (1 << TAG_BITS) && set.nnz > 0;
     Lo.o_epfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
     Lo.scan_bytes = 0;
@@ -2203,6 +2240,36 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
             (unsigned long long*)nullptr, (int)Lo.entries, (cudaStream_t)0));
     Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat ? (size_t)Lo.entries : 1));
     Lo.o_scantmp = take(std::max<size_t>(Lo.scan_bytes, 16));
+    // forward lists: ranks, forward entries, dyad records by owner
+    if (Lo.fwd) {
+        const size_t rows = (size_t)Lo.rows, D = (size_t)std::max<int64_t>(dyads, 1);
+        Lo.nb = (int)((Lo.rows + RK_B - 1) / RK_B);
+        Lo.item_cap = (uint32_t)std::min<int64_t>(Lo.rows + dyads / TRI_PIECE + 1, 0xffffffffll);
+        size_t b1 = 0, b2 = 0, b3 = 0;
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b1, (const uint32_t*)nullptr, (uint32_t*)nullptr,
+                                              NCLS * Lo.nb, (cudaStream_t)0));
+        TC_CUDA(cub::DeviceScan::InclusiveSum(
+            nullptr, b2, FwdFlagIt(thrust::counting_iterator<int64_t>(0), FwdFlag{}), (int32_t*)nullptr,
+            (int)Lo.entries, (cudaStream_t)0));
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b3, (const uint32_t*)nullptr, (uint32_t*)nullptr,
+                                              (int)(rows + 1), (cudaStream_t)0));
+        Lo.fscan_bytes = std::max(b1, std::max(b2, b3));
+        Lo.o_hist = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
+        Lo.o_hex = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
+        Lo.o_co = take(sizeof(int64_t) * NCLS * (size_t)nseg);
+        Lo.o_rank = take(sizeof(int32_t) * rows);
+        Lo.o_perm = take(sizeof(int32_t) * rows);
+        Lo.o_fs = take(sizeof(int32_t) * (size_t)Lo.entries);
+        Lo.o_fptr = take(sizeof(uint32_t) * (rows + 1));
+        Lo.o_nown = take(sizeof(uint32_t) * (rows + 1));
+        Lo.o_tptr = take(sizeof(uint32_t) * (rows + 1));
+        Lo.o_tcur = take(sizeof(uint32_t) * rows);
+        Lo.o_fid = take(sizeof(uint32_t) * D);
+        Lo.o_fwd = take(sizeof(uint32_t) * D);
+        Lo.o_trec = take(sizeof(uint4) * D);
+        Lo.o_items = take(sizeof(uint4) * (size_t)Lo.item_cap);
+        Lo.o_fscantmp = take(std::max<size_t>(Lo.fscan_bytes, 16));
+    }
     Lo.need = off;
     return TC_OK;
 }
@@ -2216,6 +2283,111 @@ tc_status upload_layout(const Layout& Lo, char* ws, cudaStream_t st) {
                             cudaMemcpyHostToDevice, st));
     TC_CUDA(cudaMemcpyAsync(ws + Lo.o_epfx, Lo.epfx.data(), sizeof(int64_t) * ((size_t)Lo.nseg + 1),
                             cudaMemcpyHostToDevice, st));
+    return TC_OK;
+}
+
+// The forward path (tri_path = TC_TRI_FORWARD): the task pass adds every
+// dyad's suffix and dyadic terms and emits no task; the vertex ranks, the
+// forward lists and the dyad records by owner are built; the two lookup
+// kernels apply each triangle's correction once.  Marks 1 (task pass), 2
+// (forward lists), 3 (tag-map owners), 4..7 (the other owners).
+template <class Mark>
+tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaStream_t st, const Launch& L,
+                          const BinParams& bp, const Bins& bins, Mark& mark) {
+    unsigned long long* acc = (unsigned long long*)(ws + Lo.o_acc);
+    unsigned int* ctr = (unsigned int*)(ws + Lo.o_ctr);
+    const SegDev* d_seg = (const SegDev*)(ws + Lo.o_seg);
+    const int64_t* d_pfx = (const int64_t*)(ws + Lo.o_pfx);
+    const int64_t* d_epfx = (const int64_t*)(ws + Lo.o_epfx);
+    unsigned long long* cursor = (unsigned long long*)(ctr + 8);
+    if (Lo.flat) {
+        unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
+        size_t sb = Lo.scan_bytes;
+        const OneHotIt words(thrust::counting_iterator<int64_t>(0), OneHot{set.adj, d_seg, d_epfx, Lo.nseg});
+        TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, words, scan, (int)Lo.entries, st));
+        k_tasks_flat<<<L.sms * L.occ_flat, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, set.vtag, scan,
+                                                         d_seg, d_epfx, Lo.nseg, Lo.entries, bp, bins, acc, cursor);
+    } else {
+        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
+                                                     bp, bins, acc, cursor);
+    }
+    TC_CUDA(cudaGetLastError());
+    mark(1);
+    // vertex ranks
+    uint32_t* hist = (uint32_t*)(ws + Lo.o_hist);
+    uint32_t* hex = (uint32_t*)(ws + Lo.o_hex);
+    int64_t* co = (int64_t*)(ws + Lo.o_co);
+    int32_t* rank = (int32_t*)(ws + Lo.o_rank);
+    int32_t* perm = (int32_t*)(ws + Lo.o_perm);
+    void* tmp = ws + Lo.o_fscantmp;
+    k_rank_hist<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hist);
+    TC_CUDA(cudaGetLastError());
+    size_t tb = Lo.fscan_bytes;
+    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, hist, hex, NCLS * Lo.nb, st));
+    k_rank_seg<<<std::min(Lo.nseg, L.sms * 16), 32, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co);
+    TC_CUDA(cudaGetLastError());
+    k_rank_assign<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co, rank, perm,
+                                          bins.overflow);
+    TC_CUDA(cudaGetLastError());
+    // forward lists and the dyad records by owner
+    FwdLayout F;
+    F.fs = (const int32_t*)(ws + Lo.o_fs);
+    F.fptr = (uint32_t*)(ws + Lo.o_fptr);
+    F.nown = (uint32_t*)(ws + Lo.o_nown);
+    F.tptr = (uint32_t*)(ws + Lo.o_tptr);
+    F.tcur = (uint32_t*)(ws + Lo.o_tcur);
+    F.fid = (uint32_t*)(ws + Lo.o_fid);
+    F.fwd = (uint32_t*)(ws + Lo.o_fwd);
+    F.trec = (uint4*)(ws + Lo.o_trec);
+    F.items = (uint4*)(ws + Lo.o_items);
+    F.item_cap = Lo.item_cap;
+    F.nitems = ctr + 40;
+    F.cursor = ctr + 42;
+    F.stat = (unsigned long long*)(ctr + 44);
+    F.rank = rank;
+    F.perm = perm;
+    tb = Lo.fscan_bytes;
+    const FwdFlagIt flags(thrust::counting_iterator<int64_t>(0),
+                          FwdFlag{set.adj, set.arow, d_seg, d_pfx, d_epfx, rank, Lo.nseg});
+    TC_CUDA(cub::DeviceScan::InclusiveSum(tmp, tb, flags, (int32_t*)(ws + Lo.o_fs), (int)Lo.entries, st));
+    TC_CUDA(cudaMemsetAsync(F.tcur, 0, sizeof(uint32_t) * (size_t)Lo.rows, st));
+    k_fwd_rows<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.deg, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.rows, Lo.o.fwd_big,
+                                           F);
+    TC_CUDA(cudaGetLastError());
+    tb = Lo.fscan_bytes;
+    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, F.nown, F.tptr, (int)(Lo.rows + 1), st));
+    k_fwd_ids<<<L.sms * 16, 256, 0, st>>>(set.adj, d_seg, d_epfx, Lo.nseg, Lo.entries, F);
+    TC_CUDA(cudaGetLastError());
+    k_fwd_sort<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, F);
+    TC_CUDA(cudaGetLastError());
+    mark(2);
+    TriArgs ta;
+    ta.seg = d_seg;
+    ta.pfx = d_pfx;
+    ta.nseg = Lo.nseg;
+    ta.rows = Lo.rows;
+    ta.big_min = Lo.o.fwd_big;
+    ta.fptr = F.fptr;
+    ta.tptr = F.tptr;
+    ta.nown = F.nown;
+    ta.fwd = F.fwd;
+    ta.trec = F.trec;
+    ta.items = F.items;
+    ta.nitems = F.nitems;
+    ta.item_cap = F.item_cap;
+    ta.cursor = F.cursor;
+    ta.rank = rank;
+    ta.perm = perm;
+    ta.acc = acc;
+    ta.stat = F.stat;
+    ta.ntrec = (uint32_t)Lo.dyads;
+    ta.err = bins.overflow;
+    k_tri_big<<<L.sms * L.occ_tri_big, TB_NT, TB_SMEM, st>>>(ta);
+    TC_CUDA(cudaGetLastError());
+    mark(3);
+    k_tri_small<<<L.sms * L.occ_tri_small, 256, 0, st>>>(ta);
+    TC_CUDA(cudaGetLastError());
+    for (int k = 4; k <= 7; ++k) mark(k);
     return TC_OK;
 }
 
@@ -2248,14 +2420,16 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     const __half2* mlp = o.bin_mode == TC_BIN_MLP ? (const __half2*)cost_model_weights() : nullptr;
     // with a cost model, every task above the warp bin is first collected in
     // bin 2 and then routed by k_route (stream bin or tiles)
-    const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, o.own_min, mlp, set.vtag};
+    const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, o.own_min, mlp, set.vtag, Lo.fwd ? 1 : 0};
     uint4* split_tasks = (uint4*)(ws + Lo.o_rt);
     auto mark = [&](int k) {
         if (pe) cudaEventRecord(pe->ev[k], st);
     };
     TC_CUDA(cudaMemsetAsync(ws, 0, Lo.o_seg, st));  // accumulators + counters
     mark(0);
-    if (Lo.rows > 0) {
+    if (Lo.fwd) {
+        if (tc_status r = enqueue_forward(set, Lo, ws, st, L, bp, bins, mark); r != TC_OK) return r;
+    } else if (Lo.rows > 0) {
         if (Lo.flat) {
             unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
             const int64_t* d_epfx = (const int64_t*)(ws + Lo.o_epfx);
@@ -2303,10 +2477,13 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             else
                 k_owner_prep<<<L.sms * 8, 256, 0, st>>>(oa);
             TC_CUDA(cudaGetLastError());
+            mark(3);
             k_owner<<<L.sms * L.occ_owner, OWN_NT, OWN_SMEM, st>>>(oa);
             TC_CUDA(cudaGetLastError());
+        } else {
+            mark(3);
         }
-        mark(3);
+        mark(4);
         auto hub_launch = [&]() {
             k_hub<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split,
                                                                               bins.rec[3], ctr + 7, bins.cap[3],
@@ -2329,15 +2506,15 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             q.split = set.split;
             q.ins = ins ? *ins : Instr{nullptr, nullptr, 0, 0};
             TC_CUDA(hub_launch());
-            mark(4);
+            mark(5);
             if (ins)
                 k_merge<STREAM_EPL, true><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
             else
                 k_merge<STREAM_EPL, false><<<L.sms * L.occ_merge, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, q, acc);
             TC_CUDA(cudaGetLastError());
-            mark(5);
             mark(6);
             mark(7);
+            mark(8);
         } else {
             if (o.split_cta)
                 k_cta<<<L.sms * L.occ_cta, CTA_NT, 0, st>>>(set.row_ptr, set.adj, d_seg, d_tiles, d_ia, ctr + 5, cap2,
@@ -2346,32 +2523,35 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
                 k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split, d_tiles, d_ia,
                                                             ctr + 5, cap2, o.chunk, acc);
             TC_CUDA(cudaGetLastError());
-            mark(4);
+            mark(5);
             k_stream<STREAM_EPL><<<L.sms * L.occ_stream, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split,
                                                                                bins.rec[3], ctr + 3, bins.cap[3], acc);
             TC_CUDA(cudaGetLastError());
             TC_CUDA(hub_launch());
-            mark(5);
+            mark(6);
             k_warp<<<L.sms * L.occ_warp, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split, bins.rec[1], nullptr,
                                                         ctr + 1, bins.cap[1], 0, acc);
             TC_CUDA(cudaGetLastError());
-            mark(6);
+            mark(7);
             k_thread<<<L.sms * L.occ_thread, 256, 0, st>>>(set.row_ptr, set.adj, d_seg, set.split, bins.rec[0],
                                                             ctr + 0, bins.cap[0], acc);
             TC_CUDA(cudaGetLastError());
         }
     } else {
-        for (int k = 1; k <= 6; ++k) mark(k);
+        for (int k = 1; k <= 7; ++k) mark(k);
     }
-    mark(7);
+    mark(8);
     k_fold<<<(Lo.nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, Lo.nseg, d_out, d_codes);
     TC_CUDA(cudaGetLastError());
-    mark(8);
+    mark(9);
     return TC_OK;
 }
 
+// Kernels of this library a census launches (the library scans not counted).
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
+    // task pass, 3 rank kernels, 3 forward-list kernels, 2 lookup kernels, k_fold
+    if (Lo.fwd) return 10;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
     const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 2 : 1) : 1;  // k_owner_rows, k_tasks_flat
     return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0);
@@ -2383,25 +2563,33 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     TC_CUDA(cudaStreamSynchronize(st));
     tc_profile_t& P = g_profile;
     P = tc_profile_t{};
-    // marks: 0 start, 1 tasks, 2 split, 3 owners, 4..7 merge kernels, 8 fold
+    // marks: 0 start, 1 tasks, 2 split (forward lists), 3 owner prep
+    // (tag-map owners), 4 owners (the other owners), 5..8 merge kernels, 9 fold
     float ms[NEV] = {0};
     for (int k = 0; k + 1 < NEV; ++k) TC_CUDA(cudaEventElapsedTime(&ms[k], pe->ev[k], pe->ev[k + 1]));
     float total = 0;
     TC_CUDA(cudaEventElapsedTime(&total, pe->ev[0], pe->ev[NEV - 1]));
     P.ms_tasks = ms[0];
-    P.ms_split = ms[1];
-    P.ms_owner = ms[2];
-    if (Lo.o.persistent) {
-        P.ms_stream = ms[3];          // hub tasks
-        P.ms_merge = ms[3] + ms[4];   // hub tasks + k_merge
+    if (Lo.fwd) {
+        P.ms_forward = ms[1];
+        P.ms_tri_map = ms[2];
+        P.ms_tri_search = ms[3];
     } else {
-        P.ms_tiles = ms[3];
-        P.ms_stream = ms[4];
-        P.ms_warp = ms[5];
-        P.ms_thread = ms[6];
-        P.ms_merge = ms[3] + ms[4] + ms[5] + ms[6];
+        P.ms_split = ms[1];
+        P.ms_owner_prep = ms[2];
+        P.ms_owner = ms[3];
+        if (Lo.o.persistent) {
+            P.ms_stream = ms[4];          // hub tasks
+            P.ms_merge = ms[4] + ms[5];   // hub tasks + k_merge
+        } else {
+            P.ms_tiles = ms[4];
+            P.ms_stream = ms[5];
+            P.ms_warp = ms[6];
+            P.ms_thread = ms[7];
+            P.ms_merge = ms[4] + ms[5] + ms[6] + ms[7];
+        }
     }
-    P.ms_fold = ms[7];
+    P.ms_fold = ms[8];
     P.ms_total = total;
     P.launches = census_launches(Lo);
     const bool routed = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights();
@@ -2418,6 +2606,14 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     P.owner_entries = u64(34);
     P.owner_probes = u64(36);
     P.owner_staged = u64(38);
+    if (Lo.fwd) {
+        P.fwd_entries = Lo.dyads;
+        P.map_items = std::min<int64_t>(c[40], Lo.item_cap);
+        P.map_lookups = u64(44);
+        P.map_triangles = u64(46);
+        P.search_lookups = u64(48);
+        P.search_triangles = u64(50);
+    }
     g_profile_valid = true;
     return TC_OK;
 }
@@ -2566,6 +2762,7 @@ constexpr int64_t NOALLOC_MAX_DYADS = TC_NOALLOC_MAX_DYADS;
 struct NoallocLayout {
     unsigned long long acc[ACC];  // per-code accumulators + dyadic slots
     unsigned int ctr[32];         // bin counters, capacity flag, row cursor, bin sums
+    unsigned int bad[4];          // CSR checks: [0] row offsets, [1] neighbour id outside [0, n)
     SegDev seg;                   // the single graph
     int64_t pfx[2];
     int32_t deg[NOALLOC_MAX_N];
@@ -2576,30 +2773,26 @@ struct NoallocLayout {
 // device object: kernels receive the address looked up below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocLayout)];
 
-std::mutex g_noalloc_mu;
-NoallocLayout* g_noalloc_ptr[64];
-
-// Set-up, once per device with that device current: the device address of
-// the scratch.
+// The device address of the scratch on the current device.  Looked up on
+// every call: cudaGetSymbolAddress allocates nothing once the module is
+// loaded on the device (the first call on a device loads it), and a fresh
+// lookup stays right after the caller resets the device, when the module is
+// loaded again and the array may sit elsewhere.
 tc_status noalloc_scratch(NoallocLayout** out) {
-    int dev = 0;
-    TC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: device index >= 64");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
-        g_noalloc_ptr[dev] = (NoallocLayout*)p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
+    *out = (NoallocLayout*)p;
     return TC_OK;
 }
 
-// Clears the accumulators and counters left by the previous call and fills
-// the graph descriptor and the degree array.
-__global__ void k_noalloc_init(NoallocLayout* s, const int64_t* __restrict__ row_ptr, int32_t n) {
+// Clears the accumulators and counters left by the previous call, fills the
+// graph descriptor and the degree array, and checks the caller's CSR: row
+// offsets from 0 to nnz without decreasing, every neighbour id in [0, n).
+__global__ void k_noalloc_init(NoallocLayout* s, const int64_t* __restrict__ row_ptr,
+                               const uint32_t* __restrict__ adj, int32_t n, int64_t nnz) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
     if (tid < ACC) s->acc[tid] = 0;
     if (tid < 32) s->ctr[tid] = 0;
     if (tid == 0) {
@@ -2610,9 +2803,15 @@ __global__ void k_noalloc_init(NoallocLayout* s, const int64_t* __restrict__ row
         s->seg.pad = 0;
         s->pfx[0] = 0;
         s->pfx[1] = n;
+        if (row_ptr[0] != 0 || row_ptr[n] != nnz) s->bad[0] = 1;
     }
-    for (int64_t x = tid; x < n; x += (int64_t)gridDim.x * blockDim.x)
-        s->deg[x] = (int32_t)(row_ptr[x + 1] - row_ptr[x]);
+    for (int64_t x = tid; x < n; x += step) {
+        const int64_t d = row_ptr[x + 1] - row_ptr[x];
+        if (d < 0) s->bad[0] = 1;
+        s->deg[x] = (int32_t)d;
+    }
+    for (int64_t k = tid; k < nnz; k += step)
+        if ((adj[k] >> 2) >= (uint32_t)n) s->bad[1] = 1;
 }
 
 tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj, int64_t nnz,
@@ -2623,16 +2822,29 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
         return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: n exceeds TC_NOALLOC_MAX_N (262144)");
     if (nnz / 2 > NOALLOC_MAX_DYADS)
         return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: nnz/2 exceeds TC_NOALLOC_MAX_DYADS (262144)");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    TC_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(TC_ERR_ARG, "tc_census_csr_noalloc: the stream is capturing (the call synchronises it)");
     NoallocLayout* s = nullptr;
     if (tc_status r = noalloc_scratch(&s); r != TC_OK) return r;
     Launch L;
     if (tc_status r = launch_info(L); r != TC_OK) return r;
-    k_noalloc_init<<<std::max(1, (int)std::min<int64_t>((n + 255) / 256, (int64_t)L.sms * 8)), 256, 0, st>>>(
-        s, row_ptr, n);
+    TC_CUDA(cudaMemsetAsync(s->bad, 0, sizeof(s->bad), st));
+    const int64_t span = std::max<int64_t>(n, nnz);
+    k_noalloc_init<<<std::max(1, (int)std::min<int64_t>((span + 255) / 256, (int64_t)L.sms * 8)), 256, 0, st>>>(
+        s, row_ptr, adj, n, nnz);
     TC_CUDA(cudaGetLastError());
+    unsigned int bad[2] = {0, 0};
+    TC_CUDA(cudaMemcpyAsync(bad, s->bad, sizeof(bad), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (bad[0])
+        return fail(TC_ERR_ARG, "tc_census_csr_noalloc: row_ptr does not run from 0 to nnz without decreasing");
+    if (bad[1]) return fail(TC_ERR_ID_RANGE, "tc_census_csr_noalloc: a neighbour id outside [0, n)");
     Bins bins;
     bins.rec[0] = bins.rec[1] = bins.rec[2] = bins.rec[3] = s->rec;
-    bins.cap[0] = (uint32_t)NOALLOC_MAX_DYADS;
+    // a well-formed CSR lists each dyad in both rows, so it has nnz/2 dyads
+    bins.cap[0] = (uint32_t)(nnz / 2);
     bins.cap[1] = bins.cap[2] = bins.cap[3] = 0;
     bins.cnt = s->ctr;
     bins.overflow = (int*)(s->ctr + 4);
@@ -2642,7 +2854,7 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
     bins.own_cap = 0;
     bins.own_cnt = nullptr;
     bins.own_stat = nullptr;
-    const BinParams bp{0x7fffffff, 0x7fffffff, 0, 0, nullptr, nullptr};
+    const BinParams bp{0x7fffffff, 0x7fffffff, 0, 0, nullptr, nullptr, 0};
     if (n > 0) {
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
                                                      s->acc, cursor);
@@ -2657,8 +2869,8 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
     TC_CUDA(cudaMemcpyAsync(&ovf, s->ctr + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));
     if (ovf)
-        return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: the CSR holds more dyads than nnz/2 says "
-                                        "(scratch capacity exceeded; result invalid)");
+        return fail(TC_ERR_UNSUPPORTED, "tc_census_csr_noalloc: the CSR holds more dyads than nnz/2 "
+                                        "(not symmetric; result invalid)");
     return TC_OK;
 }
 
@@ -2822,8 +3034,12 @@ tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t m
     };
     float cur_ms = 0;
     if (tc_status s = timeit(cur, cur_ms); s != TC_OK) return s;
-    // coordinate descent over these fields, two passes; the owner threshold
-    // first (it decides which dyads reach the merge bins at all)
+    // coordinate descent over these fields, two passes: first how triangles
+    // are found, then that path's own settings (the tag-map threshold of the
+    // forward path; for the merge path the owner threshold first, since it
+    // decides which dyads reach the merge bins at all)
+    const int32_t path_c[] = {TC_TRI_FORWARD, TC_TRI_MERGE};
+    const int32_t big_c[] = {8, 16, 32, 64, 128, 256};
     const int32_t own_c[] = {0, 64, 128, 256, 512, 1024, 4096};
     const int32_t thr_thread_c[] = {0, 16, 32, 48, 64, 96, 128, 192};
     const int32_t thr_warp_c[] = {64, 128, 256, 512, 1024};
@@ -2835,13 +3051,17 @@ tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t m
         const int32_t* cand;
         int nc;
     };
-    const Field fields[] = {{&tc_opts::own_min, own_c, 7},       {&tc_opts::thr_thread, thr_thread_c, 8},
+    const Field fields[] = {{&tc_opts::tri_path, path_c, 2},     {&tc_opts::fwd_big, big_c, 6},
+                            {&tc_opts::own_min, own_c, 7},       {&tc_opts::thr_thread, thr_thread_c, 8},
                             {&tc_opts::thr_warp, thr_warp_c, 5}, {&tc_opts::stream_max, stream_c, 4},
                             {&tc_opts::chunk, chunk_c, 3},       {&tc_opts::persistent, pers_c, 2}};
     for (int pass = 0; pass < 2; ++pass) {
         for (const Field& fd : fields) {
             const int32_t* cand = fd.cand;
             const int nc = fd.nc;
+            // a field of the other path changes nothing: skip it
+            const bool fwd_field = fd.f == &tc_opts::fwd_big, path_field = fd.f == &tc_opts::tri_path;
+            if (!path_field && (cur.tri_path == TC_TRI_FORWARD) != fwd_field) continue;
             for (int k = 0; k < nc; ++k) {
                 if (max_trials > 0 && trials >= max_trials) break;
                 tc_opts o = cur;
@@ -2888,6 +3108,7 @@ tc_status cost_sample(int32_t G, const tc_graph* gs, int32_t bin, int32_t mask, 
     if (tc_status s = check_handles(G, gs, "tc_cost_sample"); s != TC_OK) return s;
     tc_opts o;
     tc_opts_default(&o);
+    o.tri_path = TC_TRI_MERGE;  // per-task timings come from the merge bins
     o.persistent = 1;
     o.split_cta = 0;
     if (bin == 0) {

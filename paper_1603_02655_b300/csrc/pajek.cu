@@ -1,5 +1,5 @@
 // tc_graph_build_text: a network file in the Pajek-style text format the
-// thesis reads (Sec. 3.1 "Implementation details": the order of the graph,
+// thesis reads (Sec. 4.2.1 "Implementation details": the order of the graph,
 // optional vertex lines with labels, then the arcs of a directed or the
 // edges of an undirected graph, told apart by their section keyword; Sec.
 // 5.1.1: 0- or 1-based vertex ids) parsed on the device and built into a

@@ -17,7 +17,9 @@ c4     4096 independent graphs, n log-uniform in [64, 65536], even index
        G(n,p) with mean out-degree U(4,32), odd index R-MAT edge factor 8,
        reciprocity U(0, 0.5)
 c5     directed Chung-Lu, n=2^22, power-law exponent 2.1, mean total degree
-       16, largest expected degree 1e5, reciprocity 0.15, ids permuted
+       16, reciprocity 0.15, ids permuted; the largest expected total degree
+       is set to 1.6e5 so that the largest realised degree, after loops and
+       duplicate arcs are dropped, is ~1e5 (101,076)
 =====  ======================================================================
 """
 from __future__ import annotations
@@ -155,7 +157,7 @@ def c4(G: int = 4096) -> Batch:
 
 
 def c5() -> Arcs:
-    return chung_lu(1 << 22, 2.1, 16.0, 1e5, 0.15, seed=5)
+    return chung_lu(1 << 22, 2.1, 16.0, 1.6e5, 0.15, seed=5)
 
 
 def c3s() -> Arcs:

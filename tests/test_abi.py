@@ -77,3 +77,17 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(tc, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError):
         tc.load()
+
+
+def test_noalloc_binding_refuses_host_or_short_tensors(lib):
+    """The binding checks device, dtype and length before the call reaches
+    the library (a short or host tensor would be read past its end)."""
+    import torch
+    rp = torch.zeros(4, dtype=torch.int64)
+    adj = torch.zeros(2, dtype=torch.int32)
+    out = torch.zeros(17, dtype=torch.int64)
+    for args in ((3, rp, adj, 2, out), (3, rp.int(), adj, 2, out), (9, rp, adj, 2, out),
+                 (3, rp, adj, 6, out), (3, rp, adj, 2, out[:5])):
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_census_csr_noalloc(*args)
+        assert e.value.status == tc.TC_ERR_ARG

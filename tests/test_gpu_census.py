@@ -18,27 +18,38 @@ BIG = 1 << 30
 
 # binning configurations: default, everything per thread, per warp, per CTA
 # chunk (tiny chunks: every task split), and small mixed thresholds
+MERGE = tc.TC_TRI_MERGE
 BINS = {
+    # forward path (the default): owners by tag map and by binary search
     "default": {},
-    "no_owner": dict(own_min=0),
-    "nostream": dict(stream_max=0, own_min=0),
-    "stream_all": dict(thr_thread=0, thr_warp=0, stream_max=1024, own_min=0),
-    "stream_chunks": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30, own_min=0),
-    "hub_separate": dict(thr_thread=0, thr_warp=0, stream_max=1 << 30, persistent=0, own_min=0),
-    "thread": dict(thr_thread=BIG, thr_warp=BIG, own_min=0),
-    "warp": dict(thr_thread=0, thr_warp=BIG, stream_max=0, own_min=0),
-    "separate": dict(persistent=0, own_min=0),
-    "cta": dict(thr_thread=0, thr_warp=0, chunk=256, split_cta=1, stream_max=0, persistent=0, own_min=0),
-    "wtile": dict(thr_thread=0, thr_warp=0, chunk=256, stream_max=0, own_min=0),
-    "cta_big": dict(thr_thread=16, thr_warp=200, chunk=3840, split_cta=1, stream_max=8, persistent=0, own_min=0),
-    "mixed": dict(thr_thread=8, thr_warp=40, chunk=512, own_min=0),
-    "persistent": dict(persistent=1, own_min=0),
-    "persistent_small": dict(persistent=1, thr_thread=8, thr_warp=64, chunk=256, stream_max=32, own_min=0),
-    "owner_all": dict(own_min=1),
-    "owner_mid": dict(own_min=64, thr_thread=8, thr_warp=64),
-    "owner_sep": dict(own_min=32, persistent=0, stream_max=0),
-    "row_tasks": dict(row_tasks=1),
-    "row_tasks_merge": dict(row_tasks=1, own_min=0, thr_thread=8, thr_warp=64),
+    "fwd_map_all": dict(fwd_big=1),
+    "fwd_search_all": dict(fwd_big=BIG),
+    "fwd_map_mid": dict(fwd_big=4),
+    "fwd_row_tasks": dict(row_tasks=1),
+    # merge path: owner lookups and merge bins
+    "merge_default": dict(tri_path=MERGE),
+    "no_owner": dict(tri_path=MERGE, own_min=0),
+    "nostream": dict(tri_path=MERGE, stream_max=0, own_min=0),
+    "stream_all": dict(tri_path=MERGE, thr_thread=0, thr_warp=0, stream_max=1024, own_min=0),
+    "stream_chunks": dict(tri_path=MERGE, thr_thread=0, thr_warp=0, stream_max=1 << 30, own_min=0),
+    "hub_separate": dict(tri_path=MERGE, thr_thread=0, thr_warp=0, stream_max=1 << 30, persistent=0, own_min=0),
+    "thread": dict(tri_path=MERGE, thr_thread=BIG, thr_warp=BIG, own_min=0),
+    "warp": dict(tri_path=MERGE, thr_thread=0, thr_warp=BIG, stream_max=0, own_min=0),
+    "separate": dict(tri_path=MERGE, persistent=0, own_min=0),
+    "cta": dict(tri_path=MERGE, thr_thread=0, thr_warp=0, chunk=256, split_cta=1, stream_max=0, persistent=0,
+                own_min=0),
+    "wtile": dict(tri_path=MERGE, thr_thread=0, thr_warp=0, chunk=256, stream_max=0, own_min=0),
+    "cta_big": dict(tri_path=MERGE, thr_thread=16, thr_warp=200, chunk=3840, split_cta=1, stream_max=8,
+                    persistent=0, own_min=0),
+    "mixed": dict(tri_path=MERGE, thr_thread=8, thr_warp=40, chunk=512, own_min=0),
+    "persistent": dict(tri_path=MERGE, persistent=1, own_min=0),
+    "persistent_small": dict(tri_path=MERGE, persistent=1, thr_thread=8, thr_warp=64, chunk=256, stream_max=32,
+                             own_min=0),
+    "owner_all": dict(tri_path=MERGE, own_min=1),
+    "owner_mid": dict(tri_path=MERGE, own_min=64, thr_thread=8, thr_warp=64),
+    "owner_sep": dict(tri_path=MERGE, own_min=32, persistent=0, stream_max=0),
+    "row_tasks": dict(tri_path=MERGE, row_tasks=1),
+    "row_tasks_merge": dict(tri_path=MERGE, row_tasks=1, own_min=0, thr_thread=8, thr_warp=64),
 }
 
 
@@ -122,7 +133,7 @@ def test_all_4096_four_vertex_digraphs_batched():
         want.append(oracle.brute_census(4, s, d))
     gs = tc.tc_graph_build_batched([4] * 4096, off, src, dst)
     try:
-        for name in ("default", "cta", "mixed"):
+        for name in ("default", "fwd_map_all", "fwd_search_all", "cta", "mixed"):
             assert tc.tc_census_batched(gs, opts(name)) == want, name
         # a shuffled subset keeps each result with its own graph
         rng = np.random.default_rng(3)
@@ -150,7 +161,8 @@ def test_codes_match_oracle():
         want = oracle.census_codes(n, src, dst)
         g = tc.tc_graph_build(n, src, dst)
         try:
-            for name in ("default", "owner_all", "no_owner", "row_tasks", "cta", "stream_all"):
+            for name in ("default", "fwd_map_all", "fwd_search_all", "merge_default", "owner_all", "no_owner",
+                         "row_tasks", "cta", "stream_all"):
                 got = tc.tc_census_codes(g, opts(name))
                 assert got == want, (n, name)
                 assert fold(got) == tc.tc_census(g, opts(name)), (n, name)
@@ -171,7 +183,7 @@ def test_codes_batched_all_64_triads():
         want.append(oracle.brute_census_codes(3, s, d))
     gs = tc.tc_graph_build_batched([3] * 64, off, src, dst)
     try:
-        for name in ("default", "owner_all", "thread"):
+        for name in ("default", "fwd_map_all", "owner_all", "thread"):
             assert tc.tc_census_codes_batched(gs, opts(name)) == want, name
     finally:
         for g in gs:
@@ -231,17 +243,31 @@ def test_hub_tasks_stage_short_list_in_pieces():
     for h, D in enumerate(degs):  # |N(h)|: distinct neighbours either way
         assert np.unique(np.concatenate([dst[src == h], src[dst == h]])).size == D
     hubs = sum(1 for i in range(H) for j in range(i + 1, H) if min(degs[i], degs[j]) > 1024)
-    for name in ("default", "no_owner", "separate", "stream_chunks", "hub_separate", "nostream"):
+    for name in ("default", "merge_default", "no_owner", "separate", "stream_chunks", "hub_separate", "nostream"):
         o = tc.tc_opts_default(profile=1, **BINS[name])
         assert gpu_census(n, src, dst, o) == want, name
         p = tc.tc_census_profile()
-        if o.own_min > 0:  # the hubs own their dyads: looked up, not streamed
+        if o.tri_path == tc.TC_TRI_FORWARD:  # no merge bins: every triangle from the forward lists
+            assert sum(p["bin_tasks"]) == 0 and p["owner_tasks"] == 0, name
+            assert p["map_triangles"] + p["search_triangles"] == triangles(want), name
+        elif o.own_min > 0:  # the hubs own their dyads: looked up, not streamed
             assert p["hub_tasks"] == 0 and p["owner_tasks"] > 0, name
         elif o.stream_max > 1024:
             assert p["hub_tasks"] == hubs, name
             assert p["hub_entries"] > 0
         else:
             assert p["hub_tasks"] == 0, name
+
+
+def triangles(census):
+    """Triads whose three pairs are all adjacent."""
+    return sum(census[idx(t)] for t in ("030T", "030C", "120D", "120U", "120C", "210", "300"))
+
+
+def forward_profile(n, src, dst, name):
+    o = tc.tc_opts_default(profile=1, **BINS[name])
+    c = gpu_census(n, src, dst, o)
+    return c, tc.tc_census_profile()
 
 
 def star_plus(rng, n, hub, leaves, extra):
@@ -257,7 +283,7 @@ def star_plus(rng, n, hub, leaves, extra):
 
 
 def owner_profile(n, src, dst, **over):
-    o = tc.tc_opts_default(profile=1, **over)
+    o = tc.tc_opts_default(profile=1, **{"tri_path": MERGE, **over})
     c = gpu_census(n, src, dst, o)
     return c, tc.tc_census_profile()
 
@@ -332,6 +358,10 @@ def test_owner_large_and_skewed():
         c, p = owner_profile(n, src, dst, own_min=own_min)
         assert c == want, own_min
         assert p["owner_items"] >= 1 and p["owner_tasks"] > 0
+    for name in ("default", "fwd_map_all", "fwd_search_all"):  # both lookup forms in one graph
+        c, p = forward_profile(n, src, dst, name)
+        assert c == want, name
+        assert p["map_triangles"] + p["search_triangles"] == triangles(want), name
     # an owner whose neighbours all have small ids: they crowd into a few id
     # buckets (long scans), which must stay exact
     n = 1_000_000
@@ -486,7 +516,7 @@ def test_batch_plan_replays_match_oracle():
     want = [oracle.census(n, a[0], a[1], threads=THREADS) for n, a in zip(ns, arcs)]
     gs = tc.tc_graph_build_batched(ns, off, src, dst)
     try:
-        for name in ("default", "persistent", "persistent_small"):
+        for name in ("default", "fwd_map_all", "fwd_search_all", "persistent", "persistent_small"):
             out = torch.zeros(17 * len(gs), dtype=torch.int64, device="cuda")
             plan = tc.tc_plan_create(gs, out, opts(name))
             try:
@@ -530,3 +560,41 @@ def test_autotune_returns_valid_options_and_same_counts(tmp_path):
         assert tc.tc_census(g, o2) == want
     finally:
         tc.tc_graph_free(g)
+
+
+# ------------------------------------------------------------ forward path
+
+@pytest.mark.parametrize("seed", range(4))
+def test_forward_path_finds_each_triangle_once(seed):
+    """Every triangle is found exactly once, whichever lookup form its owner
+    takes (tag map, binary search, or a mix), and the lookups equal the
+    suffix lengths the ranking defines (computed here with numpy)."""
+    rng = np.random.default_rng(300 + seed)
+    n = 20_000
+    src, dst = hub_graph(rng, n, hubs=4, hub_deg=int(rng.integers(1000, 6000)), extra=80_000, recip=0.3)
+    want = oracle.census(n, src, dst, threads=THREADS)
+    s = src.astype(np.int64)
+    d = dst.astype(np.int64)
+    keep = s != d
+    pair = np.unique(np.minimum(s[keep], d[keep]) * n + np.maximum(s[keep], d[keep]))
+    u, v = pair // n, pair % n
+    deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
+    cls = np.where(deg > 0, np.floor(np.log2(np.maximum(deg, 1))), 0).astype(np.int64)
+    rk = cls * n + np.arange(n)  # the rank order: (floor(log2 d), id)
+    lo = np.where(rk[u] < rk[v], u, v)
+    hi = np.where(rk[u] < rk[v], v, u)
+    nplus = np.bincount(lo, minlength=n)
+    order = np.lexsort((rk[hi], lo))
+    start = np.concatenate([[0], np.cumsum(nplus)])
+    pos = np.arange(order.size) - start[lo[order]]
+    suffix = nplus[lo[order]] - pos - 1
+    owner_has_fwd = nplus[hi[order]] > 0
+    lookups = int(suffix[owner_has_fwd].sum())
+    for name in ("default", "fwd_map_all", "fwd_search_all", "fwd_map_mid", "fwd_row_tasks"):
+        c, p = forward_profile(n, src, dst, name)
+        assert c == want, name
+        assert p["map_triangles"] + p["search_triangles"] == triangles(want), name
+        assert p["map_lookups"] + p["search_lookups"] == lookups, name
+        assert p["fwd_entries"] == pair.size, name
+    _, p = forward_profile(n, src, dst, "fwd_search_all")
+    assert p["map_lookups"] == 0 and p["map_items"] == 0

@@ -146,7 +146,7 @@ def test_learned_binning_never_changes_counts(seed):
             p[-4:] = [50, 50, 50, 0]      # every eligible large task streamed
         tc.tc_cost_model_load(p)
         for extra in ({}, {"persistent": 0}, {"thr_thread": 0, "thr_warp": 64}):
-            o = tc.tc_opts_default(bin_mode=tc.TC_BIN_MLP, profile=1, own_min=0, **extra)
+            o = tc.tc_opts_default(bin_mode=tc.TC_BIN_MLP, profile=1, own_min=0, tri_path=tc.TC_TRI_MERGE, **extra)
             assert tc.tc_census(g, o) == want
             bt = tc.tc_census_profile()["bin_tasks"]
             if seed == 1:
@@ -206,7 +206,7 @@ def test_pipeline_trains_and_reports_its_gain():
         assert np.isfinite(rep["rmse_exact_size"])
         tc.tc_cost_model_load(params)
         want = tc.tc_census(g)
-        assert tc.tc_census(g, tc.tc_opts_default(bin_mode=tc.TC_BIN_MLP)) == want
+        assert tc.tc_census(g, tc.tc_opts_default(bin_mode=tc.TC_BIN_MLP, tri_path=tc.TC_TRI_MERGE)) == want
     finally:
         tc.tc_cost_model_load(None)
         tc.tc_graph_free(g)

@@ -44,26 +44,31 @@ def test_single_graph_workloads_match_oracle(name):
         c = gold["census"]
         assert sum(c) == a.n * (a.n - 1) * (a.n - 2) // 6
         out = torch.zeros(17, dtype=torch.int64, device="cuda")
-        for o in (tc.tc_opts_default(), tc.tc_opts_default(persistent=0), tc.tc_opts_default(own_min=0),
-                  tc.tc_opts_default(thr_warp=256, chunk=512, stream_max=256, own_min=1024)):
+        M = tc.TC_TRI_MERGE
+        for o in (tc.tc_opts_default(), tc.tc_opts_default(fwd_big=1), tc.tc_opts_default(fwd_big=1 << 30),
+                  tc.tc_opts_default(tri_path=M), tc.tc_opts_default(tri_path=M, own_min=0),
+                  tc.tc_opts_default(tri_path=M, thr_warp=256, chunk=512, stream_max=256, own_min=1024)):
             tc.tc_census(g, o, out=out)
             torch.cuda.synchronize()
             assert tc.census_from_device_words(out.cpu().tolist()) == c
         assert tc.tc_census(g) == c  # host output path
         # the 64-code census maps onto the golden 16-type census, and the
-        # connected codes agree between the owner and merge-only paths
+        # codes agree between the forward and merge paths
         T = oracle.triad_table()
         codes = tc.tc_census_codes(g)
         folded = [0] * 16
         for code, k in enumerate(codes):
             folded[T[code]] += k
         assert folded == c
-        assert tc.tc_census_codes(g, tc.tc_opts_default(own_min=0)) == codes
+        assert tc.tc_census_codes(g, tc.tc_opts_default(tri_path=M, own_min=0)) == codes
     finally:
         tc.tc_graph_free(g)
 
 
-def test_batched_workload_matches_oracle_checksums():
+def test_batched_workload_matches_oracle_per_graph():
+    """Every one of the 4096 graphs' 16 counts against the oracle's census of
+    that graph; the per-type sums and (g+1)-weighted sums are kept as extra
+    checks."""
     import torch
     gold = golden("c4")
     b = synth.c4()
@@ -76,10 +81,14 @@ def test_batched_workload_matches_oracle_checksums():
         tc.tc_plan_free(plan)
         w = out.cpu().tolist()
         census = [tc.census_from_device_words(w[17 * i:17 * i + 17]) for i in range(len(gs))]
+        assert len(gold["census"]) == len(census) == 4096
+        bad = [i for i, (got, want) in enumerate(zip(census, gold["census"])) if got != want]
+        assert not bad, f"{len(bad)} graphs differ, first {bad[:5]}"
         assert [sum(c[t] for c in census) for t in range(16)] == gold["total"]
         assert [sum((i + 1) * c[t] for i, c in enumerate(census)) for t in range(16)] == gold["weighted"]
         for k, v in gold["sample"].items():
             assert census[int(k)] == v["census"], k
+            assert tc.tc_graph_stats(gs[int(k)]) == v["stats"], k
     finally:
         for g in gs:
             tc.tc_graph_free(g)

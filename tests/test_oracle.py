@@ -365,3 +365,58 @@ def test_codes_random_graphs_vs_brute(seed):
     assert oracle.census_codes(n, s, d) == b
     assert fold(b) == oracle.census(n, s, d)
     assert sum(b) == math.comb(n, 3)
+
+
+# -------------------------------------------------------- graph statistics
+def numpy_stats(n, src, dst):
+    """The statistics from their definitions, by numpy set operations on the
+    raw arcs (independent of the oracle's CRS): distinct arcs without loops,
+    unordered adjacent pairs, mutual pairs, degrees by bincount over the
+    distinct pairs, merged entries = sum over pairs of d_u + d_v."""
+    s = np.asarray(src, np.int64)
+    d = np.asarray(dst, np.int64)
+    keep = s != d
+    s, d = s[keep], d[keep]
+    arcs = np.unique(s * n + d)
+    lo, hi = np.minimum(arcs // n, arcs % n), np.maximum(arcs // n, arcs % n)
+    pair, times = np.unique(lo * n + hi, return_counts=True)
+    u, v = pair // n, pair % n
+    deg = np.bincount(u, minlength=n) + np.bincount(v, minlength=n)
+    return {"n": n, "arcs": int(arcs.size), "dyads": int(pair.size), "mutual": int((times == 2).sum()),
+            "asym": int((times == 1).sum()), "merged_entries": int((deg[u] + deg[v]).sum()),
+            "max_degree": int(deg.max()) if n else 0}
+
+
+@pytest.mark.parametrize("case", ["c1", "multi", "star", "rmat"])
+def test_graph_stats_follow_their_definitions(case):
+    """oracle_graph_stats is the reference for the library's statistics and
+    for every bench rate (merged entries = sum_v d_v^2, max degree)."""
+    rng = np.random.default_rng(7)
+    if case == "c1":
+        a = synth.c1()
+        n, src, dst = a.n, a.src, a.dst
+    elif case == "multi":  # duplicates, loops and both directions of some pairs
+        n = 300
+        src = rng.integers(0, n, 4000)
+        dst = rng.integers(0, n, 4000)
+        src = np.concatenate([src, dst[:500], np.arange(20)])
+        dst = np.concatenate([dst, src[:500], np.arange(20)])
+    elif case == "star":  # one hub: max degree n-1, merged entries (n-1)(n-1+1)
+        n = 500
+        src = np.zeros(n - 1, np.int64)
+        dst = np.arange(1, n)
+    else:
+        a = synth.rmat(12, 8, recip=0.2, seed=9)
+        n, src, dst = a.n, a.src, a.dst
+    st = oracle.Graph(n, src, dst).stats()
+    want = numpy_stats(n, src, dst)
+    assert st == want
+    if case == "star":
+        assert st["max_degree"] == n - 1 and st["merged_entries"] == (n - 1) * n
+    # merged entries = sum_v d_v^2 (each vertex's degree counted once per incident pair)
+    s = np.asarray(src, np.int64)
+    d = np.asarray(dst, np.int64)
+    keep = s != d
+    pair = np.unique(np.minimum(s[keep], d[keep]) * n + np.maximum(s[keep], d[keep]))
+    deg_sq = np.bincount(np.concatenate([pair // n, pair % n]), minlength=n).astype(np.int64) ** 2
+    assert st["merged_entries"] == int(deg_sq.sum())
