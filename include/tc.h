@@ -137,7 +137,7 @@ typedef struct {
                              neighbours (and at most 2^17 vertices ranked above
                              them) get a CTA and an exact tag map of their
                              forward list in shared memory; the others a
-                             binary search per lookup.  >= 1; default 32 */
+                             binary search per lookup.  >= 1; default 64 */
 } tc_opts;
 
 enum { TC_TRI_FORWARD = 0, TC_TRI_MERGE = 1 };

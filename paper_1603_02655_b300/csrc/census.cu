@@ -414,6 +414,14 @@ __global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __re
     }
 }
 
+// Forward flags of the forward path, written by the task pass as it reads
+// each entry (flag null: none).
+struct FlagOut {
+    uint8_t* flag;         // [entries] 1 when the entry's neighbour ranks above its row
+    const int32_t* rank;   // per selected row
+    const int64_t* pfx;    // first selected row of each graph
+};
+
 // Warps take runs of FLAT_RUN entries of the selected graphs' concatenated
 // adjacency (graph boundaries rarely fall inside one); lanes whose entry lies
 // in another graph than the warp's accumulators add directly.
@@ -429,7 +437,7 @@ __global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict
                                                     const int64_t* __restrict__ epfx, int nseg,
                                                     int64_t total_entries, BinParams bp, Bins bins,
                                                     unsigned long long* __restrict__ acc,
-                                                    unsigned long long* __restrict__ cursor) {
+                                                    unsigned long long* __restrict__ cursor, FlagOut fo) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const unsigned below = (1u << lane) - 1u;
@@ -488,6 +496,10 @@ __global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict
             uint32_t S1 = 0, S2 = 0, S3 = 0;
             int d = 0;
             int64_t rp = 0;
+            if (fo.flag && valid) {  // forward entry: its neighbour ranks above its row
+                const int64_t p = fo.pfx[ls];
+                fo.flag[f] = fo.rank[p + y] > fo.rank[p + xl] ? 1 : 0;
+            }
             if (valid) {
                 rp = row_ptr[x];
                 const int64_t frs = epfx[ls] + (rp - sg.eb);  // the row's first entry, in scan order
@@ -2134,8 +2146,8 @@ struct Layout {
     int64_t dyads = 0;     // canonical dyads of the selection
     uint32_t item_cap = 0;
     size_t fscan_bytes = 0;
-    size_t o_hist, o_hex, o_co, o_rank, o_perm, o_fs, o_fptr, o_nown, o_tptr, o_tcur, o_fid, o_fwd, o_trec, o_items,
-        o_fscantmp;
+    size_t o_hist, o_hex, o_co, o_rank, o_perm, o_flag, o_fs, o_fptr, o_kind, o_tcnt, o_tpre, o_longs,
+        o_fid, o_fwd, o_trec, o_items, o_fscantmp;
 };
 
 // counters (uint32 words): [0..3] records per bin, [4] overflow flag,
@@ -2248,26 +2260,27 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         size_t b1 = 0, b2 = 0, b3 = 0;
         TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b1, (const uint32_t*)nullptr, (uint32_t*)nullptr,
                                               NCLS * Lo.nb, (cudaStream_t)0));
-        TC_CUDA(cub::DeviceScan::InclusiveSum(
-            nullptr, b2, FwdFlagIt(thrust::counting_iterator<int64_t>(0), FwdFlag{}), (int32_t*)nullptr,
-            (int)Lo.entries, (cudaStream_t)0));
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b3, (const uint32_t*)nullptr, (uint32_t*)nullptr,
-                                              (int)(rows + 1), (cudaStream_t)0));
+        TC_CUDA(cub::DeviceScan::InclusiveSum(nullptr, b2, FlagIt((const uint8_t*)nullptr, U8ToInt{}),
+                                              (int32_t*)nullptr, (int)Lo.entries, (cudaStream_t)0));
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b3, (const unsigned long long*)nullptr,
+                                              (unsigned long long*)nullptr, (int)(rows + 1), (cudaStream_t)0));
         Lo.fscan_bytes = std::max(b1, std::max(b2, b3));
         Lo.o_hist = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
         Lo.o_hex = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
         Lo.o_co = take(sizeof(int64_t) * NCLS * (size_t)nseg);
         Lo.o_rank = take(sizeof(int32_t) * rows);
         Lo.o_perm = take(sizeof(int32_t) * rows);
+        Lo.o_flag = take(sizeof(uint8_t) * (size_t)Lo.entries);
         Lo.o_fs = take(sizeof(int32_t) * (size_t)Lo.entries);
         Lo.o_fptr = take(sizeof(uint32_t) * (rows + 1));
-        Lo.o_nown = take(sizeof(uint32_t) * (rows + 1));
-        Lo.o_tptr = take(sizeof(uint32_t) * (rows + 1));
-        Lo.o_tcur = take(sizeof(uint32_t) * rows);
+        Lo.o_kind = take(sizeof(uint8_t) * rows);
+        Lo.o_tcnt = take(sizeof(unsigned long long) * (rows + 1));
+        Lo.o_tpre = take(sizeof(unsigned long long) * (rows + 1));
+        Lo.o_longs = take(sizeof(uint32_t) * rows);
         Lo.o_fid = take(sizeof(uint32_t) * D);
         Lo.o_fwd = take(sizeof(uint32_t) * D);
         Lo.o_trec = take(sizeof(uint4) * D);
-        Lo.o_items = take(sizeof(uint4) * (size_t)Lo.item_cap);
+        Lo.o_items = take(sizeof(uint4) * 2 * (size_t)Lo.item_cap);
         Lo.o_fscantmp = take(std::max<size_t>(Lo.fscan_bytes, 16));
     }
     Lo.need = off;
@@ -2286,11 +2299,12 @@ tc_status upload_layout(const Layout& Lo, char* ws, cudaStream_t st) {
     return TC_OK;
 }
 
-// The forward path (tri_path = TC_TRI_FORWARD): the task pass adds every
-// dyad's suffix and dyadic terms and emits no task; the vertex ranks, the
-// forward lists and the dyad records by owner are built; the two lookup
-// kernels apply each triangle's correction once.  Marks 1 (task pass), 2
-// (forward lists), 3 (tag-map owners), 4..7 (the other owners).
+// The forward path (tri_path = TC_TRI_FORWARD): the vertex ranks; the task
+// pass adds every dyad's suffix and dyadic terms, emits no task and flags
+// the forward entries; the forward lists and the dyad records are built;
+// the two lookup kernels apply each triangle's correction once.  Marks 1
+// (ranks + task pass), 2 (forward lists), 3 (tag-map owners), 4..8 (the
+// other owners).
 template <class Mark>
 tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaStream_t st, const Launch& L,
                           const BinParams& bp, const Bins& bins, Mark& mark) {
@@ -2300,26 +2314,14 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     const int64_t* d_pfx = (const int64_t*)(ws + Lo.o_pfx);
     const int64_t* d_epfx = (const int64_t*)(ws + Lo.o_epfx);
     unsigned long long* cursor = (unsigned long long*)(ctr + 8);
-    if (Lo.flat) {
-        unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
-        size_t sb = Lo.scan_bytes;
-        const OneHotIt words(thrust::counting_iterator<int64_t>(0), OneHot{set.adj, d_seg, d_epfx, Lo.nseg});
-        TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, words, scan, (int)Lo.entries, st));
-        k_tasks_flat<<<L.sms * L.occ_flat, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, set.vtag, scan,
-                                                         d_seg, d_epfx, Lo.nseg, Lo.entries, bp, bins, acc, cursor);
-    } else {
-        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
-                                                     bp, bins, acc, cursor);
-    }
-    TC_CUDA(cudaGetLastError());
-    mark(1);
-    // vertex ranks
     uint32_t* hist = (uint32_t*)(ws + Lo.o_hist);
     uint32_t* hex = (uint32_t*)(ws + Lo.o_hex);
     int64_t* co = (int64_t*)(ws + Lo.o_co);
     int32_t* rank = (int32_t*)(ws + Lo.o_rank);
     int32_t* perm = (int32_t*)(ws + Lo.o_perm);
+    uint8_t* flag = (uint8_t*)(ws + Lo.o_flag);
     void* tmp = ws + Lo.o_fscantmp;
+    // vertex ranks: (floor(log2 d), id) per graph
     k_rank_hist<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hist);
     TC_CUDA(cudaGetLastError());
     size_t tb = Lo.fscan_bytes;
@@ -2329,36 +2331,61 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     k_rank_assign<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co, rank, perm,
                                           bins.overflow);
     TC_CUDA(cudaGetLastError());
-    // forward lists and the dyad records by owner
+    // the task pass, with the forward flags
+    if (Lo.flat) {
+        unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
+        size_t sb = Lo.scan_bytes;
+        const OneHotIt words(thrust::counting_iterator<int64_t>(0), OneHot{set.adj, d_seg, d_epfx, Lo.nseg});
+        TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, words, scan, (int)Lo.entries, st));
+        k_tasks_flat<<<L.sms * L.occ_flat, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, set.vtag, scan,
+                                                         d_seg, d_epfx, Lo.nseg, Lo.entries, bp, bins, acc, cursor,
+                                                         FlagOut{flag, rank, d_pfx});
+    } else {
+        k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
+                                                     bp, bins, acc, cursor);
+        TC_CUDA(cudaGetLastError());
+        k_fwd_flags<<<L.sms * 16, 256, 0, st>>>(set.adj, set.arow, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.entries, rank,
+                                                flag);
+    }
+    TC_CUDA(cudaGetLastError());
+    mark(1);
+    // forward lists and the dyad records
     FwdLayout F;
     F.fs = (const int32_t*)(ws + Lo.o_fs);
     F.fptr = (uint32_t*)(ws + Lo.o_fptr);
-    F.nown = (uint32_t*)(ws + Lo.o_nown);
-    F.tptr = (uint32_t*)(ws + Lo.o_tptr);
-    F.tcur = (uint32_t*)(ws + Lo.o_tcur);
+    F.kind = (uint8_t*)(ws + Lo.o_kind);
+    F.tcnt = (unsigned long long*)(ws + Lo.o_tcnt);
+    F.tpre = (unsigned long long*)(ws + Lo.o_tpre);
     F.fid = (uint32_t*)(ws + Lo.o_fid);
     F.fwd = (uint32_t*)(ws + Lo.o_fwd);
     F.trec = (uint4*)(ws + Lo.o_trec);
     F.items = (uint4*)(ws + Lo.o_items);
     F.item_cap = Lo.item_cap;
+    F.longs = (uint32_t*)(ws + Lo.o_longs);
     F.nitems = ctr + 40;
+    F.nlong = ctr + 41;
     F.cursor = ctr + 42;
     F.stat = (unsigned long long*)(ctr + 44);
     F.rank = rank;
     F.perm = perm;
     tb = Lo.fscan_bytes;
-    const FwdFlagIt flags(thrust::counting_iterator<int64_t>(0),
-                          FwdFlag{set.adj, set.arow, d_seg, d_pfx, d_epfx, rank, Lo.nseg});
-    TC_CUDA(cub::DeviceScan::InclusiveSum(tmp, tb, flags, (int32_t*)(ws + Lo.o_fs), (int)Lo.entries, st));
-    TC_CUDA(cudaMemsetAsync(F.tcur, 0, sizeof(uint32_t) * (size_t)Lo.rows, st));
-    k_fwd_rows<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.deg, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.rows, Lo.o.fwd_big,
+    TC_CUDA(cub::DeviceScan::InclusiveSum(tmp, tb, FlagIt(flag, U8ToInt{}), (int32_t*)(ws + Lo.o_fs),
+                                          (int)Lo.entries, st));
+    k_fwd_rows<<<L.sms * 8, FR_NT, 0, st>>>(set.row_ptr, set.deg, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.rows, Lo.o.fwd_big,
                                            F);
     TC_CUDA(cudaGetLastError());
     tb = Lo.fscan_bytes;
-    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, F.nown, F.tptr, (int)(Lo.rows + 1), st));
-    k_fwd_ids<<<L.sms * 16, 256, 0, st>>>(set.adj, d_seg, d_epfx, Lo.nseg, Lo.entries, F);
+    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, F.tcnt, F.tpre, (int)(Lo.rows + 1), st));
+    k_fwd_items<<<L.sms * 4, 256, 0, st>>>(d_pfx, Lo.nseg, F);
     TC_CUDA(cudaGetLastError());
-    k_fwd_sort<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, F);
+    k_fwd_fill<<<L.sms * 16, 256, 0, st>>>(set.adj, set.arow, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.entries, F);
+    TC_CUDA(cudaGetLastError());
+    k_fwd_sort_short<<<L.sms * 8, 256, 0, st>>>(Lo.rows, F);
+    TC_CUDA(cudaGetLastError());
+    k_fwd_sort<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, F);
+    TC_CUDA(cudaGetLastError());
+    k_fwd_recs<<<L.sms * 16, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, d_seg, d_pfx, d_epfx, Lo.nseg,
+                                           Lo.entries, Lo.rows, F);
     TC_CUDA(cudaGetLastError());
     mark(2);
     TriArgs ta;
@@ -2366,10 +2393,8 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     ta.pfx = d_pfx;
     ta.nseg = Lo.nseg;
     ta.rows = Lo.rows;
-    ta.big_min = Lo.o.fwd_big;
     ta.fptr = F.fptr;
-    ta.tptr = F.tptr;
-    ta.nown = F.nown;
+    ta.tpre = F.tpre;
     ta.fwd = F.fwd;
     ta.trec = F.trec;
     ta.items = F.items;
@@ -2380,8 +2405,6 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     ta.perm = perm;
     ta.acc = acc;
     ta.stat = F.stat;
-    ta.ntrec = (uint32_t)Lo.dyads;
-    ta.err = bins.overflow;
     k_tri_big<<<L.sms * L.occ_tri_big, TB_NT, TB_SMEM, st>>>(ta);
     TC_CUDA(cudaGetLastError());
     mark(3);
@@ -2442,7 +2465,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             }
             k_tasks_flat<<<L.sms * L.occ_flat, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, set.vtag, scan,
                                                              d_seg, (const int64_t*)(ws + Lo.o_epfx), Lo.nseg,
-                                                             Lo.entries, bp, bins, acc, cursor);
+                                                             Lo.entries, bp, bins, acc, cursor,
+                                                             FlagOut{nullptr, nullptr, nullptr});
         } else {
             k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg,
                                                          Lo.rows, bp, bins, acc, cursor);
@@ -2550,8 +2574,9 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
 // Kernels of this library a census launches (the library scans not counted).
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
-    // task pass, 3 rank kernels, 3 forward-list kernels, 2 lookup kernels, k_fold
-    if (Lo.fwd) return 10;
+    // 3 rank kernels, the task pass (+ k_fwd_flags after k_tasks), 6
+    // forward-list kernels, 2 lookup kernels, k_fold
+    if (Lo.fwd) return Lo.flat ? 13 : 14;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
     const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 2 : 1) : 1;  // k_owner_rows, k_tasks_flat
     return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0);

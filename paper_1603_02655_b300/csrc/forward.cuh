@@ -18,10 +18,11 @@
 //
 // How triangles are found.  Vertices are ranked by (floor(log2 d), id) per
 // graph (rank R, 0 .. n-1).  The forward list F(x) holds the neighbours of x
-// of higher rank, sorted by rank, as R << 2 | tag seen from x.  A triangle
-// x, h, w with R(x) < R(h) < R(w) is found exactly once: at the dyad {x, h},
-// owned by h, as an element w of the suffix of F(x) after h that also lies
-// in F(h).  Because high-degree vertices rank last, every F(h) is short (at
+// of higher rank, as R << 2 | tag seen from x (in rank order when it has
+// more than FWD_SHORT entries, else in id order).  A triangle x, h, w with
+// R(x) < R(h) < R(w) is found exactly once: at the dyad {x, h}, owned by h,
+// as an element w of F(x) ranked above h (the suffix after h of a sorted
+// list, the whole of a short one) that also lies in F(h).  Because high-degree vertices rank last, every F(h) is short (at
 // most a few hundred entries on the power-law workloads), and the suffixes
 // sum to about half the lookups of an id-ordered search (R-MAT scale 22:
 // 5.3e8 instead of 1.1e9 for the hub dyads alone).
@@ -34,8 +35,8 @@
 //    at most TRI_PIECE at a time, are laid out as concatenated suffixes that
 //    the warps split evenly.
 //  * k_tri_small: every other owner: warps take runs of dyad records; a
-//    lookup is a binary search of F(h) (global memory, cached: a run's dyads
-//    share few owners).
+//    lookup scans F(h) when it is short (id order) or binary-searches it
+//    (rank order) (global memory, cached: a run's dyads share few owners).
 // Hits (triangles) are queued per warp and applied 32 at a time: the third
 // vertex's id is read from the rank permutation, the three vertices are
 // ordered by id, and the four histogram updates are made.
@@ -155,113 +156,205 @@ __global__ void __launch_bounds__(RK_B) k_rank_assign(const int32_t* __restrict_
 
 // -------------------------------------------------------- forward lists --
 // Entry f of the selection (graphs' adjacency concatenated) is forward when
-// its neighbour ranks above its row.
-struct FwdFlag {
-    const uint32_t* adj;
-    const int32_t* arow;
-    const SegDev* seg;
-    const int64_t* pfx;
-    const int64_t* epfx;
-    const int32_t* rank;
-    int nseg;
-    __device__ int operator()(int64_t f) const {
+// its neighbour ranks above its row: flag[f] = 1.  The task pass writes the
+// flags as it reads each entry (k_tasks_flat); k_fwd_flags does the same for
+// the row-per-warp task pass.
+__global__ void k_fwd_flags(const uint32_t* __restrict__ adj, const int32_t* __restrict__ arow,
+                            const SegDev* __restrict__ seg, const int64_t* __restrict__ pfx,
+                            const int64_t* __restrict__ epfx, int nseg, int64_t entries,
+                            const int32_t* __restrict__ rank, uint8_t* __restrict__ flag) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < entries;
+         f += (int64_t)gridDim.x * blockDim.x) {
         const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
         const SegDev& g = seg[s];
         const int64_t k = g.eb + (f - epfx[s]);
-        const int64_t rx = pfx[s] + ((int64_t)arow[k] - g.rb);
-        const int64_t ry = pfx[s] + (int64_t)(__ldg(adj + k) >> 2);
-        return rank[ry] > rank[rx] ? 1 : 0;
+        const int64_t p = pfx[s];
+        flag[f] = rank[p + (__ldg(adj + k) >> 2)] > rank[p + ((int64_t)arow[k] - g.rb)] ? 1 : 0;
     }
+}
+
+// The flags read as int for the scan that places the forward entries.
+struct U8ToInt {
+    __host__ __device__ int operator()(uint8_t v) const { return (int)v; }
 };
-using FwdFlagIt = thrust::transform_iterator<FwdFlag, thrust::counting_iterator<int64_t>, int>;
+using FlagIt = thrust::transform_iterator<U8ToInt, const uint8_t*, int>;
 
-// Per row: the start of its forward list (from the inclusive scan fs of the
-// forward flags), its number of lower-ranked neighbours (the dyads it owns),
-// and, for an owner that takes the tag-map path, its work items (pieces of
-// TRI_PIECE dyads).
-constexpr int TRI_PIECE = 1024;
+// Rows whose forward list has at most FWD_SHORT entries keep it in id order:
+// a dyad of such a row looks up its whole forward list instead of the part
+// ranked above the owner (an entry ranked below the owner cannot lie in the
+// owner's forward list, so the result is the same); R-MAT scale 22: +3%
+// lookups, 15x fewer rows to sort.
+constexpr int FWD_SHORT = 16;
+constexpr int TRI_PIECE = 512;     // dyad records per tag-map work item
 constexpr int MAP_KEYS = 1 << 17;  // ranks a tag map covers (2 bits each: 32 KB)
+constexpr int MLIST = 1024;        // longest forward list of a tag-map owner
 
+// Dyad records (one per dyad whose owner has a forward list), in two parts:
+// first the tag-map owners' records, grouped by owner (their work items
+// refer to these ranges), then the other owners', grouped by owner.  A
+// record is {first entry of the lookup list, its length, x << 2 | t_x(h),
+// owner row h}.
 struct FwdLayout {
-    const int32_t* fs;     // [entries] inclusive count of forward entries
-    uint32_t* fptr;        // [rows + 1] forward list start
-    uint32_t* nown;        // [rows + 1] dyads owned (lower-ranked neighbours); nown[rows] = 0
-    uint32_t* tptr;        // [rows + 1] exclusive scan of nown
-    uint32_t* tcur;        // [rows] fill cursors of the dyad records
-    uint32_t* fid;         // [dyads] forward entries in id order
-    uint32_t* fwd;         // [dyads] forward entries in rank order: R << 2 | tag
-    uint4* trec;           // [dyads] dyad records by owner
-    uint4* items;          // tag-map work items {owner row, piece, 0, 0}
+    const int32_t* fs;         // [entries] inclusive count of forward entries
+    uint32_t* fptr;            // [rows + 1] forward list start
+    uint8_t* kind;             // [rows] owner kind: 0 no records, 1 tag map, 2 search
+    unsigned long long* tcnt;  // [rows + 1] records per owner: map << 32 | search
+    unsigned long long* tpre;  // [rows + 1] exclusive scan of tcnt
+    uint32_t* fid;             // [dyads] forward entries in id order (adjacency words)
+    uint32_t* fwd;             // [dyads] forward entries: R << 2 | tag, rank order in long rows
+    uint4* trec;               // [dyads] dyad records
+    uint4* items;              // tag-map work items, two words each (see k_fwd_items)
     uint32_t item_cap;
-    unsigned* nitems;      // [1]
-    unsigned* cursor;      // [2] work cursors (tag-map items, record runs)
-    unsigned long long* stat;  // [4] lookups and triangles of each path
+    uint32_t* longs;           // rows whose forward list is sorted (more than FWD_SHORT entries)
+    unsigned* nitems;          // [1]
+    unsigned* nlong;           // [1]
+    unsigned* cursor;          // [2] work cursors (tag-map items, search records)
+    unsigned long long* stat;  // [4] lookups and triangles of each lookup form
     const int32_t* rank;
     const int32_t* perm;
 };
 
 __device__ __forceinline__ bool map_owner(int nplus, int64_t n, int32_t R, int big_min) {
-    return nplus >= big_min && nplus > 0 && n - (int64_t)R - 1 <= MAP_KEYS;
+    return nplus >= big_min && nplus > 0 && nplus <= MLIST && n - (int64_t)R - 1 <= MAP_KEYS;
 }
 
-__global__ void k_fwd_rows(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ deg,
-                           const SegDev* __restrict__ seg, const int64_t* __restrict__ pfx,
-                           const int64_t* __restrict__ epfx, int nseg, int64_t rows, int big_min, FwdLayout F) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const int s = row_seg(pfx, nseg, r);
-        const SegDev& g = seg[s];
-        const int64_t x = g.rb + (r - pfx[s]);
-        const int64_t f0 = epfx[s] + (row_ptr[x] - g.eb), f1 = epfx[s] + (row_ptr[x + 1] - g.eb);
-        const uint32_t a = f0 > 0 ? (uint32_t)F.fs[f0 - 1] : 0u, b = f1 > 0 ? (uint32_t)F.fs[f1 - 1] : 0u;
-        F.fptr[r] = a;
-        const uint32_t own = (uint32_t)deg[x] - (b - a);
-        F.nown[r] = own;
-        if (r == rows - 1) {
-            F.fptr[rows] = b;
-            F.nown[rows] = 0;
+// Per row: its forward list (start from the flag scan), the dyads it owns
+// (lower-ranked neighbours) and which lookup form they take, its tag-map
+// work items, and whether its forward list is sorted.  The two lists are
+// appended with one atomic per block and list.
+constexpr int FR_NT = 256;
+
+__global__ void __launch_bounds__(FR_NT) k_fwd_rows(const int64_t* __restrict__ row_ptr,
+                                                    const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
+                                                    const int64_t* __restrict__ pfx, const int64_t* __restrict__ epfx,
+                                                    int nseg, int64_t rows, int big_min, FwdLayout F) {
+    __shared__ unsigned wsum[2][FR_NT / 32];
+    __shared__ unsigned base[2];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t b0 = (int64_t)blockIdx.x * FR_NT; b0 < rows; b0 += (int64_t)gridDim.x * FR_NT) {
+        const int64_t r = b0 + threadIdx.x;
+        unsigned np = 0, lng = 0;
+        if (r < rows) {
+            const int s = row_seg(pfx, nseg, r);
+            const SegDev& g = seg[s];
+            const int64_t x = g.rb + (r - pfx[s]);
+            const int64_t f0 = epfx[s] + (row_ptr[x] - g.eb), f1 = epfx[s] + (row_ptr[x + 1] - g.eb);
+            const uint32_t a = f0 > 0 ? (uint32_t)F.fs[f0 - 1] : 0u, b = f1 > 0 ? (uint32_t)F.fs[f1 - 1] : 0u;
+            const uint32_t m = b - a, own = (uint32_t)deg[x] - m;
+            F.fptr[r] = a;
+            if (r == rows - 1) {
+                F.fptr[rows] = b;
+                F.tcnt[rows] = 0;
+            }
+            const bool big = own > 0 && map_owner((int)m, g.n, F.rank[r], big_min);
+            const bool search = !big && own > 0 && m > 0;
+            F.kind[r] = big ? 1 : search ? 2 : 0;
+            F.tcnt[r] = big ? (unsigned long long)own << 32 : search ? (unsigned long long)own : 0ull;
+            if (big) np = (own + TRI_PIECE - 1) / TRI_PIECE;
+            lng = m > FWD_SHORT ? 1u : 0u;
         }
-        if (own > 0 && map_owner((int)(b - a), g.n, F.rank[r], big_min)) {
-            const unsigned np = (own + TRI_PIECE - 1) / TRI_PIECE;
-            const unsigned k = atomicAdd(F.nitems, np);
-            for (unsigned p = 0; p < np; ++p)
-                if (k + p < F.item_cap) F.items[k + p] = make_uint4((uint32_t)r, p, 0u, 0u);
+        // block-wide exclusive offsets of the work items and the long rows
+        unsigned ip = np, lp = lng;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t1 = __shfl_up_sync(full, ip, o), t2 = __shfl_up_sync(full, lp, o);
+            if (lane >= o) {
+                ip += t1;
+                lp += t2;
+            }
         }
+        if (lane == 31) {
+            wsum[0][warp] = ip;
+            wsum[1][warp] = lp;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            unsigned tot = 0;
+            for (int w = 0; w < FR_NT / 32; ++w) {
+                const unsigned t = wsum[threadIdx.x][w];
+                wsum[threadIdx.x][w] = tot;
+                tot += t;
+            }
+            base[threadIdx.x] = tot ? atomicAdd(threadIdx.x == 0 ? F.nitems : F.nlong, tot) : 0u;
+        }
+        __syncthreads();
+        const unsigned at = base[0] + wsum[0][warp] + ip - np;
+        for (unsigned p = 0; p < np; ++p)
+            if (at + p < F.item_cap) F.items[2 * (at + p)] = make_uint4((uint32_t)r, p, 0u, 0u);
+        if (lng) F.longs[base[1] + wsum[1][warp] + lp - 1] = (uint32_t)r;
+        __syncthreads();
     }
 }
 
-// Forward entries in id order (a flat pass over the selection's entries).
-__global__ void k_fwd_ids(const uint32_t* __restrict__ adj, const SegDev* __restrict__ seg,
-                          const int64_t* __restrict__ epfx, int nseg, int64_t entries, FwdLayout F) {
+// Forward entries, one thread per entry of the selection: in a short row
+// (kept in id order) the entry R << 2 | tag, in a long row the adjacency
+// word for the sort.
+__global__ void k_fwd_fill(const uint32_t* __restrict__ adj, const int32_t* __restrict__ arow,
+                           const SegDev* __restrict__ seg, const int64_t* __restrict__ pfx,
+                           const int64_t* __restrict__ epfx, int nseg, int64_t entries, FwdLayout F) {
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < entries;
          f += (int64_t)gridDim.x * blockDim.x) {
         const int32_t here = F.fs[f];
-        if (here > (f > 0 ? F.fs[f - 1] : 0)) {
-            const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
-            F.fid[here - 1] = __ldg(adj + seg[s].eb + (f - epfx[s]));
-        }
+        if (here == (f > 0 ? F.fs[f - 1] : 0)) continue;
+        const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
+        const SegDev& g = seg[s];
+        const int64_t k = g.eb + (f - epfx[s]);
+        const uint32_t e = __ldg(adj + k);
+        const uint32_t p = (uint32_t)here - 1u;
+        const int64_t p0 = pfx[s], rx = p0 + ((int64_t)arow[k] - g.rb);
+        if (F.fptr[rx + 1] - F.fptr[rx] > FWD_SHORT) F.fid[p] = e;
+        else F.fwd[p] = ((uint32_t)F.rank[p0 + (e >> 2)] << 2) | (e & 3u);
     }
 }
 
-// One warp per row with a forward list: a stable partition of the list (in
-// id order) by degree class gives rank order; each entry is written as
-// R << 2 | tag, and its dyad {x, y} (owned by y) gets a record in y's part
-// of trec: {first entry of the suffix after y, suffix length, x << 2 | tag
-// of y seen from x, owner row}.
+// One thread per short row (2 .. FWD_SHORT entries): its entries sorted by
+// rank in registers (a bitonic network over 16 words, unused ones padded
+// with the largest word), so that every forward list is in rank order.
+__global__ void k_fwd_sort_short(int64_t rows, FwdLayout F) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b0 = F.fptr[r], m = F.fptr[r + 1] - b0;
+        if (m < 2 || m > FWD_SHORT) continue;
+        uint32_t e[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) e[i] = i < (int)m ? F.fwd[b0 + i] : 0xffffffffu;
+#pragma unroll
+        for (int k = 2; k <= 16; k <<= 1)
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const uint32_t a = e[i], b = e[l];
+                        const bool sw = ((i & k) == 0) ? a > b : a < b;
+                        e[i] = sw ? b : a;
+                        e[l] = sw ? a : b;
+                    }
+                }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (i < (int)m) F.fwd[b0 + i] = e[i];
+    }
+}
+static_assert(FWD_SHORT <= 16, "short rows are sorted in a 16-word network");
+
+// One warp per long row: a stable partition of the forward list (in id
+// order) by degree class gives rank order; each entry is written as
+// R << 2 | tag.
 __global__ void __launch_bounds__(256) k_fwd_sort(const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
-                                                  const int64_t* __restrict__ pfx, int nseg, int64_t rows,
-                                                  FwdLayout F) {
+                                                  const int64_t* __restrict__ pfx, int nseg, FwdLayout F) {
     __shared__ unsigned cnt_all[8][NCLS + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned* cnt = cnt_all[warp];
     const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
-    const int64_t nwarps = (int64_t)gridDim.x * 8;
-    for (int64_t r = blockIdx.x * 8 + warp; r < rows; r += nwarps) {
+    const unsigned nlong = *F.nlong;
+    for (unsigned li = blockIdx.x * 8 + warp; li < nlong; li += gridDim.x * 8) {
+        const int64_t r = F.longs[li];
         const uint32_t b0 = F.fptr[r], m = F.fptr[r + 1] - b0;
-        if (m == 0) continue;
         const int s = row_seg(pfx, nseg, r);
         const int64_t rb = seg[s].rb, p0 = pfx[s];
-        const uint32_t xl = (uint32_t)(r - p0);
         cnt[lane] = 0;
         __syncwarp();
         for (uint32_t i0 = 0; i0 < m; i0 += 32) {
@@ -292,21 +385,68 @@ __global__ void __launch_bounds__(256) k_fwd_sort(const int32_t* __restrict__ de
             __syncwarp();
             if (c < NCLS && (same & lt) == 0) cnt[c] += __popc(same);
             __syncwarp();
-            if (i < m) {
-                const int64_t ry = p0 + (e >> 2);
-                F.fwd[b0 + pos] = ((uint32_t)F.rank[ry] << 2) | (e & 3u);
-                const uint32_t slot = F.tptr[ry] + atomicAdd(F.tcur + ry, 1u);
-                F.trec[slot] = make_uint4(b0 + pos + 1, m - pos - 1, (xl << 2) | (e & 3u), (uint32_t)ry);
-            }
+            if (i < m) F.fwd[b0 + pos] = ((uint32_t)F.rank[p0 + (e >> 2)] << 2) | (e & 3u);
         }
     }
 }
 
+// Dyad records, written from the owner's side with no atomics: entry f of
+// row y whose neighbour x ranks below y is the dyad {x, y} owned by y, and
+// its index among row y's such entries (the entries before it minus the
+// forward ones, from the flag scan) is its slot in y's records.  Its lookup
+// list is x's whole forward list when that is short, else the part of it
+// ranked above y (found by binary search of the sorted list).
+__global__ void k_fwd_recs(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+                           const int32_t* __restrict__ arow, const SegDev* __restrict__ seg,
+                           const int64_t* __restrict__ pfx, const int64_t* __restrict__ epfx, int nseg,
+                           int64_t entries, int64_t rows, FwdLayout F) {
+    const unsigned long long tot = F.tpre[rows];
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < entries;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t here = F.fs[f];
+        if (here != (f > 0 ? F.fs[f - 1] : 0)) continue;  // forward: not owned by this row
+        const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
+        const SegDev& g = seg[s];
+        const int64_t k = g.eb + (f - epfx[s]);
+        const int64_t p0 = pfx[s], y = arow[k], ry = p0 + (y - g.rb);
+        const uint8_t kd = F.kind[ry];
+        if (kd == 0) continue;
+        const int64_t f0 = epfx[s] + (row_ptr[y] - g.eb);  // the row's first entry
+        const uint32_t fwd_before = (uint32_t)here - (f0 > 0 ? (uint32_t)F.fs[f0 - 1] : 0u);
+        const uint32_t j = (uint32_t)(f - f0) - fwd_before;
+        const unsigned long long pre = F.tpre[ry];
+        const uint32_t slot = (kd == 1 ? (uint32_t)(pre >> 32) : (uint32_t)(tot >> 32) + (uint32_t)pre) + j;
+        const uint32_t e = __ldg(adj + k);
+        const int64_t rx = p0 + (e >> 2);
+        uint32_t a = F.fptr[rx], m = F.fptr[rx + 1] - a;
+        if (m > FWD_SHORT) {  // the part of the sorted list ranked above y
+            const uint32_t key = (uint32_t)F.rank[ry] << 2;
+            uint32_t lo = a, n = m;
+            while (n > 0) {
+                const uint32_t half = n >> 1;
+                if ((F.fwd[lo + half] & ~3u) <= key) {
+                    lo += half + 1;
+                    n -= half + 1;
+                } else {
+                    n = half;
+                }
+            }
+            m -= lo - a;
+            a = lo;
+        }
+        F.trec[slot] = make_uint4(a, m, ((e >> 2) << 2) | tag_swap(e & 3u), (uint32_t)ry);
+    }
+}
+
 // ------------------------------------------------------------ triangles --
-// The four updates a triangle makes, its vertices given in any order with
-// the tags between them (t_pq = e(p,q) + 2 e(q,p)).
-__device__ __forceinline__ void tri_correct(int32_t* h, uint32_t a, uint32_t b, uint32_t c, uint32_t t_ab,
-                                            uint32_t t_ac, uint32_t t_bc) {
+// A triangle's correction depends only on its three tags in the id order of
+// its vertices a < b < c: t_ab, t_ac, t_bc in {1, 2, 3} (27 triangle
+// types).  Dyad <a,b> moves one count from codes t_ab + 4 t_ac and
+// t_ab + 16 t_bc to t_ab + 4 t_ac + 16 t_bc, and dyad <a,c> drops the count
+// t_ac + 16 t_cb it added for b.  The lookups count triangles per type; the
+// four code updates per type are applied when the counts are flushed.
+__device__ __forceinline__ int tri_type(uint32_t a, uint32_t b, uint32_t c, uint32_t t_ab, uint32_t t_ac,
+                                        uint32_t t_bc) {
     uint32_t t;
     if (a > b) {
         t = a; a = b; b = t;
@@ -319,72 +459,60 @@ __device__ __forceinline__ void tri_correct(int32_t* h, uint32_t a, uint32_t b, 
         t = t_ab; t_ab = t_ac; t_ac = t;
     }
     if (a > b) {
-        t = a; a = b; b = t;
         t_ab = tag_swap(t_ab);
         t = t_ac; t_ac = t_bc; t_bc = t;
     }
-    atomicAdd(h + t_ab + 4 * t_ac, -1);
-    atomicAdd(h + t_ab + 16 * t_bc, -1);
-    atomicAdd(h + t_ab + 4 * t_ac + 16 * t_bc, 1);
-    atomicAdd(h + t_ac + 16 * tag_swap(t_bc), -1);
+    return (int)(9 * (t_ab - 1) + 3 * (t_ac - 1) + (t_bc - 1));
 }
 
-// Per-warp 32-bit histogram of the 64 codes for one graph, added into the
-// graph's 64-bit accumulators when the graph changes and at the end, and
-// before a slot could leave the int32 range (a triangle moves a slot by at
-// most 4).
+// Per-warp triangle counts by type for one graph; the code updates go into
+// the graph's 64-bit accumulators when the graph changes, at the end, and
+// before a count could wrap.
 struct TriHist {
-    int32_t* hs;
+    uint32_t* hs;  // [2][32]: types 0..26, one copy per lane parity
     unsigned long long* acc;
     int tag;
     int lane;
     unsigned pending;
     __device__ __forceinline__ void flush() {
-        if (tag >= 0)
-            for (int j = lane; j < 64; j += 32) {
-                const int32_t v = hs[j];
-                if (v) atomicAdd(acc + (size_t)tag * ACC + j, (unsigned long long)(long long)v);
-                hs[j] = 0;
+        if (tag >= 0 && lane < 27) {
+            const unsigned long long c = (unsigned long long)hs[lane] + hs[32 + lane];
+            if (c) {
+                unsigned long long* h = acc + (size_t)tag * ACC;
+                const uint32_t t_ab = lane / 9 + 1, t_ac = (lane / 3) % 3 + 1, t_bc = lane % 3 + 1;
+                atomicAdd(h + t_ab + 4 * t_ac, 0ull - c);
+                atomicAdd(h + t_ab + 16 * t_bc, 0ull - c);
+                atomicAdd(h + t_ab + 4 * t_ac + 16 * t_bc, c);
+                atomicAdd(h + t_ac + 16 * tag_swap(t_bc), 0ull - c);
             }
+        }
+        hs[lane] = 0;
+        hs[32 + lane] = 0;
         __syncwarp();
         pending = 0;
     }
     __device__ __forceinline__ void retag(int s) {
-        if (s != tag || pending > (1u << 28)) {
+        if (s != tag || pending > (1u << 30)) {
             flush();
             tag = s;
         }
     }
+    // one triangle per active lane (shared-memory atomics; the two copies
+    // halve the lanes that meet on one counter)
+    __device__ __forceinline__ void add(bool active, int type) {
+        if (active) atomicAdd(hs + ((lane & 1) << 5) + type, 1u);
+    }
 };
 
 constexpr int TQN = 64;  // per-warp queue of hits (ring)
-
-struct TriQueue {
-    uint2* q;   // {R << 2 | t_h(w), dyad << 2 | t_x(w)}
-    int head, n;
-};
-
-// Shared-memory layout of k_tri_big.
-constexpr int TB_NT = 512;
-constexpr int TB_W = TB_NT / 32;
-constexpr size_t TB_MAP_BYTES = sizeof(uint32_t) * (MAP_KEYS / 16);
-constexpr size_t TB_OFF_BYTES = sizeof(uint32_t) * (TRI_PIECE + 32);
-constexpr size_t TB_FST_BYTES = sizeof(uint32_t) * TRI_PIECE;
-constexpr size_t TB_XIN_BYTES = sizeof(uint32_t) * TRI_PIECE;
-constexpr size_t TB_HS_BYTES = sizeof(int32_t) * 64 * TB_W;
-constexpr size_t TB_Q_BYTES = sizeof(uint2) * TQN * TB_W;
-constexpr size_t TB_SMEM = TB_MAP_BYTES + TB_OFF_BYTES + TB_FST_BYTES + TB_XIN_BYTES + TB_HS_BYTES + TB_Q_BYTES;
-static_assert(TRI_PIECE == 2 * TB_NT, "a piece's records are read two per thread");
 
 struct TriArgs {
     const SegDev* seg;
     const int64_t* pfx;
     int nseg;
     int64_t rows;
-    int big_min;
     const uint32_t* fptr;
-    const uint32_t* tptr;
-    const uint32_t* nown;
+    const unsigned long long* tpre;
     const uint32_t* fwd;
     const uint4* trec;
     const uint4* items;
@@ -395,335 +523,470 @@ struct TriArgs {
     const int32_t* perm;
     unsigned long long* acc;
     unsigned long long* stat;  // [0] tag-map lookups, [1] their triangles, [2] search lookups, [3] triangles
-    uint32_t ntrec;            // records (dyads of the selection)
-    int* err;                  // set when a rank lies outside the range its construction gives it
 };
 
-struct TbCtl {
-    unsigned item;
-    int64_t mapped;  // owner whose tag map is in shared memory (-1: none)
-    uint32_t mb, mn;  // its forward list
-    int32_t mR;
-    int ntask, total;
-    unsigned long long wsum[TB_W];
-};
+// Lookup lists are cut into pieces of at most PIECE entries: a warp locates
+// 32 pieces at a time from the start bits of the dyads whose pieces begin in
+// that chunk (one piece per lane), then looks them up two at a time, one per
+// half-warp, each lane one entry (coalesced loads).  R-MAT scale 22: 82% of
+// the lanes' entry slots are used.
+constexpr int PIECE = 16;
+constexpr int HW_ILP = 4;  // piece pairs whose entries a warp loads together
 
-// Apply the queued hits at the head (cnt of them, one per lane): the third
-// vertex's id from the rank permutation, x and t_x(h) from the dyad table.
-__device__ __forceinline__ void big_drain(TriHist& H, TriQueue& Q, int cnt, const uint32_t* txin, const int32_t* perm,
-                                          int64_t p0, int64_t n, uint32_t hl, unsigned& hits) {
-    __syncwarp();
-    const int lane = H.lane;
-    if (lane < cnt) {
-        const uint2 e = Q.q[(Q.head + lane) & (TQN - 1)];
-        const uint32_t R = e.x >> 2, th = e.x & 3u;
-        const uint32_t xin = txin[e.y >> 2];
-        if (R < n) {  // ranks of the graph lie in [0, n)
-            const uint32_t w = (uint32_t)perm[p0 + R];
-            tri_correct(H.hs, xin >> 2, hl, w, xin & 3u, e.y & 3u, th);
-            ++hits;
-        }
-    }
-    __syncwarp();
-    Q.head = (Q.head + cnt) & (TQN - 1);
-    Q.n -= cnt;
+// Pieces of the dyads begun before chunk c: `before` is advanced past the
+// dyads whose first piece lies in [c, c + 32); returns this lane's dyad.
+// `start` is the dyad's first piece (ignored for lanes without one).
+__device__ __forceinline__ int chunk_dyad(bool has, uint32_t start, uint32_t c, int& before, int lane) {
+    const bool in = has && start >= c && start < c + 32;
+    const unsigned bits = __reduce_or_sync(0xffffffffu, in ? 1u << (start - c) : 0u);
+    const int d = before + __popc(bits & (0xffffffffu >> (31 - lane))) - 1;
+    before += __popc(bits);
+    return d;
 }
 
-// Owners with a tag map: persistent CTAs take work items (pieces of one
-// owner's dyad records); consecutive pieces of one owner reuse its map.
-__global__ void __launch_bounds__(TB_NT, 2) k_tri_big(TriArgs a) {
+// Queue a chunk-iteration's hits (one lookup per lane): {R << 2 | t_h(w),
+// dyad << 2 | t_x(w)}.
+__device__ __forceinline__ void enqueue(uint2* q, int qh, int& qn, bool hit, uint32_t kv, uint32_t th, int d, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) q[(qh + qn + __popc(m & ((1u << lane) - 1u))) & (TQN - 1)] = make_uint2((kv & ~3u) | th, ((uint32_t)d << 2) | (kv & 3u));
+    qn += __popc(m);
+}
+
+// Apply cnt queued hits (one per lane): the third vertex's id from the rank
+// permutation; x and t_x(h) from xin of the hit's dyad; the owner h.
+// Queued hits are applied in two steps, so that the gather of the third
+// vertex's id overlaps the following lookups: drain() takes cnt entries off
+// the queue (one per lane), reads x, t_x(h) and the owner from the hit's
+// dyad, issues the gather and keeps the batch pending; the pending batch is
+// counted when the next one is taken (or by finish(), before the dyad table
+// changes).
+struct Pending {
+    uint32_t w, x, h, tags;  // third vertex (loading), x << 2 | t_x(h), owner, t_x(w) << 2 | t_h(w)
+    bool on;
+};
+
+__device__ __forceinline__ void finish(TriHist& H, Pending& P, unsigned& hits) {
+    int type = 0;
+    if (P.on) {
+        type = tri_type(P.x >> 2, P.h, P.w, P.x & 3u, P.tags >> 2, P.tags & 3u);
+        ++hits;
+    }
+    H.add(P.on, type);
+    P.on = false;
+}
+
+template <class XinOf, class OwnerOf>
+__device__ __forceinline__ void drain(TriHist& H, Pending& P, uint2* q, int& head, int& n, int cnt, XinOf xin_of,
+                                      OwnerOf owner_of, const int32_t* perm, int64_t p0, int64_t ns,
+                                      unsigned& hits) {
+    const int lane = H.lane;
+    finish(H, P, hits);
+    __syncwarp();
+    const uint2 e = q[(head + (lane < cnt ? lane : 0)) & (TQN - 1)];
+    const int dq = lane < cnt ? (int)(e.y >> 2) : 0;
+    const uint32_t qx = xin_of(dq), qh = owner_of(dq);
+    P.on = lane < cnt && (e.x >> 2) < ns;  // ranks of the graph lie in [0, n)
+    if (P.on) {
+        P.w = (uint32_t)perm[p0 + (e.x >> 2)];
+        P.x = qx;
+        P.h = qh;
+        P.tags = ((e.y & 3u) << 2) | (e.x & 3u);
+    }
+    __syncwarp();
+    head = (head + cnt) & (TQN - 1);
+    n -= cnt;
+}
+
+// Shared-memory layout of k_tri_big.
+constexpr int TB_NT = 256;
+constexpr int TB_W = TB_NT / 32;
+constexpr int TB_REC = TRI_PIECE;  // records per work item, two per thread
+constexpr size_t TB_MAP_BYTES = sizeof(uint32_t) * (MAP_KEYS / 16);
+constexpr size_t TB_LIST_BYTES = sizeof(uint32_t) * 2 * MLIST;
+constexpr size_t TB_TAB_BYTES = sizeof(uint32_t) * 4 * TB_REC;
+constexpr size_t TB_HS_BYTES = sizeof(uint32_t) * 64 * TB_W;
+constexpr size_t TB_Q_BYTES = sizeof(uint2) * TQN * TB_W;
+constexpr size_t TB_SMEM = TB_MAP_BYTES + TB_LIST_BYTES + TB_TAB_BYTES + TB_HS_BYTES + TB_Q_BYTES;
+static_assert(TB_REC == 2 * TB_NT, "a work item's records are read two per thread");
+
+// Tag-map work items: two words each, {owner row, owner rank, forward list
+// start, its length} and {first record, end of records, graph, 0}
+// (k_fwd_rows writes {owner row, piece}; k_fwd_items completes them once the
+// record offsets are known).
+__global__ void k_fwd_items(const int64_t* __restrict__ pfx, int nseg, FwdLayout F) {
+    const unsigned n = min(*F.nitems, F.item_cap);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint4 it = F.items[2 * k];
+        const int64_t rh = it.x;
+        const uint32_t tb = (uint32_t)(F.tpre[rh] >> 32), te = (uint32_t)(F.tpre[rh + 1] >> 32);
+        const uint32_t t0 = tb + it.y * TB_REC, t1 = min(te, t0 + (uint32_t)TB_REC);
+        const uint32_t mb = F.fptr[rh];
+        F.items[2 * k] = make_uint4(it.x, (uint32_t)F.rank[rh], mb, F.fptr[rh + 1] - mb);
+        F.items[2 * k + 1] = make_uint4(t0, t1, (uint32_t)row_seg(pfx, nseg, rh), 0u);
+    }
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Owners with a tag map: persistent CTAs take work items (up to TB_REC of
+// one owner's records each) from a global cursor, two items ahead: the
+// descriptor of the item after next is fetched while this one runs, and
+// warp 0 copies the next owner's forward list asynchronously.  The item's
+// dyads with a non-empty lookup list are compacted into a table (first
+// entry, length, x << 2 | t_x(h), first piece), and the warps take its
+// pieces 32 at a time from a shared cursor.  The item's records load while
+// the map changes owner.
+__global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
     extern __shared__ __align__(16) unsigned char tb_smem[];
     uint32_t* map = reinterpret_cast<uint32_t*>(tb_smem);
-    uint32_t* toff = reinterpret_cast<uint32_t*>(tb_smem + TB_MAP_BYTES);
-    uint32_t* tfst = reinterpret_cast<uint32_t*>(tb_smem + TB_MAP_BYTES + TB_OFF_BYTES);
-    uint32_t* txin = reinterpret_cast<uint32_t*>(tb_smem + TB_MAP_BYTES + TB_OFF_BYTES + TB_FST_BYTES);
-    int32_t* hs_all = reinterpret_cast<int32_t*>(tb_smem + TB_MAP_BYTES + TB_OFF_BYTES + TB_FST_BYTES + TB_XIN_BYTES);
-    uint2* q_all = reinterpret_cast<uint2*>(tb_smem + TB_MAP_BYTES + TB_OFF_BYTES + TB_FST_BYTES + TB_XIN_BYTES +
-                                            TB_HS_BYTES);
-    __shared__ TbCtl ctl;
+    uint32_t* mlist = reinterpret_cast<uint32_t*>(tb_smem + TB_MAP_BYTES);
+    uint32_t* pof = reinterpret_cast<uint32_t*>(tb_smem + TB_MAP_BYTES + TB_LIST_BYTES);
+    uint32_t* tfst = pof + TB_REC;
+    uint32_t* tlen = tfst + TB_REC;
+    uint32_t* txin = tlen + TB_REC;
+    uint32_t* hs_all = reinterpret_cast<uint32_t*>(tb_smem + TB_MAP_BYTES + TB_LIST_BYTES + TB_TAB_BYTES);
+    uint2* q_all = reinterpret_cast<uint2*>(tb_smem + TB_MAP_BYTES + TB_LIST_BYTES + TB_TAB_BYTES + TB_HS_BYTES);
+    __shared__ unsigned long long wsum[TB_W];
+    __shared__ int ctl_ntask, ctl_total;
+    __shared__ unsigned ccur;  // next 32-piece chunk of the item
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     for (int j = threadIdx.x; j < MAP_KEYS / 16; j += TB_NT) map[j] = 0;
     TriHist H{hs_all + warp * 64, a.acc, -1, lane, 0u};
-    for (int j = lane; j < 64; j += 32) H.hs[j] = 0;
-    TriQueue Q{q_all + warp * TQN, 0, 0};
-    if (threadIdx.x == 0) ctl.mapped = -1;
+    H.hs[lane] = 0;
+    H.hs[32 + lane] = 0;
+    uint2* q = q_all + warp * TQN;
+    int qh = 0, qn = 0;
+    Pending P{0, 0, 0, 0, false};
     unsigned long long looked = 0, tri = 0;
     unsigned hits = 0;
     const unsigned nitems = min(*a.nitems, a.item_cap);
-    __syncthreads();
-    for (;;) {
-        if (threadIdx.x == 0) ctl.item = atomicAdd(a.cursor, 1u);
-        __syncthreads();
-        const unsigned it = ctl.item;
-        if (it >= nitems) break;
-        const uint4 rec = a.items[it];
-        const int64_t rh = rec.x;
-        const int s = row_seg(a.pfx, a.nseg, rh);
-        const int64_t p0 = a.pfx[s], ns = a.seg[s].n;
-        const uint32_t hl = (uint32_t)(rh - p0);
-        const int32_t Rh = a.rank[rh];
-        if (rh != ctl.mapped) {  // clear the previous owner's map entries, then map this owner
-            if (ctl.mapped >= 0)
-                for (uint32_t i = threadIdx.x; i < ctl.mn; i += TB_NT) {
-                    const uint32_t k = (a.fwd[ctl.mb + i] >> 2) - (uint32_t)ctl.mR - 1u;
-                    if (k < (uint32_t)MAP_KEYS) map[k >> 4] = 0;
-                }
-            __syncthreads();
-            const uint32_t mb = a.fptr[rh], mn = a.fptr[rh + 1] - mb;
-            for (uint32_t i = threadIdx.x; i < mn; i += TB_NT) {
-                const uint32_t e = a.fwd[mb + i];
-                const uint32_t k = (e >> 2) - (uint32_t)Rh - 1u;
-                if (k < (uint32_t)MAP_KEYS) atomicOr(map + (k >> 4), (e & 3u) << (2 * (k & 15u)));
-                else atomicOr(a.err, 2);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                ctl.mapped = rh;
-                ctl.mb = mb;
-                ctl.mn = mn;
-                ctl.mR = Rh;
-            }
+    // descriptors of this item and the next two (slot i % 3); y = 0xffffffff
+    // in the second word's z marks "no item"
+    __shared__ uint4 dring[3][2];
+    const uint4 none = make_uint4(0, 0, 0xffffffffu, 0);
+    auto fetch = [&](uint4& A, uint4& B) {  // lane 0 of warp 0
+        const unsigned k = atomicAdd(a.cursor, 1u);
+        if (k < nitems) {
+            A = a.items[2 * k];
+            B = a.items[2 * k + 1];
+        } else {
+            A = make_uint4(0, 0, 0, 0);
+            B = none;
         }
-        H.retag(s);
-        // the piece's dyads with a non-empty suffix, in record order: first
-        // suffix entry, running slot offset, x << 2 | t_x(h)
-        const uint32_t t0 = a.tptr[rh] + rec.y * TRI_PIECE;
-        const uint32_t t1 = min(a.tptr[rh] + a.nown[rh], t0 + TRI_PIECE);
+    };
+    uint4 fA = make_uint4(0, 0, 0, 0), fB = none;  // the item after next, in flight (warp 0 lane 0)
+    if (threadIdx.x == 0) {
+        uint4 A, B;
+        fetch(A, B);
+        dring[0][0] = A;
+        dring[0][1] = B;
+        fetch(A, B);
+        dring[1][0] = A;
+        dring[1][1] = B;
+    }
+    __syncthreads();
+    if (warp == 0 && dring[0][1].z != 0xffffffffu) {
+        for (uint32_t i = lane; i < dring[0][0].w; i += 32) cp_async4(mlist + i, a.fwd + dring[0][0].z + i);
+        cp_async_commit();
+    }
+    int64_t prev_rh = -1;
+    int32_t prev_R = 0;
+    uint32_t prev_n = 0;
+    for (int b = 0, slot = 0;; b ^= 1, slot = slot == 2 ? 0 : slot + 1) {
+        const uint4 dA = dring[slot][0], dB = dring[slot][1];
+        if (dB.z == 0xffffffffu) break;
+        const uint4 nA = dring[slot == 2 ? 0 : slot + 1][0], nB = dring[slot == 2 ? 0 : slot + 1][1];
+        if (threadIdx.x == 0) fetch(fA, fB);  // consumed at the end of this item
+        const int64_t rh = dA.x;
+        const int32_t Rh = (int32_t)dA.y;
+        const uint32_t mn = dA.w, t0 = dB.x, t1 = dB.y;
+        const int sg = (int)dB.z;
+        const int64_t p0 = a.pfx[sg], ns = a.seg[sg].n;
+        // the item's records, two per thread, in flight while the map changes
         uint4 r0 = make_uint4(0, 0, 0, 0), r1 = make_uint4(0, 0, 0, 0);
         const uint32_t i0 = t0 + 2 * threadIdx.x;
         if (i0 < t1) r0 = a.trec[i0];
         if (i0 + 1 < t1) r1 = a.trec[i0 + 1];
-        const unsigned long long v = ((unsigned long long)((r0.y > 0) + (r1.y > 0)) << 40) | (r0.y + r1.y);
+        if (warp == 0) cp_async_wait_all();  // this owner's list is in mlist[b]
+        if (rh != prev_rh) {  // clear the previous owner's entries, then map this owner
+            const uint32_t* old = mlist + (b ^ 1) * MLIST;
+            for (uint32_t i = threadIdx.x; i < prev_n; i += TB_NT) {
+                const uint32_t k = (old[i] >> 2) - (uint32_t)prev_R - 1u;
+                if (k < (uint32_t)MAP_KEYS) map[k >> 4] = 0;
+            }
+            __syncthreads();
+            const uint32_t* cur = mlist + b * MLIST;
+            for (uint32_t i = threadIdx.x; i < mn; i += TB_NT) {
+                const uint32_t e = cur[i];
+                const uint32_t k = (e >> 2) - (uint32_t)Rh - 1u;
+                if (k < (uint32_t)MAP_KEYS) atomicOr(map + (k >> 4), (e & 3u) << (2 * (k & 15u)));
+            }
+        }
+        // the item's table: one block-wide scan of (dyads << 40 | pieces)
+        const uint32_t np0 = (r0.y + PIECE - 1) / PIECE, np1 = (r1.y + PIECE - 1) / PIECE;
+        const unsigned long long v = ((unsigned long long)((np0 > 0) + (np1 > 0)) << 40) | (np0 + np1);
         unsigned long long incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long t = __shfl_up_sync(full, incl, o);
             if (lane >= o) incl += t;
         }
-        if (lane == 31) ctl.wsum[warp] = incl;
+        if (lane == 31) wsum[warp] = incl;
+        if (threadIdx.x == 0) ccur = 0;
         __syncthreads();
         unsigned long long ex = incl - v;
-        for (int w = 0; w < warp; ++w) ex += ctl.wsum[w];
+        for (int w = 0; w < warp; ++w) ex += wsum[w];
         {
             int d = (int)(ex >> 40);
-            uint32_t off = (uint32_t)(ex & 0xffffffffffull);
-            if (r0.y > 0) {
-                toff[d] = off;
+            uint32_t po = (uint32_t)(ex & 0xffffffffffull);
+            if (np0 > 0) {
+                pof[d] = po;
                 tfst[d] = r0.x;
+                tlen[d] = r0.y;
                 txin[d] = r0.z;
                 ++d;
-                off += r0.y;
+                po += np0;
             }
-            if (r1.y > 0) {
-                toff[d] = off;
+            if (np1 > 0) {
+                pof[d] = po;
                 tfst[d] = r1.x;
+                tlen[d] = r1.y;
                 txin[d] = r1.z;
             }
         }
         if (threadIdx.x == TB_NT - 1) {
             ex += v;
-            ctl.ntask = (int)(ex >> 40);
-            ctl.total = (int)(ex & 0xffffffffffull);
+            ctl_ntask = (int)(ex >> 40);
+            ctl_total = (int)(ex & 0xffffffffffull);
         }
         __syncthreads();
-        const int ntask = ctl.ntask, total = ctl.total;
-        for (int j = threadIdx.x; j < 32; j += TB_NT) toff[ntask + j] = 0xffffffffu;  // no start past the end
-        __syncthreads();
-        // this warp's equal share of the concatenated suffixes
-        const int lo = (int)((int64_t)total * warp / TB_W), hi = (int)((int64_t)total * (warp + 1) / TB_W);
-        if (lo < hi) {
-            int before;  // dyads starting below lo
+        const int ntask = ctl_ntask, total = ctl_total;
+        if (warp == 0 && nB.z != 0xffffffffu) {  // the next owner's list, asynchronously
+            uint32_t* nl = mlist + (b ^ 1) * MLIST;
+            for (uint32_t i = lane; i < nA.w; i += 32) cp_async4(nl + i, a.fwd + nA.z + i);
+            cp_async_commit();
+        }
+        H.retag(sg);
+        const uint32_t Rh1 = (uint32_t)Rh + 1u, hl = (uint32_t)(rh - p0);
+        // 32-piece chunks of the item, taken dynamically by the warps
+        for (;;) {
+            int c = 0;
+            if (lane == 0) c = (int)atomicAdd(&ccur, 32u);
+            c = __shfl_sync(full, c, 0);
+            if (c >= total) break;
+            int before;  // dyads whose first piece lies below c
             {
-                int l = 0, h = ntask;  // first d with toff[d] >= lo
+                int l = 0, h = ntask;
                 while (l < h) {
                     const int mid = (l + h) >> 1;
-                    if ((int)toff[mid] < lo) l = mid + 1;
+                    if ((int)pof[mid] < c) l = mid + 1;
                     else h = mid;
                 }
                 before = l;
             }
-            // slot -> (valid, entry index, dyad) for the chunk at c; advances `before`
-            auto locate = [&](int c, bool& ok, uint32_t& fi, int& d) {
-                const uint32_t st = before + lane < ntask + 32 ? toff[before + lane] : 0xffffffffu;
-                const bool in = st != 0xffffffffu && (int)st < c + 32;
-                // dyads starting in [c, c + 32): their start bits
-                const unsigned bits = __reduce_or_sync(full, in ? 1u << ((int)st - c) : 0u);
-                const int sl = c + lane;
-                ok = sl < hi;
-                d = before + __popc(bits & (lt | (1u << lane))) - 1;
-                before += __popc(bits);
-                fi = ok ? tfst[d] + (uint32_t)(sl - (int)toff[d]) : 0u;
-            };
-            bool ok0;
-            uint32_t fi0;
-            int d0;
-            locate(lo, ok0, fi0, d0);
-            uint32_t k0 = ok0 ? __ldg(a.fwd + fi0) : 0u;
-            for (int c = lo; c < hi; c += 32) {
-                bool ok1 = false;
-                uint32_t fi1 = 0, k1 = 0;
-                int d1 = 0;
-                if (c + 32 < hi) {
-                    locate(c + 32, ok1, fi1, d1);
-                    k1 = ok1 ? __ldg(a.fwd + fi1) : 0u;
-                }
-                const uint32_t kk = (k0 >> 2) - (uint32_t)Rh - 1u;  // < MAP_KEYS: the suffix ranks above h
-                const uint32_t th = ok0 && kk < (uint32_t)MAP_KEYS ? (map[kk >> 4] >> (2 * (kk & 15u))) & 3u : 0u;
-                const bool hit = th != 0;
-                const unsigned m = __ballot_sync(full, hit);
-                if (hit) Q.q[(Q.head + Q.n + __popc(m & lt)) & (TQN - 1)] =
-                    make_uint2(((k0 >> 2) << 2) | th, ((uint32_t)d0 << 2) | (k0 & 3u));
-                Q.n += __popc(m);
-                if (Q.n >= 32) big_drain(H, Q, 32, txin, a.perm, p0, ns, hl, hits);
-                looked += ok0 ? 1 : 0;
-                ok0 = ok1;
-                fi0 = fi1;
-                k0 = k1;
-                d0 = d1;
+            const bool has = before + lane < ntask;
+            const uint32_t st = has ? pof[before + lane] : 0u;
+            const int d = chunk_dyad(has, st, (uint32_t)c, before, lane);
+            const bool ok = c + lane < total;
+            uint32_t base = 0, cnt = 0;
+            if (ok) {
+                const uint32_t pq = (uint32_t)(c + lane) - pof[d];
+                base = tfst[d] + PIECE * pq;
+                cnt = min((uint32_t)PIECE, tlen[d] - PIECE * pq);
             }
+            // the chunk's pieces two at a time, one per half-warp (lane & 15
+            // is the entry), HW_ILP pairs loaded together
+            const int npc = min(32, total - c), e = lane & 15, half = lane >> 4;
+            for (int u0 = 0; u0 < npc; u0 += 2 * HW_ILP) {
+                uint32_t kv[HW_ILP];
+                int dv[HW_ILP];
+                bool vv[HW_ILP];
+#pragma unroll
+                for (int u = 0; u < HW_ILP; ++u) {
+                    const int src = u0 + 2 * u + half;
+                    const uint32_t pb = __shfl_sync(full, base, src & 31), pc = __shfl_sync(full, cnt, src & 31);
+                    dv[u] = __shfl_sync(full, d, src & 31);
+                    vv[u] = src < npc && (uint32_t)e < pc;
+                    kv[u] = vv[u] ? __ldg(a.fwd + pb + e) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < HW_ILP; ++u) {
+                    const uint32_t kk = (kv[u] >> 2) - Rh1;  // ranks at or below h fall outside the map
+                    const uint32_t th =
+                        vv[u] && kk < (uint32_t)MAP_KEYS ? (map[kk >> 4] >> (2 * (kk & 15u))) & 3u : 0u;
+                    enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
+                    if (qn >= 32)
+                        drain(H, P, q, qh, qn, 32, [&](int dq) { return txin[dq]; }, [&](int) { return hl; },
+                              a.perm, p0, ns, hits);
+                }
+            }
+            looked += cnt;
         }
-        if (Q.n > 0) big_drain(H, Q, Q.n, txin, a.perm, p0, ns, hl, hits);  // the table changes next
+        if (qn > 0)  // the table changes next
+            drain(H, P, q, qh, qn, qn, [&](int dq) { return txin[dq]; }, [&](int) { return hl; }, a.perm, p0, ns,
+                  hits);
+        finish(H, P, hits);
         const unsigned wh = __reduce_add_sync(full, hits);
         H.pending += wh;
         tri += wh;
         hits = 0;
+        prev_rh = rh;
+        prev_R = Rh;
+        prev_n = mn;
+        if (threadIdx.x == 0) {
+            const int s2 = slot == 0 ? 2 : slot - 1;  // (slot + 2) % 3
+            dring[s2][0] = fA;
+            dring[s2][1] = fB;
+        }
         __syncthreads();
     }
+    if (warp == 0) cp_async_wait_all();
     H.flush();
     looked = warp_sum64(looked);
     if (lane == 0 && looked) atomicAdd(a.stat + 0, looked);
     if (lane == 0 && tri) atomicAdd(a.stat + 1, tri);
 }
 
-// Every other owner: warps take runs of TS_RUN dyad records (in owner
-// order) and, 32 records at a time, search each suffix entry in its owner's
-// forward list.  Records of tag-map owners, of owners without forward
-// neighbours and with empty suffixes are skipped.
+// Every other owner: warps take runs of TS_RUN records of the search part
+// (grouped by owner) and, 32 records at a time, look each piece's entries up
+// in its owner's forward list (sorted by rank) by binary search, the piece's
+// searches in lockstep (a run's dyads share few owners, so their lists stay
+// in cache).
 constexpr int TS_RUN = 1024;
 
 __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
-    __shared__ int32_t hs_all[8][64];
+    __shared__ uint32_t hs_all[8][64];
     __shared__ uint2 q_all[8][TQN];
-    __shared__ uint4 cr_all[8][32];   // compacted records
-    __shared__ uint2 co_all[8][32];   // their owners' forward lists
+    __shared__ uint4 st_all[8][32];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     TriHist H{hs_all[warp], a.acc, -1, lane, 0u};
-    for (int j = lane; j < 64; j += 32) H.hs[j] = 0;
-    TriQueue Q{q_all[warp], 0, 0};
+    H.hs[lane] = 0;
+    H.hs[32 + lane] = 0;
+    uint2* q = q_all[warp];
+    uint4* stage = st_all[warp];
+    int qh = 0, qn = 0;
+    Pending P{0, 0, 0, 0, false};
     __syncwarp();
     unsigned long long looked = 0, tri = 0;
     unsigned hits = 0;
+    const unsigned long long tot = a.tpre[a.rows];
+    const uint32_t r0 = (uint32_t)(tot >> 32), r1 = r0 + (uint32_t)(tot & 0xffffffffull);
     for (;;) {
         unsigned run = 0;
-        if (lane == 0) run = atomicAdd(a.cursor + 1, (unsigned)TS_RUN);
+        if (lane == 0) run = r0 + atomicAdd(a.cursor + 1, (unsigned)TS_RUN);
         run = __shfl_sync(full, run, 0);
-        if (run >= a.ntrec) break;
-        const uint32_t rend = min(a.ntrec, run + TS_RUN);
+        if (run >= r1) break;
+        const uint32_t rend = min(r1, run + TS_RUN);
         for (uint32_t g0 = run; g0 < rend;) {
             const uint32_t t = g0 + lane;
             const bool valid = t < rend;
             const uint4 rec = valid ? a.trec[t] : make_uint4(0, 0, 0, 0);
-            const int64_t rh = rec.w;
-            int s = valid ? row_seg(a.pfx, a.nseg, rh) : -1;
+            const int s = valid ? row_seg(a.pfx, a.nseg, (int64_t)rec.w) : -1;
             const int s0 = __shfl_sync(full, s, 0);
-            // a group stays within one graph (records are in owner order)
+            // a group stays within one graph (records are grouped by owner)
             const unsigned other = __ballot_sync(full, !valid || s != s0);
             const int take = other ? __ffs(other) - 1 : 32;
-            const bool in = lane < take;
-            uint32_t hb = 0, hn = 0;
-            bool use = false;
-            if (in && rec.y > 0) {
-                hb = a.fptr[rh];
-                hn = a.fptr[rh + 1] - hb;
-                use = hn > 0 && !map_owner((int)hn, a.seg[s].n, a.rank[rh], a.big_min);
-            }
             const int64_t p0 = a.pfx[s0], ns0 = a.seg[s0].n;
             H.retag(s0);
-            // compact the used records into lanes 0 .. ng-1
+            // the group's dyads with a non-empty lookup list, compacted
+            const bool use = lane < take && rec.y > 0;
             const unsigned um = __ballot_sync(full, use);
             const int ng = __popc(um);
-            if (use) {
-                const int at = __popc(um & lt);
-                cr_all[warp][at] = make_uint4(rec.x, rec.y, rec.z, (uint32_t)(rh - p0));
-                co_all[warp][at] = make_uint2(hb, hn);
-            }
+            if (use) stage[__popc(um & lt)] = rec;
             __syncwarp();
-            uint32_t fst = 0, len = 0, xin = 0, ob = 0, on = 0, hl = 0;
+            uint32_t fst = 0, len = 0, xin = 0, hl = 0, hb = 0, hn = 0;
             if (lane < ng) {
-                const uint4 c = cr_all[warp][lane];
-                const uint2 o = co_all[warp][lane];
+                const uint4 c = stage[lane];
                 fst = c.x;
                 len = c.y;
                 xin = c.z;
-                hl = c.w;
-                ob = o.x;
-                on = o.y;
+                hl = (uint32_t)((int64_t)c.w - p0);
+                hb = a.fptr[c.w];
+                hn = a.fptr[c.w + 1] - hb;
             }
             __syncwarp();
-            uint32_t off = len;
+            const uint32_t np = (len + PIECE - 1) / PIECE;
+            uint32_t poff = np;  // first piece of this lane's dyad
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(full, off, o);
-                if (lane >= o) off += v;
+                const uint32_t v = __shfl_up_sync(full, poff, o);
+                if (lane >= o) poff += v;
             }
-            const uint32_t total = __shfl_sync(full, off, 31);
-            off -= len;  // exclusive start of this lane's dyad
+            const uint32_t total = __shfl_sync(full, poff, 31);
+            poff -= np;
             int before = 0;
             for (uint32_t c = 0; c < total; c += 32) {
-                const bool st_in = lane < ng && off >= c && off < c + 32;
-                const unsigned bits = __reduce_or_sync(full, st_in ? 1u << (off - c) : 0u);
-                const int d = before + __popc(bits & (lt | (1u << lane))) - 1;
-                before += __popc(bits);
-                const uint32_t sl = c + lane;
-                const bool ok = sl < total;
+                const int d = chunk_dyad(lane < ng, poff, c, before, lane);
+                const bool ok = c + lane < total;
                 const int dd = ok ? d : 0;
-                const uint32_t f_st = __shfl_sync(full, fst, dd), f_off = __shfl_sync(full, off, dd);
-                const uint32_t h_b = __shfl_sync(full, ob, dd), h_n = __shfl_sync(full, on, dd);
-                uint32_t th = 0, kv = 0;
+                const uint32_t d_fst = __shfl_sync(full, fst, dd), d_len = __shfl_sync(full, len, dd);
+                const uint32_t d_off = __shfl_sync(full, poff, dd);
+                const uint32_t h_b = __shfl_sync(full, hb, dd), h_n = __shfl_sync(full, hn, dd);
+                uint32_t cnt = 0, base = 0;
                 if (ok) {
-                    kv = __ldg(a.fwd + f_st + (sl - f_off));
-                    const uint32_t key = kv & ~3u;  // R << 2
-                    uint32_t lo = h_b, n = h_n;
-                    while (n > 0) {
-                        const uint32_t half = n >> 1;
-                        if ((__ldg(a.fwd + lo + half) & ~3u) < key) {
-                            lo += half + 1;
-                            n -= half + 1;
-                        } else {
-                            n = half;
+                    const uint32_t pq = c + lane - d_off;
+                    base = d_fst + PIECE * pq;
+                    cnt = min((uint32_t)PIECE, d_len - PIECE * pq);
+                }
+                // the chunk's pieces two at a time, one per half-warp (lane & 15
+                // is the entry): each lane searches its key in the piece's
+                // owner list, HW_ILP pairs in lockstep
+                const int npc = (int)min(32u, total - c), e = lane & 15, half = lane >> 4;
+                for (int t0 = 0; t0 < npc; t0 += 2 * HW_ILP) {
+                    uint32_t kv[HW_ILP], ob[HW_ILP], on[HW_ILP], pos[HW_ILP];
+                    int dv[HW_ILP];
+                    bool vv[HW_ILP];
+                    uint32_t maxn = 0;
+#pragma unroll
+                    for (int u = 0; u < HW_ILP; ++u) {
+                        const int src = t0 + 2 * u + half;
+                        const uint32_t pb = __shfl_sync(full, base, src & 31), pc = __shfl_sync(full, cnt, src & 31);
+                        dv[u] = __shfl_sync(full, d, src & 31);
+                        const int od = dv[u] < 0 ? 0 : dv[u];
+                        ob[u] = __shfl_sync(full, hb, od & 31);
+                        on[u] = __shfl_sync(full, hn, od & 31);
+                        vv[u] = src < npc && (uint32_t)e < pc;
+                        kv[u] = vv[u] ? __ldg(a.fwd + pb + e) : 0u;
+                        if (!vv[u]) on[u] = 0;
+                        pos[u] = 0;
+                        maxn = max(maxn, on[u]);
+                    }
+                    // lower bound of each key in its owner's sorted list
+                    for (uint32_t step = maxn ? 1u << (31 - __clz(maxn)) : 0u; step > 0; step >>= 1) {
+#pragma unroll
+                        for (int u = 0; u < HW_ILP; ++u)
+                            if (pos[u] + step <= on[u] &&
+                                (__ldg(a.fwd + ob[u] + pos[u] + step - 1) & ~3u) < (kv[u] & ~3u))
+                                pos[u] += step;
+                    }
+#pragma unroll
+                    for (int u = 0; u < HW_ILP; ++u) {
+                        uint32_t th = 0;
+                        if (vv[u] && pos[u] < on[u]) {
+                            const uint32_t w = __ldg(a.fwd + ob[u] + pos[u]);
+                            if ((w & ~3u) == (kv[u] & ~3u)) th = w & 3u;
                         }
+                        enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
+                        if (qn >= 32)
+                            drain(H, P, q, qh, qn, 32, [&](int dq) { return __shfl_sync(full, xin, dq); },
+                                  [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
                     }
-                    if (lo < h_b + h_n) {
-                        const uint32_t e = __ldg(a.fwd + lo);
-                        if ((e & ~3u) == key) th = e & 3u;
-                    }
-                    ++looked;
                 }
-                const bool hit = th != 0;
-                const unsigned m = __ballot_sync(full, hit);
-                if (hit) Q.q[(Q.head + Q.n + __popc(m & lt)) & (TQN - 1)] =
-                    make_uint2((kv & ~3u) | th, ((uint32_t)d << 2) | (kv & 3u));
-                Q.n += __popc(m);
-                while (Q.n >= 32 || (Q.n > 0 && c + 32 >= total)) {  // drain (all before the group changes)
-                    const int cnt = min(Q.n, 32);
-                    __syncwarp();
-                    const uint2 e = Q.q[(Q.head + (lane < cnt ? lane : 0)) & (TQN - 1)];
-                    const int dq = lane < cnt ? (int)(e.y >> 2) : 0;
-                    const uint32_t qx = __shfl_sync(full, xin, dq), qh = __shfl_sync(full, hl, dq);
-                    if (lane < cnt && (e.x >> 2) < ns0) {  // ranks of the graph lie in [0, n)
-                        const uint32_t w = (uint32_t)a.perm[p0 + (e.x >> 2)];
-                        tri_correct(H.hs, qx >> 2, qh, w, qx & 3u, e.y & 3u, e.x & 3u);
-                        ++hits;
-                    }
-                    __syncwarp();
-                    Q.head = (Q.head + cnt) & (TQN - 1);
-                    Q.n -= cnt;
-                }
+                looked += cnt;
             }
+            if (qn > 0)  // the group changes next
+                drain(H, P, q, qh, qn, qn, [&](int dq) { return __shfl_sync(full, xin, dq); },
+                      [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
+            finish(H, P, hits);
             const unsigned wh = __reduce_add_sync(full, hits);
             H.pending += wh;
             tri += wh;
