@@ -2,11 +2,16 @@
 """Benchmark of the triad-census hot path on B300 (one JSON line on stdout).
 
 A step is one pass of the whole hot path over the workload's arc list, which
-is already resident in HBM: device graph build (dedup, tagged adjacency) and
-the census (task build + binning, union merges, classification, fold and
-003 closure).  `value` is merged adjacency entries per second of step time
-(entries = sum over canonical dyads of |N(u)|+|N(v)|, the data the merges must
-read); `census_ms` in the breakdown is the census alone.
+is already resident in HBM: the device graph build (dedup, tagged adjacency)
+and the census (vertex ranks, suffix and dyadic terms, forward lists, the
+triangle lookups, fold and 003 closure).  `census_ms` is the census alone.
+`value` is an effective rate: sum over canonical dyads of |N(u)|+|N(v)|
+(= sum_v d_v^2, what a full union merge of every dyad would read) per second
+of step time; the census reads far less than that, so `roofline` reports the
+dominant kernel against its own algorithmic bytes.  The default run (c3)
+adds sub-records for the heavy-skew workload (`c5`) and the batched one
+(`c4`: graphs/s of a CUDA-graph plan replay, each graph checked against the
+oracle's stored census).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3]
     python bench.py --impl reference ...   # the CPU oracle on host cores
@@ -30,14 +35,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "census time; merged adjacency entries/s vs HBM roofline; graphs/s batched"
-UNIT = "merged adjacency entries/s"
+UNIT = "effective merged adjacency entries/s (full-union equivalent)"
 WORKLOAD_DESC = {
     "c1": "G(n,p) n=1024 p=8/1023 reciprocity 0.25 seed 1",
     "c2": "R-MAT scale 20 edge factor 8 (.57,.19,.19,.05) 10% reciprocated, ids permuted, seed 2",
     "c3": "R-MAT scale 22 edge factor 4 (.57,.19,.19,.05), arcs oriented high->low id, ids permuted, seed 3",
     "c3s": "R-MAT scale 21 edge factor 4, arcs oriented high->low id, ids permuted, seed 3 (profiling case)",
     "c4": "4096 graphs, n log-uniform in [64, 65536], even G(n,p) mean out-degree U(4,32), odd R-MAT edge factor 8, reciprocity U(0,0.5), seed 4",
-    "c5": "Chung-Lu n=2^22 gamma 2.1 mean total degree 16 max 1e5 reciprocity 0.15, seed 5",
+    "c5": "Chung-Lu n=2^22 gamma 2.1 mean total degree 16, largest realised degree ~1e5, reciprocity 0.15, seed 5",
 }
 OWN_BUILD_KERNELS = 8   # k_dyad_keys k_heads k_dyads k_row_counts k_place_lo k_place_up k_fill_sent k_rowstats (plus CUB sort/scan)
 FLUSH_BYTES = 512 << 20  # > 126 MB L2
@@ -83,7 +88,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -333,6 +338,196 @@ def run_reference(args, world, rank, pg):
 
 # ------------------------------------------------------------ native arm
 
+def dominant_kernel(tc, profs, stats):
+    """The census kernel with the largest share of the step, its algorithmic
+    bytes per launch and its event-timed duration.  Forward path: the tag-map
+    lookups (k_tri_big) read, per lookup, one 4-byte lookup-list entry; per
+    dyad record 16 B; per staged owner-list entry 4 B; per triangle the 4-byte
+    rank-permutation entry of its third vertex.  Merge path: k_owner (4 B per
+    lookup plus 4 B per indexed owner entry)."""
+    pl = profs[-1]
+    mean = lambda k: float(np.mean([p[k] for p in profs]))
+    if pl["fwd_entries"] > 0:
+        kern = {"k_tri_big": "ms_tri_map", "k_tri_small": "ms_tri_search", "forward lists": "ms_forward",
+                "task pass": "ms_tasks", "k_fold": "ms_fold"}
+        ms = {k: mean(f) for k, f in kern.items()}
+        big = {"kernel": "k_tri_big", "ms": ms["k_tri_big"],
+               "bytes": 4 * pl["map_lookups"] + 16 * pl["map_dyads"] + 4 * pl["map_list_entries"]
+               + 4 * pl["map_triangles"],
+               "units": {"lookups": pl["map_lookups"], "dyad_records": pl["map_dyads"],
+                         "staged_list_entries": pl["map_list_entries"], "triangles": pl["map_triangles"]},
+               "bytes_per_unit": "4 B per lookup-list entry + 16 B per dyad record + 4 B per staged "
+                                 "owner-list entry + 4 B per triangle (third vertex's id)"}
+        small = {"kernel": "k_tri_small", "ms": ms["k_tri_small"],
+                 "bytes": 4 * pl["search_lookups"] + 16 * pl["search_dyads"] + 4 * pl["search_triangles"]}
+        top = big if big["ms"] >= small["ms"] else small
+    else:
+        kern = {"task pass": "ms_tasks", "k_owner_prep": "ms_owner_prep", "k_owner": "ms_owner",
+                "merge kernels": "ms_merge", "k_fold": "ms_fold"}
+        ms = {k: mean(f) for k, f in kern.items()}
+        top = {"kernel": "k_owner", "ms": ms["k_owner"], "bytes": 4 * (pl["owner_probes"] + pl["owner_staged"]),
+               "units": {"lookups": pl["owner_probes"], "indexed_owner_entries": pl["owner_staged"]},
+               "bytes_per_unit": "4 B per lookup + 4 B per indexed owner entry"}
+    return top, ms
+
+
+def issue_record(kernel):
+    """Warp instructions per lookup of `kernel` from the committed ncu summary
+    (profiles/issue.txt), if it was taken on the current kernel source."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1603_02655_b300", "csrc")
+    h = hashlib.sha256()
+    for f in ("census.cu", "forward.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    sha = h.hexdigest()[:16]
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "issue.txt")):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[2] == sha:
+                return float(parts[1]), sha
+    except OSError:
+        pass
+    return None, sha
+
+
+def recorded_traffic_fwd(kernel, sha):
+    """DRAM bytes per lookup of `kernel` from profiles/traffic.txt for this
+    source (None if the capture predates it)."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[2] == sha:
+                return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+def time_census(tc, torch, g, opts, out, stream, flush, steps):
+    """CUDA-event times (ms) of `steps` census calls, L2 flushed before each."""
+    ts = []
+    for k in range(steps):
+        flush.fill_(k)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tc.tc_census(g, opts, out=out, stream=stream)
+        c.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(c))
+    return ts
+
+
+def c5_record(tc, torch, stream, flush, steps, peak):
+    """The heavy-skew Chung-Lu workload: census time (device-resident graph,
+    default options), the dominant kernel's own-byte fraction, and the census
+    checked against the oracle's stored census."""
+    import synth
+    a = synth.c5()
+    src = torch.from_numpy(a.src).cuda()
+    dst = torch.from_numpy(a.dst).cuda()
+    g = tc.tc_graph_build(a.n, src, dst)
+    del src, dst
+    out = torch.zeros(17, dtype=torch.int64, device="cuda")
+    st = tc.tc_graph_stats(g)
+    run = tc.tc_opts_default()
+    prof = tc.tc_opts_default(profile=1)
+    for _ in range(3):
+        tc.tc_census(g, run, out=out, stream=stream)
+    ts = time_census(tc, torch, g, run, out, stream, flush, steps)
+    census = tc.census_from_device_words(out.cpu().tolist())
+    profs = []
+    for k in range(3):
+        flush.fill_(k)
+        tc.tc_census(g, prof, out=out, stream=stream)
+        profs.append(tc.tc_census_profile())
+    merge = tc.tc_opts_default(tri_path=tc.TC_TRI_MERGE)
+    merge_ms = float(np.median(time_census(tc, torch, g, merge, out, stream, flush, 3)))
+    tc.tc_graph_free(g)
+    top, ms = dominant_kernel(tc, profs, st)
+    gpath = os.path.join(ROOT, "tests", "golden", "census_c5.json")
+    gold = json.load(open(gpath)) if os.path.exists(gpath) else None
+    match = None
+    if gold and gold["stats"]["arcs"] == st["arcs"]:
+        match = gold["census"] == census
+    cms = float(np.median(ts))
+    return {"workload": f"c5: {WORKLOAD_DESC['c5']}", "n": a.n, "arcs": st["arcs"], "dyads": st["dyads"],
+            "max_degree": st["max_degree"], "merged_entries": st["merged_entries"],
+            "census_ms": cms, "census_ms_merge_path": merge_ms,
+            "effective_entries_per_s": st["merged_entries"] / (cms / 1e3),
+            "kernel_ms": ms,
+            "roofline": {"kernel": top["kernel"], "bytes_per_launch": top["bytes"], "ms_per_launch": top["ms"],
+                         "achieved": top["bytes"] / (top["ms"] / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": top["bytes"] / (top["ms"] / 1e3) / 1e9 / peak},
+            "oracle_census_match": match}
+
+
+def c4_record(tc, torch, stream, flush, steps):
+    """The batched workload: 4096 graphs censused by one CUDA-graph plan
+    replay (graphs/s), against one tc_census call per graph, and every
+    graph's census checked against the oracle's stored per-graph census."""
+    import synth
+    t0 = time.perf_counter()
+    b = synth.c4()
+    gen_s = time.perf_counter() - t0
+    G = len(b)
+    src = torch.from_numpy(b.src).cuda()
+    dst = torch.from_numpy(b.dst).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gs = tc.tc_graph_build_batched(b.ns, b.goff, src, dst)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del src, dst
+    merged = sum(tc.tc_graph_stats(g)["merged_entries"] for g in gs)
+    out = torch.zeros(17 * G, dtype=torch.int64, device="cuda")
+    opts = tc.tc_opts_default()
+    plan = tc.tc_plan_create(gs, out, opts, stream=stream)
+    for _ in range(3):
+        tc.tc_plan_run(plan, stream)
+    torch.cuda.synchronize()
+    ts = []
+    for k in range(steps):
+        flush.fill_(k)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tc.tc_plan_run(plan, stream)
+        c.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(c))
+    tc.tc_plan_free(plan)
+    words = out.cpu().tolist()
+    census = [tc.census_from_device_words(words[17 * i:17 * i + 17]) for i in range(G)]
+    # one census call (one launch sequence) per graph
+    per_out = torch.zeros(17 * G, dtype=torch.int64, device="cuda")
+    flush.fill_(0)
+    torch.cuda.synchronize()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i, g in enumerate(gs):
+        tc.tc_census(g, opts, out=per_out[17 * i:17 * i + 17], stream=stream)
+    c.record(stream)
+    torch.cuda.synchronize()
+    per_ms = a.elapsed_time(c)
+    same = per_out.cpu().tolist() == words
+    for g in gs:
+        tc.tc_graph_free(g)
+    gpath = os.path.join(ROOT, "tests", "golden", "census_c4.json")
+    match = None
+    if os.path.exists(gpath):
+        gold = json.load(open(gpath))
+        if "census" in gold:
+            match = gold["census"] == census
+    ms = float(np.median(ts))
+    return {"workload": f"c4: {WORKLOAD_DESC['c4']}", "graphs": G, "arcs": int(b.src.size),
+            "vertices": int(b.ns.sum()), "merged_entries": merged,
+            "ms_per_replay": ms, "graphs_per_s": G / (ms / 1e3),
+            "per_graph_calls": {"ms": per_ms, "graphs_per_s": G / (per_ms / 1e3),
+                                "same_counts": same},
+            "speedup_vs_per_graph": per_ms / ms,
+            "step": "census of all 4096 graphs of one batched build (CUDA-graph plan replay; build excluded)",
+            "build_s": build_s, "generate_s": gen_s, "oracle_census_match_every_graph": match}
+
+
 def run_native(args, world, rank, local, pg):
     import torch
     import synth
@@ -353,11 +548,6 @@ def run_native(args, world, rank, local, pg):
     over = dict(kv.split("=") for kv in args.opts.split(",") if kv) if args.opts else {}
     prof_opts = tc.tc_opts_default(profile=1, **{k: int(v) for k, v in over.items()})
 
-    def step_device():
-        g = tc.tc_graph_build(arcs.n, src_d, dst_d, stream=stream)
-        tc.tc_census(g, prof_opts, out=out, stream=stream)
-        return g
-
     learned = None
     if args.mlp:
         learned, prof_opts = train_and_compare(tc, [tc.tc_graph_build(arcs.n, src_d, dst_d)], prof_opts,
@@ -373,23 +563,20 @@ def run_native(args, world, rank, local, pg):
         best.profile = 1
         prof_opts = best
         tc.tc_graph_free(g)
-    # warm-up
-    for _ in range(args.warmup):
-        g = step_device()
+    # the timed steps run uninstrumented; the per-kernel breakdown comes from
+    # separate profiled steps afterwards (per-kernel events and a counter read)
+    run_opts = tc.tc_opts_default(**{k: getattr(prof_opts, k) for k in tc.TUNED_FIELDS})
+    for _ in range(args.warmup):  # warm-up steps
+        g = tc.tc_graph_build(arcs.n, src_d, dst_d, stream=stream)
+        tc.tc_census(g, run_opts, out=out, stream=stream)
         tc.tc_graph_free(g)
     torch.cuda.synchronize()
     g = tc.tc_graph_build(arcs.n, src_d, dst_d)
     stats = tc.tc_graph_stats(g)
-    tc.tc_census(g, prof_opts, out=out)
-    torch.cuda.synchronize()
-    census = tc.census_from_device_words(out.cpu().tolist())
     tc.tc_graph_free(g)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    # the timed steps run uninstrumented; the per-kernel breakdown comes from
-    # separate profiled steps afterwards (per-kernel events and a counter read)
-    run_opts = tc.tc_opts_default(**{k: getattr(prof_opts, k) for k in tc.TUNED_FIELDS})
     barrier(pg)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -404,6 +591,14 @@ def run_native(args, world, rank, local, pg):
             tc.tc_graph_free(g)
         torch.cuda.synchronize()
     barrier(pg)
+    census = tc.census_from_device_words(out.cpu().tolist())
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    build_ms = [a.elapsed_time(b) for a, b, c in ev]
+    census_ms = [b.elapsed_time(c) for a, b, c in ev]
+    total_ms = max_over_ranks(sum(step_ms), pg)
+    ms_per_step = total_ms / args.steps
+    value = world * stats["merged_entries"] * args.steps / (total_ms / 1e3)
+
     profs = []
     for k in range(max(3, min(args.steps, 5))):
         flush.fill_(k)
@@ -412,59 +607,39 @@ def run_native(args, world, rank, local, pg):
         profs.append(tc.tc_census_profile())
         tc.tc_graph_free(g)
     torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    build_ms = [a.elapsed_time(b) for a, b, c in ev]
-    census_ms = [b.elapsed_time(c) for a, b, c in ev]
-    total_ms = max_over_ranks(sum(step_ms), pg)
-    ms_per_step = total_ms / args.steps
-    value = world * stats["merged_entries"] * args.steps / (total_ms / 1e3)
-
-    # dominant kernel and its roofline (algorithmic bytes = 4 B per merged entry)
-    # merged entries per merge kernel: the bins it runs, hub tasks (streamed
-    # by k_hub, counted in bin 2) moved out of the kernel that would cut them
     pl = profs[-1]
-    hub = pl["hub_entries"]
-    # k_owner reads, per owner dyad, the other endpoint's list (one lookup per
-    # entry) and, per work item, the owner's list: those are its bytes
-    own_bytes_entries = pl["owner_probes"] + pl["owner_staged"]
-    if prof_opts.persistent:
-        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_owner": "ms_owner", "k_hub": "ms_stream",
-                "k_fold": "ms_fold"}
-        avg = {k: float(np.mean([p[f] for p in profs])) for k, f in kern.items()}
-        avg["k_merge"] = float(np.mean([p["ms_merge"] - p["ms_stream"] for p in profs]))
-        merge_entries = {"k_merge": sum(pl["bin_entries"]) - hub, "k_hub": hub, "k_owner": own_bytes_entries}
-    else:
-        kern = {"k_tasks": "ms_tasks", "k_split": "ms_split", "k_owner": "ms_owner", "k_warp[tiles]": "ms_tiles",
-                "k_stream+k_hub": "ms_stream", "k_warp": "ms_warp", "k_thread": "ms_thread", "k_fold": "ms_fold"}
-        avg = {k: float(np.mean([p[f] for p in profs])) for k, f in kern.items()}
-        be = pl["bin_entries"]
-        merge_entries = {"k_warp[tiles]": be[2] - hub, "k_stream+k_hub": be[3] + hub, "k_warp": be[1],
-                         "k_thread": be[0], "k_owner": own_bytes_entries}
-    top = max(merge_entries, key=lambda k: avg[k])
-    entries_top = merge_entries[top]
+    top, kernel_ms = dominant_kernel(tc, profs, stats)
     peak, peak_kind = peaks()
-    achieved = 4.0 * entries_top / (avg[top] / 1e3) / 1e9
-    traffic = recorded_traffic(top)
-    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": 4 * entries_top,
-                "bytes_per_unit": ("4 B per lookup plus 4 B per owner-list entry indexed" if top == "k_owner"
-                                   else "4 B per merged adjacency entry"),
-                "ms_per_launch": avg[top],
-                # the full-union merge work over the whole census (the paper's
-                # cost), as if every dyad were merged: an effective rate
-                "effective_frac": 4.0 * stats["merged_entries"] / (np.mean(census_ms) / 1e3) / 1e9 / peak}
-    merge_ms = sum(avg[k] for k in merge_entries)
+    achieved = top["bytes"] / (top["ms"] / 1e3) / 1e9
+    ipl, sha = issue_record(top["kernel"])
+    clocks = clk.summary()
+    lookups = (top.get("units") or {}).get("lookups")
+    dram_per_lookup = recorded_traffic_fwd(top["kernel"], sha)
+    roofline = {"bound": "hbm", "kernel": top["kernel"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": (dram_per_lookup * lookups) if (dram_per_lookup and lookups) else None,
+                "algorithmic_bytes_per_launch": top["bytes"], "units_per_launch": top.get("units"),
+                "bytes_per_unit": top.get("bytes_per_unit"), "ms_per_launch": top["ms"]}
+    if ipl and lookups:
+        # issue roofline: warp instructions the launch executes (ncu count per
+        # lookup on this source x lookups) over what 4 schedulers per SM
+        # issue at the sampled clock in the launch's time
+        import torch as _t
+        sms = _t.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_mhz") or 1.0
+        inst = ipl * lookups
+        roofline["issue"] = {"warp_instructions": inst, "per_lookup": ipl, "sms": sms, "sm_mhz": mhz,
+                             "frac": inst / (sms * 4 * mhz * 1e6 * top["ms"] / 1e3)}
 
-    # end to end through the public API from pinned host memory
-    e2e_steps = max(3, min(args.steps, 5))
+    # end to end through the public API from pinned host memory (run options)
+    e2e_steps = max(3, min(args.steps, 10))
     host_out = None
     e2e_ms = []
     for k in range(e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = tc.tc_graph_build(arcs.n, src_h.numpy(), dst_h.numpy())
-        host_out = tc.tc_census(g, prof_opts)
+        host_out = tc.tc_census(g, run_opts)
         t1 = time.perf_counter()
         tc.tc_graph_free(g)
         if k > 0:
@@ -475,6 +650,18 @@ def run_native(args, world, rank, local, pg):
            "h2d_bytes_per_step": int(arcs.src.nbytes + arcs.dst.nbytes),
            "d2h_bytes_per_step": 17 * 8, "ms_per_step": e2e_total / e2e_steps}
 
+    gold_ok = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"census_{args.workload}.json")
+    if os.path.exists(gpath):
+        gold = json.load(open(gpath))
+        if gold.get("stats", {}).get("arcs") == stats["arcs"]:
+            gold_ok = gold["census"] == census
+
+    subs = {}
+    if rank == 0 and world == 1 and args.workload == "c3" and not args.no_sub:
+        subs["c5"] = c5_record(tc, torch, stream, flush, 10, peak)
+        subs["c4"] = c4_record(tc, torch, stream, flush, 10)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, thr, verts, ents, wall, skipped = oracle_sample_rate(arcs, args.cpu_seconds)
@@ -482,150 +669,70 @@ def run_native(args, world, rank, local, pg):
                "sample": f"oracle census of the canonical dyads with lower endpoint in {verts} of "
                          f"{arcs.n} vertices, random ranges sized by merged entries ({ents:.3e} "
                          f"merged entries, {wall:.1f} s on {thr} host threads; {skipped} ranges "
-                         f"too heavy for one thread in that time left out)"}
+                         f"too heavy for one thread in that time left out, so the rate is that of "
+                         f"the cheaper dyads)"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "census_ms": float(np.median(census_ms)), "build_ms": float(np.median(build_ms)),
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC.get(args.workload, '')}",
                        "n": arcs.n, "arcs": stats["arcs"], "dyads": stats["dyads"],
                        "merged_entries": stats["merged_entries"],
                        "max_degree": stats["max_degree"],
                        "step": "graph build + census, arc list resident in HBM",
+                       "value": "effective rate: sum_v d_v^2 (the merged entries a full union merge of every "
+                                "canonical dyad would read) per step time; no kernel reads at this rate",
                        "l2": "512 MB buffer written between timed steps (L2 flush)",
                        "parallelism": "single GPU" if world == 1 else f"replicas x{world}",
                        "census_opts": {k: getattr(prof_opts, k) for k in tc.TUNED_FIELDS}},
-            "breakdown": {"census_ms": float(np.mean(census_ms)), "build_ms": float(np.mean(build_ms)),
-                          "census_ms_steps": [round(float(x), 3) for x in census_ms],
-                          "merge_ms": merge_ms, "kernel_ms": avg,
-                          "bin_tasks": profs[-1]["bin_tasks"], "bin_entries": profs[-1]["bin_entries"],
-                          "hub_tasks": profs[-1]["hub_tasks"], "hub_entries": hub,
-                          "owner": {k: pl[k] for k in ("owner_items", "owner_tasks", "owner_entries",
-                                                       "owner_probes", "owner_staged")},
-                          "chunks": profs[-1]["chunks"],
-                          "census_entries_per_s": stats["merged_entries"] / (np.mean(census_ms) / 1e3)},
+            "breakdown": {"census_ms_steps": [round(float(x), 3) for x in census_ms],
+                          "kernel_ms": kernel_ms,
+                          "forward": {k: pl[k] for k in ("fwd_entries", "map_items", "map_dyads", "map_lookups",
+                                                         "map_triangles", "search_dyads", "search_lookups",
+                                                         "search_triangles", "map_list_entries")},
+                          "census_entries_per_s": stats["merged_entries"] / (np.median(census_ms) / 1e3)},
+            "oracle_census_match": gold_ok,
             "roofline": roofline,
             "autotune": tune,
             "learned_binning": learned,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "clocks": clk.summary(),
-            "gpu_launches": args.steps * (OWN_BUILD_KERNELS + profs[-1]["launches"]),
+            "clocks": clocks,
+            "gpu_launches": args.steps * (OWN_BUILD_KERNELS + pl["launches"]),
             "census": [str(x) for x in census],
         }
+        line.update(subs)
         print(json.dumps(line), flush=True)
 
 
 def run_batched(args, world, rank, local, pg):
-    """Workload c4: every graph censused in one batch (a CUDA-graph plan over
-    one batched build), against one census call per graph."""
+    """Workload c4 alone: the batched plan replay timed over --steps, with
+    the per-graph comparison and the oracle check of every graph."""
     import torch
-    import synth
     import paper_1603_02655_b300 as tc
     from paper_1603_02655_b300 import build as tcbuild
 
     torch.cuda.set_device(local)
     tcbuild.build()
     tc.load()
-    t0 = time.perf_counter()
-    b = synth.c4()
-    gen_s = time.perf_counter() - t0
-    G = len(b)
-    over = dict(kv.split("=") for kv in args.opts.split(",") if kv) if args.opts else {}
-    opts = tc.tc_opts_default(**{k: int(v) for k, v in over.items()})
-    src_d = torch.from_numpy(b.src).cuda()
-    dst_d = torch.from_numpy(b.dst).cuda()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    gs = tc.tc_graph_build_batched(b.ns, b.goff, src_d, dst_d)
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    del src_d, dst_d
-    stats = [tc.tc_graph_stats(g) for g in gs]
-    merged = sum(st["merged_entries"] for st in stats)
-    out = torch.zeros(17 * G, dtype=torch.int64, device="cuda")
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
-    learned = None
-    if args.mlp:
-        learned, opts = train_and_compare(tc, gs, opts, stream, free=False)
-    tune = None
-    if args.autotune:
-        t0 = time.perf_counter()
-        default_ms = tc.tc_autotune(gs, opts, max_trials=1, stream=stream)[1]
-        opts, tuned_ms, trials = tc.tc_autotune(gs, opts, max_trials=args.autotune, stream=stream)
-        tune = {"default_ms": default_ms, "tuned_ms": tuned_ms, "trials": trials,
-                "seconds": time.perf_counter() - t0}
-    plan = tc.tc_plan_create(gs, out, opts, stream=stream)
-    for _ in range(args.warmup):
-        tc.tc_plan_run(plan, stream)
-    torch.cuda.synchronize()
-    words = out.cpu().tolist()
-    census = [tc.census_from_device_words(words[17 * i:17 * i + 17]) for i in range(G)]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     barrier(pg)
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(k)
-            ev[k][0].record(stream)
-            tc.tc_plan_run(plan, stream)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        rec = c4_record(tc, torch, stream, flush, args.steps)
     barrier(pg)
-    total_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), pg)
-    ms = total_ms / args.steps
-    tc.tc_plan_free(plan)
-    # one census call (one launch sequence) per graph, plain degree-sum binning
-    heur = tc.tc_opts_default(persistent=0)
-    per_out = torch.zeros(17 * G, dtype=torch.int64, device="cuda")
-    per_ms = []
-    for rep_ in range(2):
-        flush.fill_(rep_)
-        torch.cuda.synchronize()
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for i, g in enumerate(gs):
-            tc.tc_census(g, heur, out=per_out[17 * i:17 * i + 17], stream=stream)
-        c.record(stream)
-        torch.cuda.synchronize()
-        per_ms.append(a.elapsed_time(c))
-    per_words = per_out.cpu().tolist()
-    assert per_words == words, "per-graph census differs from the batched census"
-    # checksum against the stored oracle values when present
-    gold_ok = None
-    gpath = os.path.join(ROOT, "tests", "golden", "census_c4.json")
-    if os.path.exists(gpath):
-        gold = json.load(open(gpath))
-        tot = [sum(c[t] for c in census) for t in range(16)]
-        wsum = [sum((i + 1) * c[t] for i, c in enumerate(census)) for t in range(16)]
-        gold_ok = tot == gold["total"] and wsum == gold["weighted"]
-    for g in gs:
-        tc.tc_graph_free(g)
+    ms = max_over_ranks(rec["ms_per_replay"], pg)
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": world * G / (ms / 1e3), "unit": "graphs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"c4: {WORKLOAD_DESC['c4']}", "graphs": G, "arcs": int(b.src.size),
-                       "vertices": int(b.ns.sum()), "merged_entries": merged,
-                       "step": "batched census of all graphs (CUDA-graph plan replay), graphs built",
-                       "l2": "512 MB buffer written between timed steps (L2 flush)",
-                       "census_opts": {k: getattr(opts, k) for k in
-                                       ("bin_mode", "thr_thread", "thr_warp", "chunk", "stream_max",
-                                        "persistent")}},
-            "merged_entries_per_s": merged / (ms / 1e3),
-            "per_graph_launches": {"ms": float(np.min(per_ms)), "graphs_per_s": G / (np.min(per_ms) / 1e3),
-                                   "opts": "degree-sum binning, one tc_census per graph"},
-            "speedup_vs_per_graph": float(np.min(per_ms)) / ms,
-            "build_s": build_s, "generate_s": gen_s, "golden_checksums_match": gold_ok,
-            "autotune": tune,
-            "learned_binning": learned,
-            "clocks": clk.summary(),
-        }
+        line = {"metric": METRIC, "value": world * rec["graphs"] / (ms / 1e3), "unit": "graphs/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": rec["workload"], "graphs": rec["graphs"], "step": rec["step"],
+                           "l2": "512 MB buffer written between timed steps (L2 flush)"},
+                "c4": rec, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 
 
@@ -682,12 +789,13 @@ def train_and_compare(tc, gs, opts, stream, free):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the c5 and c4 sub-records of the default run")
     ap.add_argument("--opts", default="", help="census options, e.g. thr_warp=512,stream_max=1024")
     ap.add_argument("--mlp", action="store_true",
                     help="train the learned cost model on the workload and bin with it")

@@ -178,10 +178,13 @@ typedef struct {
                                 (k_owner_prep), not part of ms_owner */
     int64_t fwd_entries;     /* forward-list entries (= dyads) */
     int64_t map_items;       /* tag-map work items (pieces of <= 1024 dyads) */
-    int64_t map_lookups;     /* suffix entries looked up in tag maps */
+    int64_t map_lookups;     /* lookup-list entries looked up in tag maps */
     int64_t map_triangles;   /* triangles found there */
-    int64_t search_lookups;  /* suffix entries looked up by binary search */
+    int64_t search_lookups;  /* lookup-list entries looked up by binary search */
     int64_t search_triangles;
+    int64_t map_dyads;       /* dyad records of the tag-map owners */
+    int64_t search_dyads;    /* dyad records of the other owners */
+    int64_t map_list_entries;  /* forward-list entries of the tag-map items' owners */
 } tc_profile_t;
 
 tc_status tc_census_profile(tc_profile_t* out);

@@ -101,7 +101,9 @@ class TcProfile(ctypes.Structure):
                 ("ms_tri_search", ctypes.c_float), ("ms_owner_prep", ctypes.c_float),
                 ("fwd_entries", ctypes.c_int64), ("map_items", ctypes.c_int64),
                 ("map_lookups", ctypes.c_int64), ("map_triangles", ctypes.c_int64),
-                ("search_lookups", ctypes.c_int64), ("search_triangles", ctypes.c_int64)]
+                ("search_lookups", ctypes.c_int64), ("search_triangles", ctypes.c_int64),
+                ("map_dyads", ctypes.c_int64), ("search_dyads", ctypes.c_int64),
+                ("map_list_entries", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

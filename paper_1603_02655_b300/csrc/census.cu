@@ -2157,8 +2157,9 @@ struct Layout {
 // 7 hub tasks, 8-9 task-build row cursor, 10-17 bin entries, 20-23 merge
 // cursors, 24-25 hub entries, 26-27 owner cursors, 28-29 owner rows (larger,
 // smaller), 32-39 owner tasks, merged entries, probes, staged entries.
-// Forward path: 40 tag-map items, 42-43 work cursors, 44-51 lookups and
-// triangles of each lookup form (u64).
+// Forward path: 40 tag-map items, 41 long rows, 42-43 work cursors, 44-51
+// lookups and triangles of each lookup form (u64), 52-53 forward-list
+// entries the tag-map items stage (u64).
 constexpr int CTR_WORDS = 64;
 
 tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
@@ -2638,6 +2639,13 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
         P.map_triangles = u64(46);
         P.search_lookups = u64(48);
         P.search_triangles = u64(50);
+        unsigned long long tot = 0;  // records: tag-map owners << 32 | the others
+        TC_CUDA(cudaMemcpyAsync(&tot, ws + Lo.o_tpre + sizeof(unsigned long long) * (size_t)Lo.rows,
+                                sizeof tot, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        P.map_dyads = (int64_t)(tot >> 32);
+        P.search_dyads = (int64_t)(tot & 0xffffffffull);
+        P.map_list_entries = u64(52);
     }
     g_profile_valid = true;
     return TC_OK;

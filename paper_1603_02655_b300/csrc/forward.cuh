@@ -209,7 +209,7 @@ struct FwdLayout {
     unsigned* nitems;          // [1]
     unsigned* nlong;           // [1]
     unsigned* cursor;          // [2] work cursors (tag-map items, search records)
-    unsigned long long* stat;  // [4] lookups and triangles of each lookup form
+    unsigned long long* stat;  // [5] lookups and triangles of each lookup form, staged list entries
     const int32_t* rank;
     const int32_t* perm;
 };
@@ -620,9 +620,10 @@ __global__ void k_fwd_items(const int64_t* __restrict__ pfx, int nseg, FwdLayout
         const int64_t rh = it.x;
         const uint32_t tb = (uint32_t)(F.tpre[rh] >> 32), te = (uint32_t)(F.tpre[rh + 1] >> 32);
         const uint32_t t0 = tb + it.y * TB_REC, t1 = min(te, t0 + (uint32_t)TB_REC);
-        const uint32_t mb = F.fptr[rh];
-        F.items[2 * k] = make_uint4(it.x, (uint32_t)F.rank[rh], mb, F.fptr[rh + 1] - mb);
+        const uint32_t mb = F.fptr[rh], mn = F.fptr[rh + 1] - mb;
+        F.items[2 * k] = make_uint4(it.x, (uint32_t)F.rank[rh], mb, mn);
         F.items[2 * k + 1] = make_uint4(t0, t1, (uint32_t)row_seg(pfx, nseg, rh), 0u);
+        atomicAdd(F.stat + 4, (unsigned long long)mn);  // forward-list entries the items stage
     }
 }
 
