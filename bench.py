@@ -461,7 +461,53 @@ def c5_record(tc, torch, stream, flush, steps, peak):
             "oracle_census_match": match}
 
 
-def c4_record(tc, torch, stream, flush, steps):
+def path_routing(tc, torch, gs, stream, words):
+    """Plan-replay time of the batch with every graph on the forward path,
+    on the merge path, routed by the degree-skew rule (the default), and
+    routed by the learned path model trained on batch-scale costs of a
+    separate batch of 160 graphs (same generator, seed 40)."""
+    from paper_1603_02655_b300 import costmodel
+    import synth
+    G = len(gs)
+
+    def replay(over):
+        out = torch.zeros(17 * G, dtype=torch.int64, device="cuda")
+        plan = tc.tc_plan_create(gs, out, tc.tc_opts_default(**over), stream=stream)
+        for _ in range(2):
+            tc.tc_plan_run(plan, stream)
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(5):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tc.tc_plan_run(plan, stream)
+            c.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(c))
+        tc.tc_plan_free(plan)
+        assert out.cpu().tolist() == words, "a route changed the counts"
+        return float(np.median(ts))
+
+    rec = {"forward_ms": replay(dict(tri_path=tc.TC_TRI_FORWARD)),
+           "merge_ms": replay(dict(tri_path=tc.TC_TRI_MERGE)),
+           "skew_rule_ms": replay(dict(tri_path=tc.TC_TRI_AUTO)),
+           "skew_rule_merge_graphs": sum(tc.tc_path_route(gs))}
+    t0 = time.perf_counter()
+    train = synth.batch(160, 64, 65536, 4.0, 32.0, 8, 0.5, seed=40)
+    params, rep = costmodel.train_path_model([train.graph(i) for i in range(len(train))], copies=32)
+    rec["train_s"] = time.perf_counter() - t0
+    rec["train_report"] = rep
+    tc.tc_path_model_load(params)
+    try:
+        rec["learned_ms"] = replay(dict(tri_path=tc.TC_TRI_AUTO))
+        rec["learned_merge_graphs"] = sum(tc.tc_path_route(gs))
+    finally:
+        tc.tc_path_model_load(None)
+    rec["learned_vs_skew_rule"] = rec["skew_rule_ms"] / rec["learned_ms"]
+    return rec
+
+
+def c4_record(tc, torch, stream, flush, steps, route=True):
     """The batched workload: 4096 graphs censused by one CUDA-graph plan
     replay (graphs/s), against one tc_census call per graph, and every
     graph's census checked against the oracle's stored per-graph census."""
@@ -509,6 +555,7 @@ def c4_record(tc, torch, stream, flush, steps):
     torch.cuda.synchronize()
     per_ms = a.elapsed_time(c)
     same = per_out.cpu().tolist() == words
+    routing = path_routing(tc, torch, gs, stream, words) if route else None
     for g in gs:
         tc.tc_graph_free(g)
     gpath = os.path.join(ROOT, "tests", "golden", "census_c4.json")
@@ -525,6 +572,7 @@ def c4_record(tc, torch, stream, flush, steps):
                                 "same_counts": same},
             "speedup_vs_per_graph": per_ms / ms,
             "step": "census of all 4096 graphs of one batched build (CUDA-graph plan replay; build excluded)",
+            "path_routing": routing,
             "build_s": build_s, "generate_s": gen_s, "oracle_census_match_every_graph": match}
 
 

@@ -125,14 +125,17 @@ typedef struct {
                              entries); 0: one thread per adjacency entry */
     int32_t tri_path;     /* how the shared neighbours of the dyads (the
                              triangles) are found:
-                             TC_TRI_FORWARD (0, default): each triangle once,
+                             TC_TRI_FORWARD (0): each triangle once,
                              from degree-ranked forward lists (vertices ranked
                              by (floor(log2 degree), id); a dyad's owner is its
                              higher-ranked endpoint);
                              TC_TRI_MERGE (1): per-dyad owner lookups and merge
                              bins, tuned by the fields above (own_min,
                              thr_thread, thr_warp, chunk, stream_max, hub_ratio,
-                             persistent, split_cta, bin_mode) */
+                             persistent, split_cta, bin_mode);
+                             TC_TRI_AUTO (2, default): each graph takes the
+                             path its router picks (tc_path_route): the
+                             installed path model, else the degree-skew rule */
     int32_t fwd_big;      /* TC_TRI_FORWARD: owners with at least fwd_big forward
                              neighbours (and at most 2^17 vertices ranked above
                              them) get a CTA and an exact tag map of their
@@ -140,7 +143,7 @@ typedef struct {
                              binary search per lookup.  >= 1; default 64 */
 } tc_opts;
 
-enum { TC_TRI_FORWARD = 0, TC_TRI_MERGE = 1 };
+enum { TC_TRI_FORWARD = 0, TC_TRI_MERGE = 1, TC_TRI_AUTO = 2 };
 
 /* Per-kernel timing and binning of the calling thread's most recent
  * tc_census / tc_census_batched call made with opts.profile = 1. */
@@ -198,7 +201,8 @@ tc_status tc_census_profile(tc_profile_t* out);
 #define TC_OUT_DEVICE 2u    /* out is device memory: the call only enqueues work
                                on `stream` and returns without synchronising */
 
-/* Fill *o with the defaults (degree-sum binning, tuned thresholds). */
+/* Fill *o with the defaults (tri_path TC_TRI_AUTO, fwd_big 64; for the merge
+ * path degree-sum binning and tuned thresholds). */
 tc_status tc_opts_default(tc_opts* o);
 
 /*
@@ -426,6 +430,32 @@ tc_status tc_mlp_train(float* params, const float* feat, const int32_t* bin, con
 tc_status tc_mlp_predict(const float* params, const float* feat, int32_t n, int32_t half_precision, float* out,
                          void* stream);
 tc_status tc_cost_model_load(const float* params);
+
+/*
+ * Path routing (tri_path = TC_TRI_AUTO).  The thesis has one way of finding
+ * the shared neighbours; this library has two (forward lists, merge bins),
+ * and which is faster depends on the graph: degree-skewed graphs (R-MAT,
+ * power laws) favour the forward path, near-regular ones (G(n,p)) the merge
+ * path.  A census of several graphs then runs each graph on its path.
+ *   tc_path_features    float[G][8] (host) of G graphs: log2(1+n)/32,
+ *                       log2(1+dyads)/32, log2(1+mean degree)/8,
+ *                       log2(1+max degree)/20, log2(max/mean degree)/8,
+ *                       log2(1+merged entries/dyads)/20, mutual fraction,
+ *                       log2(1+merged entries)/40 (from the build statistics).
+ *   tc_path_model_load  install host float[TC_MLP_NPARAM] (the 8-32-32-4 MLP
+ *                       layout above; output 0 = predicted log2 census time of
+ *                       a graph on the forward path, output 1 = on the merge
+ *                       path) on the current device, evaluated in FP16; NULL
+ *                       uninstalls.  Without a model the router uses the
+ *                       degree-skew rule: the forward path when the largest
+ *                       degree is at least 8x the mean degree.
+ *   tc_path_route       path[i] (host int32[G]) = TC_TRI_FORWARD or
+ *                       TC_TRI_MERGE for gs[i] (handles of one build).
+ * The counts never depend on the route, only the time does.
+ */
+tc_status tc_path_features(int32_t G, const tc_graph* gs, float* feat);
+tc_status tc_path_model_load(const float* params);
+tc_status tc_path_route(int32_t G, const tc_graph* gs, int32_t* path, void* stream);
 
 /* Release a graph handle (synchronises the device first). NULL is a no-op. */
 void tc_graph_free(tc_graph g);

@@ -33,7 +33,7 @@ TYPE_NAMES = ("003", "012", "102", "021D", "021U", "021C", "111D", "111U",
 
 TC_OK, TC_ERR_ARG, TC_ERR_ID_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED = range(7)
 TC_BIN_HEURISTIC, TC_BIN_MLP = 0, 1
-TC_TRI_FORWARD, TC_TRI_MERGE = 0, 1
+TC_TRI_FORWARD, TC_TRI_MERGE, TC_TRI_AUTO = 0, 1, 2
 TC_DEVICE_PTRS = 1
 TC_UNDIRECTED = 4
 TC_OUT_DEVICE = 2
@@ -44,7 +44,8 @@ EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_gr
            "tc_census_csr_noalloc", "tc_plan_create", "tc_plan_run", "tc_plan_free", "tc_autotune",
            "tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
            "tc_cost_model_load", "tc_census_codes", "tc_census_codes_batched",
-           "tc_graph_build_text", "tc_union_sizes")
+           "tc_graph_build_text", "tc_union_sizes", "tc_path_features", "tc_path_model_load",
+           "tc_path_route")
 TC_MLP_NPARAM = 1476
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
@@ -164,6 +165,11 @@ def load():
     lib.tc_mlp_train.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, P, P]
     lib.tc_mlp_predict.argtypes = [P, P, i32, i32, P, P]
     lib.tc_cost_model_load.argtypes = [P]
+    lib.tc_path_features.argtypes = [i32, P, P]
+    lib.tc_path_model_load.argtypes = [P]
+    lib.tc_path_route.argtypes = [i32, P, P, P]
+    for name in ("tc_path_features", "tc_path_model_load", "tc_path_route"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
                  "tc_cost_model_load"):
         getattr(lib, name).restype = ctypes.c_int
@@ -544,6 +550,41 @@ def tc_cost_model_load(params) -> None:
     if a.size != TC_MLP_NPARAM:
         raise ValueError(f"expected {TC_MLP_NPARAM} parameters")
     _check(load().tc_cost_model_load(a.ctypes.data), "tc_cost_model_load")
+
+
+def _handles(gs):
+    arr = (ctypes.c_void_p * max(1, len(gs)))()
+    for i, g in enumerate(gs):
+        arr[i] = g
+    return arr
+
+
+def tc_path_features(gs) -> np.ndarray:
+    """Routing features float32[G, 8] of graphs of one build (host)."""
+    out = np.zeros((len(gs), 8), dtype=np.float32)
+    _check(load().tc_path_features(len(gs), _handles(gs), out.ctypes.data), "tc_path_features")
+    return out
+
+
+def tc_path_model_load(params) -> None:
+    """Install the path-routing model (host float32, 1476 values: output 0 =
+    log2 time on the forward path, 1 = on the merge path) on the current
+    device for TC_TRI_AUTO; None uninstalls (the degree-skew rule routes)."""
+    if params is None:
+        _check(load().tc_path_model_load(None), "tc_path_model_load")
+        return
+    a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    if a.size != TC_MLP_NPARAM:
+        raise ValueError(f"expected {TC_MLP_NPARAM} parameters")
+    _check(load().tc_path_model_load(a.ctypes.data), "tc_path_model_load")
+
+
+def tc_path_route(gs, stream=None) -> list[int]:
+    """The path (TC_TRI_FORWARD or TC_TRI_MERGE) each graph takes under
+    TC_TRI_AUTO."""
+    out = np.zeros(len(gs), dtype=np.int32)
+    _check(load().tc_path_route(len(gs), _handles(gs), out.ctypes.data, _stream(stream)), "tc_path_route")
+    return [int(x) for x in out]
 
 
 def tc_graph_free(g: int) -> None:

@@ -137,3 +137,125 @@ def train_cost_model(gs, mask: int = 63, steps: int = 3000, batch: int = 4096, l
     rep["train_loss"] = loss
     rep["graph_stats"] = [tc_graph_stats(g) for g in gs[:4]]
     return params, rep
+
+
+# ------------------------------------------------------------ path routing
+# The same network, trained on graph-level features (tc_path_features) to
+# predict log2 of a graph's census time on each path (output 0 forward,
+# 1 merge); TC_TRI_AUTO sends each graph to the cheaper prediction.  The
+# yardstick is the degree-skew rule (forward when the largest degree is at
+# least 8x the mean degree), the router without a model.
+
+def call_costs(gs, reps: int = 3, stream=None) -> np.ndarray:
+    """Single-call census time (microseconds, CUDA events, best of `reps`
+    after one warm-up) of each graph on the forward and on the merge path:
+    float[G, 2].  (Dominated by the fixed cost per call for small graphs; the
+    router is trained on `batch_costs` instead.)"""
+    import torch
+    from . import TC_TRI_FORWARD, TC_TRI_MERGE, tc_census, tc_opts_default
+    st = torch.cuda.current_stream() if stream is None else stream
+    out = torch.zeros(17, dtype=torch.int64, device="cuda")
+    costs = np.zeros((len(gs), 2))
+    for k, path in enumerate((TC_TRI_FORWARD, TC_TRI_MERGE)):
+        o = tc_opts_default(tri_path=path)
+        for i, g in enumerate(gs):
+            best = float("inf")
+            for r in range(reps + 1):
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                tc_census(g, o, out=out, stream=st)
+                c.record(st)
+                torch.cuda.synchronize()
+                if r > 0:
+                    best = min(best, a.elapsed_time(c) * 1e3)
+            costs[i, k] = best
+    return costs
+
+
+def skew_rule(feat: np.ndarray) -> np.ndarray:
+    """The router without a model: 1 (merge) unless max degree >= 8 x mean
+    degree (feature 4 = log2(max/mean) / 8)."""
+    return (feat[:, 4] * 8.0 < 3.0).astype(np.int32)
+
+
+def batch_costs(graphs, copies: int = 32, reps: int = 3, stream=None) -> tuple[np.ndarray, np.ndarray]:
+    """A graph's cost inside a batched census (microseconds) on each path:
+    each graph (objects with n, src, dst) is built `copies` times into one
+    batched build, and its cost is (time of the census of all copies - time
+    of one copy) / (copies - 1), so the census's fixed cost per call
+    (launches, scans, the fold) cancels and the kernels run at batch scale.
+    Returns (features float32[G, 8], costs float[G, 2])."""
+    import torch
+    from . import (TC_TRI_FORWARD, TC_TRI_MERGE, tc_census_batched, tc_graph_build_batched, tc_graph_free,
+                   tc_opts_default, tc_path_features)
+    st = torch.cuda.current_stream() if stream is None else stream
+    out = torch.zeros(17 * copies, dtype=torch.int64, device="cuda")
+
+    def best(sub, o):
+        t = float("inf")
+        for r in range(reps + 1):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            tc_census_batched(sub, o, out=out[:17 * len(sub)], stream=st)
+            c.record(st)
+            torch.cuda.synchronize()
+            if r > 0:
+                t = min(t, a.elapsed_time(c) * 1e3)
+        return t
+
+    feats, costs = [], []
+    for a in graphs:
+        m = int(a.src.size)
+        src = torch.from_numpy(np.tile(np.asarray(a.src, np.int32), copies)).cuda()
+        dst = torch.from_numpy(np.tile(np.asarray(a.dst, np.int32), copies)).cuda()
+        gs = tc_graph_build_batched(np.full(copies, a.n, np.int32), np.arange(copies + 1, dtype=np.int64) * m,
+                                    src, dst)
+        try:
+            feats.append(tc_path_features(gs[:1])[0])
+            row = []
+            for path in (TC_TRI_FORWARD, TC_TRI_MERGE):
+                o = tc_opts_default(tri_path=path)
+                row.append(max((best(gs, o) - best(gs[:1], o)) / (copies - 1), 1.0))
+            costs.append(row)
+        finally:
+            for g in gs:
+                tc_graph_free(g)
+    return np.array(feats, np.float32).reshape(-1, 8), np.array(costs, np.float64).reshape(-1, 2)
+
+
+def train_path_model(graphs, copies: int = 32, steps: int = 4000, lr: float = 3e-3, seed: int = 1,
+                     holdout: float = 0.25, stream=None):
+    """Measure (`batch_costs`), train (FP32 kernels) and evaluate the path
+    model on a list of graphs (objects with n, src, dst); returns (params,
+    report).  Does not install.  The report compares, on the held-out
+    graphs, the summed batch costs of the learned routes with the
+    degree-skew rule's, each path alone, and the best route per graph."""
+    import torch
+    feat, costs = batch_costs(graphs, copies, stream=stream)
+    G = costs.shape[0]
+    rng = np.random.default_rng(seed)
+    train = rng.random(G) >= holdout
+    # one sample per graph and path: the output of that path is trained
+    f2 = np.repeat(feat, 2, axis=0)
+    b2 = np.tile(np.array([0, 1], np.int32), G)
+    t2 = np.log2(np.maximum(costs.reshape(-1), 1.0)).astype(np.float32)
+    m2 = np.repeat(train, 2)
+    params, loss = fit(torch.from_numpy(f2[m2]).cuda(), b2[m2], t2[m2], steps, 4096, lr, seed, stream=stream)
+    p = torch.from_numpy(params).cuda()
+    pred = tc_mlp_predict(p, torch.from_numpy(feat).cuda(), True).cpu().numpy()[:, :2]
+    learned = (pred[:, 1] < pred[:, 0]).astype(np.int32)
+    rule = skew_rule(feat)
+    best = np.argmin(costs, axis=1)
+    test = ~train
+
+    def cost(route, mask):
+        return float(costs[np.arange(G)[mask], route[mask]].sum())
+
+    rep = {"graphs": G, "test_graphs": int(test.sum()), "copies": copies, "train_loss": loss,
+           "rmse_log2_us": float(np.sqrt(np.mean((pred[test] - np.log2(np.maximum(costs[test], 1.0))) ** 2))),
+           "test_us": {"all_forward": cost(np.zeros(G, np.int32), test), "all_merge": cost(np.ones(G, np.int32), test),
+                       "skew_rule": cost(rule, test), "learned": cost(learned, test),
+                       "best_per_graph": cost(best, test)},
+           "test_agreement_with_best": {"learned": float(np.mean(learned[test] == best[test])),
+                                        "skew_rule": float(np.mean(rule[test] == best[test]))}}
+    return params, rep

@@ -2163,7 +2163,7 @@ struct Layout {
 constexpr int CTR_WORDS = 64;
 
 tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
-                      Layout& Lo) {
+                      Layout& Lo, const std::vector<int32_t>* slots = nullptr) {
     tc_opts o;
     tc_opts_default(&o);
     if (opts_in) o = *opts_in;
@@ -2179,6 +2179,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     if (o.persistent && o.split_cta)
         return fail(TC_ERR_ARG, "census: the persistent merge runs warp tiles (split_cta must be 0)");
     if (o.tri_path != TC_TRI_FORWARD && o.tri_path != TC_TRI_MERGE) return fail(TC_ERR_ARG, "census: unknown tri_path");
+    // (TC_TRI_AUTO is resolved per graph before a layout is made)
     if (o.fwd_big < 1) return fail(TC_ERR_ARG, "census: fwd_big < 1");
     // a warp holds both lists (or the short list) in shared memory
     o.thr_warp = std::min(o.thr_warp, WARP_LMAX);
@@ -2196,7 +2197,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         Lo.segs[(size_t)i].n = set.voff[(size_t)g + 1] - set.voff[(size_t)g];
         Lo.segs[(size_t)i].eb = gent[(size_t)g];
         Lo.epfx[(size_t)i + 1] = Lo.epfx[(size_t)i] + 2 * set.stats[(size_t)g].dyads;
-        Lo.segs[(size_t)i].slot = i;
+        Lo.segs[(size_t)i].slot = slots ? (*slots)[(size_t)i] : i;
         Lo.segs[(size_t)i].pad = 0;
         Lo.pfx[(size_t)i + 1] = Lo.pfx[(size_t)i] + Lo.segs[(size_t)i].n;
         dyads += set.stats[(size_t)g].dyads;
@@ -2651,14 +2652,13 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     return TC_OK;
 }
 
-// out and/or codes (either may be null): one record per graph, host memory
-// or, with TC_OUT_DEVICE, device memory.
-tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
+// One census over the graphs gidx with a resolved tri_path; with slots,
+// graph i's record goes to out[slots[i]] (device output only).
+tc_status census_part(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
                       tc_census_t* out, uint32_t flags, cudaStream_t st, const Instr* ins = nullptr,
-                      tc_census64_t* codes = nullptr) {
-    if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
+                      tc_census64_t* codes = nullptr, const std::vector<int32_t>* slots = nullptr) {
     Layout Lo;
-    if (tc_status s = make_layout(set, gidx, opts_in, Lo); s != TC_OK) return s;
+    if (tc_status s = make_layout(set, gidx, opts_in, Lo, slots); s != TC_OK) return s;
     if (set.ws_bytes < Lo.need) {
         dev_free(set.ws, st);
         set.ws = nullptr;
@@ -2692,6 +2692,67 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         if (ovf) return fail(TC_ERR_CUDA, "census: task bin overflow (internal error)");
     }
     return TC_OK;
+}
+
+// tri_path = TC_TRI_AUTO: the graphs routed to each path (path_route), with
+// their positions in the caller's list.
+struct Parts {
+    std::vector<int32_t> gidx[2], slots[2];  // [0] forward, [1] merge
+};
+
+tc_status split_parts(const GraphSet& set, const std::vector<int32_t>& gidx, cudaStream_t st, Parts& P) {
+    std::vector<uint8_t> merge;
+    if (tc_status s = path_route(set, gidx, merge, st); s != TC_OK) return s;
+    for (size_t i = 0; i < gidx.size(); ++i) {
+        P.gidx[merge[i]].push_back(gidx[i]);
+        P.slots[merge[i]].push_back((int32_t)i);
+    }
+    return TC_OK;
+}
+
+// out and/or codes (either may be null): one record per graph, host memory
+// or, with TC_OUT_DEVICE, device memory.  With tri_path = TC_TRI_AUTO each
+// graph is censused on the path the router picks (two censuses, records in
+// the caller's order; a profiled call profiles the second).
+tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
+                      tc_census_t* out, uint32_t flags, cudaStream_t st, const Instr* ins = nullptr,
+                      tc_census64_t* codes = nullptr) {
+    if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
+    tc_opts resolved;
+    if (!opts_in) {  // the defaults (tri_path TC_TRI_AUTO)
+        tc_opts_default(&resolved);
+        opts_in = &resolved;
+    }
+    if (opts_in->tri_path != TC_TRI_AUTO) return census_part(set, gidx, opts_in, out, flags, st, ins, codes);
+    Parts P;
+    if (tc_status s = split_parts(set, gidx, st, P); s != TC_OK) return s;
+    const bool dev = (flags & TC_OUT_DEVICE) != 0;
+    const size_t G = gidx.size();
+    tc_census_t* d_out = dev ? out : nullptr;
+    tc_census64_t* d_codes = dev ? codes : nullptr;
+    if (!dev) {  // device staging for the records, copied back at the end
+        if (out) TC_CUDA(dev_alloc((void**)&d_out, sizeof(tc_census_t) * std::max<size_t>(G, 1), st));
+        if (codes) TC_CUDA(dev_alloc((void**)&d_codes, sizeof(tc_census64_t) * std::max<size_t>(G, 1), st));
+    }
+    tc_status r = TC_OK;
+    for (int k = 0; k < 2 && r == TC_OK; ++k) {
+        if (P.gidx[k].empty()) continue;
+        tc_opts o = *opts_in;
+        o.tri_path = k == 0 ? TC_TRI_FORWARD : TC_TRI_MERGE;
+        r = census_part(set, P.gidx[k], &o, d_out, TC_OUT_DEVICE, st, ins, d_codes, &P.slots[k]);
+    }
+    if (!dev) {
+        if (r == TC_OK && out)
+            r = cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * G, cudaMemcpyDeviceToHost, st) == cudaSuccess
+                    ? TC_OK : fail(TC_ERR_CUDA, "census: copy of the records");
+        if (r == TC_OK && codes)
+            r = cudaMemcpyAsync(codes, d_codes, sizeof(tc_census64_t) * G, cudaMemcpyDeviceToHost, st) == cudaSuccess
+                    ? TC_OK : fail(TC_ERR_CUDA, "census: copy of the records");
+        if (r == TC_OK && cudaStreamSynchronize(st) != cudaSuccess) r = fail(TC_ERR_CUDA, "census: synchronise");
+        if (d_out) dev_free(d_out, st);
+        if (d_codes) dev_free(d_codes, st);
+    }
+    return r;
 }
 
 std::vector<int32_t> handle_indices(int32_t G, const tc_graph* gs) {
@@ -2922,8 +2983,9 @@ extern "C" tc_status tc_census_csr_noalloc(int32_t n, const int64_t* row_ptr, co
 // ------------------------------------------------------------ batch plans --
 struct tc_plan_s {
     std::shared_ptr<tc::GraphSet> set;
-    tc::Layout lo;
-    char* ws = nullptr;
+    tc::Layout lo[2];        // one census, or (TC_TRI_AUTO) the forward and the merge part
+    char* ws[2] = {nullptr, nullptr};
+    int parts = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -2938,10 +3000,31 @@ tc_status plan_create(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_cen
     if (opts && opts->profile) return fail(TC_ERR_ARG, "tc_plan_create: profile must be 0 in a plan");
     std::unique_ptr<tc_plan_s> p(new tc_plan_s);
     p->set = gs[0]->set;
-    if (tc_status s = make_layout(*p->set, handle_indices(G, gs), opts, p->lo); s != TC_OK) return s;
+    const std::vector<int32_t> idx = handle_indices(G, gs);
+    tc_opts resolved;
+    if (!opts) {  // the defaults (tri_path TC_TRI_AUTO)
+        tc_opts_default(&resolved);
+        opts = &resolved;
+    }
+    Parts P;
+    tc_opts po[2];
+    if (opts && opts->tri_path == TC_TRI_AUTO) {  // a census per path, records in the caller's order
+        if (tc_status s = split_parts(*p->set, idx, st, P); s != TC_OK) return s;
+        for (int k = 0; k < 2; ++k) {
+            if (P.gidx[k].empty()) continue;
+            po[p->parts] = *opts;
+            po[p->parts].tri_path = k == 0 ? TC_TRI_FORWARD : TC_TRI_MERGE;
+            if (tc_status s = make_layout(*p->set, P.gidx[k], &po[p->parts], p->lo[p->parts], &P.slots[k]);
+                s != TC_OK)
+                return s;
+            ++p->parts;
+        }
+    } else {
+        if (tc_status s = make_layout(*p->set, idx, opts, p->lo[0]); s != TC_OK) return s;
+        p->parts = 1;
+    }
     Launch L;
     if (tc_status s = launch_info(L); s != TC_OK) return s;
-    TC_CUDA(dev_alloc((void**)&p->ws, p->lo.need, st));
     struct Guard {
         tc_plan_s* p;
         cudaStream_t st;
@@ -2951,19 +3034,23 @@ tc_status plan_create(int32_t G, const tc_graph* gs, const tc_opts* opts, tc_cen
                 cudaStreamSynchronize(st);
                 if (p->exec) cudaGraphExecDestroy(p->exec);
                 if (p->graph) cudaGraphDestroy(p->graph);
-                dev_free(p->ws, st);
+                for (int k = 0; k < 2; ++k) dev_free(p->ws[k], st);
                 cudaStreamSynchronize(st);
             }
         }
     } guard{p.get(), st};
-    if (tc_status s = upload_layout(p->lo, p->ws, st); s != TC_OK) return s;
+    for (int k = 0; k < p->parts; ++k) {
+        TC_CUDA(dev_alloc((void**)&p->ws[k], p->lo[k].need, st));
+        if (tc_status s = upload_layout(p->lo[k], p->ws[k], st); s != TC_OK) return s;
+    }
     TC_CUDA(cudaStreamSynchronize(st));
     cudaStream_t cap = nullptr;
     TC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     tc_status s = TC_OK;
     if (e == cudaSuccess) {
-        s = enqueue_census(*p->set, p->lo, p->ws, out, cap, nullptr);
+        for (int k = 0; k < p->parts && s == TC_OK; ++k)
+            s = enqueue_census(*p->set, p->lo[k], p->ws[k], out, cap, nullptr);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (s == TC_OK && e2 != cudaSuccess) s = cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
@@ -3007,7 +3094,7 @@ void tc_plan_free(tc_plan plan) {
     cudaDeviceSynchronize();
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
-    tc::dev_free(plan->ws, 0);
+    for (int k = 0; k < 2; ++k) tc::dev_free(plan->ws[k], 0);
     cudaStreamSynchronize(0);
     delete plan;
 }
@@ -3071,7 +3158,7 @@ tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t m
     // are found, then that path's own settings (the tag-map threshold of the
     // forward path; for the merge path the owner threshold first, since it
     // decides which dyads reach the merge bins at all)
-    const int32_t path_c[] = {TC_TRI_FORWARD, TC_TRI_MERGE};
+    const int32_t path_c[] = {TC_TRI_FORWARD, TC_TRI_MERGE, TC_TRI_AUTO};
     const int32_t big_c[] = {8, 16, 32, 64, 128, 256};
     const int32_t own_c[] = {0, 64, 128, 256, 512, 1024, 4096};
     const int32_t thr_thread_c[] = {0, 16, 32, 48, 64, 96, 128, 192};
@@ -3084,7 +3171,7 @@ tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t m
         const int32_t* cand;
         int nc;
     };
-    const Field fields[] = {{&tc_opts::tri_path, path_c, 2},     {&tc_opts::fwd_big, big_c, 6},
+    const Field fields[] = {{&tc_opts::tri_path, path_c, 3},     {&tc_opts::fwd_big, big_c, 6},
                             {&tc_opts::own_min, own_c, 7},       {&tc_opts::thr_thread, thr_thread_c, 8},
                             {&tc_opts::thr_warp, thr_warp_c, 5}, {&tc_opts::stream_max, stream_c, 4},
                             {&tc_opts::chunk, chunk_c, 3},       {&tc_opts::persistent, pers_c, 2}};
@@ -3094,7 +3181,8 @@ tc_status autotune(int32_t G, const tc_graph* gs, const tc_opts* base, int32_t m
             const int nc = fd.nc;
             // a field of the other path changes nothing: skip it
             const bool fwd_field = fd.f == &tc_opts::fwd_big, path_field = fd.f == &tc_opts::tri_path;
-            if (!path_field && (cur.tri_path == TC_TRI_FORWARD) != fwd_field) continue;
+            const bool uses_fwd = cur.tri_path != TC_TRI_MERGE, uses_merge = cur.tri_path != TC_TRI_FORWARD;
+            if (!path_field && (fwd_field ? !uses_fwd : !uses_merge)) continue;
             for (int k = 0; k < nc; ++k) {
                 if (max_trials > 0 && trials >= max_trials) break;
                 tc_opts o = cur;

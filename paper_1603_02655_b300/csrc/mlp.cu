@@ -5,6 +5,7 @@
 // The thesis bins tasks by the degree sum |N(u)|+|N(v)|-2 (Sec. 4.3.1); that
 // heuristic stays the fallback when no model is installed.
 #include <cstring>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -286,6 +287,65 @@ void pack_half(const float* prm, std::vector<__half2>& P) {
 std::mutex g_model_mu;
 __half2* g_model[64];  // installed packed weights per device (library-owned)
 
+__half2* g_path_model[64];  // installed path-routing model per device (library-owned)
+
+// Routing features of one graph (host, from its build statistics), the
+// inputs of the path model: log2(1+n)/32, log2(1+dyads)/32,
+// log2(1+mean degree)/8, log2(1+max degree)/20, log2(max/mean degree)/8,
+// log2(1+merged entries/dyads)/20, mutual fraction, log2(1+merged)/40.
+void path_features(const tc_graph_stats_t& s, float f[MLP_IN]) {
+    const double n = (double)s.n, dy = (double)s.dyads, mean = n > 0 ? 2.0 * dy / n : 0.0;
+    const double mx = (double)s.max_degree, merged = (double)s.merged_entries;
+    f[0] = (float)(std::log2(1.0 + n) / 32.0);
+    f[1] = (float)(std::log2(1.0 + dy) / 32.0);
+    f[2] = (float)(std::log2(1.0 + mean) / 8.0);
+    f[3] = (float)(std::log2(1.0 + mx) / 20.0);
+    f[4] = (float)(mean > 0 ? std::log2(std::max(1.0, mx / mean)) / 8.0 : 0.0);
+    f[5] = (float)(std::log2(1.0 + merged / std::max(1.0, dy)) / 20.0);
+    f[6] = (float)(dy > 0 ? (double)s.mutual / dy : 0.0);
+    f[7] = (float)(std::log2(1.0 + merged) / 40.0);
+}
+
+// The degree-skew rule: the forward path when the largest degree is at
+// least PATH_SKEW times the mean degree (hubs: the forward lists stay short
+// and the merge path's hub dyads are long), else the merge path.
+constexpr double PATH_SKEW = 8.0;
+
+tc_status path_route_impl(const GraphSet& set, const std::vector<int32_t>& gidx, std::vector<uint8_t>& merge,
+                          cudaStream_t st) {
+    const size_t G = gidx.size();
+    merge.assign(G, 0);
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    __half2* model = (dev >= 0 && dev < 64) ? g_path_model[dev] : nullptr;
+    if (!model) {
+        for (size_t i = 0; i < G; ++i) {
+            const tc_graph_stats_t& s = set.stats[(size_t)gidx[i]];
+            const double mean = s.n > 0 ? 2.0 * (double)s.dyads / (double)s.n : 0.0;
+            merge[i] = (double)s.max_degree < PATH_SKEW * mean ? 1 : 0;
+        }
+        return TC_OK;
+    }
+    // the installed network, FP16 as in binning: output 0 = log2 cost of the
+    // forward path, 1 = of the merge path
+    std::vector<float> f(G * MLP_IN), o(G * MLP_OUT);
+    for (size_t i = 0; i < G; ++i) path_features(set.stats[(size_t)gidx[i]], f.data() + i * MLP_IN);
+    float* d = nullptr;
+    TC_CUDA(dev_alloc((void**)&d, sizeof(float) * G * (MLP_IN + MLP_OUT), st));
+    cudaError_t e = cudaMemcpyAsync(d, f.data(), sizeof(float) * G * MLP_IN, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_mlp_predict16<<<(int)((G + 255) / 256), 256, 0, st>>>(model, d, (int32_t)G, d + G * MLP_IN);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(o.data(), d + G * MLP_IN, sizeof(float) * G * MLP_OUT, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(d, st);
+    if (e != cudaSuccess) return cuda_fail(e, "path model inference", __FILE__, __LINE__);
+    for (size_t i = 0; i < G; ++i) merge[i] = o[i * MLP_OUT + 1] < o[i * MLP_OUT + 0] ? 1 : 0;
+    return TC_OK;
+}
+
 struct TrainBuffers {
     float *X = nullptr, *H1 = nullptr, *H2 = nullptr, *D1 = nullptr, *D2 = nullptr, *D3 = nullptr;
     double* part = nullptr;
@@ -331,6 +391,11 @@ tc_status grad_step(const float* prm, const float* feat, const int32_t* bin, con
 }
 
 }  // namespace
+
+tc_status path_route(const GraphSet& set, const std::vector<int32_t>& gidx, std::vector<uint8_t>& merge,
+                     cudaStream_t st) {
+    return path_route_impl(set, gidx, merge, st);
+}
 
 // Installed FP16 weights of the current device, or nullptr.
 const void* cost_model_weights() {
@@ -477,6 +542,54 @@ tc_status tc_cost_model_load(const float* params) {
     tc::pack_half(params, P);
     if (!tc::g_model[dev]) TC_CUDA(cudaMalloc((void**)&tc::g_model[dev], sizeof(__half2) * tc::MLPH_N));
     TC_CUDA(cudaMemcpy(tc::g_model[dev], P.data(), sizeof(__half2) * P.size(), cudaMemcpyHostToDevice));
+    return TC_OK;
+}
+
+tc_status tc_path_features(int32_t G, const tc_graph* gs, float* feat) {
+    if (G < 0 || (G > 0 && (!gs || !feat))) return tc::fail(TC_ERR_ARG, "tc_path_features: bad arguments");
+    for (int32_t i = 0; i < G; ++i) {
+        if (!gs[i]) return tc::fail(TC_ERR_ARG, "tc_path_features: null handle");
+        tc::path_features(gs[i]->set->stats[(size_t)gs[i]->index], feat + (size_t)i * tc::MLP_IN);
+    }
+    return TC_OK;
+}
+
+tc_status tc_path_model_load(const float* params) {
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return tc::fail(TC_ERR_UNSUPPORTED, "tc_path_model_load: device index >= 64");
+    std::lock_guard<std::mutex> lk(tc::g_model_mu);
+    if (!params) {  // uninstall: routing falls back to the degree-skew rule
+        if (tc::g_path_model[dev]) {
+            TC_CUDA(cudaDeviceSynchronize());
+            TC_CUDA(cudaFree(tc::g_path_model[dev]));
+            tc::g_path_model[dev] = nullptr;
+        }
+        return TC_OK;
+    }
+    std::vector<__half2> P;
+    tc::pack_half(params, P);
+    if (!tc::g_path_model[dev]) TC_CUDA(cudaMalloc((void**)&tc::g_path_model[dev], sizeof(__half2) * tc::MLPH_N));
+    TC_CUDA(cudaMemcpy(tc::g_path_model[dev], P.data(), sizeof(__half2) * P.size(), cudaMemcpyHostToDevice));
+    return TC_OK;
+}
+
+tc_status tc_path_route(int32_t G, const tc_graph* gs, int32_t* path, void* stream) {
+    if (G < 0 || (G > 0 && (!gs || !path))) return tc::fail(TC_ERR_ARG, "tc_path_route: bad arguments");
+    if (G == 0) return TC_OK;
+    for (int32_t i = 0; i < G; ++i) {
+        if (!gs[i]) return tc::fail(TC_ERR_ARG, "tc_path_route: null handle");
+        if (gs[i]->set != gs[0]->set) return tc::fail(TC_ERR_UNSUPPORTED, "tc_path_route: handles of different builds");
+    }
+    std::vector<int32_t> idx((size_t)G);
+    for (int32_t i = 0; i < G; ++i) idx[(size_t)i] = gs[i]->index;
+    std::vector<uint8_t> merge;
+    try {
+        if (tc_status s = tc::path_route(*gs[0]->set, idx, merge, (cudaStream_t)stream); s != TC_OK) return s;
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_path_route: unexpected exception");
+    }
+    for (int32_t i = 0; i < G; ++i) path[i] = merge[(size_t)i] ? TC_TRI_MERGE : TC_TRI_FORWARD;
     return TC_OK;
 }
 

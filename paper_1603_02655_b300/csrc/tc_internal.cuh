@@ -67,6 +67,12 @@ struct GraphSet {
 // Packed FP16 cost-model weights installed on the current device (or null).
 const void* cost_model_weights();
 
+// tri_path = TC_TRI_AUTO: for each graph of gidx, merge[i] = 1 when it takes
+// the merge path, 0 the forward path (installed path model, else the
+// degree-skew rule).
+tc_status path_route(const GraphSet& set, const std::vector<int32_t>& gidx, std::vector<uint8_t>& merge,
+                     cudaStream_t st);
+
 }  // namespace tc
 
 struct tc_graph_s {

@@ -18,14 +18,16 @@ BIG = 1 << 30
 
 # binning configurations: default, everything per thread, per warp, per CTA
 # chunk (tiny chunks: every task split), and small mixed thresholds
-MERGE = tc.TC_TRI_MERGE
+MERGE, FWD = tc.TC_TRI_MERGE, tc.TC_TRI_FORWARD
 BINS = {
-    # forward path (the default): owners by tag map and by binary search
+    # the default: each graph on the path its router picks (degree-skew rule)
     "default": {},
-    "fwd_map_all": dict(fwd_big=1),
-    "fwd_search_all": dict(fwd_big=BIG),
-    "fwd_map_mid": dict(fwd_big=4),
-    "fwd_row_tasks": dict(row_tasks=1),
+    # forward path: owners by tag map and by binary search
+    "fwd": dict(tri_path=FWD),
+    "fwd_map_all": dict(tri_path=FWD, fwd_big=1),
+    "fwd_search_all": dict(tri_path=FWD, fwd_big=BIG),
+    "fwd_map_mid": dict(tri_path=FWD, fwd_big=4),
+    "fwd_row_tasks": dict(tri_path=FWD, row_tasks=1),
     # merge path: owner lookups and merge bins
     "merge_default": dict(tri_path=MERGE),
     "no_owner": dict(tri_path=MERGE, own_min=0),
@@ -247,7 +249,8 @@ def test_hub_tasks_stage_short_list_in_pieces():
         o = tc.tc_opts_default(profile=1, **BINS[name])
         assert gpu_census(n, src, dst, o) == want, name
         p = tc.tc_census_profile()
-        if o.tri_path == tc.TC_TRI_FORWARD:  # no merge bins: every triangle from the forward lists
+        path = o.tri_path if o.tri_path != tc.TC_TRI_AUTO else route_of(n, src, dst)
+        if path == tc.TC_TRI_FORWARD:  # no merge bins: every triangle from the forward lists
             assert sum(p["bin_tasks"]) == 0 and p["owner_tasks"] == 0, name
             assert p["map_triangles"] + p["search_triangles"] == triangles(want), name
         elif o.own_min > 0:  # the hubs own their dyads: looked up, not streamed
@@ -257,6 +260,14 @@ def test_hub_tasks_stage_short_list_in_pieces():
             assert p["hub_entries"] > 0
         else:
             assert p["hub_tasks"] == 0, name
+
+
+def route_of(n, src, dst):
+    g = tc.tc_graph_build(n, src, dst)
+    try:
+        return tc.tc_path_route([g])[0]
+    finally:
+        tc.tc_graph_free(g)
 
 
 def triangles(census):
@@ -358,7 +369,7 @@ def test_owner_large_and_skewed():
         c, p = owner_profile(n, src, dst, own_min=own_min)
         assert c == want, own_min
         assert p["owner_items"] >= 1 and p["owner_tasks"] > 0
-    for name in ("default", "fwd_map_all", "fwd_search_all"):  # both lookup forms in one graph
+    for name in ("fwd", "fwd_map_all", "fwd_search_all"):  # both lookup forms in one graph
         c, p = forward_profile(n, src, dst, name)
         assert c == want, name
         assert p["map_triangles"] + p["search_triangles"] == triangles(want), name
@@ -593,7 +604,7 @@ def test_forward_path_finds_each_triangle_once(seed):
     looked = np.where(nplus[lo[order]] <= 16, nplus[lo[order]], suffix)
     owner_has_fwd = nplus[hi[order]] > 0
     lookups = int(looked[owner_has_fwd].sum())
-    for name in ("default", "fwd_map_all", "fwd_search_all", "fwd_map_mid", "fwd_row_tasks"):
+    for name in ("fwd", "fwd_map_all", "fwd_search_all", "fwd_map_mid", "fwd_row_tasks"):
         c, p = forward_profile(n, src, dst, name)
         assert c == want, name
         assert p["map_triangles"] + p["search_triangles"] == triangles(want), name
@@ -601,3 +612,66 @@ def test_forward_path_finds_each_triangle_once(seed):
         assert p["fwd_entries"] == pair.size, name
     _, p = forward_profile(n, src, dst, "fwd_search_all")
     assert p["map_lookups"] == 0 and p["map_items"] == 0
+
+
+# ------------------------------------------------------------ path routing
+
+def mixed_batch(rng, k):
+    """Near-regular random graphs and hub graphs, alternating."""
+    arcs, ns = [], []
+    for i in range(k):
+        if i % 2:
+            n = int(rng.integers(2000, 6000))
+            s_, d_ = hub_graph(rng, n, 2, int(rng.integers(500, 1500)), 4 * n, 0.2)
+        else:
+            n = int(rng.integers(100, 400))
+            s_, d_ = rand_graph(rng, n, float(rng.choice([0.02, 0.05])), 0.3)
+        arcs.append((s_, d_))
+        ns.append(n)
+    off = np.cumsum([0] + [a[0].size for a in arcs])
+    return ns, off, np.concatenate([a[0] for a in arcs]).astype(np.int32), \
+        np.concatenate([a[1] for a in arcs]).astype(np.int32), arcs
+
+
+def test_auto_routing_never_changes_counts():
+    """Whatever path the router gives each graph (the degree-skew rule, or
+    models that send every graph one way, or a random one), the batched
+    census, its plan and its 64-code form equal the oracle's."""
+    import torch
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(404)
+    ns, off, src, dst, arcs = mixed_batch(rng, 12)
+    want = [oracle.census(n, a[0], a[1], threads=THREADS) for n, a in zip(ns, arcs)]
+    gs = tc.tc_graph_build_batched(ns, off, src, dst)
+    try:
+        feat = tc.tc_path_features(gs)
+        rule = [tc.TC_TRI_MERGE if f[4] * 8.0 < 3.0 else tc.TC_TRI_FORWARD for f in feat]
+        assert tc.tc_path_route(gs) == rule
+        assert set(rule) == {tc.TC_TRI_FORWARD, tc.TC_TRI_MERGE}  # both paths in one census
+        models = []
+        for bias in ([0.0, 50.0, 0.0, 0.0], [50.0, 0.0, 0.0, 0.0], None):
+            p = omlp.init(7).astype(np.float32)
+            if bias is not None:
+                p[-4:] = bias  # outputs: log2 time forward, merge
+            models.append((bias, p))
+        for bias, p in [(None, None)] + models:
+            tc.tc_path_model_load(p)
+            if bias == [0.0, 50.0, 0.0, 0.0]:
+                assert tc.tc_path_route(gs) == [tc.TC_TRI_FORWARD] * len(gs)
+            if bias == [50.0, 0.0, 0.0, 0.0]:
+                assert tc.tc_path_route(gs) == [tc.TC_TRI_MERGE] * len(gs)
+            o = tc.tc_opts_default(tri_path=tc.TC_TRI_AUTO)
+            assert tc.tc_census_batched(gs, o) == want
+            codes = tc.tc_census_codes_batched(gs, o)
+            assert [fold(c) for c in codes] == want
+            out = torch.zeros(17 * len(gs), dtype=torch.int64, device="cuda")
+            plan = tc.tc_plan_create(gs, out, o)
+            tc.tc_plan_run(plan)
+            torch.cuda.synchronize()
+            tc.tc_plan_free(plan)
+            words = out.cpu().tolist()
+            assert [tc.census_from_device_words(words[17 * i:17 * i + 17]) for i in range(len(gs))] == want
+    finally:
+        tc.tc_path_model_load(None)
+        for g in gs:
+            tc.tc_graph_free(g)
