@@ -57,23 +57,6 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_1603_02655_b300", "csrc", "census.cu")
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        for line in open(path):
-            parts = line.split()
-            if len(parts) >= 3 and parts[0] == kernel and parts[2] == sha:
-                return int(parts[1])
-    except OSError:
-        pass
-    return None
-
-
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -371,15 +354,27 @@ def dominant_kernel(tc, profs, stats):
     return top, ms
 
 
-def issue_record(kernel):
-    """Warp instructions per lookup of `kernel` from the committed ncu summary
-    (profiles/issue.txt), if it was taken on the current kernel source."""
+def source_key():
+    """sha256 prefix of the census kernels' code (census.cu, forward.cuh) with
+    comments and blank space removed: the key under which profiles/issue.txt
+    and profiles/traffic.txt store counters, so that a record is used only on
+    the code it was taken on, and comment edits do not void it."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_1603_02655_b300", "csrc")
     h = hashlib.sha256()
     for f in ("census.cu", "forward.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
-    sha = h.hexdigest()[:16]
+        text = open(os.path.join(csrc, f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
+def issue_record(kernel):
+    """Warp instructions per lookup of `kernel` from the committed ncu summary
+    (profiles/issue.txt), if it was taken on the current kernel code."""
+    sha = source_key()
     try:
         for line in open(os.path.join(ROOT, "profiles", "issue.txt")):
             parts = line.split()

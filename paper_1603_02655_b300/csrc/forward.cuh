@@ -18,14 +18,14 @@
 //
 // How triangles are found.  Vertices are ranked by (floor(log2 d), id) per
 // graph (rank R, 0 .. n-1).  The forward list F(x) holds the neighbours of x
-// of higher rank, as R << 2 | tag seen from x (in rank order when it has
-// more than FWD_SHORT entries, else in id order).  A triangle x, h, w with
-// R(x) < R(h) < R(w) is found exactly once: at the dyad {x, h}, owned by h,
-// as an element w of F(x) ranked above h (the suffix after h of a sorted
-// list, the whole of a short one) that also lies in F(h).  Because high-degree vertices rank last, every F(h) is short (at
-// most a few hundred entries on the power-law workloads), and the suffixes
-// sum to about half the lookups of an id-ordered search (R-MAT scale 22:
-// 5.3e8 instead of 1.1e9 for the hub dyads alone).
+// of higher rank, as R << 2 | tag seen from x, in rank order.  A triangle
+// x, h, w with R(x) < R(h) < R(w) is found exactly once: at the dyad {x, h},
+// owned by h, as an element w of F(x) ranked above h (the suffix after h of
+// a list of more than FWD_SHORT entries, the whole of a shorter one) that
+// also lies in F(h).  Because high-degree vertices rank last, every F(h) is
+// short (at most a few hundred entries on the power-law workloads), and the
+// suffixes sum to about half the lookups of an id-ordered search (R-MAT
+// scale 22: 5.3e8 instead of 1.1e9 for the hub dyads alone).
 //
 // Two lookup forms:
 //  * k_tri_big: an owner with many forward neighbours and few vertices
@@ -35,8 +35,8 @@
 //    at most TRI_PIECE at a time, are laid out as concatenated suffixes that
 //    the warps split evenly.
 //  * k_tri_small: every other owner: warps take runs of dyad records; a
-//    lookup scans F(h) when it is short (id order) or binary-searches it
-//    (rank order) (global memory, cached: a run's dyads share few owners).
+//    lookup binary-searches F(h) (global memory, cached: a run's dyads
+//    share few owners).
 // Hits (triangles) are queued per warp and applied 32 at a time: the third
 // vertex's id is read from the rank permutation, the three vertices are
 // ordered by id, and the four histogram updates are made.
@@ -179,11 +179,12 @@ struct U8ToInt {
 };
 using FlagIt = thrust::transform_iterator<U8ToInt, const uint8_t*, int>;
 
-// Rows whose forward list has at most FWD_SHORT entries keep it in id order:
-// a dyad of such a row looks up its whole forward list instead of the part
-// ranked above the owner (an entry ranked below the owner cannot lie in the
-// owner's forward list, so the result is the same); R-MAT scale 22: +3%
-// lookups, 15x fewer rows to sort.
+// Rows whose forward list has at most FWD_SHORT entries are sorted in
+// registers (k_fwd_sort_short) and a dyad of such a row looks up its whole
+// forward list instead of the part ranked above the owner (an entry ranked
+// below the owner cannot lie in the owner's forward list, so the result is
+// the same, and no search for the suffix is needed); R-MAT scale 22: +3%
+// lookups, 15x fewer rows for the warp-per-row sort.
 constexpr int FWD_SHORT = 16;
 constexpr int TRI_PIECE = 512;     // dyad records per tag-map work item
 constexpr int MAP_KEYS = 1 << 17;  // ranks a tag map covers (2 bits each: 32 KB)
@@ -288,8 +289,8 @@ __global__ void __launch_bounds__(FR_NT) k_fwd_rows(const int64_t* __restrict__ 
 }
 
 // Forward entries, one thread per entry of the selection: in a short row
-// (kept in id order) the entry R << 2 | tag, in a long row the adjacency
-// word for the sort.
+// the entry R << 2 | tag (in id order until k_fwd_sort_short), in a long row
+// the adjacency word for k_fwd_sort.
 __global__ void k_fwd_fill(const uint32_t* __restrict__ adj, const int32_t* __restrict__ arow,
                            const SegDev* __restrict__ seg, const int64_t* __restrict__ pfx,
                            const int64_t* __restrict__ epfx, int nseg, int64_t entries, FwdLayout F) {
