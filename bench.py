@@ -780,10 +780,13 @@ def run_batched(args, world, rank, local, pg):
 
 
 def train_and_compare(tc, gs, opts, stream, free):
-    """Train the task-cost model on timings recorded on these graphs, install
-    it, and time the census with degree-sum binning and with learned binning
-    (best of 5 after 2 warm-ups each).  Returns (report, opts with learned
-    binning)."""
+    """Binning on the merge path (the only path with bins): train the
+    task-cost model on timings recorded on these graphs, install it, and time
+    the census (best of 5 after 2 warm-ups) with degree-sum binning, with
+    exact-|S| binning (its |S| pass timed apart: the census time without it
+    is the ceiling of a one-number cost rule) and with learned binning, each
+    with owner lookups for hub dyads (own_min as given) and with merges only
+    (own_min = 0).  Returns (report, opts with learned binning)."""
     import torch
     from paper_1603_02655_b300 import costmodel
     t0 = time.perf_counter()
@@ -804,25 +807,38 @@ def train_and_compare(tc, gs, opts, stream, free):
                 ts.append(a.elapsed_time(c))
         return float(np.min(ts)), out.cpu().tolist()
 
-    heur = tc.tc_opts_default(**{k: getattr(opts, k) for k in tc.TUNED_FIELDS})
-    heur.bin_mode = tc.TC_BIN_HEURISTIC
-    learn = tc.tc_opts_default(**{k: getattr(opts, k) for k in tc.TUNED_FIELDS})
-    learn.bin_mode = tc.TC_BIN_MLP
-    h_ms, h_out = best_ms(heur)
-    l_ms, l_out = best_ms(learn)
-    bins_used = {}
-    for name, o in (("degree_sum", heur), ("learned", learn)):
-        o.profile = 1
-        tc.tc_census_batched(gs, o, stream=stream)
-        bins_used[name] = tc.tc_census_profile()["bin_tasks"]
-        o.profile = 0
-    assert h_out == l_out, "learned binning changed the counts"
-    learn.profile = opts.profile
-    report = {"census_ms_degree_sum": h_ms, "census_ms_learned": l_ms, "speedup": h_ms / l_ms,
+    def with_mode(mode, own_min):
+        o = tc.tc_opts_default(**{k: getattr(opts, k) for k in tc.TUNED_FIELDS})
+        o.bin_mode, o.tri_path, o.own_min = mode, tc.TC_TRI_MERGE, own_min
+        return o
+
+    report = {"path": "merge (tri_path = TC_TRI_MERGE): the bins exist only there",
               "rmse_log2_cycles_mlp": rep["rmse_mlp"], "rmse_log2_cycles_degree_sum": rep["rmse_degree_sum"],
               "rmse_log2_cycles_exact_size": rep.get("rmse_exact_size"),
-              "samples": rep["samples"], "train_s": train_s,
-              "bin_tasks": bins_used}
+              "samples": rep["samples"], "train_s": train_s}
+    ref = None
+    for label, own_min in (("owner_lookups", opts.own_min if opts.own_min > 0 else 128), ("merges_only", 0)):
+        rec = {"own_min": own_min}
+        for name, mode in (("degree_sum", tc.TC_BIN_HEURISTIC), ("exact_size", tc.TC_BIN_EXACT),
+                           ("learned", tc.TC_BIN_MLP)):
+            o = with_mode(mode, own_min)
+            ms, out = best_ms(o)
+            if ref is None:
+                ref = out
+            assert out == ref, f"{name} binning changed the counts"
+            o.profile = 1
+            tc.tc_census_batched(gs, o, stream=stream)
+            p = tc.tc_census_profile()
+            rec[name] = {"census_ms": ms, "bin_tasks": p["bin_tasks"]}
+            if mode == tc.TC_BIN_EXACT:
+                rec[name]["exact_pass_ms"] = p["ms_exact_cost"]
+                rec[name]["census_ms_without_pass"] = ms - p["ms_exact_cost"]
+        rec["speedup_learned"] = rec["degree_sum"]["census_ms"] / rec["learned"]["census_ms"]
+        rec["speedup_exact_ceiling"] = rec["degree_sum"]["census_ms"] / rec["exact_size"]["census_ms_without_pass"]
+        report[label] = rec
+    learn = with_mode(tc.TC_BIN_MLP, opts.own_min)
+    learn.tri_path = opts.tri_path
+    learn.profile = opts.profile
     if free:
         for g in gs:
             tc.tc_graph_free(g)

@@ -83,11 +83,20 @@ typedef struct {
     int64_t max_degree;     /* largest undirected degree */
 } tc_graph_stats_t;
 
-/* Task binning (Sec. 4.3.1: canonical-dyad tasks, cost |N(u)|+|N(v)|-2). */
-enum { TC_BIN_HEURISTIC = 0, TC_BIN_MLP = 1 };
+/* Task binning of the merge path (Sec. 4.3.1: canonical-dyad tasks, cost
+ * |N(u)|+|N(v)|-2, the uniform distribution).  TC_BIN_EXACT bins by the exact
+ * task cost |S| = |N(u) u N(v) \ {u,v}| instead (the W3 workload of Sec. 4.3,
+ * balanced by the non-uniform distribution of Sec. 4.3.2): a pass before the
+ * task pass (k_union_entries, one binary search per entry of the shorter
+ * list) computes it for every canonical dyad, and a task goes to the thread
+ * bin when |S|+2 <= thr_thread, the warp bin when <= thr_warp.  It is the
+ * ceiling of a one-number cost rule; its pass is timed apart
+ * (tc_profile_t.ms_exact_cost, not in ms_total).  Graphs on the forward path
+ * have no bins and ignore bin_mode. */
+enum { TC_BIN_HEURISTIC = 0, TC_BIN_MLP = 1, TC_BIN_EXACT = 2 };
 
 typedef struct {
-    int32_t bin_mode;     /* TC_BIN_HEURISTIC (degree sum) or TC_BIN_MLP */
+    int32_t bin_mode;     /* TC_BIN_HEURISTIC (degree sum), TC_BIN_MLP or TC_BIN_EXACT */
     int32_t thr_thread;   /* tasks with |N(u)|+|N(v)| <= thr_thread: one thread each */
     int32_t thr_warp;     /* <= thr_warp (capped at 1024): one warp each;
                              larger tasks are split into tiles */
@@ -188,6 +197,7 @@ typedef struct {
     int64_t map_dyads;       /* dyad records of the tag-map owners */
     int64_t search_dyads;    /* dyad records of the other owners */
     int64_t map_list_entries;  /* forward-list entries of the tag-map items' owners */
+    float ms_exact_cost;     /* TC_BIN_EXACT: the |S| pass before the task pass */
 } tc_profile_t;
 
 tc_status tc_census_profile(tc_profile_t* out);

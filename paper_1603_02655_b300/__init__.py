@@ -32,7 +32,7 @@ TYPE_NAMES = ("003", "012", "102", "021D", "021U", "021C", "111D", "111U",
               "030T", "030C", "201", "120D", "120U", "120C", "210", "300")
 
 TC_OK, TC_ERR_ARG, TC_ERR_ID_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED = range(7)
-TC_BIN_HEURISTIC, TC_BIN_MLP = 0, 1
+TC_BIN_HEURISTIC, TC_BIN_MLP, TC_BIN_EXACT = 0, 1, 2
 TC_TRI_FORWARD, TC_TRI_MERGE, TC_TRI_AUTO = 0, 1, 2
 TC_DEVICE_PTRS = 1
 TC_UNDIRECTED = 4
@@ -104,7 +104,7 @@ class TcProfile(ctypes.Structure):
                 ("map_lookups", ctypes.c_int64), ("map_triangles", ctypes.c_int64),
                 ("search_lookups", ctypes.c_int64), ("search_triangles", ctypes.c_int64),
                 ("map_dyads", ctypes.c_int64), ("search_dyads", ctypes.c_int64),
-                ("map_list_entries", ctypes.c_int64)]
+                ("map_list_entries", ctypes.c_int64), ("ms_exact_cost", ctypes.c_float)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -83,7 +83,7 @@ thread_local bool g_profile_valid = false;
 constexpr int NEV = 10;
 
 struct ProfileEvents {
-    cudaEvent_t ev[NEV];
+    cudaEvent_t ev[NEV + 1];  // ev[NEV]: before the exact-cost pass (TC_BIN_EXACT)
 };
 
 tc_status profile_events(ProfileEvents** out) {
@@ -93,7 +93,7 @@ tc_status profile_events(ProfileEvents** out) {
     TC_CUDA(cudaGetDevice(&dev));
     dev &= 63;
     if (!made[dev]) {
-        for (int k = 0; k < NEV; ++k) TC_CUDA(cudaEventCreate(&pe[dev].ev[k]));
+        for (int k = 0; k <= NEV; ++k) TC_CUDA(cudaEventCreate(&pe[dev].ev[k]));
         made[dev] = true;
     }
     *out = &pe[dev];
@@ -176,6 +176,8 @@ struct BinParams {
     const __half2* mlp;     // packed FP16 cost model, or null for the degree-sum rule
     const int32_t* vtag;    // per-vertex tag counts (model features)
     int fwd;                // 1: the triangles come from the forward lists: emit no task
+    const uint32_t* exact;  // TC_BIN_EXACT: |S| of each canonical dyad at its adjacency
+                            // position in row u (k_union_entries), else null
 };
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
@@ -323,8 +325,9 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                         Os[1] += (unsigned long long)L;
 
                     } else {
-                        bin = L <= bp.thr_thread ? 0
-                              : L <= bp.thr_warp ? 1
+                        const int c = bp.exact ? (int)bp.exact[beg + k] + 2 : L;  // |S| + 2 = L - c_uv
+                        bin = c <= bp.thr_thread ? 0
+                              : c <= bp.thr_warp ? 1
                               : min(d, dv) <= min(bp.stream_max, STREAM_SMAX) ? 3 : 2;
                     }
                 }
@@ -526,8 +529,9 @@ __global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict
                     Os[0] += 1;
                     Os[1] += (unsigned long long)L;
                 } else {
-                    bin = L <= bp.thr_thread ? 0
-                          : L <= bp.thr_warp ? 1
+                    const int c = bp.exact ? (int)bp.exact[k] + 2 : L;  // |S| + 2 = L - c_uv
+                    bin = c <= bp.thr_thread ? 0
+                          : c <= bp.thr_warp ? 1
                           : min(d, dv) <= min(bp.stream_max, STREAM_SMAX) ? 3 : 2;
                 }
             }
@@ -586,6 +590,55 @@ __global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict
     for (int k = 0; k < 2; ++k) {
         const unsigned long long e = warp_sum64(Os[k]);
         if (lane == 0 && e) atomicAdd(bins.own_stat + k, e);
+    }
+}
+
+// ------------------------------------------------------- k_union_entries --
+// Exact task cost for bin_mode = TC_BIN_EXACT: |S| = |N(u) u N(v) \ {u, v}|
+// of every canonical dyad <u, v> of the selection (the W3 workload of a task,
+// Sec. 4.3: the cost the non-uniform distribution of Sec. 4.3.2 balances),
+// written at the dyad's adjacency position in row u.  |S| = d_u + d_v - 2 -
+// c_uv, with c_uv the common neighbours.  Warps take 32 entries at a time;
+// the canonical ones (neighbour above the row) are done one after the other,
+// the lanes binary-searching the shorter list's entries in the longer one.
+__global__ void __launch_bounds__(256) k_union_entries(const int64_t* __restrict__ row_ptr,
+                                                       const uint32_t* __restrict__ adj,
+                                                       const int32_t* __restrict__ arow,
+                                                       const int32_t* __restrict__ deg,
+                                                       const SegDev* __restrict__ seg,
+                                                       const int64_t* __restrict__ epfx, int nseg,
+                                                       int64_t entries, uint32_t* __restrict__ usz) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t f0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; f0 < entries;
+         f0 += warps * 32) {
+        const int64_t f = f0 + lane;
+        int64_t k = 0, x = 0, y = 0;
+        bool canon = false;
+        if (f < entries) {
+            const int s = nseg == 1 ? 0 : seg_of(epfx, nseg, f);
+            const SegDev& g = seg[s];
+            k = g.eb + (f - epfx[s]);
+            x = arow[k];
+            y = g.rb + (int64_t)(__ldg(adj + k) >> 2);
+            canon = y > x;
+        }
+        for (unsigned m = __ballot_sync(full, canon); m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const int64_t kk = __shfl_sync(full, k, src), u = __shfl_sync(full, x, src),
+                          v = __shfl_sync(full, y, src);
+            const int du = deg[u], dv = deg[v];
+            const bool u_short = du <= dv;
+            const uint32_t* sl = adj + row_ptr[u_short ? u : v];
+            const uint32_t* gl = adj + row_ptr[u_short ? v : u];
+            const int ns = u_short ? du : dv, ng = u_short ? dv : du;
+            int common = 0;
+            for (int i = lane; i < ns; i += 32) common += list_has(gl, ng, __ldg(sl + i) >> 2) ? 1 : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) common += __shfl_xor_sync(full, common, o);
+            if (lane == 0) usz[kk] = (uint32_t)(du + dv - 2 - common);
+        }
     }
 }
 
@@ -2140,6 +2193,8 @@ struct Layout {
     size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_codes, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, o_epfx,
         o_scan, o_scantmp, need;
     uint32_t own_cap = 0;
+    bool exact = false;  // TC_BIN_EXACT on the merge path: |S| per canonical dyad first
+    size_t o_usz = 0;
     // forward path (tri_path = TC_TRI_FORWARD)
     bool fwd = false;
     int nb = 0;            // blocks of the rank computation
@@ -2167,7 +2222,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     tc_opts o;
     tc_opts_default(&o);
     if (opts_in) o = *opts_in;
-    if (o.bin_mode != TC_BIN_HEURISTIC && o.bin_mode != TC_BIN_MLP)
+    if (o.bin_mode != TC_BIN_HEURISTIC && o.bin_mode != TC_BIN_MLP && o.bin_mode != TC_BIN_EXACT)
         return fail(TC_ERR_ARG, "census: unknown bin_mode");
     if (o.thr_thread < 0 || o.thr_warp < o.thr_thread || o.chunk < 256 ||
         o.chunk > (o.split_cta ? TILE : WARP_LMAX))
@@ -2231,6 +2286,9 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.o_rt = o.bin_mode == TC_BIN_MLP ? take(sizeof(uint4) * c01) : Lo.o_r[2];
     Lo.o_tl = take(sizeof(uint4) * c2);
     Lo.o_ia = take(sizeof(int32_t) * c2);
+    // exact task costs, one word per adjacency entry of the build
+    Lo.exact = o.bin_mode == TC_BIN_EXACT && !Lo.fwd && set.arow != nullptr && Lo.entries > 0;
+    Lo.o_usz = take(sizeof(uint32_t) * (Lo.exact ? (size_t)set.nnz : 1));
     if (Lo.fwd) {
         Lo.cap01 = Lo.cap2 = 1;
         o.own_min = 0;
@@ -2445,11 +2503,20 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     const __half2* mlp = o.bin_mode == TC_BIN_MLP ? (const __half2*)cost_model_weights() : nullptr;
     // with a cost model, every task above the warp bin is first collected in
     // bin 2 and then routed by k_route (stream bin or tiles)
-    const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, o.own_min, mlp, set.vtag, Lo.fwd ? 1 : 0};
+    const uint32_t* exact = Lo.exact ? (const uint32_t*)(ws + Lo.o_usz) : nullptr;
+    const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, o.own_min, mlp, set.vtag, Lo.fwd ? 1 : 0,
+                       exact};
     uint4* split_tasks = (uint4*)(ws + Lo.o_rt);
     auto mark = [&](int k) {
         if (pe) cudaEventRecord(pe->ev[k], st);
     };
+    if (Lo.exact) {  // the exact costs first (timed apart from the census kernels)
+        if (pe) cudaEventRecord(pe->ev[NEV], st);
+        k_union_entries<<<L.sms * 8, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, d_seg,
+                                                   (const int64_t*)(ws + Lo.o_epfx), Lo.nseg, Lo.entries,
+                                                   (uint32_t*)(ws + Lo.o_usz));
+        TC_CUDA(cudaGetLastError());
+    }
     TC_CUDA(cudaMemsetAsync(ws, 0, Lo.o_seg, st));  // accumulators + counters
     mark(0);
     if (Lo.fwd) {
@@ -2581,7 +2648,7 @@ int census_launches(const Layout& Lo) {
     if (Lo.fwd) return Lo.flat ? 13 : 14;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
     const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 2 : 1) : 1;  // k_owner_rows, k_tasks_flat
-    return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0);
+    return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0) + (Lo.exact ? 1 : 0);
 }
 
 tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cudaStream_t st) {
@@ -2618,6 +2685,7 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     }
     P.ms_fold = ms[8];
     P.ms_total = total;
+    if (Lo.exact) TC_CUDA(cudaEventElapsedTime(&P.ms_exact_cost, pe->ev[NEV], pe->ev[0]));
     P.launches = census_launches(Lo);
     const bool routed = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights();
     auto u64 = [&](int w) { return (int64_t)(((unsigned long long)c[w + 1] << 32) | c[w]); };
@@ -2948,7 +3016,7 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
     bins.own_cap = 0;
     bins.own_cnt = nullptr;
     bins.own_stat = nullptr;
-    const BinParams bp{0x7fffffff, 0x7fffffff, 0, 0, nullptr, nullptr, 0};
+    const BinParams bp{0x7fffffff, 0x7fffffff, 0, 0, nullptr, nullptr, 0, nullptr};
     if (n > 0) {
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
                                                      s->acc, cursor);

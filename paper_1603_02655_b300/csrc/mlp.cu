@@ -40,15 +40,6 @@ __global__ void k_features(const int32_t* __restrict__ deg, const int32_t* __res
 // One warp per pair: lanes take the shorter list's entries in turn and
 // binary-search them in the longer one; |S| = d_u + d_v - |common| - 2 when
 // u and v are adjacent (each list then holds the other endpoint).
-__device__ __forceinline__ bool list_has(const uint32_t* l, int n, uint32_t key) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((l[mid] >> 2) < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo < n && (l[lo] >> 2) == key;
-}
 
 __global__ void k_union_sizes(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
                               const int64_t* __restrict__ voff, int G, const int32_t* __restrict__ uv, int32_t n,

@@ -18,6 +18,18 @@ constexpr uint32_t SENT = 0xFFFFFFFFu;
 // Sentinel words stored after the adjacency array so that vector loads of a
 // merge window may run past the last row.
 constexpr int64_t ADJ_PAD = 8192;
+
+// Whether the sorted adjacency row l[0..n) holds neighbour id `key`
+// (binary search on the id bits of the tagged words).
+__device__ __forceinline__ bool list_has(const uint32_t* l, int n, uint32_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((l[mid] >> 2) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < n && (l[lo] >> 2) == key;
+}
 // Accumulator slots per graph: 64 triad codes, then the dyadic sums
 // n - |N(u)| - |N(v)| over the dyads with pre = 1, 2, 3 (slots 64, 65, 66).
 constexpr int ACC = 67;

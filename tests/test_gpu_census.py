@@ -52,6 +52,10 @@ BINS = {
     "owner_sep": dict(tri_path=MERGE, own_min=32, persistent=0, stream_max=0),
     "row_tasks": dict(tri_path=MERGE, row_tasks=1),
     "row_tasks_merge": dict(tri_path=MERGE, row_tasks=1, own_min=0, thr_thread=8, thr_warp=64),
+    "exact": dict(tri_path=MERGE, bin_mode=tc.TC_BIN_EXACT),
+    "exact_merges": dict(tri_path=MERGE, bin_mode=tc.TC_BIN_EXACT, own_min=0, thr_thread=16, thr_warp=96),
+    "exact_rows": dict(tri_path=MERGE, bin_mode=tc.TC_BIN_EXACT, own_min=0, row_tasks=1, thr_thread=16,
+                       thr_warp=96),
 }
 
 
@@ -599,8 +603,8 @@ def test_forward_path_finds_each_triangle_once(seed):
     start = np.concatenate([[0], np.cumsum(nplus)])
     pos = np.arange(order.size) - start[lo[order]]
     suffix = nplus[lo[order]] - pos - 1
-    # a forward list of at most 16 entries stays in id order and is looked
-    # up whole (its entries ranked below the owner cannot be hits)
+    # a forward list of at most 16 entries is looked up whole (its entries
+    # ranked below the owner cannot be hits)
     looked = np.where(nplus[lo[order]] <= 16, nplus[lo[order]], suffix)
     owner_has_fwd = nplus[hi[order]] > 0
     lookups = int(looked[owner_has_fwd].sum())
@@ -612,6 +616,54 @@ def test_forward_path_finds_each_triangle_once(seed):
         assert p["fwd_entries"] == pair.size, name
     _, p = forward_profile(n, src, dst, "fwd_search_all")
     assert p["map_lookups"] == 0 and p["map_items"] == 0
+
+
+# ------------------------------------------------------- exact-cost binning
+
+def union_sizes(n, src, dst):
+    """|S| = |N(u) u N(v) \\ {u, v}| of every canonical dyad u < v, from a
+    sparse adjacency product (c_uv = common neighbours)."""
+    import scipy.sparse as sp
+    s = src.astype(np.int64)
+    d = dst.astype(np.int64)
+    keep = s != d
+    pair = np.unique(np.minimum(s[keep], d[keep]) * n + np.maximum(s[keep], d[keep]))
+    u, v = pair // n, pair % n
+    A = sp.coo_matrix((np.ones(u.size, np.int64), (u, v)), shape=(n, n)).tocsr()
+    A = ((A + A.T) > 0).astype(np.int64)
+    deg = np.asarray(A.sum(axis=1)).ravel()
+    common = np.asarray((A @ A)[u, v]).ravel()
+    return u, v, deg, deg[u] + deg[v] - 2 - common
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_exact_binning_bins_by_union_size(seed):
+    """bin_mode = TC_BIN_EXACT puts a merge task in the thread bin when
+    |S| + 2 <= thr_thread and in the warp bin when <= thr_warp: the bin
+    counts equal those |S| gives (computed here from the adjacency), differ
+    from the degree-sum rule's, and the counts equal the oracle's."""
+    rng = np.random.default_rng(900 + seed)
+    n = 600
+    src, dst = rand_graph(rng, n, 0.06, 0.3)
+    want = oracle.census(n, src, dst, threads=THREADS)
+    u, v, deg, S = union_sizes(n, src, dst)
+    T, W = int(np.percentile(S + 2, 40)), int(np.percentile(S + 2, 80))  # thresholds inside the spread
+    got = {}
+    for mode, cost in ((tc.TC_BIN_EXACT, S + 2), (tc.TC_BIN_HEURISTIC, deg[u] + deg[v])):
+        o = tc.tc_opts_default(tri_path=MERGE, bin_mode=mode, own_min=0, thr_thread=T, thr_warp=W, profile=1)
+        g = tc.tc_graph_build(n, src, dst)
+        try:
+            assert tc.tc_census(g, o) == want, mode
+            p = tc.tc_census_profile()
+        finally:
+            tc.tc_graph_free(g)
+        b = p["bin_tasks"]
+        assert b[0] == int((cost <= T).sum()), mode
+        assert b[1] == int(((cost > T) & (cost <= W)).sum()), mode
+        assert b[2] + b[3] == int((cost > W).sum()), mode
+        assert (p["ms_exact_cost"] > 0) == (mode == tc.TC_BIN_EXACT)
+        got[mode] = b
+    assert got[tc.TC_BIN_EXACT] != got[tc.TC_BIN_HEURISTIC]
 
 
 # ------------------------------------------------------------ path routing
