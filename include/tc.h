@@ -302,6 +302,41 @@ tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts,
                             tc_census_t* out, uint32_t flags, void* stream);
 
 /*
+ * Sharded census -- the census of G graphs of one build cut into `nshards`
+ * shards whose accumulators add up, for callers that spread one census over
+ * several processes or devices (the thesis names a multi-GPU system as
+ * future work, Ch. 6).  Every canonical dyad's contributions are independent
+ * (Sec. 2.2) and the only exchange is a sum: each shard runs the whole census
+ * pipeline on the full graph (each process holds its own replica of the
+ * build) but adds only its share, and the shares are summed word by word
+ * (mod 2^64) before the fold and the 003 closure.
+ *
+ * tc_census_shard -- shard `shard` (0 <= shard < nshards) of the census of
+ *   gs[0..G): the suffix and dyadic terms of the selection's adjacency
+ *   entries [shard E / nshards, (shard+1) E / nshards) and the shared-
+ *   neighbour corrections of the dyads owned by the rows [shard R / nshards,
+ *   (shard+1) R / nshards) (E entries, R rows of the selection, graphs in
+ *   the order given; with tri_path TC_TRI_AUTO, of each path's part).
+ *   acc     device uint64[G][TC_ACC_WORDS]: graph i's raw accumulators (64
+ *           codes, then sum (n - d_u - d_v) over the dyads with pre = 1, 2,
+ *           3), overwritten.  Asynchronous on `stream`.
+ * tc_census_fold -- out[i] (and/or codes[i]; either may be NULL) from the
+ *   summed accumulators acc (device, [G][TC_ACC_WORDS]) of gs[i]: the 64->16
+ *   fold, the common-neighbour share of the dyadic term and the 003 closure
+ *   (k_fold).  out / codes are host memory (the call synchronises `stream`)
+ *   or, with TC_OUT_DEVICE, device memory.
+ * The sum over shards 0..nshards-1 of tc_census_shard's acc, folded, equals
+ * tc_census_batched's result for the same graphs and opts.
+ * Errors: TC_ERR_ARG, TC_ERR_UNSUPPORTED (handles from different builds),
+ * TC_ERR_OOM, TC_ERR_CUDA.
+ */
+#define TC_ACC_WORDS 67
+tc_status tc_census_shard(int32_t G, const tc_graph* gs, const tc_opts* opts, int32_t shard, int32_t nshards,
+                          uint64_t* acc, void* stream);
+tc_status tc_census_fold(int32_t G, const tc_graph* gs, const uint64_t* acc, tc_census_t* out,
+                         tc_census64_t* codes, uint32_t flags, void* stream);
+
+/*
  * tc_census_codes / tc_census_codes_batched -- the 64-code census of one
  * graph, or of G graphs of one build (out[i] for gs[i]); arguments, memory
  * and errors as tc_census / tc_census_batched.

@@ -45,8 +45,9 @@ EXPORTS = ("tc_opts_default", "tc_graph_build", "tc_graph_build_batched", "tc_gr
            "tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",
            "tc_cost_model_load", "tc_census_codes", "tc_census_codes_batched",
            "tc_graph_build_text", "tc_union_sizes", "tc_path_features", "tc_path_model_load",
-           "tc_path_route")
+           "tc_path_route", "tc_census_shard", "tc_census_fold")
 TC_MLP_NPARAM = 1476
+TC_ACC_WORDS = 67
 TC_NOALLOC_MAX_N = 262144
 TC_NOALLOC_MAX_DYADS = 262144
 
@@ -331,6 +332,47 @@ def tc_census_batched(gs, opts: TcOpts | None = None, out=None, stream=None):
         return [res[i].to_list() for i in range(G)]
     _check(lib.tc_census_batched(G, arr, po, out.data_ptr(), TC_OUT_DEVICE, _stream(stream)),
            "tc_census_batched")
+    return out
+
+
+def _device_words(t, need, what):
+    """A CUDA int64 tensor of at least `need` elements, contiguous (checked
+    here: the library reads and writes `need` words through its pointer)."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != "torch.int64" or not t.is_contiguous() \
+            or t.numel() < need:
+        raise TcError(TC_ERR_ARG, f"{what}: need a contiguous CUDA int64 tensor of >= {need} elements")
+    return t.data_ptr()
+
+
+def tc_census_shard(gs, shard: int, nshards: int, acc, opts: TcOpts | None = None, stream=None):
+    """Shard `shard` of `nshards` of the census of graphs `gs` (one build):
+    the raw accumulators of graph i go to acc[i*TC_ACC_WORDS:(i+1)*TC_ACC_WORDS]
+    (CUDA int64 tensor, asynchronous).  Summed over all shards (int64 sums wrap
+    like the library's uint64 words) and folded with tc_census_fold, they give
+    tc_census_batched's result."""
+    lib = load()
+    G = len(gs)
+    arr = (ctypes.c_void_p * max(G, 1))(*gs)
+    po = ctypes.byref(opts) if opts is not None else None
+    ptr = _device_words(acc, TC_ACC_WORDS * G, "tc_census_shard") if G else None
+    _check(lib.tc_census_shard(G, arr, po, int(shard), int(nshards), ptr, _stream(stream)), "tc_census_shard")
+    return acc
+
+
+def tc_census_fold(gs, acc, out=None, stream=None):
+    """Fold summed shard accumulators (CUDA int64 tensor, TC_ACC_WORDS per
+    graph) into censuses: host lists without `out`, else into `out` (CUDA
+    tensor of >= 17*G int64, asynchronous)."""
+    lib = load()
+    G = len(gs)
+    arr = (ctypes.c_void_p * max(G, 1))(*gs)
+    ptr = _device_words(acc, TC_ACC_WORDS * G, "tc_census_fold") if G else None
+    if out is None:
+        res = (TcCensus * max(G, 1))()
+        _check(lib.tc_census_fold(G, arr, ptr, res, None, 0, _stream(stream)), "tc_census_fold")
+        return [res[i].to_list() for i in range(G)]
+    _check(lib.tc_census_fold(G, arr, ptr, _device_words(out, 17 * G, "tc_census_fold"), None, TC_OUT_DEVICE,
+                              _stream(stream)), "tc_census_fold")
     return out
 
 

@@ -178,6 +178,10 @@ struct BinParams {
     int fwd;                // 1: the triangles come from the forward lists: emit no task
     const uint32_t* exact;  // TC_BIN_EXACT: |S| of each canonical dyad at its adjacency
                             // position in row u (k_union_entries), else null
+    // shard of the work (tc_census_shard; everything when unsharded): the task
+    // terms of the selection's entries [e_lo, e_hi) (k_tasks_flat) or of its
+    // rows [r_lo, r_hi) (k_tasks), and the dyads owned by rows [r_lo, r_hi)
+    int64_t e_lo, e_hi, r_lo, r_hi;
 };
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
@@ -261,6 +265,7 @@ __global__ void __launch_bounds__(256) k_tasks(const int64_t* __restrict__ row_p
                 n = seg[s].n;
                 sp = pfx[s];
             }
+            if (r < bp.r_lo || r >= bp.r_hi) continue;  // another shard's row
             const int64_t xl = r - sp;
             const int64_t x = rb + xl;
             const int64_t beg = row_ptr[x];
@@ -397,8 +402,9 @@ using OneHotIt = thrust::transform_iterator<OneHot, thrust::counting_iterator<in
 // Thread per row of the selected graphs: register each owner's work items.
 __global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
                              const int64_t* __restrict__ pfx, int nseg, int64_t total_rows, int own_min,
-                             Bins bins) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total_rows;
+                             Bins bins, int64_t r_lo, int64_t r_hi) {
+    const int64_t r_end = min(total_rows, r_hi);
+    for (int64_t r = r_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < r_end;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int s = nseg == 1 ? 0 : seg_of(pfx, nseg, r);
         const int64_t x = seg[s].rb + (r - pfx[s]);
@@ -512,8 +518,9 @@ __global__ void __launch_bounds__(256, 4) k_tasks_flat(const int64_t* __restrict
                 S3 = (uint32_t)vtag[3 * x + 2] - (uint32_t)((I >> (2 * TAG_BITS)) & TAG_MASK);
                 d = deg[x];
             }
-            const bool is_task = valid && (int64_t)y > xl;
-            const bool is_twin = valid && (int64_t)y < xl;
+            const bool part = valid && f >= bp.e_lo && f < bp.e_hi;  // this shard's entry
+            const bool is_task = part && (int64_t)y > xl;
+            const bool is_twin = part && (int64_t)y < xl;
             const int pre_task = t;
             const int pre_twin = ((t & 1) << 1) | (t >> 1);
             int L = 0;
@@ -1525,11 +1532,18 @@ __global__ void __launch_bounds__(CTA_NT) k_cta(const int64_t* __restrict__ row_
 
 // ---------------------------------------------------------------- k_fold --
 // 64 codes -> 16 MAN types; 003 = C(n,3) - the rest, in 128-bit (Sec. 2.2).
+// With raw non-null (a shard of the census) the accumulators themselves go
+// to raw[slot]: shards are summed word by word before they are folded.
 __global__ void k_fold(const unsigned long long* __restrict__ acc, const SegDev* __restrict__ seg, int nseg,
-                       tc_census_t* __restrict__ out, tc_census64_t* __restrict__ codes) {
+                       tc_census_t* __restrict__ out, tc_census64_t* __restrict__ codes,
+                       unsigned long long* __restrict__ raw) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     const unsigned long long* h = acc + (size_t)s * ACC;
+    if (raw) {
+        for (int w = 0; w < ACC; ++w) raw[(size_t)seg[s].slot * ACC + w] = h[w];
+        return;
+    }
     unsigned long long cnt[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) cnt[t] = 0;
@@ -2195,6 +2209,10 @@ struct Layout {
     uint32_t own_cap = 0;
     bool exact = false;  // TC_BIN_EXACT on the merge path: |S| per canonical dyad first
     size_t o_usz = 0;
+    // tc_census_shard: this call does shard `shard` of `nshards` and writes the
+    // raw accumulators of each graph to raw[slot] instead of folding them
+    int32_t shard = 0, nshards = 1;
+    unsigned long long* raw = nullptr;
     // forward path (tri_path = TC_TRI_FORWARD)
     bool fwd = false;
     int nb = 0;            // blocks of the rank computation
@@ -2432,7 +2450,7 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     TC_CUDA(cub::DeviceScan::InclusiveSum(tmp, tb, FlagIt(flag, U8ToInt{}), (int32_t*)(ws + Lo.o_fs),
                                           (int)Lo.entries, st));
     k_fwd_rows<<<L.sms * 8, FR_NT, 0, st>>>(set.row_ptr, set.deg, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.rows, Lo.o.fwd_big,
-                                           F);
+                                           F, bp.r_lo, bp.r_hi);
     TC_CUDA(cudaGetLastError());
     tb = Lo.fscan_bytes;
     TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, F.tcnt, F.tpre, (int)(Lo.rows + 1), st));
@@ -2504,8 +2522,15 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     // with a cost model, every task above the warp bin is first collected in
     // bin 2 and then routed by k_route (stream bin or tiles)
     const uint32_t* exact = Lo.exact ? (const uint32_t*)(ws + Lo.o_usz) : nullptr;
+    // shard k of N: entries [k E / N, (k+1) E / N) for the task terms, rows
+    // [k R / N, (k+1) R / N) for the owned dyads (the ids are arbitrary, so
+    // an even cut of the rows spreads the owners' work)
+    const auto cut = [&](int64_t total, int32_t k) {
+        return (int64_t)((unsigned __int128)(uint64_t)total * (uint64_t)k / (uint64_t)Lo.nshards);
+    };
     const BinParams bp{o.thr_thread, o.thr_warp, mlp ? 0 : o.stream_max, o.own_min, mlp, set.vtag, Lo.fwd ? 1 : 0,
-                       exact};
+                       exact, cut(Lo.entries, Lo.shard), cut(Lo.entries, Lo.shard + 1), cut(Lo.rows, Lo.shard),
+                       cut(Lo.rows, Lo.shard + 1)};
     uint4* split_tasks = (uint4*)(ws + Lo.o_rt);
     auto mark = [&](int k) {
         if (pe) cudaEventRecord(pe->ev[k], st);
@@ -2529,7 +2554,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
             const OneHotIt words(thrust::counting_iterator<int64_t>(0), OneHot{set.adj, d_seg, d_epfx, Lo.nseg});
             TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, words, scan, (int)Lo.entries, st));
             if (bp.own_min > 0) {
-                k_owner_rows<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, bp.own_min, bins);
+                k_owner_rows<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, bp.own_min, bins,
+                                                        bp.r_lo, bp.r_hi);
                 TC_CUDA(cudaGetLastError());
             }
             k_tasks_flat<<<L.sms * L.occ_flat, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, set.vtag, scan,
@@ -2634,7 +2660,7 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         for (int k = 1; k <= 7; ++k) mark(k);
     }
     mark(8);
-    k_fold<<<(Lo.nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, Lo.nseg, d_out, d_codes);
+    k_fold<<<(Lo.nseg + 127) / 128, 128, 0, st>>>(acc, d_seg, Lo.nseg, d_out, d_codes, Lo.raw);
     TC_CUDA(cudaGetLastError());
     mark(9);
     return TC_OK;
@@ -2720,13 +2746,26 @@ tc_status read_profile(const Layout& Lo, const char* ws, ProfileEvents* pe, cuda
     return TC_OK;
 }
 
+// A shard of the census (tc_census_shard): shard `shard` of `nshards`, the
+// raw accumulators of graph i written to raw[slot(i)] (device).
+struct Shard {
+    int32_t shard = 0, nshards = 1;
+    unsigned long long* raw = nullptr;
+};
+
 // One census over the graphs gidx with a resolved tri_path; with slots,
 // graph i's record goes to out[slots[i]] (device output only).
 tc_status census_part(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
                       tc_census_t* out, uint32_t flags, cudaStream_t st, const Instr* ins = nullptr,
-                      tc_census64_t* codes = nullptr, const std::vector<int32_t>* slots = nullptr) {
+                      tc_census64_t* codes = nullptr, const std::vector<int32_t>* slots = nullptr,
+                      const Shard* sh = nullptr) {
     Layout Lo;
     if (tc_status s = make_layout(set, gidx, opts_in, Lo, slots); s != TC_OK) return s;
+    if (sh) {
+        Lo.shard = sh->shard;
+        Lo.nshards = sh->nshards;
+        Lo.raw = sh->raw;
+    }
     if (set.ws_bytes < Lo.need) {
         dev_free(set.ws, st);
         set.ws = nullptr;
@@ -2784,21 +2823,22 @@ tc_status split_parts(const GraphSet& set, const std::vector<int32_t>& gidx, cud
 // the caller's order; a profiled call profiles the second).
 tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
                       tc_census_t* out, uint32_t flags, cudaStream_t st, const Instr* ins = nullptr,
-                      tc_census64_t* codes = nullptr) {
+                      tc_census64_t* codes = nullptr, const Shard* sh = nullptr) {
     if (flags & ~TC_OUT_DEVICE) return fail(TC_ERR_ARG, "census: unknown flag");
     tc_opts resolved;
     if (!opts_in) {  // the defaults (tri_path TC_TRI_AUTO)
         tc_opts_default(&resolved);
         opts_in = &resolved;
     }
-    if (opts_in->tri_path != TC_TRI_AUTO) return census_part(set, gidx, opts_in, out, flags, st, ins, codes);
+    if (opts_in->tri_path != TC_TRI_AUTO)
+        return census_part(set, gidx, opts_in, out, flags, st, ins, codes, nullptr, sh);
     Parts P;
     if (tc_status s = split_parts(set, gidx, st, P); s != TC_OK) return s;
     const bool dev = (flags & TC_OUT_DEVICE) != 0;
     const size_t G = gidx.size();
     tc_census_t* d_out = dev ? out : nullptr;
     tc_census64_t* d_codes = dev ? codes : nullptr;
-    if (!dev) {  // device staging for the records, copied back at the end
+    if (!dev && !sh) {  // device staging for the records, copied back at the end
         if (out) TC_CUDA(dev_alloc((void**)&d_out, sizeof(tc_census_t) * std::max<size_t>(G, 1), st));
         if (codes) TC_CUDA(dev_alloc((void**)&d_codes, sizeof(tc_census64_t) * std::max<size_t>(G, 1), st));
     }
@@ -2807,9 +2847,9 @@ tc_status census_impl(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         if (P.gidx[k].empty()) continue;
         tc_opts o = *opts_in;
         o.tri_path = k == 0 ? TC_TRI_FORWARD : TC_TRI_MERGE;
-        r = census_part(set, P.gidx[k], &o, d_out, TC_OUT_DEVICE, st, ins, d_codes, &P.slots[k]);
+        r = census_part(set, P.gidx[k], &o, d_out, TC_OUT_DEVICE, st, ins, d_codes, &P.slots[k], sh);
     }
-    if (!dev) {
+    if (!dev && !sh) {
         if (r == TC_OK && out)
             r = cudaMemcpyAsync(out, d_out, sizeof(tc_census_t) * G, cudaMemcpyDeviceToHost, st) == cudaSuccess
                     ? TC_OK : fail(TC_ERR_CUDA, "census: copy of the records");
@@ -2876,6 +2916,74 @@ tc_status tc_census_batched(int32_t G, const tc_graph* gs, const tc_opts* opts, 
         return tc::fail(TC_ERR_OOM, "tc_census_batched: host allocation failed");
     } catch (...) {
         return tc::fail(TC_ERR_CUDA, "tc_census_batched: unexpected exception");
+    }
+}
+
+tc_status tc_census_shard(int32_t G, const tc_graph* gs, const tc_opts* opts, int32_t shard, int32_t nshards,
+                          uint64_t* acc, void* stream) {
+    if (G < 0 || (G > 0 && (!gs || !acc)) || nshards < 1 || shard < 0 || shard >= nshards)
+        return tc::fail(TC_ERR_ARG, "tc_census_shard: bad arguments");
+    if (G == 0) return TC_OK;
+    try {
+        if (tc_status s = tc::check_handles(G, gs, "tc_census_shard"); s != TC_OK) return s;
+        tc::Shard sh;
+        sh.shard = shard;
+        sh.nshards = nshards;
+        sh.raw = (unsigned long long*)acc;
+        return tc::census_impl(*gs[0]->set, tc::handle_indices(G, gs), opts, nullptr, TC_OUT_DEVICE,
+                               (cudaStream_t)stream, nullptr, nullptr, &sh);
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_census_shard: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_census_shard: unexpected exception");
+    }
+}
+
+tc_status tc_census_fold(int32_t G, const tc_graph* gs, const uint64_t* acc, tc_census_t* out,
+                         tc_census64_t* codes, uint32_t flags, void* stream) {
+    if (G < 0 || (G > 0 && (!gs || !acc || (!out && !codes))))
+        return tc::fail(TC_ERR_ARG, "tc_census_fold: bad arguments");
+    if (flags & ~TC_OUT_DEVICE) return tc::fail(TC_ERR_ARG, "tc_census_fold: unknown flag");
+    if (G == 0) return TC_OK;
+    try {
+        if (tc_status s = tc::check_handles(G, gs, "tc_census_fold"); s != TC_OK) return s;
+        const tc::GraphSet& set = *gs[0]->set;
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<tc::SegDev> seg((size_t)G);
+        for (int32_t i = 0; i < G; ++i) {
+            const int32_t g = gs[i]->index;
+            seg[(size_t)i].rb = set.voff[(size_t)g];
+            seg[(size_t)i].n = set.voff[(size_t)g + 1] - set.voff[(size_t)g];
+            seg[(size_t)i].eb = 0;
+            seg[(size_t)i].slot = i;
+            seg[(size_t)i].pad = 0;
+        }
+        const bool dev = (flags & TC_OUT_DEVICE) != 0;
+        const size_t so = sizeof(tc_census_t) * (size_t)G, sc = sizeof(tc_census64_t) * (size_t)G;
+        const size_t bytes = sizeof(tc::SegDev) * (size_t)G + (dev ? 0 : (out ? so : 0) + (codes ? sc : 0));
+        char* buf = nullptr;
+        TC_CUDA(tc::dev_alloc((void**)&buf, bytes, st));
+        tc::SegDev* d_seg = (tc::SegDev*)buf;
+        tc_census_t* d_out = !out ? nullptr : dev ? out : (tc_census_t*)(buf + sizeof(tc::SegDev) * (size_t)G);
+        tc_census64_t* d_codes = !codes ? nullptr : dev ? codes
+                                 : (tc_census64_t*)(buf + sizeof(tc::SegDev) * (size_t)G + (out ? so : 0));
+        cudaError_t e = cudaMemcpyAsync(d_seg, seg.data(), sizeof(tc::SegDev) * (size_t)G, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            tc::k_fold<<<(G + 127) / 128, 128, 0, st>>>((const unsigned long long*)acc, d_seg, G, d_out, d_codes,
+                                                         nullptr);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && !dev && out) e = cudaMemcpyAsync(out, d_out, so, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && !dev && codes) e = cudaMemcpyAsync(codes, d_codes, sc, cudaMemcpyDeviceToHost, st);
+        // the segment table is a pageable upload: wait for it before release
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        tc::dev_free(buf, st);
+        if (e != cudaSuccess) return tc::cuda_fail(e, "tc_census_fold", __FILE__, __LINE__);
+        return TC_OK;
+    } catch (const std::bad_alloc&) {
+        return tc::fail(TC_ERR_OOM, "tc_census_fold: host allocation failed");
+    } catch (...) {
+        return tc::fail(TC_ERR_CUDA, "tc_census_fold: unexpected exception");
     }
 }
 
@@ -3016,7 +3124,7 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
     bins.own_cap = 0;
     bins.own_cnt = nullptr;
     bins.own_stat = nullptr;
-    const BinParams bp{0x7fffffff, 0x7fffffff, 0, 0, nullptr, nullptr, 0, nullptr};
+    const BinParams bp{0x7fffffff, 0x7fffffff, 0, 0, nullptr, nullptr, 0, nullptr, 0, INT64_MAX, 0, INT64_MAX};
     if (n > 0) {
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(row_ptr, adj, s->deg, &s->seg, s->pfx, 1, n, bp, bins,
                                                      s->acc, cursor);
@@ -3025,7 +3133,7 @@ tc_status census_noalloc(int32_t n, const int64_t* row_ptr, const uint32_t* adj,
                                                         bins.cap[0], s->acc);
         TC_CUDA(cudaGetLastError());
     }
-    k_fold<<<1, 128, 0, st>>>(s->acc, &s->seg, 1, out, nullptr);
+    k_fold<<<1, 128, 0, st>>>(s->acc, &s->seg, 1, out, nullptr, nullptr);
     TC_CUDA(cudaGetLastError());
     int ovf = 0;
     TC_CUDA(cudaMemcpyAsync(&ovf, s->ctr + 4, sizeof(int), cudaMemcpyDeviceToHost, st));

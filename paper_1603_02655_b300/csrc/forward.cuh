@@ -228,7 +228,8 @@ constexpr int FR_NT = 256;
 __global__ void __launch_bounds__(FR_NT) k_fwd_rows(const int64_t* __restrict__ row_ptr,
                                                     const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
                                                     const int64_t* __restrict__ pfx, const int64_t* __restrict__ epfx,
-                                                    int nseg, int64_t rows, int big_min, FwdLayout F) {
+                                                    int nseg, int64_t rows, int big_min, FwdLayout F,
+                                                    int64_t r_lo, int64_t r_hi) {
     __shared__ unsigned wsum[2][FR_NT / 32];
     __shared__ unsigned base[2];
     const unsigned full = 0xffffffffu;
@@ -242,7 +243,9 @@ __global__ void __launch_bounds__(FR_NT) k_fwd_rows(const int64_t* __restrict__ 
             const int64_t x = g.rb + (r - pfx[s]);
             const int64_t f0 = epfx[s] + (row_ptr[x] - g.eb), f1 = epfx[s] + (row_ptr[x + 1] - g.eb);
             const uint32_t a = f0 > 0 ? (uint32_t)F.fs[f0 - 1] : 0u, b = f1 > 0 ? (uint32_t)F.fs[f1 - 1] : 0u;
-            const uint32_t m = b - a, own = (uint32_t)deg[x] - m;
+            // dyads owned by r: its neighbours ranked below it (none when the
+            // row belongs to another shard)
+            const uint32_t m = b - a, own = r >= r_lo && r < r_hi ? (uint32_t)deg[x] - m : 0u;
             F.fptr[r] = a;
             if (r == rows - 1) {
                 F.fptr[rows] = b;

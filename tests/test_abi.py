@@ -66,6 +66,14 @@ def test_argument_errors_need_no_device(lib):
     assert lib.tc_graph_build_text(b"*Vertices 3\n", 12, 1, 0x80, None, ctypes.byref(h)) == tc.TC_ERR_ARG
     assert lib.tc_graph_build_text(None, 0, 1, 0, None, ctypes.byref(h)) == tc.TC_ERR_ARG  # empty file
     assert lib.tc_graph_build(5, None, None, 0, 0x80 | tc.TC_UNDIRECTED, None, ctypes.byref(h)) == tc.TC_ERR_ARG
+    assert lib.tc_census_shard(-1, None, None, 0, 1, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_shard(0, None, None, 0, 0, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_shard(0, None, None, 3, 2, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_shard(0, None, None, 1, 2, None, None) == tc.TC_OK
+    assert lib.tc_census_shard(1, None, None, 0, 1, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_fold(-1, None, None, None, None, 0, None) == tc.TC_ERR_ARG
+    assert lib.tc_census_fold(0, None, None, None, None, 0, None) == tc.TC_OK
+    assert lib.tc_census_fold(0, None, None, None, None, 0x80, None) == tc.TC_ERR_ARG
     assert lib.tc_graph_stats(None, None) == tc.TC_ERR_ARG
     assert lib.tc_opts_default(None) == tc.TC_ERR_ARG
     assert "null" in tc.tc_last_error() or tc.tc_last_error()
@@ -90,4 +98,17 @@ def test_noalloc_binding_refuses_host_or_short_tensors(lib):
                  (3, rp, adj, 6, out), (3, rp, adj, 2, out[:5])):
         with pytest.raises(tc.TcError) as e:
             tc.tc_census_csr_noalloc(*args)
+        assert e.value.status == tc.TC_ERR_ARG
+
+
+def test_shard_binding_refuses_host_or_short_accumulators(lib):
+    """The accumulator tensor is checked before the call reaches the library
+    (TC_ACC_WORDS int64 words per graph, on the device)."""
+    import torch
+    for acc in (torch.zeros(tc.TC_ACC_WORDS, dtype=torch.int64), torch.zeros(tc.TC_ACC_WORDS, dtype=torch.int32)):
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_census_shard([1], 0, 1, acc)
+        assert e.value.status == tc.TC_ERR_ARG
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_census_fold([1], acc)
         assert e.value.status == tc.TC_ERR_ARG
