@@ -169,6 +169,10 @@ def load():
     lib.tc_path_features.argtypes = [i32, P, P]
     lib.tc_path_model_load.argtypes = [P]
     lib.tc_path_route.argtypes = [i32, P, P, P]
+    lib.tc_census_shard.argtypes = [i32, P, P, i32, i32, P, P]
+    lib.tc_census_fold.argtypes = [i32, P, P, P, P, u32, P]
+    for name in ("tc_census_shard", "tc_census_fold"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("tc_path_features", "tc_path_model_load", "tc_path_route"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("tc_cost_sample", "tc_cost_features", "tc_mlp_loss_grad", "tc_mlp_train", "tc_mlp_predict",

@@ -30,8 +30,12 @@ def test_exports_every_declared_symbol(lib):
     assert len(names) >= 11
     for name in names:
         assert hasattr(lib, name), name
-    # the Python binding wraps exactly the declared entry points
+    # the Python binding wraps exactly the declared entry points, each with
+    # its argument types declared (an undeclared pointer argument would be
+    # passed as a 32-bit int)
     assert set(names) == set(tc.EXPORTS)
+    for name in names:
+        assert getattr(lib, name).argtypes is not None, name
 
 
 def test_library_table_matches_oracle_table(lib):
