@@ -2149,7 +2149,7 @@ constexpr int STREAM_EPL = 8;
 struct Launch {
     int sms = 148;
     int occ_tasks = 1, occ_thread = 1, occ_warp = 1, occ_cta = 1, occ_stream = 1, occ_merge = 1, occ_flat = 1;
-    int occ_owner = 1, occ_tri_big = 1, occ_tri_small = 1;
+    int occ_owner = 1, occ_tri_big = 1, occ_tri_small = 1, occ_tri_big_ids = 1, occ_tri_small_ids = 1;
     bool ready = false;
 };
 
@@ -2177,11 +2177,16 @@ tc_status launch_info(Launch& L) {
         TC_CUDA(cudaFuncSetAttribute(k_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OWN_SMEM));
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_owner, k_owner, OWN_NT, OWN_SMEM));
         c.occ_owner = std::max(1, c.occ_owner);
-        TC_CUDA(cudaFuncSetAttribute(k_tri_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TB_SMEM));
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_big, k_tri_big, TB_NT, TB_SMEM));
+        TC_CUDA(cudaFuncSetAttribute(k_tri_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TB_SMEM));
+        TC_CUDA(cudaFuncSetAttribute(k_tri_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TB_SMEM));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_big, k_tri_big<false>, TB_NT, TB_SMEM));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_big_ids, k_tri_big<true>, TB_NT, TB_SMEM));
         c.occ_tri_big = std::max(1, c.occ_tri_big);
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_small, k_tri_small, 256, 0));
+        c.occ_tri_big_ids = std::max(1, c.occ_tri_big_ids);
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_small, k_tri_small<false>, 256, 0));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ_tri_small_ids, k_tri_small<true>, 256, 0));
         c.occ_tri_small = std::max(1, c.occ_tri_small);
+        c.occ_tri_small_ids = std::max(1, c.occ_tri_small_ids);
         c.ready = true;
     }
     L = c;
@@ -2213,6 +2218,9 @@ struct Layout {
     // raw accumulators of each graph to raw[slot] instead of folding them
     int32_t shard = 0, nshards = 1;
     unsigned long long* raw = nullptr;
+    // triangles classified in id order (the 64-code census, shards), else in
+    // rank order (the 16-type census)
+    bool ids = false;
     // forward path (tri_path = TC_TRI_FORWARD)
     bool fwd = false;
     int nb = 0;            // blocks of the rank computation
@@ -2483,10 +2491,14 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     ta.perm = perm;
     ta.acc = acc;
     ta.stat = F.stat;
-    k_tri_big<<<L.sms * L.occ_tri_big, TB_NT, TB_SMEM, st>>>(ta);
+    // the 64-code census and shards need each triangle in id order; the
+    // 16-type census takes it in rank order
+    if (Lo.ids) k_tri_big<true><<<L.sms * L.occ_tri_big_ids, TB_NT, TB_SMEM, st>>>(ta);
+    else k_tri_big<false><<<L.sms * L.occ_tri_big, TB_NT, TB_SMEM, st>>>(ta);
     TC_CUDA(cudaGetLastError());
     mark(3);
-    k_tri_small<<<L.sms * L.occ_tri_small, 256, 0, st>>>(ta);
+    if (Lo.ids) k_tri_small<true><<<L.sms * L.occ_tri_small_ids, 256, 0, st>>>(ta);
+    else k_tri_small<false><<<L.sms * L.occ_tri_small, 256, 0, st>>>(ta);
     TC_CUDA(cudaGetLastError());
     for (int k = 4; k <= 7; ++k) mark(k);
     return TC_OK;
@@ -2766,6 +2778,7 @@ tc_status census_part(GraphSet& set, const std::vector<int32_t>& gidx, const tc_
         Lo.nshards = sh->nshards;
         Lo.raw = sh->raw;
     }
+    Lo.ids = codes != nullptr || sh != nullptr;
     if (set.ws_bytes < Lo.need) {
         dev_free(set.ws, st);
         set.ws = nullptr;

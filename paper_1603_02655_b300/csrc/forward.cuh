@@ -449,6 +449,15 @@ __global__ void k_fwd_recs(const int64_t* __restrict__ row_ptr, const uint32_t* 
 // t_ab + 16 t_bc to t_ab + 4 t_ac + 16 t_bc, and dyad <a,c> drops the count
 // t_ac + 16 t_cb it added for b.  The lookups count triangles per type; the
 // four code updates per type are applied when the counts are flushed.
+//
+// Seen by type rather than by code, the correction is symmetric in the three
+// vertices: the suffix terms counted the triad once as each of the three
+// two-edge triads (edges ab, ac; ab, bc; ac, cb: one per vertex as the
+// centre), and it is one full triangle.  So for the 16-type census any order
+// of a, b, c gives the same counts after the fold, and the lookups take them
+// in rank order (x, h, w: no id needed, tags straight from the lookup); the
+// 64-code census (and a shard, whose accumulators may be folded to codes)
+// needs the id order, which costs a gather of w's id per triangle.
 __device__ __forceinline__ int tri_type(uint32_t a, uint32_t b, uint32_t c, uint32_t t_ab, uint32_t t_ac,
                                         uint32_t t_bc) {
     uint32_t t;
@@ -647,6 +656,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // entry, length, x << 2 | t_x(h), first piece), and the warps take its
 // pieces 32 at a time from a shared cursor.  The item's records load while
 // the map changes owner.
+template <bool IDS>
 __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
     extern __shared__ __align__(16) unsigned char tb_smem[];
     uint32_t* map = reinterpret_cast<uint32_t*>(tb_smem);
@@ -800,25 +810,26 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
             const uint32_t st = has ? pof[before + lane] : 0u;
             const int d = chunk_dyad(has, st, (uint32_t)c, before, lane);
             const bool ok = c + lane < total;
-            uint32_t base = 0, cnt = 0;
+            uint32_t base = 0, cnt = 0;  // cnt: entries | t_x(h) << 8
             if (ok) {
                 const uint32_t pq = (uint32_t)(c + lane) - pof[d];
                 base = tfst[d] + PIECE * pq;
-                cnt = min((uint32_t)PIECE, tlen[d] - PIECE * pq);
+                cnt = min((uint32_t)PIECE, tlen[d] - PIECE * pq) | ((txin[d] & 3u) << 8);
             }
             // the chunk's pieces two at a time, one per half-warp (lane & 15
             // is the entry), HW_ILP pairs loaded together
             const int npc = min(32, total - c), e = lane & 15, half = lane >> 4;
             for (int u0 = 0; u0 < npc; u0 += 2 * HW_ILP) {
-                uint32_t kv[HW_ILP];
+                uint32_t kv[HW_ILP], xt[HW_ILP];
                 int dv[HW_ILP];
                 bool vv[HW_ILP];
 #pragma unroll
                 for (int u = 0; u < HW_ILP; ++u) {
                     const int src = u0 + 2 * u + half;
                     const uint32_t pb = __shfl_sync(full, base, src & 31), pc = __shfl_sync(full, cnt, src & 31);
-                    dv[u] = __shfl_sync(full, d, src & 31);
-                    vv[u] = src < npc && (uint32_t)e < pc;
+                    if (IDS) dv[u] = __shfl_sync(full, d, src & 31);
+                    vv[u] = src < npc && (uint32_t)e < (pc & 0xffu);
+                    xt[u] = pc >> 8;
                     kv[u] = vv[u] ? __ldg(a.fwd + pb + e) : 0u;
                 }
 #pragma unroll
@@ -826,18 +837,25 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
                     const uint32_t kk = (kv[u] >> 2) - Rh1;  // ranks at or below h fall outside the map
                     const uint32_t th =
                         vv[u] && kk < (uint32_t)MAP_KEYS ? (map[kk >> 4] >> (2 * (kk & 15u))) & 3u : 0u;
-                    enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
-                    if (qn >= 32)
-                        drain(H, P, q, qh, qn, 32, [&](int dq) { return txin[dq]; }, [&](int) { return hl; },
-                              a.perm, p0, ns, hits);
+                    if (IDS) {
+                        enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
+                        if (qn >= 32)
+                            drain(H, P, q, qh, qn, 32, [&](int dq) { return txin[dq]; }, [&](int) { return hl; },
+                                  a.perm, p0, ns, hits);
+                    } else {  // rank order x < h < w: the type from the three tags
+                        hits += th != 0 ? 1u : 0u;
+                        H.add(th != 0, (int)(9 * xt[u] + 3 * (kv[u] & 3u) + th) - 13);
+                    }
                 }
             }
-            looked += cnt;
+            looked += cnt & 0xffu;
         }
-        if (qn > 0)  // the table changes next
-            drain(H, P, q, qh, qn, qn, [&](int dq) { return txin[dq]; }, [&](int) { return hl; }, a.perm, p0, ns,
-                  hits);
-        finish(H, P, hits);
+        if (IDS) {
+            if (qn > 0)  // the table changes next
+                drain(H, P, q, qh, qn, qn, [&](int dq) { return txin[dq]; }, [&](int) { return hl; }, a.perm, p0,
+                      ns, hits);
+            finish(H, P, hits);
+        }
         const unsigned wh = __reduce_add_sync(full, hits);
         H.pending += wh;
         tri += wh;
@@ -866,6 +884,7 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
 // in cache).
 constexpr int TS_RUN = 1024;
 
+template <bool IDS>
 __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
     __shared__ uint32_t hs_all[8][64];
     __shared__ uint2 q_all[8][TQN];
@@ -935,19 +954,19 @@ __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
                 const int dd = ok ? d : 0;
                 const uint32_t d_fst = __shfl_sync(full, fst, dd), d_len = __shfl_sync(full, len, dd);
                 const uint32_t d_off = __shfl_sync(full, poff, dd);
-                const uint32_t h_b = __shfl_sync(full, hb, dd), h_n = __shfl_sync(full, hn, dd);
-                uint32_t cnt = 0, base = 0;
+                const uint32_t d_xin = __shfl_sync(full, xin, dd);
+                uint32_t cnt = 0, base = 0;  // cnt: entries | t_x(h) << 8
                 if (ok) {
                     const uint32_t pq = c + lane - d_off;
                     base = d_fst + PIECE * pq;
-                    cnt = min((uint32_t)PIECE, d_len - PIECE * pq);
+                    cnt = min((uint32_t)PIECE, d_len - PIECE * pq) | ((d_xin & 3u) << 8);
                 }
                 // the chunk's pieces two at a time, one per half-warp (lane & 15
                 // is the entry): each lane searches its key in the piece's
                 // owner list, HW_ILP pairs in lockstep
                 const int npc = (int)min(32u, total - c), e = lane & 15, half = lane >> 4;
                 for (int t0 = 0; t0 < npc; t0 += 2 * HW_ILP) {
-                    uint32_t kv[HW_ILP], ob[HW_ILP], on[HW_ILP], pos[HW_ILP];
+                    uint32_t kv[HW_ILP], ob[HW_ILP], on[HW_ILP], pos[HW_ILP], xt[HW_ILP];
                     int dv[HW_ILP];
                     bool vv[HW_ILP];
                     uint32_t maxn = 0;
@@ -959,7 +978,8 @@ __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
                         const int od = dv[u] < 0 ? 0 : dv[u];
                         ob[u] = __shfl_sync(full, hb, od & 31);
                         on[u] = __shfl_sync(full, hn, od & 31);
-                        vv[u] = src < npc && (uint32_t)e < pc;
+                        vv[u] = src < npc && (uint32_t)e < (pc & 0xffu);
+                        xt[u] = pc >> 8;
                         kv[u] = vv[u] ? __ldg(a.fwd + pb + e) : 0u;
                         if (!vv[u]) on[u] = 0;
                         pos[u] = 0;
@@ -980,18 +1000,25 @@ __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
                             const uint32_t w = __ldg(a.fwd + ob[u] + pos[u]);
                             if ((w & ~3u) == (kv[u] & ~3u)) th = w & 3u;
                         }
-                        enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
-                        if (qn >= 32)
-                            drain(H, P, q, qh, qn, 32, [&](int dq) { return __shfl_sync(full, xin, dq); },
-                                  [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
+                        if (IDS) {
+                            enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
+                            if (qn >= 32)
+                                drain(H, P, q, qh, qn, 32, [&](int dq) { return __shfl_sync(full, xin, dq); },
+                                      [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
+                        } else {  // rank order x < h < w: the type from the three tags
+                            hits += th != 0 ? 1u : 0u;
+                            H.add(th != 0, (int)(9 * xt[u] + 3 * (kv[u] & 3u) + th) - 13);
+                        }
                     }
                 }
-                looked += cnt;
+                looked += cnt & 0xffu;
             }
-            if (qn > 0)  // the group changes next
-                drain(H, P, q, qh, qn, qn, [&](int dq) { return __shfl_sync(full, xin, dq); },
-                      [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
-            finish(H, P, hits);
+            if (IDS) {
+                if (qn > 0)  // the group changes next
+                    drain(H, P, q, qh, qn, qn, [&](int dq) { return __shfl_sync(full, xin, dq); },
+                          [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
+                finish(H, P, hits);
+            }
             const unsigned wh = __reduce_add_sync(full, hits);
             H.pending += wh;
             tri += wh;

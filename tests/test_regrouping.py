@@ -110,3 +110,68 @@ def test_dyadic_codes_from_degree_sums_and_closed_codes(seed, n, p):
     for q in (1, 2, 3):
         assert closed[q] == cuv[q], q
         assert codes[q] == dsum[q] + cuv[q], q
+
+
+def rank_order_regrouped(tag, nb, n, pos):
+    """Suffix terms in id order, but each triangle's correction taken with
+    its vertices in the order `pos` (a < b < c by pos, as the forward path's
+    degree ranks): the corrections of the three two-edge triads and the full
+    triangle, labelled in that order."""
+    got = [0] * 64
+    for u in range(n):
+        for v in nb[u]:
+            if v <= u:
+                continue
+            pre = tag(u, v)
+            for w in nb[u]:
+                if w > v:
+                    got[pre + 4 * tag(u, w)] += 1
+            for w in nb[v]:
+                if w > u and w != v:
+                    got[pre + 16 * tag(v, w)] += 1
+    for u in range(n):
+        for v in nb[u]:
+            for w in nb[v]:
+                if not (u < v < w) or w not in nb[u]:
+                    continue
+                a, b, c = sorted((u, v, w), key=lambda x: pos[x])
+                t_ab, t_ac, t_bc = tag(a, b), tag(a, c), tag(b, c)
+                got[t_ab + 4 * t_ac] -= 1
+                got[t_ab + 16 * t_bc] -= 1
+                got[t_ab + 4 * t_ac + 16 * t_bc] += 1
+                got[t_ac + 16 * swap(t_bc)] -= 1
+    return got
+
+
+def fold16(codes):
+    T = oracle.triad_table()
+    out = [0] * 16
+    for c in range(1, 64):
+        out[T[c]] += codes[c]
+    return out
+
+
+@pytest.mark.parametrize("seed,n,p", CASES)
+def test_triangle_corrections_in_any_vertex_order_give_the_same_types(seed, n, p):
+    """By type the correction is symmetric in the triangle's vertices (the
+    suffix terms counted it once as each vertex's two-edge triad), so the
+    16-type census does not depend on the order the triangles are classified
+    in; the 64 labelled codes do, which is why the code census keeps id
+    order."""
+    tag, nb, _, _ = digraph(seed, n, p)
+    want = fold16(defined(tag, nb, n))
+    rng = np.random.default_rng(seed)
+    differ = False
+    for _ in range(3):
+        pos = rng.permutation(n)
+        got = rank_order_regrouped(tag, nb, n, pos)
+        assert fold16(got) == want
+        differ |= got != defined(tag, nb, n)
+    deg = [len(nb[x]) for x in range(n)]
+    degree_rank = sorted(range(n), key=lambda x: (int(np.log2(deg[x])) if deg[x] else 0, x))
+    pos = [0] * n
+    for r, x in enumerate(degree_rank):
+        pos[x] = r
+    assert fold16(rank_order_regrouped(tag, nb, n, pos)) == want
+    if seed == 4:
+        assert differ  # the labelled codes move with the order
