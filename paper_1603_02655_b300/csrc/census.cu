@@ -2228,7 +2228,8 @@ struct Layout {
     uint32_t item_cap = 0;
     size_t fscan_bytes = 0;
     size_t o_hist, o_hex, o_co, o_rank, o_perm, o_flag, o_fs, o_fptr, o_kind, o_tcnt, o_tpre, o_longs,
-        o_fid, o_fwd, o_trec, o_items, o_fscantmp;
+        o_fid, o_fwd, o_trec, o_items, o_fscantmp, o_tp, o_tpc;
+    uint32_t piece_cap = 0;  // pieces of the longer rows in the row-wise task pass
 };
 
 // counters (uint32 words): [0..3] records per bin, [4] overflow flag,
@@ -2240,7 +2241,7 @@ struct Layout {
 // smaller), 32-39 owner tasks, merged entries, probes, staged entries.
 // Forward path: 40 tag-map items, 41 long rows, 42-43 work cursors, 44-51
 // lookups and triangles of each lookup form (u64), 52-53 forward-list
-// entries the tag-map items stage (u64).
+// entries the tag-map items stage (u64), 54 pieces of the row-wise task pass.
 constexpr int CTR_WORDS = 64;
 
 tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, const tc_opts* opts_in,
@@ -2336,7 +2337,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         TC_CUDA(cub::DeviceScan::InclusiveSum(
             nullptr, Lo.scan_bytes, OneHotIt(thrust::counting_iterator<int64_t>(0), OneHot{nullptr, nullptr, nullptr, 1}),
             (unsigned long long*)nullptr, (int)Lo.entries, (cudaStream_t)0));
-    Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat ? (size_t)Lo.entries : 1));
+    Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat && !Lo.fwd ? (size_t)Lo.entries : 1));
     Lo.o_scantmp = take(std::max<size_t>(Lo.scan_bytes, 16));
     // forward lists: ranks, forward entries, dyad records by owner
     if (Lo.fwd) {
@@ -2368,6 +2369,9 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         Lo.o_trec = take(sizeof(uint4) * D);
         Lo.o_items = take(sizeof(uint4) * 2 * (size_t)Lo.item_cap);
         Lo.o_fscantmp = take(std::max<size_t>(Lo.fscan_bytes, 16));
+        Lo.piece_cap = (uint32_t)std::min<int64_t>(Lo.rows + Lo.entries / TR_PIECE + 1, 0xffffffffll);
+        Lo.o_tp = take(sizeof(uint4) * (size_t)Lo.piece_cap);
+        Lo.o_tpc = take(sizeof(uint4) * (size_t)Lo.piece_cap);
     }
     Lo.need = off;
     return TC_OK;
@@ -2418,14 +2422,30 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
                                           bins.overflow);
     TC_CUDA(cudaGetLastError());
     // the task pass, with the forward flags
-    if (Lo.flat) {
-        unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
-        size_t sb = Lo.scan_bytes;
-        const OneHotIt words(thrust::counting_iterator<int64_t>(0), OneHot{set.adj, d_seg, d_epfx, Lo.nseg});
-        TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, words, scan, (int)Lo.entries, st));
-        k_tasks_flat<<<L.sms * L.occ_flat, 256, 0, st>>>(set.row_ptr, set.adj, set.arow, set.deg, set.vtag, scan,
-                                                         d_seg, d_epfx, Lo.nseg, Lo.entries, bp, bins, acc, cursor,
-                                                         FlagOut{flag, rank, d_pfx});
+    if (Lo.flat) {  // row-wise: a thread per short row, a warp per piece of a longer one
+        TermArgs ta;
+        ta.row_ptr = set.row_ptr;
+        ta.adj = set.adj;
+        ta.deg = set.deg;
+        ta.seg = d_seg;
+        ta.pfx = d_pfx;
+        ta.epfx = d_epfx;
+        ta.nseg = Lo.nseg;
+        ta.rows = Lo.rows;
+        ta.r_lo = bp.r_lo;
+        ta.r_hi = bp.r_hi;
+        ta.rank = rank;
+        ta.flag = flag;
+        ta.acc = acc;
+        ta.pieces = (uint4*)(ws + Lo.o_tp);
+        ta.npieces = ctr + 54;
+        ta.piece_cap = Lo.piece_cap;
+        ta.pcnt = (uint4*)(ws + Lo.o_tpc);
+        k_terms_rows<<<L.sms * 8, 256, 0, st>>>(ta);
+        TC_CUDA(cudaGetLastError());
+        k_piece_counts<<<L.sms * 4, 256, 0, st>>>(ta);
+        TC_CUDA(cudaGetLastError());
+        k_terms_pieces<<<L.sms * 8, 256, 0, st>>>(ta);
     } else {
         k_tasks<<<L.sms * L.occ_tasks, 256, 0, st>>>(set.row_ptr, set.adj, set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows,
                                                      bp, bins, acc, cursor);
@@ -2681,9 +2701,9 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
 // Kernels of this library a census launches (the library scans not counted).
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
-    // 3 rank kernels, the task pass (+ k_fwd_flags after k_tasks), 6
-    // forward-list kernels, 2 lookup kernels, k_fold
-    if (Lo.fwd) return Lo.flat ? 13 : 14;
+    // 3 rank kernels, the task pass (3 row-wise kernels, or k_tasks +
+    // k_fwd_flags), 6 forward-list kernels, 2 lookup kernels, k_fold
+    if (Lo.fwd) return Lo.flat ? 15 : 14;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
     const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 2 : 1) : 1;  // k_owner_rows, k_tasks_flat
     return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0) + (Lo.exact ? 1 : 0);

@@ -173,6 +173,259 @@ __global__ void k_fwd_flags(const uint32_t* __restrict__ adj, const int32_t* __r
     }
 }
 
+// ------------------------------------------------------ row-wise terms --
+// The forward path's task pass, row by row instead of entry by entry (no
+// global scan of tag words).  In row x (sorted by neighbour id) every pair of
+// entries i < j counts once: when y_i lies above x (the dyad <x, y_i>) as code
+// t_i + 4 t_j (an entry of row u after v), when y_i lies below x (the dyad
+// <y_i, x>) as code swap(t_i) + 16 t_j (an entry of row v after u).  And each
+// entry adds, to the dyadic sum of its dyad's pre value (t_i above x,
+// swap(t_i) below), n when it lies above x and -d_x always: summed over both
+// entries of a dyad <u, v> that is n - d_u - d_v.  (The same terms k_tasks
+// adds per canonical dyad, Sec. 2.2 regrouped.)  Each entry also gets its
+// forward flag.  Rows of at most TR_SHORT entries are done by one thread;
+// longer rows are cut into pieces of TR_PIECE entries, one warp each
+// (k_terms_pieces), the counts of later pieces of the same row carried in
+// (k_piece_counts).
+constexpr int TR_SHORT = 32;
+constexpr int TR_PIECE = 2048;
+constexpr int TR_RUN = 8;  // 32-row groups a warp takes at a time
+
+// Per-thread term sums for one graph: A[p][q], B[p][q] (pairs, p, q = tag - 1;
+// 32-bit, flushed before they could wrap) and D[p] (dyadic), added to the
+// graph's accumulators by flush().
+struct TermSums {
+    uint32_t A[3][3], B[3][3];
+    unsigned long long D[3];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A[p][q] = B[p][q] = 0;
+            D[p] = 0;
+        }
+    }
+    // one entry of tag t (1..3) with c[q] entries of tag q + 1 after it in its row
+    __device__ __forceinline__ void add(bool on, bool up, uint32_t t, const uint32_t c[3], unsigned long long dy) {
+        const uint32_t pa = up ? t : tag_swap(t);  // the dyad's pre value
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const bool ia = on && up && t == (uint32_t)(p + 1), ib = on && !up && pa == (uint32_t)(p + 1);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                A[p][q] += ia ? c[q] : 0u;
+                B[p][q] += ib ? c[q] : 0u;
+            }
+            D[p] += (on && pa == (uint32_t)(p + 1)) ? dy : 0ull;
+        }
+    }
+    // warp sums into graph s's accumulators (lane 0 adds)
+    __device__ __forceinline__ void flush(unsigned long long* acc, int s, int lane) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const unsigned long long a = warp_sum64(A[p][q]), b = warp_sum64(B[p][q]);  // (widened)
+                if (lane == 0 && s >= 0) {
+                    if (a) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 4 * (q + 1), a);
+                    if (b) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 16 * (q + 1), b);
+                }
+            }
+            const unsigned long long dd = warp_sum64(D[p]);
+            if (lane == 0 && s >= 0 && dd) atomicAdd(acc + (size_t)s * ACC + 64 + p, dd);
+        }
+        zero();
+    }
+    // one lane's sums straight into graph s's accumulators
+    __device__ __forceinline__ void add_direct(unsigned long long* acc, int s) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (A[p][q]) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 4 * (q + 1), (unsigned long long)A[p][q]);
+                if (B[p][q]) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 16 * (q + 1), (unsigned long long)B[p][q]);
+            }
+            if (D[p]) atomicAdd(acc + (size_t)s * ACC + 64 + p, D[p]);
+        }
+        zero();
+    }
+};
+
+struct TermArgs {
+    const int64_t* row_ptr;
+    const uint32_t* adj;
+    const int32_t* deg;
+    const SegDev* seg;
+    const int64_t* pfx;
+    const int64_t* epfx;
+    int nseg;
+    int64_t rows;
+    int64_t r_lo, r_hi;   // the rows whose terms this call adds (a shard), all flags regardless
+    const int32_t* rank;  // per selected row
+    uint8_t* flag;        // [entries] forward flags
+    unsigned long long* acc;
+    uint4* pieces;        // {row, piece, pieces of the row, 0} of the longer rows
+    unsigned* npieces;
+    uint32_t piece_cap;
+    uint4* pcnt;          // [piece_cap] tag counts of the pieces of rows of several pieces
+};
+
+// One thread per row of at most TR_SHORT entries (warps take TR_RUN groups
+// of 32 consecutive rows); longer rows are listed as pieces.
+__global__ void __launch_bounds__(256) k_terms_rows(TermArgs a) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    TermSums T;
+    T.zero();
+    int cur = -1;  // the graph of the warp's sums
+    unsigned groups = 0;  // 32-row groups since the last flush (a lane adds < 2^9 per group)
+    for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 * TR_RUN; g0 < a.rows;
+         g0 += warps * 32 * TR_RUN) {
+        for (int it = 0; it < TR_RUN; ++it) {
+            const int64_t r = g0 + 32 * it + lane;
+            const bool valid = r < a.rows;
+            const int s = valid ? row_seg(a.pfx, a.nseg, r) : -1;
+            const int s0 = __shfl_sync(full, s, 0);
+            if (s0 < 0) break;
+            // rows of two graphs in one group: each lane adds its own row's
+            // terms to its graph directly (after the warp's sums are flushed)
+            const bool mixed = __any_sync(full, valid && s != s0);
+            if (s0 != cur || mixed || ++groups >= (1u << 20)) {
+                T.flush(a.acc, cur, lane);
+                cur = s0;
+                groups = 0;
+            }
+            unsigned np = 0;
+            if (valid) {
+                const SegDev& g = a.seg[s];
+                const int64_t p0 = a.pfx[s], xl = r - p0, x = g.rb + xl;
+                const int64_t beg = a.row_ptr[x];
+                const int d = (int)(a.row_ptr[x + 1] - beg);
+                if (d > TR_SHORT) {
+                    np = (unsigned)((d + TR_PIECE - 1) / TR_PIECE);
+                } else if (d > 0) {
+                    const int32_t R = a.rank[r];
+                    const int64_t f0 = a.epfx[s] + (beg - g.eb);
+                    const bool terms = r >= a.r_lo && r < a.r_hi;
+                    const unsigned long long n = (unsigned long long)g.n, dx = (unsigned long long)d;
+                    uint32_t c[3] = {0, 0, 0};
+                    for (int k = d - 1; k >= 0; --k) {
+                        const uint32_t e = __ldg(a.adj + beg + k), y = e >> 2, t = e & 3u;
+                        a.flag[f0 + k] = a.rank[p0 + y] > R ? 1 : 0;
+                        const bool up = (int64_t)y > xl;
+                        T.add(terms, up, t, c, (up ? n : 0ull) - dx);
+                        c[0] += t == 1u;
+                        c[1] += t == 2u;
+                        c[2] += t == 3u;
+                    }
+                }
+                if (mixed) T.add_direct(a.acc, s);
+            }
+            // the pieces of the longer rows: one atomic per warp
+            unsigned incl = np;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned tot = __shfl_sync(full, incl, 31);
+            unsigned at = 0;
+            if (lane == 31 && tot) at = atomicAdd(a.npieces, tot);
+            at = __shfl_sync(full, at, 31) + incl - np;
+            for (unsigned q = 0; q < np; ++q)
+                if (at + q < a.piece_cap) a.pieces[at + q] = make_uint4((uint32_t)r, q, np, 0u);
+        }
+    }
+    T.flush(a.acc, cur, lane);
+}
+
+// Tag counts of every piece of a row of several pieces (one warp per piece).
+__global__ void __launch_bounds__(256) k_piece_counts(TermArgs a) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const uint32_t np_all = min(*a.npieces, a.piece_cap);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < np_all; w += warps) {
+        const uint4 pc = a.pieces[w];
+        if (pc.z < 2) continue;
+        const int64_t r = pc.x;
+        const int s = row_seg(a.pfx, a.nseg, r);
+        const int64_t x = a.seg[s].rb + (r - a.pfx[s]);
+        const int64_t beg = a.row_ptr[x];
+        const int d = (int)(a.row_ptr[x + 1] - beg);
+        const int k0 = (int)pc.y * TR_PIECE, k1 = min(d, k0 + TR_PIECE);
+        uint32_t c1 = 0, c2 = 0, c3 = 0;
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const uint32_t t = __ldg(a.adj + beg + k) & 3u;
+            c1 += t == 1u;
+            c2 += t == 2u;
+            c3 += t == 3u;
+        }
+        c1 = __reduce_add_sync(full, c1);
+        c2 = __reduce_add_sync(full, c2);
+        c3 = __reduce_add_sync(full, c3);
+        if (lane == 0) a.pcnt[w] = make_uint4(c1, c2, c3, 0u);
+    }
+}
+
+// One warp per piece of a longer row: 32 entries at a time from the piece's
+// end, the counts after each entry from ballots plus those carried from the
+// later entries (and the later pieces of the row).
+__global__ void __launch_bounds__(256) k_terms_pieces(TermArgs a) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned after = ~((2u << lane) - 1u);  // lanes above this one
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const uint32_t np_all = min(*a.npieces, a.piece_cap);
+    TermSums T;
+    T.zero();
+    int cur = -1;
+    unsigned since = 0;  // pieces since the last flush (a lane adds < 64 * 2^21 per piece)
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < np_all; w += warps) {
+        const uint4 pc = a.pieces[w];
+        const int64_t r = pc.x;
+        const int s = row_seg(a.pfx, a.nseg, r);
+        if (s != cur || ++since >= 16) {
+            T.flush(a.acc, cur, lane);
+            cur = s;
+            since = 0;
+        }
+        const SegDev& g = a.seg[s];
+        const int64_t p0 = a.pfx[s], xl = r - p0, x = g.rb + xl;
+        const int64_t beg = a.row_ptr[x];
+        const int d = (int)(a.row_ptr[x + 1] - beg);
+        const int k0 = (int)pc.y * TR_PIECE, k1 = min(d, k0 + TR_PIECE);
+        const int32_t R = a.rank[r];
+        const int64_t f0 = a.epfx[s] + (beg - g.eb);
+        const bool terms = r >= a.r_lo && r < a.r_hi;
+        const unsigned long long n = (unsigned long long)g.n, dx = (unsigned long long)d;
+        uint32_t cc[3] = {0, 0, 0};  // entries of each tag after the current chunk
+        for (uint32_t q = pc.y + 1; q < pc.z; ++q) {  // the row's later pieces
+            const uint4 c = a.pcnt[w - pc.y + q];
+            cc[0] += c.x;
+            cc[1] += c.y;
+            cc[2] += c.z;
+        }
+        for (int c0 = k0 + ((k1 - k0 - 1) & ~31); c0 >= k0; c0 -= 32) {
+            const int k = c0 + lane;
+            const bool valid = k < k1;
+            const uint32_t e = valid ? __ldg(a.adj + beg + k) : 0u, y = e >> 2, t = e & 3u;
+            if (valid) a.flag[f0 + k] = a.rank[p0 + y] > R ? 1 : 0;
+            const unsigned m1 = __ballot_sync(full, valid && t == 1u), m2 = __ballot_sync(full, valid && t == 2u),
+                           m3 = __ballot_sync(full, valid && t == 3u);
+            const uint32_t c[3] = {cc[0] + __popc(m1 & after), cc[1] + __popc(m2 & after),
+                                   cc[2] + __popc(m3 & after)};
+            const bool up = (int64_t)y > xl;
+            T.add(terms && valid, up, t, c, (up ? n : 0ull) - dx);
+            cc[0] += __popc(m1);
+            cc[1] += __popc(m2);
+            cc[2] += __popc(m3);
+        }
+    }
+    T.flush(a.acc, cur, lane);
+}
+
 // The flags read as int for the scan that places the forward entries.
 struct U8ToInt {
     __host__ __device__ int operator()(uint8_t v) const { return (int)v; }
