@@ -2370,7 +2370,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         Lo.o_items = take(sizeof(uint4) * 2 * (size_t)Lo.item_cap);
         Lo.o_fscantmp = take(std::max<size_t>(Lo.fscan_bytes, 16));
         Lo.piece_cap = (uint32_t)std::min<int64_t>(Lo.rows + Lo.entries / TR_PIECE + 1, 0xffffffffll);
-        Lo.o_tp = take(sizeof(uint4) * (size_t)Lo.piece_cap);
+        Lo.o_tp = take(sizeof(uint4) * 3 * (size_t)Lo.piece_cap);
         Lo.o_tpc = take(sizeof(uint4) * (size_t)Lo.piece_cap);
     }
     Lo.need = off;
@@ -2426,7 +2426,6 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
         TermArgs ta;
         ta.row_ptr = set.row_ptr;
         ta.adj = set.adj;
-        ta.deg = set.deg;
         ta.seg = d_seg;
         ta.pfx = d_pfx;
         ta.epfx = d_epfx;

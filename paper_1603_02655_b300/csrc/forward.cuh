@@ -189,72 +189,74 @@ __global__ void k_fwd_flags(const uint32_t* __restrict__ adj, const int32_t* __r
 // (k_piece_counts).
 constexpr int TR_SHORT = 32;
 constexpr int TR_PIECE = 2048;
+constexpr int TR_ILP = 4;  // chunks of 32 entries a piece's warp has in flight
 constexpr int TR_RUN = 8;  // 32-row groups a warp takes at a time
 
-// Per-thread term sums for one graph: A[p][q], B[p][q] (pairs, p, q = tag - 1;
-// 32-bit, flushed before they could wrap) and D[p] (dyadic), added to the
-// graph's accumulators by flush().
+// Per-thread term sums for one graph: the pair counts A[p][q], B[p][q]
+// (p, q = tag - 1) in 32-bit counters in shared memory, [18][32] per warp
+// (word (pair * 32 + lane): no bank conflicts), flushed before they could
+// wrap; the dyadic sums D[p] in registers.  flush() adds the warp's sums to
+// the graph's accumulators.
 struct TermSums {
-    uint32_t A[3][3], B[3][3];
+    uint32_t* sm;  // this warp's [18][32] counters
+    int lane;
     unsigned long long D[3];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) A[p][q] = B[p][q] = 0;
-            D[p] = 0;
-        }
+        for (int i = 0; i < 18; ++i) sm[i * 32 + lane] = 0;
+        D[0] = D[1] = D[2] = 0;
     }
     // one entry of tag t (1..3) with c[q] entries of tag q + 1 after it in its row
     __device__ __forceinline__ void add(bool on, bool up, uint32_t t, const uint32_t c[3], unsigned long long dy) {
         const uint32_t pa = up ? t : tag_swap(t);  // the dyad's pre value
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            const bool ia = on && up && t == (uint32_t)(p + 1), ib = on && !up && pa == (uint32_t)(p + 1);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                A[p][q] += ia ? c[q] : 0u;
-                B[p][q] += ib ? c[q] : 0u;
-            }
-            D[p] += (on && pa == (uint32_t)(p + 1)) ? dy : 0ull;
+        if (on) {
+            uint32_t* b = sm + ((up ? 0u : 9u) + 3u * (pa - 1u)) * 32u + lane;
+            b[0] += c[0];
+            b[32] += c[1];
+            b[64] += c[2];
         }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) D[p] += (on && pa == (uint32_t)(p + 1)) ? dy : 0ull;
     }
     // warp sums into graph s's accumulators (lane 0 adds)
-    __device__ __forceinline__ void flush(unsigned long long* acc, int s, int lane) {
+    __device__ __forceinline__ void flush(unsigned long long* acc, int s) {
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 18; ++i) {
+            const unsigned long long v = warp_sum64(sm[i * 32 + lane]);
+            const int p = (i % 9) / 3, q = i % 3;
+            if (lane == 0 && s >= 0 && v)
+                atomicAdd(acc + (size_t)s * ACC + (p + 1) + (i < 9 ? 4 : 16) * (q + 1), v);
+        }
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const unsigned long long a = warp_sum64(A[p][q]), b = warp_sum64(B[p][q]);  // (widened)
-                if (lane == 0 && s >= 0) {
-                    if (a) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 4 * (q + 1), a);
-                    if (b) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 16 * (q + 1), b);
-                }
-            }
             const unsigned long long dd = warp_sum64(D[p]);
             if (lane == 0 && s >= 0 && dd) atomicAdd(acc + (size_t)s * ACC + 64 + p, dd);
         }
+        __syncwarp();
         zero();
+        __syncwarp();
     }
     // one lane's sums straight into graph s's accumulators
     __device__ __forceinline__ void add_direct(unsigned long long* acc, int s) {
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (A[p][q]) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 4 * (q + 1), (unsigned long long)A[p][q]);
-                if (B[p][q]) atomicAdd(acc + (size_t)s * ACC + (p + 1) + 16 * (q + 1), (unsigned long long)B[p][q]);
-            }
-            if (D[p]) atomicAdd(acc + (size_t)s * ACC + 64 + p, D[p]);
+        for (int i = 0; i < 18; ++i) {
+            const uint32_t v = sm[i * 32 + lane];
+            const int p = (i % 9) / 3, q = i % 3;
+            if (v) atomicAdd(acc + (size_t)s * ACC + (p + 1) + (i < 9 ? 4 : 16) * (q + 1), (unsigned long long)v);
+            sm[i * 32 + lane] = 0;
         }
-        zero();
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            if (D[p]) atomicAdd(acc + (size_t)s * ACC + 64 + p, D[p]);
+            D[p] = 0;
+        }
     }
 };
 
 struct TermArgs {
     const int64_t* row_ptr;
     const uint32_t* adj;
-    const int32_t* deg;
     const SegDev* seg;
     const int64_t* pfx;
     const int64_t* epfx;
@@ -264,22 +266,59 @@ struct TermArgs {
     const int32_t* rank;  // per selected row
     uint8_t* flag;        // [entries] forward flags
     unsigned long long* acc;
-    uint4* pieces;        // {row, piece, pieces of the row, 0} of the longer rows
+    uint4* pieces;        // [3 * piece_cap] piece records of the longer rows (Piece)
     unsigned* npieces;
     uint32_t piece_cap;
     uint4* pcnt;          // [piece_cap] tag counts of the pieces of rows of several pieces
 };
 
+// A piece of a longer row, everything its warp needs: the row's first
+// adjacency entry and first selection entry, the graph's first selected
+// row, the row's length and rank, the row, the piece and the row's pieces,
+// the graph.
+struct Piece {
+    int64_t beg, f0, p0;
+    int32_t d, R;
+    uint32_t r, k, np;
+    int32_t s;
+};
+
+__device__ __forceinline__ void put_piece(uint4* q, const Piece& P) {
+    q[0] = make_uint4((uint32_t)P.beg, (uint32_t)((uint64_t)P.beg >> 32), (uint32_t)P.f0,
+                      (uint32_t)((uint64_t)P.f0 >> 32));
+    q[1] = make_uint4((uint32_t)P.p0, (uint32_t)((uint64_t)P.p0 >> 32), (uint32_t)P.d, (uint32_t)P.R);
+    q[2] = make_uint4(P.r, P.k, P.np, (uint32_t)P.s);
+}
+
+__device__ __forceinline__ Piece get_piece(const uint4& a, const uint4& b, const uint4& c) {
+    Piece P;
+    P.beg = (int64_t)(((uint64_t)a.y << 32) | a.x);
+    P.f0 = (int64_t)(((uint64_t)a.w << 32) | a.z);
+    P.p0 = (int64_t)(((uint64_t)b.y << 32) | b.x);
+    P.d = (int32_t)b.z;
+    P.R = (int32_t)b.w;
+    P.r = c.x;
+    P.k = c.y;
+    P.np = c.z;
+    P.s = (int32_t)c.w;
+    return P;
+}
+
 // One thread per row of at most TR_SHORT entries (warps take TR_RUN groups
-// of 32 consecutive rows); longer rows are listed as pieces.
-__global__ void __launch_bounds__(256) k_terms_rows(TermArgs a) {
+// of 32 consecutive rows), in batches of 16 entries from the row's end, each
+// batch's loads issued before its entries are counted; longer rows are
+// listed as pieces.
+__global__ void __launch_bounds__(256, 3) k_terms_rows(TermArgs a) {
+    __shared__ uint32_t tsm[8][18 * 32];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     TermSums T;
+    T.sm = tsm[threadIdx.x >> 5];
+    T.lane = lane;
     T.zero();
     int cur = -1;  // the graph of the warp's sums
-    unsigned groups = 0;  // 32-row groups since the last flush (a lane adds < 2^9 per group)
+    unsigned groups = 0;  // 32-row groups since the last flush (a lane adds < 2^10 per group)
     for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 * TR_RUN; g0 < a.rows;
          g0 += warps * 32 * TR_RUN) {
         for (int it = 0; it < TR_RUN; ++it) {
@@ -292,32 +331,52 @@ __global__ void __launch_bounds__(256) k_terms_rows(TermArgs a) {
             // terms to its graph directly (after the warp's sums are flushed)
             const bool mixed = __any_sync(full, valid && s != s0);
             if (s0 != cur || mixed || ++groups >= (1u << 20)) {
-                T.flush(a.acc, cur, lane);
+                T.flush(a.acc, cur);
                 cur = s0;
                 groups = 0;
             }
             unsigned np = 0;
+            Piece P;
             if (valid) {
                 const SegDev& g = a.seg[s];
                 const int64_t p0 = a.pfx[s], xl = r - p0, x = g.rb + xl;
                 const int64_t beg = a.row_ptr[x];
                 const int d = (int)(a.row_ptr[x + 1] - beg);
+                const int32_t R = a.rank[r];
+                const int64_t f0 = a.epfx[s] + (beg - g.eb);
                 if (d > TR_SHORT) {
                     np = (unsigned)((d + TR_PIECE - 1) / TR_PIECE);
+                    P.beg = beg;
+                    P.f0 = f0;
+                    P.p0 = p0;
+                    P.d = d;
+                    P.R = R;
+                    P.r = (uint32_t)r;
+                    P.np = np;
+                    P.s = s;
                 } else if (d > 0) {
-                    const int32_t R = a.rank[r];
-                    const int64_t f0 = a.epfx[s] + (beg - g.eb);
                     const bool terms = r >= a.r_lo && r < a.r_hi;
                     const unsigned long long n = (unsigned long long)g.n, dx = (unsigned long long)d;
                     uint32_t c[3] = {0, 0, 0};
-                    for (int k = d - 1; k >= 0; --k) {
-                        const uint32_t e = __ldg(a.adj + beg + k), y = e >> 2, t = e & 3u;
-                        a.flag[f0 + k] = a.rank[p0 + y] > R ? 1 : 0;
-                        const bool up = (int64_t)y > xl;
-                        T.add(terms, up, t, c, (up ? n : 0ull) - dx);
-                        c[0] += t == 1u;
-                        c[1] += t == 2u;
-                        c[2] += t == 3u;
+                    for (int kb = d > 16 ? 16 : 0; kb >= 0; kb -= 16) {
+                        uint32_t e[16];
+                        int32_t rk[16];
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) e[k] = kb + k < d ? __ldg(a.adj + beg + kb + k) : 0u;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) rk[k] = e[k] ? a.rank[p0 + (e[k] >> 2)] : 0;
+#pragma unroll
+                        for (int k = 15; k >= 0; --k) {
+                            if (e[k]) {
+                                const uint32_t y = e[k] >> 2, t = e[k] & 3u;
+                                a.flag[f0 + kb + k] = rk[k] > R ? 1 : 0;
+                                const bool up = (int64_t)y > xl;
+                                T.add(terms, up, t, c, (up ? n : 0ull) - dx);
+                                c[0] += t == 1u;
+                                c[1] += t == 2u;
+                                c[2] += t == 3u;
+                            }
+                        }
                     }
                 }
                 if (mixed) T.add_direct(a.acc, s);
@@ -334,10 +393,13 @@ __global__ void __launch_bounds__(256) k_terms_rows(TermArgs a) {
             if (lane == 31 && tot) at = atomicAdd(a.npieces, tot);
             at = __shfl_sync(full, at, 31) + incl - np;
             for (unsigned q = 0; q < np; ++q)
-                if (at + q < a.piece_cap) a.pieces[at + q] = make_uint4((uint32_t)r, q, np, 0u);
+                if (at + q < a.piece_cap) {
+                    P.k = q;
+                    put_piece(a.pieces + 3 * (size_t)(at + q), P);
+                }
         }
     }
-    T.flush(a.acc, cur, lane);
+    T.flush(a.acc, cur);
 }
 
 // Tag counts of every piece of a row of several pieces (one warp per piece).
@@ -347,17 +409,13 @@ __global__ void __launch_bounds__(256) k_piece_counts(TermArgs a) {
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const uint32_t np_all = min(*a.npieces, a.piece_cap);
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < np_all; w += warps) {
-        const uint4 pc = a.pieces[w];
-        if (pc.z < 2) continue;
-        const int64_t r = pc.x;
-        const int s = row_seg(a.pfx, a.nseg, r);
-        const int64_t x = a.seg[s].rb + (r - a.pfx[s]);
-        const int64_t beg = a.row_ptr[x];
-        const int d = (int)(a.row_ptr[x + 1] - beg);
-        const int k0 = (int)pc.y * TR_PIECE, k1 = min(d, k0 + TR_PIECE);
+        const uint4 q2 = a.pieces[3 * w + 2];
+        if (q2.z < 2) continue;
+        const Piece P = get_piece(a.pieces[3 * w], a.pieces[3 * w + 1], q2);
+        const int k0 = (int)P.k * TR_PIECE, k1 = min(P.d, k0 + TR_PIECE);
         uint32_t c1 = 0, c2 = 0, c3 = 0;
         for (int k = k0 + lane; k < k1; k += 32) {
-            const uint32_t t = __ldg(a.adj + beg + k) & 3u;
+            const uint32_t t = __ldg(a.adj + P.beg + k) & 3u;
             c1 += t == 1u;
             c2 += t == 2u;
             c3 += t == 3u;
@@ -369,61 +427,84 @@ __global__ void __launch_bounds__(256) k_piece_counts(TermArgs a) {
     }
 }
 
-// One warp per piece of a longer row: 32 entries at a time from the piece's
-// end, the counts after each entry from ballots plus those carried from the
-// later entries (and the later pieces of the row).
-__global__ void __launch_bounds__(256) k_terms_pieces(TermArgs a) {
+// One warp per piece of a longer row: TR_ILP chunks of 32 entries at a time
+// from the piece's end, the counts after each entry from ballots plus those
+// carried from the later entries (and the later pieces of the row).  The
+// next piece's record loads while this one runs.
+__global__ void __launch_bounds__(256, 3) k_terms_pieces(TermArgs a) {
+    __shared__ uint32_t tsm[8][18 * 32];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned after = ~((2u << lane) - 1u);  // lanes above this one
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const uint32_t np_all = min(*a.npieces, a.piece_cap);
     TermSums T;
+    T.sm = tsm[threadIdx.x >> 5];
+    T.lane = lane;
     T.zero();
     int cur = -1;
     unsigned since = 0;  // pieces since the last flush (a lane adds < 64 * 2^21 per piece)
-    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < np_all; w += warps) {
-        const uint4 pc = a.pieces[w];
-        const int64_t r = pc.x;
-        const int s = row_seg(a.pfx, a.nseg, r);
-        if (s != cur || ++since >= 16) {
-            T.flush(a.acc, cur, lane);
-            cur = s;
+    int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    uint4 n0 = make_uint4(0, 0, 0, 0), n1 = n0, n2 = n0;
+    if (w < np_all) {
+        n0 = a.pieces[3 * w];
+        n1 = a.pieces[3 * w + 1];
+        n2 = a.pieces[3 * w + 2];
+    }
+    for (; w < np_all; w += warps) {
+        const Piece P = get_piece(n0, n1, n2);
+        if (w + warps < np_all) {
+            n0 = a.pieces[3 * (w + warps)];
+            n1 = a.pieces[3 * (w + warps) + 1];
+            n2 = a.pieces[3 * (w + warps) + 2];
+        }
+        if (P.s != cur || ++since >= 16) {
+            T.flush(a.acc, cur);
+            cur = P.s;
             since = 0;
         }
-        const SegDev& g = a.seg[s];
-        const int64_t p0 = a.pfx[s], xl = r - p0, x = g.rb + xl;
-        const int64_t beg = a.row_ptr[x];
-        const int d = (int)(a.row_ptr[x + 1] - beg);
-        const int k0 = (int)pc.y * TR_PIECE, k1 = min(d, k0 + TR_PIECE);
-        const int32_t R = a.rank[r];
-        const int64_t f0 = a.epfx[s] + (beg - g.eb);
-        const bool terms = r >= a.r_lo && r < a.r_hi;
-        const unsigned long long n = (unsigned long long)g.n, dx = (unsigned long long)d;
+        const int64_t xl = (int64_t)P.r - P.p0;
+        const int k0 = (int)P.k * TR_PIECE, k1 = min(P.d, k0 + TR_PIECE);
+        const bool terms = (int64_t)P.r >= a.r_lo && (int64_t)P.r < a.r_hi;
+        const unsigned long long n = (unsigned long long)a.seg[P.s].n, dx = (unsigned long long)P.d;
         uint32_t cc[3] = {0, 0, 0};  // entries of each tag after the current chunk
-        for (uint32_t q = pc.y + 1; q < pc.z; ++q) {  // the row's later pieces
-            const uint4 c = a.pcnt[w - pc.y + q];
+        for (uint32_t q = P.k + 1; q < P.np; ++q) {  // the row's later pieces
+            const uint4 c = a.pcnt[w - P.k + q];
             cc[0] += c.x;
             cc[1] += c.y;
             cc[2] += c.z;
         }
-        for (int c0 = k0 + ((k1 - k0 - 1) & ~31); c0 >= k0; c0 -= 32) {
-            const int k = c0 + lane;
-            const bool valid = k < k1;
-            const uint32_t e = valid ? __ldg(a.adj + beg + k) : 0u, y = e >> 2, t = e & 3u;
-            if (valid) a.flag[f0 + k] = a.rank[p0 + y] > R ? 1 : 0;
-            const unsigned m1 = __ballot_sync(full, valid && t == 1u), m2 = __ballot_sync(full, valid && t == 2u),
-                           m3 = __ballot_sync(full, valid && t == 3u);
-            const uint32_t c[3] = {cc[0] + __popc(m1 & after), cc[1] + __popc(m2 & after),
-                                   cc[2] + __popc(m3 & after)};
-            const bool up = (int64_t)y > xl;
-            T.add(terms && valid, up, t, c, (up ? n : 0ull) - dx);
-            cc[0] += __popc(m1);
-            cc[1] += __popc(m2);
-            cc[2] += __popc(m3);
+        // TR_ILP chunks at a time from the piece's end: loads first, then the
+        // chunks in order from the last
+        for (int top = k0 + ((k1 - k0 - 1) & ~31); top >= k0; top -= 32 * TR_ILP) {
+            uint32_t e[TR_ILP];
+            int32_t rk[TR_ILP];
+#pragma unroll
+            for (int u = 0; u < TR_ILP; ++u) {
+                const int k = top - 32 * u + lane;
+                e[u] = (k >= k0 && k < k1) ? __ldg(a.adj + P.beg + k) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < TR_ILP; ++u) rk[u] = e[u] ? a.rank[P.p0 + (e[u] >> 2)] : 0;
+#pragma unroll
+            for (int u = 0; u < TR_ILP; ++u) {
+                const int k = top - 32 * u + lane;
+                const bool valid = e[u] != 0u;
+                const uint32_t y = e[u] >> 2, t = e[u] & 3u;
+                if (valid) a.flag[P.f0 + k] = rk[u] > P.R ? 1 : 0;
+                const unsigned m1 = __ballot_sync(full, t == 1u), m2 = __ballot_sync(full, t == 2u),
+                               m3 = __ballot_sync(full, t == 3u);
+                const uint32_t c[3] = {cc[0] + __popc(m1 & after), cc[1] + __popc(m2 & after),
+                                       cc[2] + __popc(m3 & after)};
+                const bool up = (int64_t)y > xl;
+                T.add(terms && valid, up, t, c, (up ? n : 0ull) - dx);
+                cc[0] += __popc(m1);
+                cc[1] += __popc(m2);
+                cc[2] += __popc(m3);
+            }
         }
     }
-    T.flush(a.acc, cur, lane);
+    T.flush(a.acc, cur);
 }
 
 // The flags read as int for the scan that places the forward entries.
