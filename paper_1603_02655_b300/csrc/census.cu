@@ -2434,6 +2434,7 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
         ta.r_lo = bp.r_lo;
         ta.r_hi = bp.r_hi;
         ta.rank = rank;
+        ta.perm = perm;
         ta.flag = flag;
         ta.acc = acc;
         ta.pieces = (uint4*)(ws + Lo.o_tp);

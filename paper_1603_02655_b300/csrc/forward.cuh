@@ -264,6 +264,7 @@ struct TermArgs {
     int64_t rows;
     int64_t r_lo, r_hi;   // the rows whose terms this call adds (a shard), all flags regardless
     const int32_t* rank;  // per selected row
+    const int32_t* perm;  // rank -> local row, per graph
     uint8_t* flag;        // [entries] forward flags
     unsigned long long* acc;
     uint4* pieces;        // [3 * piece_cap] piece records of the longer rows (Piece)
@@ -304,8 +305,10 @@ __device__ __forceinline__ Piece get_piece(const uint4& a, const uint4& b, const
     return P;
 }
 
-// One thread per row of at most TR_SHORT entries (warps take TR_RUN groups
-// of 32 consecutive rows), in batches of 16 entries from the row's end, each
+// One thread per row of at most TR_SHORT entries, the rows taken in rank
+// order (warps take TR_RUN groups of 32 consecutive ranks: rows of one
+// degree class, so the lanes' rows are about as long), in batches of 16
+// entries from the row's end up to the longest row of the group, each
 // batch's loads issued before its entries are counted; longer rows are
 // listed as pieces.
 __global__ void __launch_bounds__(256, 3) k_terms_rows(TermArgs a) {
@@ -322,9 +325,9 @@ __global__ void __launch_bounds__(256, 3) k_terms_rows(TermArgs a) {
     for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 * TR_RUN; g0 < a.rows;
          g0 += warps * 32 * TR_RUN) {
         for (int it = 0; it < TR_RUN; ++it) {
-            const int64_t r = g0 + 32 * it + lane;
-            const bool valid = r < a.rows;
-            const int s = valid ? row_seg(a.pfx, a.nseg, r) : -1;
+            const int64_t i = g0 + 32 * it + lane;  // rank position: graph s's ranks start at pfx[s]
+            const bool valid = i < a.rows;
+            const int s = valid ? row_seg(a.pfx, a.nseg, i) : -1;
             const int s0 = __shfl_sync(full, s, 0);
             if (s0 < 0) break;
             // rows of two graphs in one group: each lane adds its own row's
@@ -337,13 +340,19 @@ __global__ void __launch_bounds__(256, 3) k_terms_rows(TermArgs a) {
             }
             unsigned np = 0;
             Piece P;
+            int64_t p0 = 0, xl = 0, r = 0, beg = 0, f0 = 0;
+            int d = 0;
+            int32_t R = 0;
             if (valid) {
                 const SegDev& g = a.seg[s];
-                const int64_t p0 = a.pfx[s], xl = r - p0, x = g.rb + xl;
-                const int64_t beg = a.row_ptr[x];
-                const int d = (int)(a.row_ptr[x + 1] - beg);
-                const int32_t R = a.rank[r];
-                const int64_t f0 = a.epfx[s] + (beg - g.eb);
+                p0 = a.pfx[s];
+                xl = a.perm[i];
+                r = p0 + xl;
+                const int64_t x = g.rb + xl;
+                beg = a.row_ptr[x];
+                d = (int)(a.row_ptr[x + 1] - beg);
+                R = (int32_t)(i - p0);
+                f0 = a.epfx[s] + (beg - g.eb);
                 if (d > TR_SHORT) {
                     np = (unsigned)((d + TR_PIECE - 1) / TR_PIECE);
                     P.beg = beg;
@@ -354,33 +363,39 @@ __global__ void __launch_bounds__(256, 3) k_terms_rows(TermArgs a) {
                     P.r = (uint32_t)r;
                     P.np = np;
                     P.s = s;
-                } else if (d > 0) {
-                    const bool terms = r >= a.r_lo && r < a.r_hi;
-                    const unsigned long long n = (unsigned long long)g.n, dx = (unsigned long long)d;
-                    uint32_t c[3] = {0, 0, 0};
-                    for (int kb = d > 16 ? 16 : 0; kb >= 0; kb -= 16) {
-                        uint32_t e[16];
-                        int32_t rk[16];
+                }
+            }
+            // the group's short rows, up to its longest one (warp-uniform bounds)
+            const int ds = (valid && d <= TR_SHORT) ? d : 0;
+            const int dm = __reduce_max_sync(full, ds);
+            if (dm > 0) {
+                const bool terms = valid && r >= a.r_lo && r < a.r_hi;
+                const unsigned long long n = valid ? (unsigned long long)a.seg[s].n : 0ull;
+                const unsigned long long dx = (unsigned long long)ds;
+                uint32_t c[3] = {0, 0, 0};
+                for (int kb = dm > 16 ? 16 : 0; kb >= 0; kb -= 16) {
+                    const int nb = min(dm - kb, 16);
+                    uint32_t e[16];
+                    int32_t rk[16];
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) e[k] = kb + k < d ? __ldg(a.adj + beg + kb + k) : 0u;
+                    for (int k = 0; k < 16; ++k) e[k] = (k < nb && kb + k < ds) ? __ldg(a.adj + beg + kb + k) : 0u;
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) rk[k] = e[k] ? a.rank[p0 + (e[k] >> 2)] : 0;
+                    for (int k = 0; k < 16; ++k) rk[k] = e[k] ? a.rank[p0 + (e[k] >> 2)] : 0;
 #pragma unroll
-                        for (int k = 15; k >= 0; --k) {
-                            if (e[k]) {
-                                const uint32_t y = e[k] >> 2, t = e[k] & 3u;
-                                a.flag[f0 + kb + k] = rk[k] > R ? 1 : 0;
-                                const bool up = (int64_t)y > xl;
-                                T.add(terms, up, t, c, (up ? n : 0ull) - dx);
-                                c[0] += t == 1u;
-                                c[1] += t == 2u;
-                                c[2] += t == 3u;
-                            }
+                    for (int k = 15; k >= 0; --k) {
+                        if (k < nb && e[k]) {
+                            const uint32_t y = e[k] >> 2, t = e[k] & 3u;
+                            a.flag[f0 + kb + k] = rk[k] > R ? 1 : 0;
+                            const bool up = (int64_t)y > xl;
+                            T.add(terms, up, t, c, (up ? n : 0ull) - dx);
+                            c[0] += t == 1u;
+                            c[1] += t == 2u;
+                            c[2] += t == 3u;
                         }
                     }
                 }
-                if (mixed) T.add_direct(a.acc, s);
             }
+            if (mixed && valid) T.add_direct(a.acc, s);
             // the pieces of the longer rows: one atomic per warp
             unsigned incl = np;
 #pragma unroll
