@@ -1231,7 +1231,7 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
 // in its owner's forward list (sorted by rank) by binary search, the piece's
 // searches in lockstep (a run's dyads share few owners, so their lists stay
 // in cache).
-constexpr int TS_RUN = 1024;
+constexpr int TS_RUN = 128;
 
 template <bool IDS>
 __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
