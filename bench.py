@@ -44,7 +44,11 @@ WORKLOAD_DESC = {
     "c4": "4096 graphs, n log-uniform in [64, 65536], even G(n,p) mean out-degree U(4,32), odd R-MAT edge factor 8, reciprocity U(0,0.5), seed 4",
     "c5": "Chung-Lu n=2^22 gamma 2.1 mean total degree 16, largest realised degree ~1e5, reciprocity 0.15, seed 5",
 }
-OWN_BUILD_KERNELS = 8   # k_dyad_keys k_heads k_dyads k_row_counts k_place_lo k_place_up k_fill_sent k_rowstats (plus CUB sort/scan)
+# graph-build launches on the bucket path with no crowded hub segment (c3, c5):
+# k_bkt_hist, 3 scan kernels, k_bkt_scatter, k_bkt_rows, k_rows, k_long_split,
+# k_seg_sort, k_big_sort, k_long_count, 3 scan kernels, k_compact,
+# k_long_write, k_rowstats, k_fill_tail
+OWN_BUILD_KERNELS = 18
 FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
 
