@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "scan.cuh"
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -187,14 +188,7 @@ __global__ void k_arc_scatter(ArcIn a, bool undirected, const int32_t* __restric
     }
 }
 
-// ------------------------------------------------------------------ scans
-// out[0..n) = exclusive prefix sums of in[0..n), out[n] = the total: tiles of
-// SC_NT * SC_IT items, a sum per tile, a scan of the tile sums by one block,
-// then each tile rescanned from its offset.
-constexpr int SC_NT = 512;
-constexpr int SC_IT = 8;
-constexpr int SC_TILE = SC_NT * SC_IT;
-
+// ------------------------------------------------------------ block scan
 // Exclusive block-wide scan of v; *total gets the block's sum.  All threads
 // of the block call it; it begins and ends with a barrier.
 __device__ __forceinline__ long long block_excl_scan(long long v, long long* wsum, long long* total) {
@@ -222,57 +216,6 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long* wsu
     return inc - v + (warp > 0 ? wsum[warp - 1] : 0);
 }
 
-__global__ void __launch_bounds__(SC_NT) k_scan_part(const int32_t* __restrict__ in, int64_t n,
-                                                     long long* __restrict__ part) {
-    __shared__ long long wsum[32];
-    const int64_t b0 = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_IT;
-    long long s = 0;
-#pragma unroll
-    for (int k = 0; k < SC_IT; ++k)
-        if (b0 + k < n) s += in[b0 + k];
-    long long total;
-    block_excl_scan(s, wsum, &total);
-    if (threadIdx.x == 0) part[blockIdx.x] = total;
-}
-
-// One block: part[0..np) -> exclusive prefixes, part[np] = the total.
-__global__ void __launch_bounds__(SC_NT) k_scan_top(long long* __restrict__ part, int64_t np) {
-    __shared__ long long wsum[32];
-    long long carry = 0;
-    for (int64_t b = 0; b < np; b += SC_NT) {
-        const int64_t i = b + threadIdx.x;
-        const long long v = i < np ? part[i] : 0;
-        long long total;
-        const long long ex = block_excl_scan(v, wsum, &total);
-        if (i < np) part[i] = carry + ex;
-        carry += total;
-    }
-    if (threadIdx.x == 0) part[np] = carry;
-}
-
-template <class OUT>
-__global__ void __launch_bounds__(SC_NT) k_scan_down(const int32_t* __restrict__ in, int64_t n,
-                                                     const long long* __restrict__ part, int64_t np,
-                                                     OUT* __restrict__ out) {
-    __shared__ long long wsum[32];
-    const int64_t b0 = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_IT;
-    int32_t v[SC_IT];
-    long long s = 0;
-#pragma unroll
-    for (int k = 0; k < SC_IT; ++k) {
-        v[k] = b0 + k < n ? in[b0 + k] : 0;
-        s += v[k];
-    }
-    long long total;
-    long long run = part[blockIdx.x] + block_excl_scan(s, wsum, &total);
-#pragma unroll
-    for (int k = 0; k < SC_IT; ++k)
-        if (b0 + k < n) {
-            out[b0 + k] = (OUT)run;
-            run += v[k];
-        }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (OUT)part[np];
-}
 
 // ------------------------------------------------------------ row sorting
 
@@ -1102,15 +1045,9 @@ int grid_for(int64_t work, int threads, int sms) {
 // out[0..n] = exclusive scan of in[0..n) and the total (n < 2^31 items).
 template <class OUT>
 tc_status scan_excl(Scratch& S, const int32_t* in, int64_t n, OUT* out, cudaStream_t st) {
-    const int64_t np = std::max<int64_t>(1, (n + SC_TILE - 1) / SC_TILE);
-    long long* part = nullptr;
-    TC_CUDA(S.get(&part, (size_t)np + 1));
-    k_scan_part<<<(unsigned)np, SC_NT, 0, st>>>(in, n, part);
-    TC_CUDA(cudaGetLastError());
-    k_scan_top<<<1, SC_NT, 0, st>>>(part, np);
-    TC_CUDA(cudaGetLastError());
-    k_scan_down<OUT><<<(unsigned)np, SC_NT, 0, st>>>(in, n, part, np, out);
-    TC_CUDA(cudaGetLastError());
+    char* tmp = nullptr;
+    TC_CUDA(S.get(&tmp, scan_tmp_bytes(n)));
+    TC_CUDA(scan_run<false>(ScanLoad<int32_t>{in}, n, out, tmp, true, st));
     return TC_OK;
 }
 

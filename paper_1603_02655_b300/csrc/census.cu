@@ -39,11 +39,8 @@
 #include <cstring>
 #include <mutex>
 
-#include <cub/device/device_scan.cuh>
-#include <thrust/iterator/counting_iterator.h>
-#include <thrust/iterator/transform_iterator.h>
-
 #include "mlp.cuh"
+#include "scan.cuh"
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -397,7 +394,6 @@ struct OneHot {
         return 1ull << (TAG_BITS * (t - 1));
     }
 };
-using OneHotIt = thrust::transform_iterator<OneHot, thrust::counting_iterator<int64_t>, unsigned long long>;
 
 // Thread per row of the selected graphs: register each owner's work items.
 __global__ void k_owner_rows(const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
@@ -2208,7 +2204,7 @@ struct Layout {
     std::vector<int64_t> epfx;  // adjacency entries of the selected graphs, running
     bool flat = false;          // per-entry task terms (k_tasks_flat)
     int64_t entries = 0;
-    size_t scan_bytes = 0;      // CUB scan temporary storage
+    size_t scan_bytes = 0;      // scan work space (scan_tmp_bytes)
     size_t o_acc, o_ctr, o_seg, o_pfx, o_out, o_codes, o_r[NBIN], o_rt, o_tl, o_ia, o_own, o_psb, o_plen, o_epfx,
         o_scan, o_scantmp, need;
     uint32_t own_cap = 0;
@@ -2333,10 +2329,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
     Lo.o_epfx = take(sizeof(int64_t) * ((size_t)nseg + 1));
     Lo.scan_bytes = 0;
     Lo.flat = Lo.flat && Lo.entries > 0;
-    if (Lo.flat)
-        TC_CUDA(cub::DeviceScan::InclusiveSum(
-            nullptr, Lo.scan_bytes, OneHotIt(thrust::counting_iterator<int64_t>(0), OneHot{nullptr, nullptr, nullptr, 1}),
-            (unsigned long long*)nullptr, (int)Lo.entries, (cudaStream_t)0));
+    if (Lo.flat) Lo.scan_bytes = scan_tmp_bytes(Lo.entries);
     Lo.o_scan = take(sizeof(unsigned long long) * (Lo.flat && !Lo.fwd ? (size_t)Lo.entries : 1));
     Lo.o_scantmp = take(std::max<size_t>(Lo.scan_bytes, 16));
     // forward lists: ranks, forward entries, dyad records by owner
@@ -2344,14 +2337,8 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         const size_t rows = (size_t)Lo.rows, D = (size_t)std::max<int64_t>(dyads, 1);
         Lo.nb = (int)((Lo.rows + RK_B - 1) / RK_B);
         Lo.item_cap = (uint32_t)std::min<int64_t>(Lo.rows + dyads / TRI_PIECE + 1, 0xffffffffll);
-        size_t b1 = 0, b2 = 0, b3 = 0;
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b1, (const uint32_t*)nullptr, (uint32_t*)nullptr,
-                                              NCLS * Lo.nb, (cudaStream_t)0));
-        TC_CUDA(cub::DeviceScan::InclusiveSum(nullptr, b2, FlagIt((const uint8_t*)nullptr, U8ToInt{}),
-                                              (int32_t*)nullptr, (int)Lo.entries, (cudaStream_t)0));
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b3, (const unsigned long long*)nullptr,
-                                              (unsigned long long*)nullptr, (int)(rows + 1), (cudaStream_t)0));
-        Lo.fscan_bytes = std::max(b1, std::max(b2, b3));
+        Lo.fscan_bytes = std::max(scan_tmp_bytes((int64_t)NCLS * Lo.nb),
+                                  std::max(scan_tmp_bytes(Lo.entries), scan_tmp_bytes((int64_t)rows + 1)));
         Lo.o_hist = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
         Lo.o_hex = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
         Lo.o_co = take(sizeof(int64_t) * NCLS * (size_t)nseg);
@@ -2414,8 +2401,7 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     // vertex ranks: (floor(log2 d), id) per graph
     k_rank_hist<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hist);
     TC_CUDA(cudaGetLastError());
-    size_t tb = Lo.fscan_bytes;
-    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, hist, hex, NCLS * Lo.nb, st));
+    TC_CUDA(scan_run<false>(ScanLoad<uint32_t>{hist}, (int64_t)NCLS * Lo.nb, hex, tmp, false, st));
     k_rank_seg<<<std::min(Lo.nseg, L.sms * 16), 32, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co);
     TC_CUDA(cudaGetLastError());
     k_rank_assign<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co, rank, perm,
@@ -2474,14 +2460,11 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     F.stat = (unsigned long long*)(ctr + 44);
     F.rank = rank;
     F.perm = perm;
-    tb = Lo.fscan_bytes;
-    TC_CUDA(cub::DeviceScan::InclusiveSum(tmp, tb, FlagIt(flag, U8ToInt{}), (int32_t*)(ws + Lo.o_fs),
-                                          (int)Lo.entries, st));
+    TC_CUDA(scan_run<true>(ScanLoad<uint8_t>{flag}, Lo.entries, (int32_t*)(ws + Lo.o_fs), tmp, false, st));
     k_fwd_rows<<<L.sms * 8, FR_NT, 0, st>>>(set.row_ptr, set.deg, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.rows, Lo.o.fwd_big,
                                            F, bp.r_lo, bp.r_hi);
     TC_CUDA(cudaGetLastError());
-    tb = Lo.fscan_bytes;
-    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, F.tcnt, F.tpre, (int)(Lo.rows + 1), st));
+    TC_CUDA(scan_run<false>(ScanLoad<unsigned long long>{F.tcnt}, Lo.rows + 1, F.tpre, tmp, false, st));
     k_fwd_items<<<L.sms * 4, 256, 0, st>>>(d_pfx, Lo.nseg, F);
     TC_CUDA(cudaGetLastError());
     k_fwd_fill<<<L.sms * 16, 256, 0, st>>>(set.adj, set.arow, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.entries, F);
@@ -2582,9 +2565,8 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
         if (Lo.flat) {
             unsigned long long* scan = (unsigned long long*)(ws + Lo.o_scan);
             const int64_t* d_epfx = (const int64_t*)(ws + Lo.o_epfx);
-            size_t sb = Lo.scan_bytes;
-            const OneHotIt words(thrust::counting_iterator<int64_t>(0), OneHot{set.adj, d_seg, d_epfx, Lo.nseg});
-            TC_CUDA(cub::DeviceScan::InclusiveSum(ws + Lo.o_scantmp, sb, words, scan, (int)Lo.entries, st));
+            TC_CUDA(scan_run<true>(OneHot{set.adj, d_seg, d_epfx, Lo.nseg}, Lo.entries, scan, ws + Lo.o_scantmp,
+                                   false, st));
             if (bp.own_min > 0) {
                 k_owner_rows<<<L.sms * 8, 256, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, bp.own_min, bins,
                                                         bp.r_lo, bp.r_hi);

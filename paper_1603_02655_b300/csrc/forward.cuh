@@ -522,12 +522,6 @@ __global__ void __launch_bounds__(256, 3) k_terms_pieces(TermArgs a) {
     T.flush(a.acc, cur);
 }
 
-// The flags read as int for the scan that places the forward entries.
-struct U8ToInt {
-    __host__ __device__ int operator()(uint8_t v) const { return (int)v; }
-};
-using FlagIt = thrust::transform_iterator<U8ToInt, const uint8_t*, int>;
-
 // Rows whose forward list has at most FWD_SHORT entries are sorted in
 // registers (k_fwd_sort_short) and a dyad of such a row looks up its whole
 // forward list instead of the part ranked above the owner (an entry ranked

@@ -16,12 +16,12 @@
 //     line, none in *Vertices); an exclusive scan gives each line its slot.
 //   4 each data line writes its arcs (ids minus the base); tc_graph_build
 //     range-checks them.
-#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <cctype>
 #include <cstring>
 
+#include "scan.cuh"
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -233,11 +233,9 @@ struct Scratch {
 
 template <class T>
 tc_status exclusive_scan(Scratch& S, const T* in, T* out, int64_t count, cudaStream_t st) {
-    size_t bytes = 0;
-    TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, (int)count, st));
     void* tmp = nullptr;
-    TC_CUDA(S.get((char**)&tmp, bytes));
-    TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, in, out, (int)count, st));
+    TC_CUDA(S.get((char**)&tmp, scan_tmp_bytes(count)));
+    TC_CUDA(scan_run<false>(ScanLoad<T>{in}, count, out, tmp, false, st));
     return TC_OK;
 }
 
