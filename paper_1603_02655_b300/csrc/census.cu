@@ -2680,14 +2680,15 @@ tc_status enqueue_census(const GraphSet& set, const Layout& Lo, char* ws, tc_cen
     return TC_OK;
 }
 
-// Kernels of this library a census launches (the library scans not counted).
+// Kernels of this library a census launches (a prefix scan is 3 kernels).
 int census_launches(const Layout& Lo) {
     if (Lo.rows == 0) return 1;
     // 3 rank kernels, the task pass (3 row-wise kernels, or k_tasks +
-    // k_fwd_flags), 6 forward-list kernels, 2 lookup kernels, k_fold
-    if (Lo.fwd) return Lo.flat ? 15 : 14;
+    // k_fwd_flags), 6 forward-list kernels, 2 lookup kernels, k_fold, and
+    // the scans of the rank classes, the forward flags and the owned dyads
+    if (Lo.fwd) return (Lo.flat ? 15 : 14) + 9;
     const int route = Lo.o.bin_mode == TC_BIN_MLP && cost_model_weights() ? 1 : 0;
-    const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 2 : 1) : 1;  // k_owner_rows, k_tasks_flat
+    const int tasks = Lo.flat ? (Lo.o.own_min > 0 ? 2 : 1) + 3 : 1;  // the tag scan, k_owner_rows, k_tasks_flat
     return (Lo.o.persistent ? 4 : 7) + tasks + route + (Lo.o.own_min > 0 ? 2 : 0) + (Lo.exact ? 1 : 0);
 }
 
