@@ -830,9 +830,11 @@ struct TriHist {
     int tag;
     int lane;
     unsigned pending;
+    unsigned long long seen;  // triangles flushed by this lane's counter
     __device__ __forceinline__ void flush() {
         if (tag >= 0 && lane < 27) {
             const unsigned long long c = (unsigned long long)hs[lane] + hs[32 + lane];
+            seen += c;
             if (c) {
                 unsigned long long* h = acc + (size_t)tag * ACC;
                 const uint32_t t_ab = lane / 9 + 1, t_ac = (lane / 3) % 3 + 1, t_bc = lane % 3 + 1;
@@ -857,6 +859,10 @@ struct TriHist {
     // halve the lanes that meet on one counter)
     __device__ __forceinline__ void add(bool active, int type) {
         if (active) atomicAdd(hs + ((lane & 1) << 5) + type, 1u);
+    }
+    // the same at base = hs + ((lane & 1) << 5) - 13, type + 13 given
+    __device__ __forceinline__ static void add_at(uint32_t* base, bool active, uint32_t type13) {
+        if (active) atomicAdd(base + type13, 1u);
     }
 };
 
@@ -1017,6 +1023,7 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = threadIdx.x; j < MAP_KEYS / 16; j += TB_NT) map[j] = 0;
     TriHist H{hs_all + warp * 64, a.acc, -1, lane, 0u};
+    uint32_t* const hbase = H.hs + ((lane & 1) << 5) - 13;
     H.hs[lane] = 0;
     H.hs[32 + lane] = 0;
     uint2* q = q_all + warp * TQN;
@@ -1153,11 +1160,11 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
             const uint32_t st = has ? pof[before + lane] : 0u;
             const int d = chunk_dyad(has, st, (uint32_t)c, before, lane);
             const bool ok = c + lane < total;
-            uint32_t base = 0, cnt = 0;  // cnt: entries | t_x(h) << 8
+            uint32_t base = 0, cnt = 0;  // cnt: entries | 9 t_x(h) << 8
             if (ok) {
                 const uint32_t pq = (uint32_t)(c + lane) - pof[d];
                 base = tfst[d] + PIECE * pq;
-                cnt = min((uint32_t)PIECE, tlen[d] - PIECE * pq) | ((txin[d] & 3u) << 8);
+                cnt = min((uint32_t)PIECE, tlen[d] - PIECE * pq) | ((9u * (txin[d] & 3u)) << 8);
             }
             // the chunk's pieces two at a time, one per half-warp (lane & 15
             // is the entry), HW_ILP pairs loaded together
@@ -1177,17 +1184,17 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
                 }
 #pragma unroll
                 for (int u = 0; u < HW_ILP; ++u) {
-                    const uint32_t kk = (kv[u] >> 2) - Rh1;  // ranks at or below h fall outside the map
-                    const uint32_t th =
-                        vv[u] && kk < (uint32_t)MAP_KEYS ? (map[kk >> 4] >> (2 * (kk & 15u))) & 3u : 0u;
+                    // ranks at or below h, and the zero word of an idle lane,
+                    // fall outside the map
+                    const uint32_t kk = (kv[u] >> 2) - Rh1;
+                    const uint32_t th = kk < (uint32_t)MAP_KEYS ? (map[kk >> 4] >> (2 * (kk & 15u))) & 3u : 0u;
                     if (IDS) {
                         enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
                         if (qn >= 32)
                             drain(H, P, q, qh, qn, 32, [&](int dq) { return txin[dq]; }, [&](int) { return hl; },
                                   a.perm, p0, ns, hits);
-                    } else {  // rank order x < h < w: the type from the three tags
-                        hits += th != 0 ? 1u : 0u;
-                        H.add(th != 0, (int)(9 * xt[u] + 3 * (kv[u] & 3u) + th) - 13);
+                    } else {  // rank order x < h < w: the type from the three tags (counted at flush)
+                        TriHist::add_at(hbase, th != 0, xt[u] + 3u * (kv[u] & 3u) + th);
                     }
                 }
             }
@@ -1199,8 +1206,10 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
                       ns, hits);
             finish(H, P, hits);
         }
-        const unsigned wh = __reduce_add_sync(full, hits);
-        H.pending += wh;
+        // hits bound the histogram's growth: counted in IDS mode, else the
+        // item's entry slots (its triangles are counted at flush)
+        const unsigned wh = IDS ? __reduce_add_sync(full, hits) : 0u;
+        H.pending += IDS ? wh : (unsigned)total * PIECE;
         tri += wh;
         hits = 0;
         prev_rh = rh;
@@ -1215,6 +1224,7 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
     }
     if (warp == 0) cp_async_wait_all();
     H.flush();
+    if (!IDS) tri = warp_sum64(H.seen);
     looked = warp_sum64(looked);
     if (lane == 0 && looked) atomicAdd(a.stat + 0, looked);
     if (lane == 0 && tri) atomicAdd(a.stat + 1, tri);
