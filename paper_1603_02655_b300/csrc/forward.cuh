@@ -893,7 +893,8 @@ struct TriArgs {
 // half-warp, each lane one entry (coalesced loads).  R-MAT scale 22: 82% of
 // the lanes' entry slots are used.
 constexpr int PIECE = 16;
-constexpr int HW_ILP = 4;  // piece pairs whose entries a warp loads together
+constexpr int HW_ILP = 4;  // piece pairs whose entries a warp loads together (searches)
+constexpr int TB_ILP = 8;  // the same for the tag-map lookups (a chunk's 32 pieces in two steps)
 
 // Pieces of the dyads begun before chunk c: `before` is advanced past the
 // dyads whose first piece lies in [c, c + 32); returns this lane's dyad.
@@ -1167,14 +1168,14 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
                 cnt = min((uint32_t)PIECE, tlen[d] - PIECE * pq) | ((9u * (txin[d] & 3u)) << 8);
             }
             // the chunk's pieces two at a time, one per half-warp (lane & 15
-            // is the entry), HW_ILP pairs loaded together
+            // is the entry), TB_ILP pairs loaded together
             const int npc = min(32, total - c), e = lane & 15, half = lane >> 4;
-            for (int u0 = 0; u0 < npc; u0 += 2 * HW_ILP) {
-                uint32_t kv[HW_ILP], xt[HW_ILP];
-                int dv[HW_ILP];
-                bool vv[HW_ILP];
+            for (int u0 = 0; u0 < npc; u0 += 2 * TB_ILP) {
+                uint32_t kv[TB_ILP], xt[TB_ILP];
+                int dv[TB_ILP];
+                bool vv[TB_ILP];
 #pragma unroll
-                for (int u = 0; u < HW_ILP; ++u) {
+                for (int u = 0; u < TB_ILP; ++u) {
                     const int src = u0 + 2 * u + half;
                     const uint32_t pb = __shfl_sync(full, base, src & 31), pc = __shfl_sync(full, cnt, src & 31);
                     if (IDS) dv[u] = __shfl_sync(full, d, src & 31);
@@ -1183,7 +1184,7 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
                     kv[u] = vv[u] ? __ldg(a.fwd + pb + e) : 0u;
                 }
 #pragma unroll
-                for (int u = 0; u < HW_ILP; ++u) {
+                for (int u = 0; u < TB_ILP; ++u) {
                     // ranks at or below h, and the zero word of an idle lane,
                     // fall outside the map
                     const uint32_t kk = (kv[u] >> 2) - Rh1;
