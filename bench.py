@@ -570,7 +570,7 @@ def c4_record(tc, torch, stream, flush, steps, route=True):
             "per_graph_calls": {"ms": per_ms, "graphs_per_s": G / (per_ms / 1e3),
                                 "same_counts": same},
             "speedup_vs_per_graph": per_ms / ms,
-            "step": "census of all 4096 graphs of one batched build (CUDA-graph plan replay; build excluded)",
+            "step": "census of all 4096 graphs of one batched build (CUDA-graph plan replay of separate kernel launches; the one-persistent-launch form, persistent = 1, is slower and not used; build excluded)",
             "path_routing": routing,
             "build_s": build_s, "generate_s": gen_s, "oracle_census_match_every_graph": match}
 
