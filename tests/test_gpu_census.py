@@ -482,6 +482,57 @@ def test_build_layout_matches_definition():
         assert st[k] == og[k], k
 
 
+def test_build_crowded_hub_rows_match_definition():
+    """Hub rows whose neighbour ids crowd into a few id ranges, with many
+    duplicate and reversed arcs: the build's long-row path splits a hub row by
+    id range, and ranges of more than 512 entries (sorted in shared-memory
+    pieces) and of more than 8192 (pieces merged pairwise) take its slower
+    forms.  The hubs' rows against the definition, every statistic and the
+    census against the oracle."""
+    rng = np.random.default_rng(31)
+    n = 200_000
+    parts = []
+
+    def arcs_to(h, ids, reps):
+        t = np.repeat(ids, reps)
+        out = rng.random(t.size) < 0.6
+        parts.append((np.where(out, h, t), np.where(out, t, h)))
+
+    arcs_to(7, rng.choice(n, 6000, replace=False), rng.integers(1, 3, 6000))  # spread: many short ranges
+    arcs_to(11, np.arange(100, 400), 40)                             # one range of ~12k entries
+    arcs_to(13, np.arange(2000, 2101), 30)                           # two ranges of 1.4-1.6k entries
+    parts.append((rng.integers(0, n, 150_000), rng.integers(0, n, 150_000)))
+    src = np.concatenate([p[0] for p in parts]).astype(np.int32)
+    dst = np.concatenate([p[1] for p in parts]).astype(np.int32)
+    g = tc.tc_graph_build(n, src, dst)
+    try:
+        rp, adj = tc.tc_graph_export(g)
+        st = tc.tc_graph_stats(g)
+        got = tc.tc_census(g)
+    finally:
+        tc.tc_graph_free(g)
+    for h in (7, 11, 13):
+        row = {}
+        for a, b in zip(src.tolist(), dst.tolist()):
+            if a == b:
+                continue
+            if a == h:
+                row[b] = row.get(b, 0) | 1
+            elif b == h:
+                row[a] = row.get(a, 0) | 2
+        got_row = [(int(e) >> 2, int(e) & 3) for e in adj[rp[h]:rp[h + 1]]]
+        assert got_row == sorted(row.items()), h
+    og = oracle.Graph(n, src, dst)
+    try:
+        ost = og.stats()
+        want = og.census(THREADS)
+    finally:
+        og.close()
+    for k in ("arcs", "dyads", "mutual", "asym", "merged_entries", "max_degree"):
+        assert st[k] == ost[k], k
+    assert got == want
+
+
 def test_device_inputs_and_device_output_on_a_stream():
     import torch
     a = synth.c1()
