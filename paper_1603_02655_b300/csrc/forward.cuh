@@ -1247,6 +1247,7 @@ __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     TriHist H{hs_all[warp], a.acc, -1, lane, 0u};
+    uint32_t* const hbase = H.hs + ((lane & 1) << 5) - 13;
     H.hs[lane] = 0;
     H.hs[32 + lane] = 0;
     uint2* q = q_all[warp];
@@ -1309,11 +1310,11 @@ __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
                 const uint32_t d_fst = __shfl_sync(full, fst, dd), d_len = __shfl_sync(full, len, dd);
                 const uint32_t d_off = __shfl_sync(full, poff, dd);
                 const uint32_t d_xin = __shfl_sync(full, xin, dd);
-                uint32_t cnt = 0, base = 0;  // cnt: entries | t_x(h) << 8
+                uint32_t cnt = 0, base = 0;  // cnt: entries | 9 t_x(h) << 8
                 if (ok) {
                     const uint32_t pq = c + lane - d_off;
                     base = d_fst + PIECE * pq;
-                    cnt = min((uint32_t)PIECE, d_len - PIECE * pq) | ((d_xin & 3u) << 8);
+                    cnt = min((uint32_t)PIECE, d_len - PIECE * pq) | ((9u * (d_xin & 3u)) << 8);
                 }
                 // the chunk's pieces two at a time, one per half-warp (lane & 15
                 // is the entry): each lane searches its key in the piece's
@@ -1359,9 +1360,8 @@ __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
                             if (qn >= 32)
                                 drain(H, P, q, qh, qn, 32, [&](int dq) { return __shfl_sync(full, xin, dq); },
                                       [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
-                        } else {  // rank order x < h < w: the type from the three tags
-                            hits += th != 0 ? 1u : 0u;
-                            H.add(th != 0, (int)(9 * xt[u] + 3 * (kv[u] & 3u) + th) - 13);
+                        } else {  // rank order x < h < w: the type from the three tags (counted at flush)
+                            TriHist::add_at(hbase, th != 0, xt[u] + 3u * (kv[u] & 3u) + th);
                         }
                     }
                 }
@@ -1373,14 +1373,17 @@ __global__ void __launch_bounds__(256) k_tri_small(TriArgs a) {
                           [&](int dq) { return __shfl_sync(full, hl, dq); }, a.perm, p0, ns0, hits);
                 finish(H, P, hits);
             }
-            const unsigned wh = __reduce_add_sync(full, hits);
-            H.pending += wh;
+            // hits bound the histogram's growth: counted in IDS mode, else
+            // the group's entry slots (its triangles are counted at flush)
+            const unsigned wh = IDS ? __reduce_add_sync(full, hits) : 0u;
+            H.pending += IDS ? wh : total * PIECE;
             tri += wh;
             hits = 0;
             g0 += (uint32_t)take;
         }
     }
     H.flush();
+    if (!IDS) tri = warp_sum64(H.seen);
     looked = warp_sum64(looked);
     if (lane == 0 && looked) atomicAdd(a.stat + 2, looked);
     if (lane == 0 && tri) atomicAdd(a.stat + 3, tri);
