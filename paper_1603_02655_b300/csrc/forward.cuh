@@ -860,9 +860,12 @@ struct TriHist {
     __device__ __forceinline__ void add(bool active, int type) {
         if (active) atomicAdd(hs + ((lane & 1) << 5) + type, 1u);
     }
-    // the same at base = hs + ((lane & 1) << 5) - 13, type + 13 given
+    // the same at base = hs + ((lane & 1) << 5) - 13, type + 13 given: a
+    // predicated shared-memory reduction (no branch around it)
     __device__ __forceinline__ static void add_at(uint32_t* base, bool active, uint32_t type13) {
-        if (active) atomicAdd(base + type13, 1u);
+        const unsigned addr = (unsigned)__cvta_generic_to_shared(base + type13);
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, 0;\n\t@p red.shared.add.u32 [%1], 1;\n\t}"
+                     :: "r"((unsigned)active), "r"(addr) : "memory");
     }
 };
 
@@ -1188,7 +1191,8 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
                     // ranks at or below h, and the zero word of an idle lane,
                     // fall outside the map
                     const uint32_t kk = (kv[u] >> 2) - Rh1;
-                    const uint32_t th = kk < (uint32_t)MAP_KEYS ? (map[kk >> 4] >> (2 * (kk & 15u))) & 3u : 0u;
+                    const uint32_t mw = map[(kk >> 4) & (MAP_KEYS / 16 - 1)];  // always in range
+                    const uint32_t th = kk < (uint32_t)MAP_KEYS ? (mw >> (2 * (kk & 15u))) & 3u : 0u;
                     if (IDS) {
                         enqueue(q, qh, qn, th != 0, kv[u], th, dv[u], lane);
                         if (qn >= 32)
