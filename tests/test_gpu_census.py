@@ -533,6 +533,93 @@ def test_build_crowded_hub_rows_match_definition():
     assert got == want
 
 
+def csr_definition(n, src, dst, undirected=False):
+    """The tagged combined CRS by its definition (numpy): every arc x->y, not
+    a self-loop, gives neighbour y of row x with tag bit 0 and neighbour x of
+    row y with tag bit 1 (both bits for an undirected edge); one word per
+    (row, neighbour), tags OR-ed, rows sorted by neighbour."""
+    s = np.asarray(src, dtype=np.int64)
+    d = np.asarray(dst, dtype=np.int64)
+    keep = s != d
+    s, d = s[keep], d[keep]
+    t_out, t_in = (3, 3) if undirected else (1, 2)
+    rows = np.concatenate([s, d])
+    nbr = np.concatenate([d, s])
+    tag = np.concatenate([np.full(s.size, t_out), np.full(s.size, t_in)]).astype(np.int64)
+    uk, inv = np.unique(rows * n + nbr, return_inverse=True)
+    t = np.zeros(uk.size, dtype=np.int64)
+    np.bitwise_or.at(t, inv, tag)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, uk // n + 1, 1)
+    return np.cumsum(rp), ((uk % n) << 2 | t).astype(np.uint32)
+
+
+def hub_mix(rng, n, m0, hubs):
+    """Random arcs plus, for each (hub, entries), that many arcs between the
+    hub and random vertices in either direction, a third of them repeated."""
+    parts = [(rng.integers(0, n, m0), rng.integers(0, n, m0))]
+    for h, L in hubs:
+        other = rng.integers(0, n, L)
+        other = np.concatenate([other, other[: L // 3]])
+        out = rng.random(other.size) < 0.5
+        parts.append((np.where(out, h, other), np.where(out, other, h)))
+    loops = rng.integers(0, n, 100)
+    parts.append((loops, loops))
+    src = np.concatenate([p[0] for p in parts]).astype(np.int32)
+    dst = np.concatenate([p[1] for p in parts]).astype(np.int32)
+    perm = rng.permutation(src.size)
+    return src[perm], dst[perm]
+
+
+@pytest.mark.parametrize("undirected", [False, True])
+def test_build_rows_of_every_length_match_definition(undirected):
+    """Whole-graph layout against the definition, rows of every length: short
+    rows, rows of 513-4000 entries inside buckets that fit in shared memory
+    (sorted and merged in the bucket), and hub rows whose buckets do not fit
+    (the long-row path); duplicates, reversed arcs and self-loops."""
+    rng = np.random.default_rng(41)
+    n = 65536
+    hubs = [(1000 * i + 7, int(rng.integers(513, 4000))) for i in range(40)] + [(50_021, 12_000), (60_013, 30_000)]
+    src, dst = hub_mix(rng, n, 200_000, hubs)
+    g = tc.tc_graph_build(n, src, dst, undirected=undirected)
+    try:
+        rp, adj = tc.tc_graph_export(g)
+        st = tc.tc_graph_stats(g)
+    finally:
+        tc.tc_graph_free(g)
+    want_rp, want_adj = csr_definition(n, src, dst, undirected)
+    assert np.array_equal(rp, want_rp)
+    assert np.array_equal(adj, want_adj)
+    deg = np.diff(want_rp)
+    assert st["merged_entries"] == int((deg.astype(np.int64) ** 2).sum())
+    assert st["max_degree"] == int(deg.max())
+
+
+def test_build_batched_rows_match_definition():
+    """A batch whose buckets span graph boundaries: every graph's layout
+    against the definition (local ids, the split point of each row counted
+    against the row's local id through the census)."""
+    rng = np.random.default_rng(43)
+    ns = [5000, 7001, 3000, 1]
+    graphs = [hub_mix(rng, n, 6 * n, [(n // 2, 700)] if n > 1000 else []) if n > 1 else
+              (np.zeros(0, np.int32), np.zeros(0, np.int32)) for n in ns]
+    off = np.cumsum([0] + [s.size for s, _ in graphs])
+    src = np.concatenate([s for s, _ in graphs]).astype(np.int32)
+    dst = np.concatenate([d for _, d in graphs]).astype(np.int32)
+    hs = tc.tc_graph_build_batched(ns, off, src, dst)
+    try:
+        for h, n, (s, d) in zip(hs, ns, graphs):
+            rp, adj = tc.tc_graph_export(h)
+            want_rp, want_adj = csr_definition(n, s, d)
+            assert np.array_equal(rp, want_rp)
+            assert np.array_equal(adj, want_adj)
+            if n > 1:
+                assert tc.tc_census(h) == oracle.census(n, s, d)
+    finally:
+        for h in hs:
+            tc.tc_graph_free(h)
+
+
 def test_device_inputs_and_device_output_on_a_stream():
     import torch
     a = synth.c1()
