@@ -640,7 +640,12 @@ constexpr int SUB_AVG = 64;    // expected entries per id range of a long row
 constexpr int SUB_MAX = 4096;  // id ranges per long row
 constexpr int LS_NT = 512;
 
-// Long rows, a block each: the row's raw entries (tmp) distributed by id
+constexpr int LW_MAX = 4096;                 // long rows split by one warp
+constexpr int LW_S = LW_MAX / (SUB_AVG / 2);  // their id ranges: fewer than L / 32 + 1
+static_assert(LW_S % 32 == 0, "whole counters per lane");
+
+// Long rows, a block each (those of more than LW_MAX entries; a warp each
+// for the others): the row's raw entries (tmp) distributed by id
 // range into tmp2, ranges of 2^sh ids sized so that an even spread of the
 // row's neighbours puts about SUB_AVG entries in each; every non-empty range
 // becomes a segment.  Ranges are disjoint intervals of ids, so sorting each
@@ -656,6 +661,7 @@ __global__ void __launch_bounds__(LS_NT) k_long_split(const int32_t* __restrict_
         const int64_t x = lo.lng[li];
         const int32_t rb = roff[x];
         const int L = roff[x + 1] - rb;
+        if (L <= LW_MAX) continue;  // split by one warp (k_long_split_w)
         const int g = G == 1 ? 0 : find_graph(voff, G, x);
         const int64_t n = voff[g + 1] - voff[g];
         int sh = 0;
@@ -692,6 +698,72 @@ __global__ void __launch_bounds__(LS_NT) k_long_split(const int32_t* __restrict_
             tmp2[rb + atomicAdd(cnt + ((w >> 2) >> sh), 1)] = w;
         }
         __syncthreads();
+    }
+}
+
+// The same for the long rows of at most LW_MAX entries, a warp each: the
+// range width follows the same rule, so a row has fewer than L / 32 + 1
+// ranges (the width 2^sh is above 32 n / L, or sh = 0 and n < L / 32), at
+// most LW_S, counted in the warp's shared counters.
+__global__ void __launch_bounds__(256) k_long_split_w(const int32_t* __restrict__ roff,
+                                                      const int64_t* __restrict__ voff, int G, LongOut lo,
+                                                      const uint32_t* __restrict__ tmp, uint32_t* __restrict__ tmp2) {
+    constexpr int PL = LW_S / 32;  // counters per lane
+    __shared__ int32_t cnt_all[8][LW_S];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t* cnt = cnt_all[warp];
+    const int nlong = lo.ctr[0];
+    for (int li = blockIdx.x * 8 + warp; li < nlong; li += gridDim.x * 8) {
+        const int64_t x = lo.lng[li];
+        const int32_t rb = roff[x];
+        const int L = roff[x + 1] - rb;
+        if (L > LW_MAX) continue;
+        const int g = G == 1 ? 0 : find_graph(voff, G, x);
+        const int64_t n = voff[g + 1] - voff[g];
+        int sh = 0;
+        while (((int64_t)L << (sh + 1)) <= n * SUB_AVG) ++sh;
+        const int S = (int)(((n - 1) >> sh) + 1);  // <= LW_S (see above)
+        for (int j = lane; j < LW_S; j += 32) cnt[j] = 0;
+        __syncwarp();
+        for (int i = lane; i < L; i += 32) atomicAdd(cnt + ((tmp[rb + i] >> 2) >> sh), 1);
+        __syncwarp();
+        int v[PL], sum = 0, ne = 0;
+#pragma unroll
+        for (int q = 0; q < PL; ++q) {
+            const int j = lane * PL + q;
+            v[q] = j < S ? cnt[j] : 0;
+            sum += v[q];
+            ne += v[q] > 0;
+        }
+        long long inc = ((long long)ne << 32) | (long long)sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(full, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const long long tot = __shfl_sync(full, inc, 31);
+        const long long ex = inc - (((long long)ne << 32) | (long long)sum);
+        int sbase = 0;
+        if (lane == 0) sbase = atomicAdd(lo.ctr + 1, (int)(tot >> 32));
+        sbase = __shfl_sync(full, sbase, 0);
+        int run = (int)(ex & 0xffffffffll), rk = (int)(ex >> 32);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < PL; ++q) {
+            const int j = lane * PL + q;
+            if (j < S) {
+                cnt[j] = run;  // now the range's cursor
+                if (v[q] > 0) lo.segs[sbase + rk++] = make_uint4((uint32_t)(rb + run), (uint32_t)v[q], (uint32_t)x, 0u);
+                run += v[q];
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < L; i += 32) {
+            const uint32_t w = tmp[rb + i];
+            tmp2[rb + atomicAdd(cnt + ((w >> 2) >> sh), 1)] = w;
+        }
+        __syncwarp();
     }
 }
 
@@ -1217,6 +1289,8 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         TC_CUDA(cudaGetLastError());
     }
     if (total_n > 0) {  // long rows: split by id range, segments sorted, crowded segments merged
+        k_long_split_w<<<(unsigned)sms * 8, 256, 0, st>>>(roff, d_voff, G, lo, tmp, tmp2);
+        TC_CUDA(cudaGetLastError());
         k_long_split<<<(unsigned)sms * 2, LS_NT, 0, st>>>(roff, d_voff, G, lo, tmp, tmp2);
         TC_CUDA(cudaGetLastError());
         k_seg_sort<<<(unsigned)sms * 8, RW_NT, 0, st>>>(lo, tmp2, tmp);
