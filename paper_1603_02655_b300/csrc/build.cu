@@ -636,12 +636,12 @@ __global__ void __launch_bounds__(RW_NT) k_rows(const int32_t* __restrict__ roff
 
 // ---------------------------------------------------- step 3: long rows
 
-constexpr int SUB_AVG = 64;    // expected entries per id range of a long row
+constexpr int SUB_AVG = 128;   // expected entries per id range of a long row
 constexpr int SUB_MAX = 4096;  // id ranges per long row
 constexpr int LS_NT = 512;
 
 constexpr int LW_MAX = 4096;                 // long rows split by one warp
-constexpr int LW_S = LW_MAX / (SUB_AVG / 2);  // their id ranges: fewer than L / 32 + 1
+constexpr int LW_S = LW_MAX / (SUB_AVG / 2);  // their id ranges: fewer than 2 L / SUB_AVG + 1
 static_assert(LW_S % 32 == 0, "whole counters per lane");
 
 // Long rows, a block each (those of more than LW_MAX entries; a warp each
@@ -702,9 +702,10 @@ __global__ void __launch_bounds__(LS_NT) k_long_split(const int32_t* __restrict_
 }
 
 // The same for the long rows of at most LW_MAX entries, a warp each: the
-// range width follows the same rule, so a row has fewer than L / 32 + 1
-// ranges (the width 2^sh is above 32 n / L, or sh = 0 and n < L / 32), at
-// most LW_S, counted in the warp's shared counters.
+// range width follows the same rule, so a row has fewer than
+// 2 L / SUB_AVG + 1 ranges (the width 2^sh is above n SUB_AVG / (2 L), or
+// sh = 0 and n < 2 L / SUB_AVG), at most LW_S, counted in the warp's shared
+// counters.
 __global__ void __launch_bounds__(256) k_long_split_w(const int32_t* __restrict__ roff,
                                                       const int64_t* __restrict__ voff, int G, LongOut lo,
                                                       const uint32_t* __restrict__ tmp, uint32_t* __restrict__ tmp2) {
@@ -1209,7 +1210,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
     LongOut lo{};
     const size_t tile_cap = (size_t)(2 * N / WCH + 16);    // WCH-word tiles of rows or segments
     const size_t long_cap = (size_t)(N / WCH + 16);        // rows longer than WCH
-    const size_t seg_cap = (size_t)(N / (SUB_AVG / 2) + long_cap);  // at most L / 32 + 1 ranges per row
+    const size_t seg_cap = (size_t)(N / (SUB_AVG / 2) + long_cap);  // fewer than 2 L / SUB_AVG + 1 ranges per row
     const size_t piece_cap = (size_t)(N / CAP + N / WCH + 16);
     TC_CUDA(S.get(&d_aoff, (size_t)G + 1));
     TC_CUDA(S.get(&d_voff, (size_t)G + 1));
@@ -1293,7 +1294,7 @@ tc_status build_impl(int32_t G, const int32_t* ns, const int64_t* arc_off, const
         TC_CUDA(cudaGetLastError());
         k_long_split<<<(unsigned)sms * 2, LS_NT, 0, st>>>(roff, d_voff, G, lo, tmp, tmp2);
         TC_CUDA(cudaGetLastError());
-        k_seg_sort<<<(unsigned)sms * 8, RW_NT, 0, st>>>(lo, tmp2, tmp);
+        k_seg_sort<<<(unsigned)sms * 16, RW_NT, 0, st>>>(lo, tmp2, tmp);
         TC_CUDA(cudaGetLastError());
         // the longest crowded segment comes back while their pieces sort
         int32_t* hw = pinned_words();

@@ -190,7 +190,7 @@ __global__ void k_fwd_flags(const uint32_t* __restrict__ adj, const int32_t* __r
 constexpr int TR_SHORT = 32;
 constexpr int TR_PIECE = 2048;
 constexpr int TR_ILP = 4;  // chunks of 32 entries a piece's warp has in flight
-constexpr int TR_RUN = 8;  // 32-row groups a warp takes at a time
+constexpr int TR_RUN = 1;  // 32-row groups a warp takes at a time (more per take measured slower)
 
 // Per-thread term sums for one graph: the pair counts A[p][q], B[p][q]
 // (p, q = tag - 1) in 32-bit counters in shared memory, [18][32] per warp
@@ -306,8 +306,8 @@ __device__ __forceinline__ Piece get_piece(const uint4& a, const uint4& b, const
 }
 
 // One thread per row of at most TR_SHORT entries, the rows taken in rank
-// order (warps take TR_RUN groups of 32 consecutive ranks: rows of one
-// degree class, so the lanes' rows are about as long), in batches of 16
+// order (a warp takes TR_RUN groups of 32 consecutive ranks at a time: rows
+// of one degree class, so the lanes' rows are about as long), in batches of 16
 // entries from the row's end up to the longest row of the group, each
 // batch's loads issued before its entries are counted; longer rows are
 // listed as pieces.
