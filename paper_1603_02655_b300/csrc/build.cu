@@ -556,19 +556,24 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bkt_rows(BktArgs a) {
         }
         __syncthreads();
         int32_t* mids = rcur;  // the cursors are spent
-        for (int j0 = 0; j0 < nr; j0 += BS_NT) {  // short rows by their threads; the others listed
+        for (int j = tid; j < nr; j += BS_NT) {  // the rows for warps and for the long path, listed
+            const int L = rpos[j + 1] - rpos[j];
+            if (L > SMAX && L <= WCH) mids[atomicAdd(&nmid, 1)] = j;
+            else if (L > WCH) longs[atomicAdd(&nlongs, 1)] = j;
+        }
+        __syncthreads();
+        // short rows by their threads; a warp with none (a bucket of fewer
+        // rows than threads) goes on to the middle rows at once
+        for (int j0 = 0; j0 < nr; j0 += BS_NT) {
             const int j = j0 + tid;
             const int p = j < nr ? rpos[j] : 0;
             const int L = j < nr ? rpos[j + 1] - p : 0;
-            if (L > SMAX && L <= WCH) mids[atomicAdd(&nmid, 1)] = j;
-            else if (L > WCH) longs[atomicAdd(&nlongs, 1)] = j;
             const int Ls = L <= SMAX ? L : 0;
             const int pmax = __reduce_max_sync(full, Ls);
             if (pmax > 0)
                 thread_row_any<SMAX>(words + p, Ls, pmax, a.tmp + e0 + p, r0 + j, local_id(a.voff, a.G, r0 + j),
                                      a.o);
         }
-        __syncthreads();
         uint32_t* s = stage + warp * SPAD;
         for (;;) {  // middle rows: a warp each
             int idx = 0;
