@@ -48,6 +48,7 @@ namespace tc {
 namespace {
 
 constexpr int SMALL_MAX = 16;   // rows sorted by one thread (at most; a build picks 8 or 16)
+constexpr int MID_LONG = 64;    // warp-sorted rows taken first in a bucket
 constexpr int WCH = 512;        // rows (and pieces) sorted by one warp
 constexpr int CAP = 8192;       // words one block sorts in shared memory
 constexpr int SPAD = WCH + WCH / 32;  // a warp's staging words (one pad word per 32)
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bkt_rows(BktArgs a) {
     int32_t* rcur = rpos + MAX_BROWS + 1;                     // row counters / cursors, then the middle rows
     uint32_t* stage = reinterpret_cast<uint32_t*>(rcur + MAX_BROWS);  // warp staging areas
     __shared__ long long wsum[32];
-    __shared__ int nmid, nlongs, mcur;
+    __shared__ int nmid, nmid_lo, nlongs, mcur;
     __shared__ int longs[CAP / (WCH + 1) + 1];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
@@ -551,17 +552,23 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bkt_rows(BktArgs a) {
         }
         if (tid == 0) {
             nmid = 0;
+            nmid_lo = 0;
             nlongs = 0;
             mcur = 0;
         }
         __syncthreads();
         int32_t* mids = rcur;  // the cursors are spent
-        for (int j = tid; j < nr; j += BS_NT) {  // the rows for warps and for the long path, listed
+        // the rows for warps (those of more than MID_LONG entries from the
+        // front, the others from the back, so that the longest are taken
+        // first) and for the long path, listed
+        for (int j = tid; j < nr; j += BS_NT) {
             const int L = rpos[j + 1] - rpos[j];
-            if (L > SMAX && L <= WCH) mids[atomicAdd(&nmid, 1)] = j;
+            if (L > MID_LONG && L <= WCH) mids[atomicAdd(&nmid, 1)] = j;
+            else if (L > SMAX && L <= WCH) mids[nr - 1 - atomicAdd(&nmid_lo, 1)] = j;
             else if (L > WCH) longs[atomicAdd(&nlongs, 1)] = j;
         }
         __syncthreads();
+        const int nhi = nmid, nall = nmid + nmid_lo;
         // short rows by their threads; a warp with none (a bucket of fewer
         // rows than threads) goes on to the middle rows at once
         for (int j0 = 0; j0 < nr; j0 += BS_NT) {
@@ -579,8 +586,8 @@ __global__ void __launch_bounds__(BS_NT, 3) k_bkt_rows(BktArgs a) {
             int idx = 0;
             if (lane == 0) idx = atomicAdd(&mcur, 1);
             idx = __shfl_sync(full, idx, 0);
-            if (idx >= nmid) break;
-            const int j = mids[idx];
+            if (idx >= nall) break;
+            const int j = idx < nhi ? mids[idx] : mids[nr - 1 - (idx - nhi)];
             const int p = rpos[j], len = rpos[j + 1] - p;
             for (int i = lane; i < len; i += 32) s[pad(i)] = words[p + i];
             __syncwarp();
