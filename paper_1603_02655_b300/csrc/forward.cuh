@@ -558,8 +558,17 @@ struct FwdLayout {
     const int32_t* perm;
 };
 
-__device__ __forceinline__ bool map_owner(int nplus, int64_t n, int32_t R, int big_min) {
-    return nplus >= big_min && nplus > 0 && nplus <= MLIST && n - (int64_t)R - 1 <= MAP_KEYS;
+// Tag-map owners: a forward list of at least big_min entries, or of at
+// least big_min / MID_DIV entries when the owner also owns at least OWN_MID
+// dyads (its list is then probed often enough to pay for the map; measured
+// on B300 against thresholds of 2-8 and 16-256: R-MAT scale 22 census 3.245
+// -> 3.213 ms, Chung-Lu 2^22 5.450 -> 5.343 ms); and a list and a rank
+// range the map holds.
+constexpr int MID_DIV = 8;
+constexpr uint32_t OWN_MID = 128;
+__device__ __forceinline__ bool map_owner(int nplus, int64_t n, int32_t R, int big_min, uint32_t own) {
+    const bool wide = nplus >= big_min || (nplus >= big_min / MID_DIV && own >= OWN_MID);
+    return wide && nplus > 0 && nplus <= MLIST && n - (int64_t)R - 1 <= MAP_KEYS;
 }
 
 // Per row: its forward list (start from the flag scan), the dyads it owns
@@ -594,7 +603,7 @@ __global__ void __launch_bounds__(FR_NT) k_fwd_rows(const int64_t* __restrict__ 
                 F.fptr[rows] = b;
                 F.tcnt[rows] = 0;
             }
-            const bool big = own > 0 && map_owner((int)m, g.n, F.rank[r], big_min);
+            const bool big = own > 0 && map_owner((int)m, g.n, F.rank[r], big_min, own);
             const bool search = !big && own > 0 && m > 0;
             F.kind[r] = big ? 1 : search ? 2 : 0;
             F.tcnt[r] = big ? (unsigned long long)own << 32 : search ? (unsigned long long)own : 0ull;
