@@ -146,8 +146,10 @@ typedef struct {
                              path its router picks (tc_path_route): the
                              installed path model, else the degree-skew rule */
     int32_t fwd_big;      /* TC_TRI_FORWARD: owners with at least fwd_big forward
-                             neighbours (and at most 2^17 vertices ranked above
-                             them) get a CTA and an exact tag map of their
+                             neighbours, or at least fwd_big / 8 of them and
+                             at least 128 owned dyads (and at most 1024
+                             forward neighbours and 2^17 vertices ranked above
+                             them), get a CTA and an exact tag map of their
                              forward list in shared memory; the others a
                              binary search per lookup.  >= 1; default 64 */
 } tc_opts;
