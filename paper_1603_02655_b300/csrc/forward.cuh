@@ -983,6 +983,9 @@ constexpr size_t TB_HS_BYTES = sizeof(uint32_t) * 64 * TB_W;
 constexpr size_t TB_Q_BYTES = sizeof(uint2) * TQN * TB_W;
 constexpr size_t TB_SMEM = TB_MAP_BYTES + TB_LIST_BYTES + TB_TAB_BYTES + TB_HS_BYTES + TB_Q_BYTES;
 static_assert(TB_REC == 2 * TB_NT, "a work item's records are read two per thread");
+// chunk counts the queue area holds: items of more pieces (lookup lists
+// longer than 2,048 entries on average) find their chunks' dyads by search
+constexpr int TB_CB_CAP = (int)(TB_Q_BYTES / sizeof(uint16_t));
 
 // Tag-map work items: two words each, {owner row, owner rank, forward list
 // start, its length} and {first record, end of records, graph, 0}
@@ -1029,6 +1032,9 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
     uint32_t* txin = tlen + TB_REC;
     uint32_t* hs_all = reinterpret_cast<uint32_t*>(tb_smem + TB_MAP_BYTES + TB_LIST_BYTES + TB_TAB_BYTES);
     uint2* q_all = reinterpret_cast<uint2*>(tb_smem + TB_MAP_BYTES + TB_LIST_BYTES + TB_TAB_BYTES + TB_HS_BYTES);
+    // rank-order counting (no hit queues): the queue area holds, per 32-piece
+    // chunk of the item, the number of the item's dyads begun before it
+    uint16_t* cbefore = reinterpret_cast<uint16_t*>(q_all);
     __shared__ unsigned long long wsum[TB_W];
     __shared__ int ctl_ntask, ctl_total;
     __shared__ unsigned ccur;  // next 32-piece chunk of the item
@@ -1124,11 +1130,21 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
         {
             int d = (int)(ex >> 40);
             uint32_t po = (uint32_t)(ex & 0xffffffffffull);
+            // chunk ch (pieces from 32 ch) begins inside exactly one dyad's
+            // pieces [po, po + np): the dyads begun before it are that dyad's
+            // index, plus one when the dyad began in an earlier chunk
+            auto mark = [&](int dd, uint32_t p0, uint32_t np) {
+                if constexpr (!IDS) {
+                    for (uint32_t ch = (p0 + 31) >> 5; (ch << 5) < p0 + np && ch < (uint32_t)TB_CB_CAP; ++ch)
+                        cbefore[ch] = (uint16_t)((ch << 5) == p0 ? dd : dd + 1);
+                }
+            };
             if (np0 > 0) {
                 pof[d] = po;
                 tfst[d] = r0.x;
                 tlen[d] = r0.y;
                 txin[d] = r0.z;
+                mark(d, po, np0);
                 ++d;
                 po += np0;
             }
@@ -1137,6 +1153,7 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
                 tfst[d] = r1.x;
                 tlen[d] = r1.y;
                 txin[d] = r1.z;
+                mark(d, po, np1);
             }
         }
         if (threadIdx.x == TB_NT - 1) {
@@ -1160,7 +1177,9 @@ __global__ void __launch_bounds__(TB_NT, 4) k_tri_big(TriArgs a) {
             c = __shfl_sync(full, c, 0);
             if (c >= total) break;
             int before;  // dyads whose first piece lies below c
-            {
+            if (!IDS && total <= TB_CB_CAP * 32) {  // c < total: an index below TB_CB_CAP
+                before = cbefore[c >> 5];
+            } else {
                 int l = 0, h = ntask;
                 while (l < h) {
                     const int mid = (l + h) >> 1;
