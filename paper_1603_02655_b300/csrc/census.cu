@@ -2223,7 +2223,7 @@ struct Layout {
     int64_t dyads = 0;     // canonical dyads of the selection
     uint32_t item_cap = 0;
     size_t fscan_bytes = 0;
-    size_t o_hist, o_hex, o_co, o_rank, o_perm, o_flag, o_fs, o_fptr, o_kind, o_tcnt, o_tpre, o_longs,
+    size_t o_hist, o_hex, o_co, o_clsb, o_rank, o_perm, o_flag, o_fs, o_fptr, o_kind, o_tcnt, o_tpre, o_longs,
         o_fid, o_fwd, o_trec, o_items, o_fscantmp, o_tp, o_tpc;
     uint32_t piece_cap = 0;  // pieces of the longer rows in the row-wise task pass
 };
@@ -2342,6 +2342,7 @@ tc_status make_layout(const GraphSet& set, const std::vector<int32_t>& gidx, con
         Lo.o_hist = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
         Lo.o_hex = take(sizeof(uint32_t) * NCLS * (size_t)Lo.nb);
         Lo.o_co = take(sizeof(int64_t) * NCLS * (size_t)nseg);
+        Lo.o_clsb = take(sizeof(int32_t) * NCLS * (size_t)nseg);
         Lo.o_rank = take(sizeof(int32_t) * rows);
         Lo.o_perm = take(sizeof(int32_t) * rows);
         Lo.o_flag = take(sizeof(uint8_t) * (size_t)Lo.entries);
@@ -2394,6 +2395,7 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     uint32_t* hist = (uint32_t*)(ws + Lo.o_hist);
     uint32_t* hex = (uint32_t*)(ws + Lo.o_hex);
     int64_t* co = (int64_t*)(ws + Lo.o_co);
+    int32_t* clsb = (int32_t*)(ws + Lo.o_clsb);
     int32_t* rank = (int32_t*)(ws + Lo.o_rank);
     int32_t* perm = (int32_t*)(ws + Lo.o_perm);
     uint8_t* flag = (uint8_t*)(ws + Lo.o_flag);
@@ -2402,7 +2404,8 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     k_rank_hist<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hist);
     TC_CUDA(cudaGetLastError());
     TC_CUDA(scan_run<false>(ScanLoad<uint32_t>{hist}, (int64_t)NCLS * Lo.nb, hex, tmp, false, st));
-    k_rank_seg<<<std::min(Lo.nseg, L.sms * 16), 32, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co);
+    k_rank_seg<<<std::min(Lo.nseg, L.sms * 16), 32, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co,
+                                                             clsb);
     TC_CUDA(cudaGetLastError());
     k_rank_assign<<<Lo.nb, RK_B, 0, st>>>(set.deg, d_seg, d_pfx, Lo.nseg, Lo.rows, Lo.nb, hex, co, rank, perm,
                                           bins.overflow);
@@ -2460,6 +2463,7 @@ tc_status enqueue_forward(const GraphSet& set, const Layout& Lo, char* ws, cudaS
     F.stat = (unsigned long long*)(ctr + 44);
     F.rank = rank;
     F.perm = perm;
+    F.clsb = clsb;
     TC_CUDA(scan_run<true>(ScanLoad<uint8_t>{flag}, Lo.entries, (int32_t*)(ws + Lo.o_fs), tmp, false, st));
     k_fwd_rows<<<L.sms * 8, FR_NT, 0, st>>>(set.row_ptr, set.deg, d_seg, d_pfx, d_epfx, Lo.nseg, Lo.rows, Lo.o.fwd_big,
                                            F, bp.r_lo, bp.r_hi);

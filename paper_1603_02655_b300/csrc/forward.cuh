@@ -88,10 +88,12 @@ __device__ __forceinline__ unsigned rank_below(const int32_t* deg, const SegDev*
 }
 
 // Per graph s: co[s][c] = (ranks before class c in the graph) - (rows of
-// class c before the graph's first row).  One warp per graph.
+// class c before the graph's first row), and clsb[s][c] = the ranks before
+// class c in the graph (its first rank).  One warp per graph.
 __global__ void k_rank_seg(const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
                            const int64_t* __restrict__ pfx, int nseg, int64_t rows, int nb,
-                           const uint32_t* __restrict__ hex, int64_t* __restrict__ co) {
+                           const uint32_t* __restrict__ hex, int64_t* __restrict__ co,
+                           int32_t* __restrict__ clsb) {
     __shared__ unsigned cnt[NCLS];
     const int lane = threadIdx.x & 31;
     for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
@@ -105,6 +107,7 @@ __global__ void k_rank_seg(const int32_t* __restrict__ deg, const SegDev* __rest
         }
         ex -= in;
         co[(size_t)s * NCLS + lane] = (int64_t)ex - (int64_t)p0;
+        clsb[(size_t)s * NCLS + lane] = (int32_t)ex;
     }
 }
 
@@ -556,6 +559,7 @@ struct FwdLayout {
     unsigned long long* stat;  // [5] lookups and triangles of each lookup form, staged list entries
     const int32_t* rank;
     const int32_t* perm;
+    const int32_t* clsb;       // [graphs][NCLS] first rank of each degree class
 };
 
 // Tag-map owners: a forward list of at least big_min entries, or of at
@@ -697,25 +701,45 @@ __global__ void k_fwd_sort_short(int64_t rows, FwdLayout F) {
 static_assert(FWD_SHORT <= 16, "short rows are sorted in a 16-word network");
 
 // One warp per long row: a stable partition of the forward list (in id
-// order) by degree class gives rank order; each entry is written as
-// R << 2 | tag.
+// order) by degree class gives rank order.  The first pass looks up each
+// entry's rank, writes R << 2 | tag over the id-order word and counts the
+// classes; the second reads those words back and places them.  An entry's
+// class comes from its rank (the last class whose first rank is at most R,
+// searched in the graph's NCLS class starts), so each entry costs one random
+// load.
 __global__ void __launch_bounds__(256) k_fwd_sort(const int32_t* __restrict__ deg, const SegDev* __restrict__ seg,
                                                   const int64_t* __restrict__ pfx, int nseg, FwdLayout F) {
     __shared__ unsigned cnt_all[8][NCLS + 1];
+    __shared__ int32_t cb_all[8][NCLS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned* cnt = cnt_all[warp];
+    int32_t* cb = cb_all[warp];
     const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
     const unsigned nlong = *F.nlong;
+    auto cls_of = [&](uint32_t R) {  // cb[0] = 0 <= R
+        int c = 0;
+#pragma unroll
+        for (int st = NCLS / 2; st > 0; st >>= 1)
+            if ((uint32_t)cb[c + st] <= R) c += st;
+        return c;
+    };
     for (unsigned li = blockIdx.x * 8 + warp; li < nlong; li += gridDim.x * 8) {
         const int64_t r = F.longs[li];
         const uint32_t b0 = F.fptr[r], m = F.fptr[r + 1] - b0;
         const int s = row_seg(pfx, nseg, r);
-        const int64_t rb = seg[s].rb, p0 = pfx[s];
+        const int64_t p0 = pfx[s];
         cnt[lane] = 0;
+        cb[lane] = F.clsb[(size_t)s * NCLS + lane];
         __syncwarp();
         for (uint32_t i0 = 0; i0 < m; i0 += 32) {
             const uint32_t i = i0 + lane;
-            const int c = i < m ? deg_class(deg[rb + (F.fid[b0 + i] >> 2)]) : NCLS;
+            int c = NCLS;
+            if (i < m) {
+                const uint32_t e = F.fid[b0 + i];
+                const uint32_t R = (uint32_t)F.rank[p0 + (e >> 2)];
+                F.fid[b0 + i] = (R << 2) | (e & 3u);
+                c = cls_of(R);
+            }
             const unsigned same = __match_any_sync(full, c);
             if (c < NCLS && (same & lt) == 0) cnt[c] += __popc(same);
             __syncwarp();
@@ -734,15 +758,16 @@ __global__ void __launch_bounds__(256) k_fwd_sort(const int32_t* __restrict__ de
         }
         for (uint32_t i0 = 0; i0 < m; i0 += 32) {
             const uint32_t i = i0 + lane;
-            const uint32_t e = i < m ? F.fid[b0 + i] : 0u;
-            const int c = i < m ? deg_class(deg[rb + (e >> 2)]) : NCLS;
+            const uint32_t w = i < m ? F.fid[b0 + i] : 0u;
+            const int c = i < m ? cls_of(w >> 2) : NCLS;
             const unsigned same = __match_any_sync(full, c);
             const uint32_t pos = c < NCLS ? cnt[c] + __popc(same & lt) : 0u;
             __syncwarp();
             if (c < NCLS && (same & lt) == 0) cnt[c] += __popc(same);
             __syncwarp();
-            if (i < m) F.fwd[b0 + pos] = ((uint32_t)F.rank[p0 + (e >> 2)] << 2) | (e & 3u);
+            if (i < m) F.fwd[b0 + pos] = w;
         }
+        __syncwarp();  // cb and cnt are rewritten for the next row
     }
 }
 
